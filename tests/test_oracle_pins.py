@@ -1,0 +1,372 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (CPU only).
+
+Each test ties one part of the oracle to something other than the oracle itself: a
+closed form, an exact invariant of the discrete scheme, a brute-force or dense-matrix
+computation, the continuum (exact-in-s) limit, the linear-response (Debye) result,
+or published known-answer vectors.  A plausible mistake (dropped Boltzmann half-step,
+wrong quadrature weight, A/B swap, sign of the Wick rotation, transposed operand,
+wrong k^2 scaling) fails at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as o
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def fd5(f, h=1e-3):
+    """Five-point central difference of f at 0: truncation O(h^4), round-off ~eps/h."""
+    return (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
+
+
+def _rand_fields(n, kind, seed, amp_p=0.3, amp_m=1.0):
+    rng = np.random.default_rng(seed)
+    wp = rng.normal(0, amp_p, n)
+    wm = rng.normal(0, amp_m, n)
+    if kind == o.CL_COMPLEX:
+        wp = wp + 1j * rng.normal(0, amp_p, n)
+        wm = wm + 1j * rng.normal(0, 0.3 * amp_m, n)
+    return wp, wm
+
+
+# ---------------------------------------------------------------- closed forms
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_uniform_fields_closed_form(kind):
+    """Uniform fields: only the k=0 mode is excited and D(0)=1, so q_n = exp(-w n ds)
+    on each block and Q = exp(-(fA wA + fB wB)) exactly (Eqs. 4, 5); phiA = fA."""
+    n, L, Ns, fA = (6, 4, 8), (3.0, 2.0, 5.0), 20, 0.35
+    NsA = o.n_A_steps(Ns, fA)
+    fa = NsA / Ns
+    if kind == o.SCFT_REAL:
+        wp, wm = np.full(n, 0.7), np.full(n, -1.3)
+        wA, wB = 0.7 + 1.3, 0.7 - 1.3
+    else:
+        wp, wm = np.full(n, 0.4 - 0.2j), np.full(n, -1.1 + 0.3j)
+        wA, wB = 1j * (0.4 - 0.2j) + 1.1 - 0.3j, 1j * (0.4 - 0.2j) - 1.1 + 0.3j
+    s = o.solve(wp, wm, n, L, Ns, fA, kind)
+    Qx = np.exp(-(fa * wA + (1 - fa) * wB))
+    assert abs(s.Q - Qx) <= 1e-13 * abs(Qx)
+    for k in range(Ns + 1):
+        ex = np.exp(-wA * k / Ns) if k <= NsA else np.exp(-wA * fa - wB * (k - NsA) / Ns)
+        assert np.max(np.abs(s.q[k] - ex)) <= 1e-13 * abs(ex)
+    assert np.max(np.abs(s.phiA - fa)) < 1e-13
+    assert np.max(np.abs(s.phiB - (1 - fa))) < 1e-13
+
+
+def test_hamiltonian_uniform_closed_form():
+    """Eq. 3 for uniform fields: H/(C V) = W-^2/chiN - W+ + fA wA + fB wB."""
+    n, L, Ns, fA, chiN, C = (4, 4, 4), (2.0, 3.0, 4.0), 10, 0.3, 17.0, 2.5
+    wpv, wmv = 0.25, -0.8
+    s = o.solve(np.full(n, wpv), np.full(n, wmv), n, L, Ns, fA, o.SCFT_REAL)
+    H = o.hamiltonian(np.full(n, wpv), np.full(n, wmv), s.lnQ, chiN, C, n, L, o.SCFT_REAL)
+    fa = o.n_A_steps(Ns, fA) / Ns
+    V = 24.0
+    Hx = C * V * (wmv ** 2 / chiN - wpv + fa * (wpv - wmv) + (1 - fa) * (wpv + wmv))
+    assert abs(H - Hx) <= 1e-13 * abs(Hx)
+
+
+def test_diffusion_alone_plane_wave():
+    """w = 0 and q_0 = exp(i k.x): the Laplacian eigenmode decays as exp(-k^2 s),
+    so after Ns steps of ds = 1/Ns, q = exp(-k^2) exp(i k.x) exactly (Eq. 5)."""
+    n, L, Ns = (8, 6, 4), (4.0, 3.0, 2.5), 16
+    x = [np.arange(n[a]) * L[a] / n[a] for a in range(3)]
+    m = (1, -2, 1)
+    k = [2 * np.pi * m[a] / L[a] for a in range(3)]
+    phase = (k[0] * x[0][:, None, None] + k[1] * x[1][None, :, None] + k[2] * x[2][None, None, :])
+    q0 = np.exp(1j * phase)
+    zero = np.zeros(n)
+    s = o.solve(zero, zero, n, L, Ns, 0.5, o.SCFT_REAL, q0=q0, qd0=q0)
+    k2 = sum(kk * kk for kk in k)
+    assert np.max(np.abs(s.q[Ns] - np.exp(-k2) * q0)) < 1e-13
+
+
+# ---------------------------------------------------------- exact invariants
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_slice_invariance(kind):
+    """Each split step is a (complex-)symmetric operator, so (1/M) sum q_n qd_{Ns-n}
+    is the same Q at every cut of the chain."""
+    n, L = (8, 6, 4), (4.0, 3.5, 2.0)
+    wp, wm = _rand_fields(n, kind, 3)
+    s = o.solve(wp, wm, n, L, 24, 0.4, kind)
+    Qn = o.slice_partition_functions(s)
+    assert np.max(np.abs(Qn - s.Q)) <= 1e-13 * abs(s.Q)
+
+
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_sum_rules(kind):
+    """With trapezoid weights per block: <phiA> = fA_eff and dV sum(phiA+phiB) = V."""
+    n, L, Ns, fA = (6, 6, 6), (3.0, 3.0, 3.0), 30, 0.37
+    wp, wm = _rand_fields(n, kind, 4)
+    s = o.solve(wp, wm, n, L, Ns, fA, kind)
+    fa = o.n_A_steps(Ns, fA) / Ns
+    assert abs(s.phiA.mean() - fa) < 1e-13
+    assert abs((s.phiA + s.phiB).mean() - 1.0) < 1e-13
+
+
+def _perturbed(arr, idx, h):
+    b = arr.copy()
+    b[idx] += h
+    return b
+
+
+def test_density_is_exact_gradient_real():
+    """dlnQ/dW+_j = -(phiA+phiB)_j/M and dlnQ/dW-_j = (phiA-phiB)_j/M hold exactly for
+    the discrete 2nd-order scheme with trapezoid weights (Eq. 8 read as
+    delta lnQ/delta w); a five-point difference agrees to ~1e-10 relative."""
+    n, L, Ns, fA = (6, 4, 4), (3.0, 2.0, 2.0), 20, 0.35
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 5)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    M = wp.size
+    rng = np.random.default_rng(0)
+    for j in rng.choice(M, 5, replace=False):
+        idx = np.unravel_index(j, n)
+        fdp = fd5(lambda h: o.solve(_perturbed(wp, idx, h), wm, n, L, Ns, fA, o.SCFT_REAL).lnQ)
+        fdm = fd5(lambda h: o.solve(wp, _perturbed(wm, idx, h), n, L, Ns, fA, o.SCFT_REAL).lnQ)
+        anp = -(s.phiA + s.phiB)[idx] / M
+        anm = (s.phiA - s.phiB)[idx] / M
+        assert abs(fdp - anp) <= 1e-9 * abs(anp), (fdp, anp)
+        assert abs(fdm - anm) <= 1e-9 * abs(anm) + 1e-13, (fdm, anm)
+
+
+def test_density_is_exact_gradient_complex():
+    """Complex Langevin mapping: lnQ is holomorphic in omega, with
+    dlnQ/domega+_j = -i(phiA+phiB)_j/M and dlnQ/domega-_j = (phiA-phiB)_j/M."""
+    n, L, Ns, fA = (4, 4, 6), (2.0, 2.0, 3.0), 16, 0.3
+    wp, wm = _rand_fields(n, o.CL_COMPLEX, 6)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    M = wp.size
+    for j in (1, 17, 50):
+        idx = np.unravel_index(j, n)
+        fdp = fd5(lambda h: o.solve(_perturbed(wp, idx, h), wm, n, L, Ns, fA, o.CL_COMPLEX).lnQ)
+        fdm = fd5(lambda h: o.solve(wp, _perturbed(wm, idx, h), n, L, Ns, fA, o.CL_COMPLEX).lnQ)
+        anp = -1j * (s.phiA + s.phiB)[idx] / M
+        anm = (s.phiA - s.phiB)[idx] / M
+        assert abs(fdp - anp) <= 1e-9 * abs(anp), (fdp, anp)
+        assert abs(fdm - anm) <= 1e-9 * abs(anm) + 1e-13, (fdm, anm)
+
+
+def test_shift_invariance():
+    """A constant added to W+ shifts lnQ by -c and the field term by -c V, so H is
+    unchanged (Eq. 3), and the mean W+ force vanishes."""
+    n, L, Ns, fA, chiN, C = (6, 4, 4), (3.0, 2.0, 2.0), 16, 0.45, 15.0, 1.0
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 7)
+    s1 = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    s2 = o.solve(wp + 0.73, wm, n, L, Ns, fA, o.SCFT_REAL)
+    H1 = o.hamiltonian(wp, wm, s1.lnQ, chiN, C, n, L, o.SCFT_REAL)
+    H2 = o.hamiltonian(wp + 0.73, wm, s2.lnQ, chiN, C, n, L, o.SCFT_REAL)
+    assert abs(H1 - H2) < 1e-12 * abs(H1)
+    assert abs((s1.phiA + s1.phiB - 1).mean()) < 1e-14
+
+
+def test_symmetric_diblock():
+    """fA = 1/2, W- odd under x -> x + L/2 and W+ even: reversing the chain and shifting
+    by L/2 swaps A and B, so qd_n(x) = q_n(x + L/2) and phiA(x + L/2) = phiB(x).
+    With W- = 0 the chain is symmetric and q = qd."""
+    n, L, Ns = (8, 4, 4), (4.0, 2.0, 2.0), 20
+    rng = np.random.default_rng(8)
+    half = rng.normal(0, 1.0, (4, 4, 4))
+    wm = np.concatenate([half, -half], axis=0)
+    hp = rng.normal(0, 0.3, (4, 4, 4))
+    wp = np.concatenate([hp, hp], axis=0)
+    s = o.solve(wp, wm, n, L, Ns, 0.5, o.SCFT_REAL)
+    for k in range(Ns + 1):
+        assert np.max(np.abs(s.qd[k] - np.roll(s.q[k], -4, axis=0))) < 1e-13 * np.max(np.abs(s.q[k]))
+    assert np.max(np.abs(np.roll(s.phiA, -4, axis=0) - s.phiB)) < 1e-13
+    s0 = o.solve(wp, np.zeros(n), n, L, Ns, 0.5, o.SCFT_REAL)
+    assert np.max(np.abs(s0.q - s0.qd)) < 1e-13 * np.max(np.abs(s0.q))
+
+
+# --------------------------------------------------- brute force / dense / expm
+def test_fft_equals_bruteforce_dft():
+    """The FFT used by the oracle equals the O(M^2) DFT written out entry by entry."""
+    rng = np.random.default_rng(9)
+    x = rng.normal(size=(8, 8, 8)) + 1j * rng.normal(size=(8, 8, 8))
+    a = np.fft.fftn(x)
+    b = o.dft3_bruteforce(x)
+    assert np.max(np.abs(a - b)) < 1e-12 * np.max(np.abs(b))
+    y = rng.normal(size=(4, 6, 8))
+    assert np.max(np.abs(np.fft.fftn(y) - o.dft3_bruteforce(y))) < 1e-12 * 48
+
+
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_march_equals_dense_matrix(kind):
+    """Forward march with FFTs equals the march with the diffusion operator as the
+    explicit M x M matrix F^-1 diag(D) F (8^3 grid)."""
+    n, L, Ns, fA = (8, 8, 8), (4.0, 4.0, 4.0), 12, 0.5
+    wp, wm = _rand_fields(n, kind, 10)
+    s = o.solve(wp, wm, n, L, Ns, fA, kind)
+    Dm = o.dense_propagator_matrix(n, s.D)
+    if kind == o.SCFT_REAL:
+        assert np.max(np.abs(Dm.imag)) < 1e-13
+        Dm = Dm.real
+    qd = o.forward_march_dense(s.BA, s.BB, Dm, Ns, s.NsA)
+    assert np.max(np.abs(qd - s.q[Ns])) < 1e-12 * np.max(np.abs(s.q[Ns]))
+
+
+def test_second_order_convergence_to_continuum():
+    """Q(Ns) converges to the exact-in-s answer (dense expm of the spectral operator)
+    as ds^2: successive errors at Ns = 32 .. 512 shrink by a factor that tends to 4
+    (grid-scale noise makes the coarsest steps pre-asymptotic)."""
+    n, L = (8, 4, 4), (4.0, 2.0, 2.0)
+    xs = np.arange(8) * 4.0 / 8
+    wm = np.broadcast_to(1.5 * np.cos(2 * np.pi * xs / 4.0)[:, None, None], n).copy()
+    wm += 0.2 * np.random.default_rng(11).normal(size=n)
+    wp = 0.1 * np.random.default_rng(12).normal(size=n)
+    wA, wB = o.species_fields(wp, wm, o.SCFT_REAL)
+    Qs = o.continuum_Q(wA, wB, n, L, 0.25)
+    errs = [o.solve(wp, wm, n, L, Ns, 0.25, o.SCFT_REAL).Q - Qs for Ns in (32, 64, 128, 256, 512)]
+    ratios = [errs[i] / errs[i + 1] for i in range(4)]
+    assert all(3.4 < r < 4.1 for r in ratios), ratios
+    assert 3.95 < ratios[-1] < 4.05 and 3.9 < ratios[-2] < 4.1, ratios
+    assert abs(errs[-1]) < 1e-6 * abs(Qs)
+
+
+def test_rpa_debye_response():
+    """Weak exchange field W- = eps cos(k x): the k-mode of phiA - fA is
+    eps (gAA - gAB) and that of phiB - fB is eps (gAB - gBB) (linearised density
+    response with the Debye functions, as used for the semi-implicit update near
+    Eq. 10), up to O(eps^3) and O(ds^2); Richardson extrapolation removes the latter."""
+    eps = 1e-4
+    n, L = (16, 2, 2), (5.0, 1.0, 1.0)
+    fA = 0.25
+    x = np.arange(16) * 5.0 / 16
+    k = 2 * np.pi / 5.0
+    wm = np.broadcast_to(eps * np.cos(k * x)[:, None, None], n).copy()
+    wp = np.zeros(n)
+    amps = []
+    for Ns in (64, 128, 256):
+        s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+        cA = 2 * np.mean(s.phiA[:, 0, 0] * np.cos(k * x))
+        cB = 2 * np.mean(s.phiB[:, 0, 0] * np.cos(k * x))
+        amps.append(np.array([cA, cB]))
+    r1 = (4 * amps[1] - amps[0]) / 3
+    r2 = (4 * amps[2] - amps[1]) / 3
+    rr = (16 * r2 - r1) / 15
+    gAA, gBB, gAB = o.debye_g(k * k, fA)
+    ex = eps * np.array([gAA - gAB, gAB - gBB])
+    assert np.all(np.abs(rr - ex) <= 1e-6 * np.abs(ex)), (rr, ex)
+
+
+def test_debye_small_x_limits():
+    """gAA -> f^2, gBB -> (1-f)^2, gAB -> f(1-f) as x -> 0 (normalisation check)."""
+    gAA, gBB, gAB = o.debye_g(1e-5, 0.3)
+    assert abs(gAA - 0.09) < 1e-5 and abs(gBB - 0.49) < 1e-5 and abs(gAB - 0.21) < 1e-5
+
+
+# ------------------------------------------------------------- box derivative
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_stress_matches_finite_difference(kind):
+    """dlnQ/dL_a from the slice-by-slice derivative of the diffusion factor equals a
+    finite difference of lnQ in L_a with the fields held fixed on the grid."""
+    n, L, Ns, fA = (6, 4, 8), (3.0, 2.5, 4.0), 16, 0.35
+    wp, wm = _rand_fields(n, kind, 13)
+    s = o.solve(wp, wm, n, L, Ns, fA, kind)
+    g = o.dlnQ_dL(s, n, L)
+    for a in range(3):
+        def f(h):
+            Lh = list(L)
+            Lh[a] += h
+            return o.solve(wp, wm, n, Lh, Ns, fA, kind).lnQ
+        fd = fd5(f)
+        assert abs(fd - g[a]) <= 1e-9 * abs(g[a]) + 1e-12, (a, fd, g[a])
+
+
+def _H_at(wp, wm, n, L, Ns, fA, chiN, C):
+    return o.hamiltonian(wp, wm, o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL).lnQ, chiN, C, n, L, o.SCFT_REAL)
+
+
+def test_dH_dL_matches_finite_difference():
+    """dH/dL_a = H/L_a - C V dlnQ/dL_a against a finite difference of Eq. 3."""
+    n, L, Ns, fA, chiN, C = (4, 6, 4), (2.0, 3.0, 2.2), 12, 0.4, 18.0, 3.0
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 14)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    H = o.hamiltonian(wp, wm, s.lnQ, chiN, C, n, L, o.SCFT_REAL)
+    g = o.dH_dL(H, s, C, n, L)
+    for a in range(3):
+        def f(h):
+            Lh = list(L)
+            Lh[a] += h
+            return _H_at(wp, wm, n, Lh, Ns, fA, chiN, C)
+        fd = fd5(f)
+        assert abs(fd - g[a]) <= 1e-9 * abs(g[a]) + 1e-11
+
+
+def test_dH_dfields_matches_finite_difference():
+    """Discrete gradient of H (Eq. 3 with Eq. 7 forces times C dV) against finite
+    differences of H."""
+    n, L, Ns, fA, chiN, C = (4, 4, 6), (2.0, 2.0, 3.0), 12, 0.35, 18.0, 2.0
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 15)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    gp, gm = o.dH_dfields(wp, wm, s, chiN, C, n, L, o.SCFT_REAL)
+    for j in (3, 40, 77):
+        idx = np.unravel_index(j, n)
+        fdp = fd5(lambda h: _H_at(_perturbed(wp, idx, h), wm, n, L, Ns, fA, chiN, C))
+        fdm = fd5(lambda h: _H_at(wp, _perturbed(wm, idx, h), n, L, Ns, fA, chiN, C))
+        assert abs(fdp - gp[idx]) < 1e-9 * abs(gp[idx]) + 1e-10
+        assert abs(fdm - gm[idx]) < 1e-9 * abs(gm[idx]) + 1e-10
+
+
+# ------------------------------------------------------------- field updates
+def test_homogeneous_saddle_is_fixed_point():
+    """The homogeneous melt W+ = const, W- = chiN (2 fA - 1)/2 zeroes both forces of
+    Eq. 7, so a relaxation step and a noise-free CL step leave it unchanged."""
+    n, L, Ns, fA, chiN = (4, 4, 4), (2.0, 2.0, 2.0), 20, 0.3, 20.0
+    fa = o.n_A_steps(Ns, fA) / Ns
+    wp = np.full(n, 0.2)
+    wm = np.full(n, chiN * (2 * fa - 1) / 2)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    a, b = o.scft_euler_step(wp, wm, s.phiA, s.phiB, chiN, 0.1)
+    assert np.max(np.abs(a - wp)) < 1e-14 and np.max(np.abs(b - wm)) < 1e-13
+    cp, cm = wp.astype(complex), wm.astype(complex)
+    s2 = o.solve(cp, cm, n, L, Ns, fA, o.CL_COMPLEX)
+    z = np.zeros(n)
+    a, b = o.cl_euler_maruyama_step(cp, cm, s2.phiA, s2.phiB, chiN, 0.01, z, z)
+    assert np.max(np.abs(a - cp)) < 1e-14 and np.max(np.abs(b - cm)) < 1e-13
+
+
+def test_scft_step_signs():
+    """Wick-rotated relaxation: W+ follows +(phiA+phiB-1) (ascent on the pressure
+    field) and W- follows -(2W-/chiN + phiB - phiA) (descent on the exchange field)."""
+    n = (2, 2, 2)
+    wp = np.zeros(n)
+    wm = np.zeros(n)
+    phiA = np.full(n, 0.7)
+    phiB = np.full(n, 0.5)
+    a, b = o.scft_euler_step(wp, wm, phiA, phiB, 10.0, 0.1)
+    assert np.allclose(a, 0.1 * 0.2) and np.allclose(b, -0.1 * (0.5 - 0.7))
+
+
+# ---------------------------------------------------------------- generator
+def test_philox_known_answers():
+    rows = []
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            rows.append([int(t, 16) for t in line.split()])
+    for r in rows:
+        out = o.philox4x32_10(np.array([r[0:4]], dtype=np.uint32), (r[4], r[5]))[0]
+        assert [int(v) for v in out] == r[6:10]
+
+
+def test_philox_normals_moments():
+    z = o.philox_normals(12345, 7, 3, 1, 400001)
+    N = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(N)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2.0 / N)
+    assert abs((z ** 4).mean() - 3) < 5 * math.sqrt(96.0 / N)
+    z2 = o.philox_normals(12345, 7, 3, 0, 1000)
+    z3 = o.philox_normals(12345, 7, 4, 1, 1000)
+    assert abs(np.corrcoef(z[:1000], z2)[0, 1]) < 0.2 and abs(np.corrcoef(z[:1000], z3)[0, 1]) < 0.2
+
+
+def test_cl_noise_variance():
+    """Discrete noise variance 2 lam dt/(C dV) (below Eq. 10, force per C)."""
+    std = o.cl_noise_std(0.01, 50.0, 0.5)
+    assert abs(std ** 2 - 2 * 0.01 / (50.0 * 0.5)) < 1e-18
+    ep, em = o.cl_noise(1, 0, 0, 200000, std)
+    assert abs(ep.var() / std ** 2 - 1) < 0.02 and abs(em.var() / std ** 2 - 1) < 0.02
