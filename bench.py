@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Throughput of the diblock propagator hot path on GB300 (one JSON line on stdout).
+
+A step is one full field update of the 128^3 gyroid-seeded SCFT workload (Ns=100,
+fA=0.35, chiN=18, L=8 Rg): Boltzmann factors, forward march, Q, conjugate march with
+fused contour quadrature, densities, H and the explicit-Euler field update.  One
+step advances 2*M*Ns grid-point contour steps (M = 128^3).  The headline path runs
+the propagators and FFTs in FP32 with FP64 quadrature, reductions and field update;
+the plain FP64 path is measured on the same workload and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With --gpus N > 1 (launched by torchrun) each rank runs an independent replica of the
+workload (its own seed): the path has no exchange step, so scaling is weak.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1204_5434_gb300 import workloads as wl  # noqa: E402
+
+METRIC = "grid-pt·contour-steps/s at 128³ (FP32-mixed vs FP64), % HBM roofline"
+UNIT = "grid-pt·contour-steps/s"
+WORK = wl.GYR128
+# Mean algorithmic bytes per unit (one grid point, one contour step, one propagator)
+# with each 3D FFT on chip: forward reads q_{n-1} and B and writes q_n (2e+f); the
+# conjugate step also reads the partner q and reads+writes an FP64 accumulator
+# (3e+f+2a).  Mean (5e+2f+2a)/2 with e=f=4, a=8 (FP32-mixed) or e=f=a=8 (FP64), real fields.
+BYTES_PER_UNIT = {"fp32": 22.0, "fp64": 36.0}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.p = None
+        self.path = os.path.join("/tmp", f"pft_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _oracle_sample(seconds_target=15.0, nsteps=None):
+    """Time the FP64 oracle on a bounded sample of the workload: the forward march
+    (Boltzmann + FFT split steps) at the full 128^3 grid for a number of contour steps.
+    Returns (units/s, sample description, cores)."""
+    import oracle as o
+    wp, wm = wl.fields(WORK)
+    ds = 1.0 / WORK.Ns
+    NsA = o.n_A_steps(WORK.Ns, WORK.fA)
+    wA, wB = o.species_fields(wp, wm, o.SCFT_REAL)
+    BA, BB = o.boltzmann_factor(wA, ds), o.boltzmann_factor(wB, ds)
+    D = o.diffusion_factor(WORK.n, WORK.L, ds)
+    t0 = time.perf_counter()
+    o.forward_march(BA, BB, D, 1, NsA)  # warm-up / size the sample
+    t1 = time.perf_counter() - t0
+    if nsteps is None:
+        nsteps = max(1, min(WORK.Ns, int(seconds_target / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    o.forward_march(BA, BB, D, nsteps, NsA)
+    dt = time.perf_counter() - t0
+    units = WORK.M * nsteps
+    return units / dt, f"oracle forward march, {nsteps} contour steps of the 128^3 grid ({dt:.1f} s)", 1
+
+
+def run_reference(args):
+    ws, rank = _dist()
+    if rank != 0:
+        return 0
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, sample, cores = _oracle_sample(nsteps=10)
+        if i >= args.warmup:
+            vals.append(v)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORK.name, "grid": list(WORK.n), "Ns": WORK.Ns},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _time_device(pft, torch, h, stream, steps, warmup, units_per_step):
+    """Device-resident steps (inputs already in HBM): solve + field step per step."""
+    for _ in range(warmup):
+        pft.pft_solve(h)
+        pft.pft_field_step(h, pft.PFT_STEP_SCFT_EULER, WORK.lam)
+    pft.pft_synchronize(h)
+    s = torch.cuda.ExternalStream(stream)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        pft.pft_solve(h)
+        pft.pft_field_step(h, pft.PFT_STEP_SCFT_EULER, WORK.lam)
+    e1.record(s)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run(args):
+    import torch
+
+    from paper_1204_5434_gb300 import pft
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    peak, peak_src = _peaks()
+    wpa, wma = wl.fields(WORK.with_(seed=WORK.seed + rank))
+    units_per_step = 2 * WORK.M * WORK.Ns
+    res = {}
+    for prec_name, prec in (("fp32", pft.PFT_FP32_MIXED), ("fp64", pft.PFT_FP64)):
+        sys_ = pft.System(WORK.n, WORK.L, WORK.Ns, WORK.fA, WORK.chiN, WORK.C, pft.PFT_SCFT_REAL, prec,
+                          seed=1000 + rank)
+        h = sys_.h
+        stream = pft.pft_get_stream(h)
+        dwp = torch.from_numpy(wpa).cuda()
+        dwm = torch.from_numpy(wma).cuda()
+        torch.cuda.synchronize()
+        pft.pft_set_fields(h, dwp, dwm)
+        steps = args.steps if prec_name == "fp32" else max(3, args.steps // 2)
+        clocks = Clocks(local)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        ms = _time_device(pft, torch, h, stream, steps, args.warmup, units_per_step)
+        ck = clocks.stop()
+        torch.cuda.synchronize()
+        if ws > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            torch.distributed.barrier()
+            ms = float(t.item())
+        value = ws * units_per_step / (ms * 1e-3)
+        # per-kernel device times of one eager step (events between launches)
+        prof = pft.pft_profile_step(h, pft.PFT_STEP_SCFT_EULER, WORK.lam)
+        launches = sum(k["launches"] for k in prof["kinds"].values())
+        # end-to-end through the public API with pinned host buffers
+        hp = torch.from_numpy(wpa).pin_memory()
+        hm = torch.from_numpy(wma).pin_memory()
+        op = torch.empty_like(hp).pin_memory()
+        om = torch.empty_like(hm).pin_memory()
+        e2e_steps = max(2, steps // 2)
+        for _ in range(1):
+            pft.pft_set_fields(h, hp, hm)
+            pft.pft_solve(h)
+            pft.pft_field_step(h, pft.PFT_STEP_SCFT_EULER, WORK.lam)
+            pft.pft_get_fields(h, op, om)
+            pft.pft_get_observables(h)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            pft.pft_set_fields(h, hp, hm)
+            pft.pft_solve(h)
+            pft.pft_field_step(h, pft.PFT_STEP_SCFT_EULER, WORK.lam)
+            pft.pft_get_fields(h, op, om)
+        pft.pft_synchronize(h)
+        e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+        if ws > 1:
+            t = torch.tensor([e2e_ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        sys_.close()
+        del dwp, dwm
+        torch.cuda.empty_cache()
+        bpu = BYTES_PER_UNIT[prec_name]
+        step_ms = 0.5 * (prof["step_fwd_ms"] + prof["step_bwd_ms"])
+        achieved = bpu * WORK.M / (step_ms * 1e-3) / 1e9
+        top = max(prof["kinds"].items(), key=lambda kv: kv[1]["ms"])
+        res[prec_name] = {
+            "value": value, "ms_per_step": ms, "clocks": ck, "launches_per_step": launches,
+            "roofline": {"bound": "hbm", "kernel": "contour step (z_fwd, y_fwd, x_fused, y_inv, z_inv)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_source": f"{peak_src} hbm_gbs", "bytes_per_unit": bpu,
+                         "units_per_launch": WORK.M, "step_ms": step_ms, "traffic": None},
+            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
+                            "share": round(v["ms"] / prof["total_ms"], 4) if prof["total_ms"] else None,
+                            "GBps": round(v["bytes_per_launch"] * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
+                            if v["ms"] > 0 and v["bytes_per_launch"] > 0 else None}
+                        for k, v in prof["kinds"].items() if v["launches"]},
+            "top_kernel": top[0],
+            "e2e": {"value": ws * units_per_step / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 2 * WORK.M * 8, "d2h_bytes_per_step": 2 * WORK.M * 8},
+        }
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    cpu_v, cpu_sample, cpu_cores = _oracle_sample()
+    main = res["fp32"]
+    fp64 = res["fp64"]
+    fp64_flops_unit = None
+    line = {
+        "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "precision": "f32 propagators/FFTs, f64 quadrature/reductions/update",
+        "data": "synthetic",
+        "config": {"workload": WORK.name, "grid": list(WORK.n), "L": list(WORK.L), "Ns": WORK.Ns, "fA": WORK.fA,
+                   "chiN": WORK.chiN, "step": "solve + SCFT Euler field update (lambda=0.1)",
+                   "units_per_step": units_per_step, "parallelism": f"replicas x{ws}",
+                   "l2": "q history of 101 slices (850 MB f32) streams through HBM every step; no flush"},
+        "roofline": main["roofline"], "kernels": main["kernels"],
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_sample},
+        "e2e": main["e2e"], "gpu_launches": main["launches_per_step"] * args.steps, "clocks": main["clocks"],
+        "fp64": {"value": fp64["value"], "ms_per_step": fp64["ms_per_step"], "roofline": fp64["roofline"],
+                 "kernels": fp64["kernels"], "e2e": fp64["e2e"], "clocks": fp64["clocks"],
+                 "note": "FP64 FFTs are bound by the GB300 FP64 pipe (about 1.2 TFLOP/s measured)"},
+        "fp32_over_fp64": main["value"] / fp64["value"],
+    }
+    del fp64_flops_unit
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_1204_5434_gb300 import build
+    build.build()
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,223 @@
+/*
+ * pft.h -- C ABI of the GB300 (sm_103a) pseudo-spectral propagator library for an
+ * incompressible AB diblock melt (Delaney & Fredrickson, "Polymer Field-Theory
+ * Simulations on Graphics Processing Units", arXiv:1204.5434).
+ *
+ * What the library computes (the paper's method, Sec. "Model" and "Algorithms"):
+ *   - Boltzmann factors  B_A,B = exp(-w_A,B ds/2) from the fields           (Eq. 13)
+ *   - forward march      q_n  = B_n F^-1[ D F[ B_n q_{n-1} ] ],  q_0 = 1     (Eqs. 5, 13)
+ *   - backward march     qd_m = same step with the B block first, qd_0 = 1   (Eq. 5)
+ *     fused with the contour quadrature of q(s) qd(1-s) into phi_A, phi_B    (Eq. 8)
+ *   - Q = (1/V) int q(x, 1) and lnQ                                         (Eq. 4)
+ *   - H = C int [w-^2/chiN - i w+] - C V lnQ                                 (Eq. 3)
+ *   - field update by explicit Euler (SCFT) or Euler-Maruyama complex
+ *     Langevin with real Gaussian noise                              (Eqs. 7, 9, 10)
+ *   - exact gradients of the discrete H in the fields and box lengths (stress)
+ *
+ * Conventions (all entry points):
+ *   - grid n[3] = (nx, ny, nz), arrays row-major [x][y][z] (z contiguous),
+ *     M = nx*ny*nz.  Every n[a] must be one of 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128,
+ *     192, 256 (products of 2 and 3 with a compiled FFT plan); nz must be even.
+ *   - lengths in units of Rg; ds = 1/Ns; NsA = floor(fA*Ns + 1/2) contour steps on A.
+ *   - PFT_SCFT_REAL: fields are real float64 arrays W+ (= i*omega+) and W- (= omega-);
+ *     PFT_CL_COMPLEX: fields are complex128 arrays omega+ and omega- (interleaved
+ *     re, im).  All API-facing arrays are float64 / complex128 in either precision.
+ *   - PFT_FP64 runs every step in double; PFT_FP32_MIXED runs the propagators and FFTs
+ *     in float and the Boltzmann factors' exponentials, contour quadrature,
+ *     reductions, Hamiltonian and field update in double.
+ *   - Pointers marked "host or device" are read/written according to the pft_mem
+ *     argument.  Device pointers must be readable on the context's stream when the
+ *     call is made.  The library copies inputs; the caller keeps ownership of every
+ *     pointer it passes and of every output buffer.
+ *   - Calls are asynchronous on the context's stream except those that write host
+ *     memory, which synchronise that stream before returning.
+ *   - Every entry point returns pft_status; nothing throws or aborts.  A context is
+ *     thread-compatible, not thread-safe.
+ */
+#ifndef PFT_H
+#define PFT_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PFT_OK = 0,
+  PFT_ERR_ARG = 1,        /* null pointer, out-of-range parameter */
+  PFT_ERR_SHAPE = 2,      /* a grid size without a compiled FFT plan, odd nz */
+  PFT_ERR_OOM = 3,        /* device allocation failed */
+  PFT_ERR_CUDA = 4,       /* a CUDA runtime call or kernel launch failed */
+  PFT_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+  PFT_ERR_NONFINITE = 6,  /* Q or H is not finite (e.g. CL blow-up) */
+  PFT_ERR_STATE = 7,      /* call out of order, e.g. solve before set_fields */
+  PFT_ERR_IO = 8,         /* checkpoint file could not be read or written */
+  PFT_ERR_UNSUPPORTED = 9 /* valid request this build does not implement */
+} pft_status;
+
+typedef enum { PFT_SCFT_REAL = 0, PFT_CL_COMPLEX = 1 } pft_kind;
+typedef enum { PFT_FP64 = 0, PFT_FP32_MIXED = 1 } pft_precision;
+typedef enum { PFT_HOST = 0, PFT_DEVICE = 1 } pft_mem;
+typedef enum { PFT_STEP_SCFT_EULER = 0, PFT_STEP_CL_EULER_MARUYAMA = 1 } pft_step_kind;
+
+typedef struct { int n[3]; double L[3]; } pft_grid;          /* grid points and box (Rg) */
+typedef struct { int Ns; double fA; } pft_chain;              /* contour steps, A fraction */
+typedef struct { double chiN; double C; pft_kind kind; } pft_model;
+
+typedef struct {
+  pft_precision precision;
+  int use_graph;            /* 1: replay each solve as one captured CUDA graph */
+  void* stream;             /* cudaStream_t to run on; NULL: the library creates one */
+  unsigned long long seed;  /* Philox key of the CL noise */
+  unsigned long long instance; /* Philox counter word: independent replica streams */
+} pft_opts;
+
+/* Observables of the last solve.  Complex quantities are {re, im}; in SCFT mode the
+ * imaginary parts are zero. */
+typedef struct {
+  double Q[2];          /* single-chain partition function, Eq. 4 */
+  double lnQ[2];        /* principal logarithm of Q */
+  double H[2];          /* Hamiltonian, Eq. 3 */
+  double h[2];          /* intensive H/(C V) */
+  double phiA_mean[2];  /* volume average of phi_A (= NsA/Ns up to round-off) */
+  double phiB_mean[2];
+  double force_p_rms;   /* rms of the W+ (omega+) force of Eq. 7, per C */
+  double force_m_rms;   /* rms of the W- (omega-) force */
+  double fA_eff;        /* NsA/Ns */
+  int NsA;
+  long long step;       /* field steps taken since set_fields */
+} pft_obs;
+
+typedef struct pft_ctx pft_ctx;
+
+/* Human-readable name of a status code (static storage). */
+const char* pft_status_string(pft_status s);
+
+/* Text of the last error raised on this thread (CUDA error string or argument
+ * diagnostic); empty if none.  Static thread-local storage. */
+const char* pft_last_error(void);
+
+/* Create a context for one system: validates sizes, builds the FFT plans and the
+ * per-axis twiddle and diffusion tables, and allocates every device buffer it will
+ * use (fields, Boltzmann factors, the q history of Ns+1 slices, two qd slices, the
+ * spectrum, FP64 density accumulators, reduction scratch).  On failure *out is NULL.
+ * Errors: PFT_ERR_ARG, PFT_ERR_SHAPE, PFT_ERR_OOM, PFT_ERR_CUDA. */
+pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chain,
+                      const pft_model* model, const pft_opts* opts);
+
+/* Free every device buffer, graph and (if the library created it) stream. NULL is a no-op. */
+pft_status pft_destroy(pft_ctx* ctx);
+
+/* Device memory held by the context, in bytes. */
+pft_status pft_memory_bytes(const pft_ctx* ctx, size_t* bytes);
+
+/* The context's stream (cudaStream_t) as an opaque pointer. */
+pft_status pft_get_stream(const pft_ctx* ctx, void** stream);
+
+/* Block the host until all work queued on the context's stream has finished. */
+pft_status pft_synchronize(pft_ctx* ctx);
+
+/* Copy the two fields in (M elements each; float64 in SCFT, complex128 in CL mode),
+ * recompute the Boltzmann factors (Eq. 13) and reset the step counter.
+ * wp, wm: host or device per `where`. */
+pft_status pft_set_fields(pft_ctx* ctx, const void* wp, const void* wm, pft_mem where);
+
+/* Copy the current fields out (same layout as pft_set_fields). */
+pft_status pft_get_fields(pft_ctx* ctx, void* wp, void* wm, pft_mem where);
+
+/* Change the box lengths L[3] (Rg); the fields stay fixed on the grid. */
+pft_status pft_set_box(pft_ctx* ctx, const double L[3]);
+pft_status pft_get_box(const pft_ctx* ctx, double L[3]);
+
+/* One full solve for the current fields: forward march (Eqs. 5, 13), Q (Eq. 4),
+ * backward march with fused contour quadrature (Eq. 8), densities and H (Eq. 3).
+ * Error: PFT_ERR_STATE before the first pft_set_fields. */
+pft_status pft_solve(pft_ctx* ctx);
+
+/* Observables of the last solve (synchronises the stream).
+ * Error: PFT_ERR_STATE before a solve; PFT_ERR_NONFINITE if Q or H is not finite
+ * (the struct is still filled). */
+pft_status pft_get_observables(pft_ctx* ctx, pft_obs* obs);
+
+/* Segment densities phi_A, phi_B of the last solve (Eq. 8, phi = rho/rho0), M
+ * elements each, float64 (SCFT) or complex128 (CL).  Host or device per `where`. */
+pft_status pft_get_densities(pft_ctx* ctx, void* phiA, void* phiB, pft_mem where);
+
+/* One field update from the densities of the last solve (Eq. 9 with the Eq. 7 forces
+ * taken per C):
+ *   PFT_STEP_SCFT_EULER (SCFT mode):  W+ += lam (phiA+phiB-1);
+ *                                     W- -= lam (2 W-/chiN + phiB - phiA)
+ *   PFT_STEP_CL_EULER_MARUYAMA (CL):  w+ += -dt i (phiA+phiB-1) + eta+;
+ *                                     w- += -dt (2 w-/chiN + phiB - phiA) + eta-
+ * eta+/- are real Gaussian with variance 2 dt/(C dV) (below Eq. 10).  If eta_p and
+ * eta_m are NULL the library draws them from its Philox4x32-10 stream (key = seed,
+ * counter = (point/4, field, step, instance)); otherwise they are caller arrays of M
+ * float64 values, already scaled, host or device per `where`.  The Boltzmann factors
+ * for the next solve are recomputed in the same kernel.
+ * Errors: PFT_ERR_STATE without a prior solve; PFT_ERR_ARG for a step kind that does
+ * not match the model kind. */
+pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt,
+                          const void* eta_p, const void* eta_m, pft_mem where);
+
+/* Exact gradients of the discrete H of the last solve:
+ *   dH_dwp, dH_dwm (M float64 each, host or device per `where`, either may be NULL):
+ *     C dV (phiA+phiB-1) and C dV (2 W-/chiN + phiB - phiA)          (Eq. 7 x C dV)
+ *   dH_dL[3] (host, may be NULL): dH/dL_a = H/L_a - C V dlnQ/dL_a, the box derivative
+ *     at fixed grid values, from the bilinear contraction of the forward and
+ *     conjugate spectra with d(exp(-k^2 ds))/dL_a over every contour step.
+ *   dlnQ_dL[3] (host, may be NULL).
+ * SCFT mode only (PFT_ERR_UNSUPPORTED in CL mode).  Runs one extra march. */
+pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[3],
+                         double dlnQ_dL[3], pft_mem where);
+
+/* Per-kernel-class device times of one solve, for roofline reporting. */
+#define PFT_PROFILE_KINDS 16
+typedef struct {
+  int nkinds;
+  char name[PFT_PROFILE_KINDS][24];
+  long long launches[PFT_PROFILE_KINDS];
+  double ms[PFT_PROFILE_KINDS];                /* summed device time of the class */
+  double bytes_per_launch[PFT_PROFILE_KINDS];  /* arrays one launch must read + write */
+  double step_fwd_ms;  /* mean device time of one forward contour step (its 5 launches) */
+  double step_bwd_ms;  /* mean device time of one conjugate contour step with quadrature */
+  double total_ms;     /* first to last event */
+} pft_profile;
+
+/* Run one solve launch by launch (not graph-replayed) with a CUDA event recorded on
+ * the context's stream before every kernel, then, if step_kind >= 0, one field step
+ * of that kind with lam_or_dt and the library's own noise; fill *out with the device
+ * time per kernel class.  Same effect on the context as pft_solve (+ pft_field_step).
+ * Synchronises.  Errors: as pft_solve / pft_field_step. */
+pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_profile* out);
+
+/* Test hooks -------------------------------------------------------------- */
+
+/* 3D DFT of M complex128 values through the library's own FFT passes in the
+ * context's precision (forward: exp(-i k.x), unnormalised; inverse: exp(+i k.x),
+ * also unnormalised).  in/out host or device per `where`, may alias. */
+pft_status pft_fft3d(pft_ctx* ctx, const void* in, void* out, int inverse, pft_mem where);
+
+/* Copy slice `s` (0..Ns) of the forward propagator history (which = 0) or the last
+ * conjugate propagator slice qd_Ns (which = 1, s ignored) out as float64/complex128. */
+pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem where);
+
+/* Replace the initial condition q_0 = qd_0 = 1 by a caller array (M values, float64
+ * or complex128 by kind; NULL restores 1).  Used by the diffusion-only test. */
+pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
+
+/* Standard normals of the device Philox stream (same layout as the CL noise) for
+ * points 0..M-1 into a device float64 array, on `stream` (cudaStream_t or NULL). */
+pft_status pft_philox_normals(unsigned long long seed, unsigned long long instance,
+                              unsigned long long step, int field, long long M,
+                              double* out_device, void* stream);
+
+/* Raw Philox4x32-10 blocks: out_device receives 4*count uint32 words, block i from
+ * counter (i + ctr0, ctr1, ctr2, ctr3) and key (k0, k1). */
+pft_status pft_philox_raw(const unsigned int ctr[4], const unsigned int key[2], long long count,
+                          unsigned int* out_device, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFT_H */

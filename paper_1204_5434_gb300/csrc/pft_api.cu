@@ -1,0 +1,522 @@
+// pft_api.cu -- the extern "C" entry points declared in include/pft.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+
+#include "pft_engine.h"
+
+using pft::CtxData;
+using pft::Engine;
+
+struct pft_ctx {
+  CtxData d;
+  Engine* eng = nullptr;
+  void* io = nullptr;   // [M] complex128 staging for conversions and host noise
+  bool have_obs = false;
+};
+
+namespace pft {
+const char* const kKernelKindNames[KK_COUNT] = {"z_fwd",  "y_fwd",   "x_fused",    "y_inv",  "z_inv_fwd",
+                                                "z_inv_bwd", "reduce", "field_step", "prepare"};
+static thread_local std::string g_err;
+void set_error(const std::string& s) { g_err = s; }
+
+bool axis_supported(int n) {
+  switch (n) {
+    case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: case 64: case 96: case 128: case 192:
+    case 256:
+      return true;
+    default:
+      return false;
+  }
+}
+}  // namespace pft
+
+namespace {
+
+pft_status fail(pft_status s, const std::string& msg) {
+  pft::set_error(msg);
+  return s;
+}
+
+pft_status cuda_fail(cudaError_t e, const char* what) {
+  pft::set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  (void)cudaGetLastError();  // clear a sticky launch error so later calls can proceed
+  if (e == cudaErrorMemoryAllocation) return PFT_ERR_OOM;
+  if (e == cudaErrorNotSupported) return PFT_ERR_UNSUPPORTED;
+  return PFT_ERR_CUDA;
+}
+
+#define PFT_CK(call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+size_t welem(const CtxData& d) {  // bytes of one working-precision propagator element
+  const size_t r = (d.prec == PFT_FP64) ? 8 : 4;
+  return d.kind == PFT_SCFT_REAL ? r : 2 * r;
+}
+size_t felem(const CtxData& d) { return d.kind == PFT_SCFT_REAL ? 8 : 16; }  // API element
+
+cudaError_t dalloc(CtxData& d, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) d.bytes += bytes;
+  return e;
+}
+
+void free_all(pft_ctx* c) {
+  CtxData& d = c->d;
+  if (d.graph) cudaGraphExecDestroy(d.graph);
+  for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
+  void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
+                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (d.scal_host) cudaFreeHost(d.scal_host);
+  if (d.own_stream && d.stream) cudaStreamDestroy(d.stream);
+  delete c->eng;
+  delete c;
+}
+
+cudaMemcpyKind kind_in(pft_mem w) { return w == PFT_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice; }
+cudaMemcpyKind kind_out(pft_mem w) { return w == PFT_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice; }
+
+pft_status write_volume(CtxData& d) {
+  const double V = d.L[0] * d.L[1] * d.L[2];
+  d.scal_host[pft::S_VOL] = V;
+  PFT_CK(cudaMemcpyAsync(d.scal + pft::S_VOL, d.scal_host + pft::S_VOL, sizeof(double), cudaMemcpyHostToDevice,
+                         d.stream));
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pft_status_string(pft_status s) {
+  switch (s) {
+    case PFT_OK: return "PFT_OK";
+    case PFT_ERR_ARG: return "PFT_ERR_ARG: invalid argument";
+    case PFT_ERR_SHAPE: return "PFT_ERR_SHAPE: unsupported grid size";
+    case PFT_ERR_OOM: return "PFT_ERR_OOM: device memory exhausted";
+    case PFT_ERR_CUDA: return "PFT_ERR_CUDA: CUDA runtime error";
+    case PFT_ERR_TIMEOUT: return "PFT_ERR_TIMEOUT: bounded device wait expired";
+    case PFT_ERR_NONFINITE: return "PFT_ERR_NONFINITE: non-finite Q or H";
+    case PFT_ERR_STATE: return "PFT_ERR_STATE: call out of order";
+    case PFT_ERR_IO: return "PFT_ERR_IO: file error";
+    case PFT_ERR_UNSUPPORTED: return "PFT_ERR_UNSUPPORTED: not implemented for this configuration";
+  }
+  return "unknown pft_status";
+}
+
+const char* pft_last_error(void) { return pft::g_err.c_str(); }
+
+pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chain, const pft_model* model,
+                      const pft_opts* opts) {
+  if (!out) return fail(PFT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !chain || !model || !opts) return fail(PFT_ERR_ARG, "grid, chain, model and opts are required");
+  for (int a = 0; a < 3; a++) {
+    if (!pft::axis_supported(grid->n[a]))
+      return fail(PFT_ERR_SHAPE, "grid size n[" + std::to_string(a) + "]=" + std::to_string(grid->n[a]) +
+                                     " has no FFT plan (4,6,8,12,16,24,32,48,64,96,128,192,256)");
+    if (!(grid->L[a] > 0.0) || !isfinite(grid->L[a])) return fail(PFT_ERR_ARG, "box lengths must be positive");
+  }
+  if (chain->Ns < 1 || chain->Ns > 100000) return fail(PFT_ERR_ARG, "Ns out of range [1, 100000]");
+  if (!(chain->fA >= 0.0 && chain->fA <= 1.0)) return fail(PFT_ERR_ARG, "fA out of [0, 1]");
+  if (!(model->chiN > 0.0) || !(model->C > 0.0)) return fail(PFT_ERR_ARG, "chiN and C must be positive");
+  if (model->kind != PFT_SCFT_REAL && model->kind != PFT_CL_COMPLEX) return fail(PFT_ERR_ARG, "unknown model kind");
+  if (opts->precision != PFT_FP64 && opts->precision != PFT_FP32_MIXED) return fail(PFT_ERR_ARG, "unknown precision");
+
+  pft_ctx* c = new pft_ctx();
+  CtxData& d = c->d;
+  for (int a = 0; a < 3; a++) {
+    d.n[a] = grid->n[a];
+    d.L[a] = grid->L[a];
+  }
+  d.Ns = chain->Ns;
+  d.fA = chain->fA;
+  d.NsA = (int)floor(chain->fA * chain->Ns + 0.5);
+  d.ds = 1.0 / chain->Ns;
+  d.chiN = model->chiN;
+  d.C = model->C;
+  d.kind = model->kind;
+  d.prec = opts->precision;
+  d.use_graph = opts->use_graph != 0;
+  d.seed = opts->seed;
+  d.instance = opts->instance;
+  d.M = (long long)d.n[0] * d.n[1] * d.n[2];
+  d.nzh = (d.kind == PFT_SCFT_REAL) ? d.n[2] / 2 + 1 : d.n[2];
+  d.Ms = (long long)d.n[0] * d.n[1] * d.nzh;
+
+  cudaError_t e = cudaGetDevice(&d.device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, d.device);
+  if (e != cudaSuccess) {
+    pft_status s = cuda_fail(e, "cudaGetDevice");
+    free_all(c);
+    return s;
+  }
+  d.npart = d.sms * 4;
+  if (opts->stream) {
+    d.stream = (cudaStream_t)opts->stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&d.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      pft_status s = cuda_fail(e, "cudaStreamCreate");
+      free_all(c);
+      return s;
+    }
+    d.own_stream = true;
+  }
+  c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
+
+  const size_t M = (size_t)d.M;
+  const size_t we = welem(d), fe = felem(d);
+  const size_t ze = 2 * c->eng->elem_bytes();  // working-precision complex
+  struct {
+    void** p;
+    size_t b;
+  } plan[] = {
+      {&d.wp, M * fe},   {&d.wm, M * fe},    {&d.BA, M * we},     {&d.BB, M * we},
+      {&d.hist, (size_t)(d.Ns + 1) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
+      {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
+      {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
+      {&c->io, M * 16},
+  };
+  for (auto& a : plan) {
+    e = dalloc(d, a.p, a.b);
+    if (e != cudaSuccess) {
+      pft_status s = cuda_fail(e, "device allocation");
+      free_all(c);
+      return s;
+    }
+  }
+  e = cudaMallocHost(&d.scal_host, pft::S_COUNT * sizeof(double));
+  if (e == cudaSuccess) {
+    memset(d.scal_host, 0, pft::S_COUNT * sizeof(double));
+    e = cudaMemsetAsync(d.scal, 0, pft::S_COUNT * sizeof(double), d.stream);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.partials, 0, (size_t)d.npart * 8 * sizeof(double), d.stream);
+  if (e == cudaSuccess) e = c->eng->upload_tables(d);
+  if (e == cudaSuccess) e = c->eng->fill_ones(d, d.hist);
+  if (e == cudaSuccess) e = c->eng->fill_ones(d, d.qd0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+  if (e != cudaSuccess) {
+    pft_status s = cuda_fail(e, "pft_create initialisation");
+    free_all(c);
+    return s;
+  }
+  pft_status s = write_volume(d);
+  if (s != PFT_OK) {
+    free_all(c);
+    return s;
+  }
+  *out = c;
+  return PFT_OK;
+}
+
+pft_status pft_destroy(pft_ctx* ctx) {
+  if (!ctx) return PFT_OK;
+  if (ctx->d.stream) cudaStreamSynchronize(ctx->d.stream);
+  free_all(ctx);
+  return PFT_OK;
+}
+
+pft_status pft_memory_bytes(const pft_ctx* ctx, size_t* bytes) {
+  if (!ctx || !bytes) return fail(PFT_ERR_ARG, "NULL argument");
+  *bytes = ctx->d.bytes;
+  return PFT_OK;
+}
+
+pft_status pft_get_stream(const pft_ctx* ctx, void** stream) {
+  if (!ctx || !stream) return fail(PFT_ERR_ARG, "NULL argument");
+  *stream = (void*)ctx->d.stream;
+  return PFT_OK;
+}
+
+pft_status pft_synchronize(pft_ctx* ctx) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  PFT_CK(cudaStreamSynchronize(ctx->d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_set_fields(pft_ctx* ctx, const void* wp, const void* wm, pft_mem where) {
+  if (!ctx || !wp || !wm) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  const size_t b = (size_t)d.M * felem(d);
+  PFT_CK(cudaMemcpyAsync(d.wp, wp, b, kind_in(where), d.stream));
+  PFT_CK(cudaMemcpyAsync(d.wm, wm, b, kind_in(where), d.stream));
+  PFT_CK(ctx->eng->prepare_fields(d));
+  if (where == PFT_HOST) PFT_CK(cudaStreamSynchronize(d.stream));
+  d.fields_set = true;
+  d.solved = false;
+  ctx->have_obs = false;
+  d.step = 0;
+  return PFT_OK;
+}
+
+pft_status pft_get_fields(pft_ctx* ctx, void* wp, void* wm, pft_mem where) {
+  if (!ctx || !wp || !wm) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (!d.fields_set) return fail(PFT_ERR_STATE, "fields not set");
+  const size_t b = (size_t)d.M * felem(d);
+  PFT_CK(cudaMemcpyAsync(wp, d.wp, b, kind_out(where), d.stream));
+  PFT_CK(cudaMemcpyAsync(wm, d.wm, b, kind_out(where), d.stream));
+  if (where == PFT_HOST) PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_set_box(pft_ctx* ctx, const double L[3]) {
+  if (!ctx || !L) return fail(PFT_ERR_ARG, "NULL argument");
+  for (int a = 0; a < 3; a++)
+    if (!(L[a] > 0.0) || !isfinite(L[a])) return fail(PFT_ERR_ARG, "box lengths must be positive");
+  CtxData& d = ctx->d;
+  for (int a = 0; a < 3; a++) d.L[a] = L[a];
+  PFT_CK(ctx->eng->upload_tables(d));
+  return write_volume(d);
+}
+
+pft_status pft_get_box(const pft_ctx* ctx, double L[3]) {
+  if (!ctx || !L) return fail(PFT_ERR_ARG, "NULL argument");
+  for (int a = 0; a < 3; a++) L[a] = ctx->d.L[a];
+  return PFT_OK;
+}
+
+pft_status pft_solve(pft_ctx* ctx) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  CtxData& d = ctx->d;
+  if (!d.fields_set) return fail(PFT_ERR_STATE, "pft_solve before pft_set_fields");
+  PFT_CK(ctx->eng->enqueue_solve(d));
+  d.solved = true;
+  ctx->have_obs = true;
+  return PFT_OK;
+}
+
+pft_status pft_get_observables(pft_ctx* ctx, pft_obs* obs) {
+  if (!ctx || !obs) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (!ctx->have_obs) return fail(PFT_ERR_STATE, "no solve since the fields were set");
+  PFT_CK(cudaMemcpyAsync(d.scal_host, d.scal, pft::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  const double* s = d.scal_host;
+  const double V = d.L[0] * d.L[1] * d.L[2];
+  const double Md = (double)d.M;
+  memset(obs, 0, sizeof(*obs));
+  for (int j = 0; j < 2; j++) {
+    obs->Q[j] = s[pft::S_Q + j];
+    obs->lnQ[j] = s[pft::S_LNQ + j];
+    obs->H[j] = s[pft::S_H + j];
+    obs->h[j] = s[pft::S_H + j] / (d.C * V);
+    obs->phiA_mean[j] = s[pft::S_PHIA + j] / Md;
+    obs->phiB_mean[j] = s[pft::S_PHIB + j] / Md;
+  }
+  obs->force_p_rms = sqrt(s[pft::S_FP2] / Md);
+  obs->force_m_rms = sqrt(s[pft::S_FM2] / Md);
+  obs->fA_eff = (double)d.NsA / d.Ns;
+  obs->NsA = d.NsA;
+  obs->step = d.step;
+  if (!isfinite(obs->Q[0]) || !isfinite(obs->Q[1]) || !isfinite(obs->H[0]) || !isfinite(obs->H[1]))
+    return fail(PFT_ERR_NONFINITE, "Q or H is not finite");
+  return PFT_OK;
+}
+
+pft_status pft_get_densities(pft_ctx* ctx, void* phiA, void* phiB, pft_mem where) {
+  if (!ctx || !phiA || !phiB) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (!ctx->have_obs) return fail(PFT_ERR_STATE, "no solve since the fields were set");
+  const size_t b = (size_t)d.M * felem(d);
+  PFT_CK(cudaMemcpyAsync(phiA, d.accA, b, kind_out(where), d.stream));
+  PFT_CK(cudaMemcpyAsync(phiB, d.accB, b, kind_out(where), d.stream));
+  if (where == PFT_HOST) PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt, const void* eta_p, const void* eta_m,
+                          pft_mem where) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  CtxData& d = ctx->d;
+  if (!d.solved) return fail(PFT_ERR_STATE, "pft_field_step needs a solve at the current fields");
+  if (kind == PFT_STEP_SCFT_EULER && d.kind != PFT_SCFT_REAL)
+    return fail(PFT_ERR_ARG, "SCFT Euler step needs real SCFT fields");
+  if (kind == PFT_STEP_CL_EULER_MARUYAMA && d.kind != PFT_CL_COMPLEX)
+    return fail(PFT_ERR_ARG, "complex Langevin step needs complex fields");
+  if (kind != PFT_STEP_SCFT_EULER && kind != PFT_STEP_CL_EULER_MARUYAMA) return fail(PFT_ERR_ARG, "unknown step kind");
+  if (!isfinite(lam_or_dt) || !(lam_or_dt > 0.0)) return fail(PFT_ERR_ARG, "step size must be positive");
+  if ((eta_p == nullptr) != (eta_m == nullptr)) return fail(PFT_ERR_ARG, "give both noise arrays or neither");
+  const double* ep = nullptr;
+  const double* em = nullptr;
+  if (eta_p && kind == PFT_STEP_CL_EULER_MARUYAMA) {
+    if (where == PFT_HOST) {
+      double* io = (double*)ctx->io;
+      PFT_CK(cudaMemcpyAsync(io, eta_p, (size_t)d.M * 8, cudaMemcpyHostToDevice, d.stream));
+      PFT_CK(cudaMemcpyAsync(io + d.M, eta_m, (size_t)d.M * 8, cudaMemcpyHostToDevice, d.stream));
+      ep = io;
+      em = io + d.M;
+    } else {
+      ep = (const double*)eta_p;
+      em = (const double*)eta_m;
+    }
+  }
+  PFT_CK(ctx->eng->field_step(d, kind, lam_or_dt, ep, em));
+  if (eta_p && where == PFT_HOST) PFT_CK(cudaStreamSynchronize(d.stream));
+  d.step++;
+  d.solved = false;
+  return PFT_OK;
+}
+
+pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[3], double dlnQ_dL[3],
+                         pft_mem where) {
+  (void)dH_dwp;
+  (void)dH_dwm;
+  (void)dH_dL;
+  (void)dlnQ_dL;
+  (void)where;
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  return fail(PFT_ERR_UNSUPPORTED, "gradients are not built yet");
+}
+
+pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_profile* out) {
+  if (!ctx || !out) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (!d.fields_set) return fail(PFT_ERR_STATE, "pft_profile_step before pft_set_fields");
+  if (step_kind >= 0) {
+    if ((step_kind == PFT_STEP_SCFT_EULER) != (d.kind == PFT_SCFT_REAL) ||
+        (step_kind != PFT_STEP_SCFT_EULER && step_kind != PFT_STEP_CL_EULER_MARUYAMA))
+      return fail(PFT_ERR_ARG, "step kind does not match the model kind");
+    if (!isfinite(lam_or_dt) || !(lam_or_dt > 0.0)) return fail(PFT_ERR_ARG, "step size must be positive");
+  }
+  const size_t need = (size_t)10 * d.Ns + 64;
+  while (d.ev.size() < need) {
+    cudaEvent_t ev;
+    PFT_CK(cudaEventCreate(&ev));
+    d.ev.push_back(ev);
+  }
+  d.ev_kind.assign(d.ev.size(), -1);
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  d.profiling = true;
+  d.ev_used = 0;
+  cudaError_t e = ctx->eng->enqueue_solve(d);
+  if (e == cudaSuccess && step_kind >= 0) e = ctx->eng->field_step(d, step_kind, lam_or_dt, nullptr, nullptr);
+  pft::mark(d, -1);
+  d.profiling = false;
+  if (e != cudaSuccess) return cuda_fail(e, "profiled solve");
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  d.solved = true;
+  ctx->have_obs = true;
+  if (step_kind >= 0) {
+    d.step++;
+    d.solved = false;
+  }
+  memset(out, 0, sizeof(*out));
+  out->nkinds = pft::KK_COUNT;
+  for (int k = 0; k < pft::KK_COUNT; k++) strncpy(out->name[k], pft::kKernelKindNames[k], 23);
+  for (int i = 0; i + 1 < d.ev_used; i++) {
+    float ms = 0.f;
+    PFT_CK(cudaEventElapsedTime(&ms, d.ev[i], d.ev[i + 1]));
+    const int k = d.ev_kind[i];
+    if (k >= 0 && k < pft::KK_COUNT) {
+      out->ms[k] += ms;
+      out->launches[k]++;
+    }
+  }
+  float tot = 0.f;
+  if (d.ev_used > 1) PFT_CK(cudaEventElapsedTime(&tot, d.ev[0], d.ev[d.ev_used - 1]));
+  out->total_ms = tot;
+  // forward march: from its first launch to the first reduction; conjugate march:
+  // from the first z pass after that reduction to the next reduction.
+  int iF = -1, iR1 = -1, iB = -1, iR2 = -1;
+  for (int i = 0; i < d.ev_used; i++) {
+    const int k = d.ev_kind[i];
+    if (iF < 0 && k == pft::KK_Z_FWD) iF = i;
+    else if (iF >= 0 && iR1 < 0 && k == pft::KK_REDUCE) iR1 = i;
+    else if (iR1 >= 0 && iB < 0 && k == pft::KK_Z_FWD) iB = i;
+    else if (iB >= 0 && iR2 < 0 && k == pft::KK_REDUCE) iR2 = i;
+  }
+  if (iF >= 0 && iR1 > iF) {
+    float ms;
+    PFT_CK(cudaEventElapsedTime(&ms, d.ev[iF], d.ev[iR1]));
+    out->step_fwd_ms = ms / d.Ns;
+  }
+  if (iB >= 0 && iR2 > iB) {
+    float ms;
+    PFT_CK(cudaEventElapsedTime(&ms, d.ev[iB], d.ev[iR2]));
+    out->step_bwd_ms = ms / d.Ns;
+  }
+  // compulsory bytes of one launch of each class
+  const double M = (double)d.M, Ms = (double)d.Ms;
+  const double we = (double)welem(d), ze = 2.0 * ctx->eng->elem_bytes(), fe = (double)felem(d);
+  out->bytes_per_launch[pft::KK_Z_FWD] = 2 * M * we + Ms * ze;
+  out->bytes_per_launch[pft::KK_Y_FWD] = 2 * Ms * ze;
+  out->bytes_per_launch[pft::KK_X_FUSED] = 2 * Ms * ze;
+  out->bytes_per_launch[pft::KK_Y_INV] = 2 * Ms * ze;
+  out->bytes_per_launch[pft::KK_Z_INV_FWD] = Ms * ze + 2 * M * we;
+  out->bytes_per_launch[pft::KK_Z_INV_BWD] = Ms * ze + 3 * M * we + 2 * M * fe;
+  out->bytes_per_launch[pft::KK_FIELD_STEP] = 6 * M * fe + 2 * M * we;
+  out->bytes_per_launch[pft::KK_PREPARE] = 2 * M * fe + 2 * M * we;
+  return PFT_OK;
+}
+
+pft_status pft_fft3d(pft_ctx* ctx, const void* in, void* out, int inverse, pft_mem where) {
+  if (!ctx || !in || !out) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  const size_t b = (size_t)d.M * 16;
+  PFT_CK(cudaMemcpyAsync(ctx->io, in, b, kind_in(where), d.stream));
+  PFT_CK(ctx->eng->from_f64(d, ctx->io, d.spec2, 2 * d.M));
+  PFT_CK(ctx->eng->fft3d(d, d.spec2, inverse));
+  PFT_CK(ctx->eng->to_f64(d, d.spec2, ctx->io, 2 * d.M));
+  PFT_CK(cudaMemcpyAsync(out, ctx->io, b, kind_out(where), d.stream));
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem where) {
+  if (!ctx || !out) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (which != 0 && which != 1) return fail(PFT_ERR_ARG, "which must be 0 (q) or 1 (qd)");
+  if (which == 0 && (s < 0 || s > d.Ns)) return fail(PFT_ERR_ARG, "slice out of range");
+  const size_t we = welem(d);
+  const void* src = (which == 0) ? (const void*)((const char*)d.hist + (size_t)s * d.M * we) : d.qd[d.Ns & 1];
+  const long long cnt = d.M * (d.kind == PFT_SCFT_REAL ? 1 : 2);
+  PFT_CK(ctx->eng->to_f64(d, src, ctx->io, cnt));
+  PFT_CK(cudaMemcpyAsync(out, ctx->io, (size_t)cnt * 8, kind_out(where), d.stream));
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  CtxData& d = ctx->d;
+  if (!q0) {
+    PFT_CK(ctx->eng->fill_ones(d, d.hist));
+    PFT_CK(ctx->eng->fill_ones(d, d.qd0));
+  } else {
+    const long long cnt = d.M * (d.kind == PFT_SCFT_REAL ? 1 : 2);
+    PFT_CK(cudaMemcpyAsync(ctx->io, q0, (size_t)cnt * 8, kind_in(where), d.stream));
+    PFT_CK(ctx->eng->from_f64(d, ctx->io, d.hist, cnt));
+    PFT_CK(ctx->eng->from_f64(d, ctx->io, d.qd0, cnt));
+  }
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_philox_normals(unsigned long long seed, unsigned long long instance, unsigned long long step, int field,
+                              long long M, double* out_device, void* stream) {
+  if (!out_device || M < 0) return fail(PFT_ERR_ARG, "bad argument");
+  if (M == 0) return PFT_OK;
+  PFT_CK(pft::launch_philox_normals(seed, instance, step, field, M, out_device, (cudaStream_t)stream));
+  return PFT_OK;
+}
+
+pft_status pft_philox_raw(const unsigned int ctr[4], const unsigned int key[2], long long count,
+                          unsigned int* out_device, void* stream) {
+  if (!ctr || !key || !out_device || count < 0) return fail(PFT_ERR_ARG, "bad argument");
+  if (count == 0) return PFT_OK;
+  PFT_CK(pft::launch_philox_raw(ctr, key, count, out_device, (cudaStream_t)stream));
+  return PFT_OK;
+}
+
+}  // extern "C"

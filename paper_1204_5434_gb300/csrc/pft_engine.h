@@ -1,0 +1,125 @@
+// pft_engine.h -- host-side state of one system and the precision-specific engine
+// interface (the kernels live in pft_engine_impl.cuh, instantiated per precision).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <string>
+#include <vector>
+
+#include "../../include/pft.h"
+
+namespace pft {
+
+// Offsets into the device scalar block (doubles).
+enum ScalarSlot {
+  S_QSUM = 0,       // sum_x q_Ns (re, im)
+  S_FIELD = 2,      // sum_x [W-^2/chiN - i w+]   (re, im) of the fields the solve used
+  S_PHIA = 4,       // sum_x phiA (re, im)
+  S_PHIB = 6,       // sum_x phiB (re, im)
+  S_FP2 = 8,        // sum_x |force+|^2
+  S_FM2 = 9,        // sum_x |force-|^2
+  S_Q = 10,         // Q (re, im)
+  S_LNQ = 12,       // lnQ (re, im)
+  S_H = 14,         // H (re, im)
+  S_STRESS = 16,    // sum over steps/modes of the box-derivative contraction (3)
+  S_DLNQ = 20,      // dlnQ/dL_a (3)
+  S_VOL = 24,       // box volume V (written by the host)
+  S_COUNT = 32
+};
+
+struct CtxData {
+  // system
+  int n[3];
+  double L[3];
+  int Ns, NsA;
+  double fA, ds;
+  double chiN, C;
+  pft_kind kind;
+  pft_precision prec;
+  long long M;     // grid points
+  int nzh;         // nz/2+1 (real mode) or nz (complex mode): last spectrum extent
+  long long Ms;    // spectrum elements nx*ny*nzh
+  // runtime
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  bool graph_valid = false;
+  unsigned long long seed = 0, instance = 0;
+  long long step = 0;
+  bool fields_set = false, solved = false;
+  int sms = 152;
+  // device buffers (elements in brackets)
+  void* wp = nullptr;     // [M] f64 or c128
+  void* wm = nullptr;
+  void* BA = nullptr;     // [M] working precision, real or complex
+  void* BB = nullptr;
+  void* hist = nullptr;   // [(Ns+1) * M] q_0..q_Ns
+  void* qd[2] = {nullptr, nullptr};  // conjugate propagator ping-pong
+  void* qd0 = nullptr;    // [M] initial condition of qd
+  void* spec = nullptr;   // [M] complex working precision (>= Ms)
+  void* spec2 = nullptr;  // [M] second spectrum (box derivative)
+  void* accA = nullptr;   // [M] f64 or c128: quadrature sums, then phiA
+  void* accB = nullptr;
+  double* partials = nullptr;  // [npart * 8]
+  double* scal = nullptr;      // [S_COUNT]
+  double* scal_host = nullptr; // pinned mirror
+  void* tables = nullptr;      // twiddles + diffusion factors
+  size_t tw_off[4] = {0, 0, 0, 0};  // x, y, z (full nz), z half (nz/2): byte offsets
+  size_t d_off[3] = {0, 0, 0};      // dx (with 1/M), dy, dz
+  size_t g_off[3] = {0, 0, 0};      // box-derivative weights 2 ds k_a^2 / L_a per axis
+  size_t tables_bytes = 0;
+  int npart = 0;
+  size_t bytes = 0;
+  // profiling: an event recorded before every launch (eager solves only)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;
+  int ev_used = 0;
+};
+
+// Kernel classes reported by pft_profile_step.
+enum KernelKind {
+  KK_Z_FWD = 0, KK_Y_FWD, KK_X_FUSED, KK_Y_INV, KK_Z_INV_FWD, KK_Z_INV_BWD, KK_REDUCE, KK_FIELD_STEP,
+  KK_PREPARE, KK_COUNT
+};
+extern const char* const kKernelKindNames[KK_COUNT];
+
+// Record the event that opens the next launch (no-op unless profiling).
+inline void mark(CtxData& c, int kind) {
+  if (!c.profiling || c.ev_used >= (int)c.ev.size()) return;
+  cudaEventRecord(c.ev[c.ev_used], c.stream);
+  c.ev_kind[c.ev_used] = kind;
+  c.ev_used++;
+}
+
+class Engine {
+ public:
+  virtual ~Engine() {}
+  virtual size_t elem_bytes() const = 0;      // working-precision real element
+  virtual cudaError_t upload_tables(CtxData& c) = 0;
+  virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
+  virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term
+  virtual cudaError_t enqueue_solve(CtxData& c) = 0;    // marches, Q, densities, H
+  virtual cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p,
+                                 const double* eta_m) = 0;
+  virtual cudaError_t fft3d(CtxData& c, void* data, int inverse) = 0;   // complex, in place
+  virtual cudaError_t gradients(CtxData& c, double* dwp, double* dwm) = 0;  // + stress into scal
+  // precision conversion of `count` reals (a complex value counts as two)
+  virtual cudaError_t to_f64(CtxData& c, const void* src, void* dst_f64, long long count) = 0;
+  virtual cudaError_t from_f64(CtxData& c, const void* src_f64, void* dst, long long count) = 0;
+};
+
+Engine* make_engine_f32();
+Engine* make_engine_f64();
+
+cudaError_t launch_philox_normals(unsigned long long seed, unsigned long long instance, unsigned long long step,
+                                  int field, long long M, double* out, cudaStream_t st);
+cudaError_t launch_philox_raw(const unsigned int ctr[4], const unsigned int key[2], long long count,
+                              unsigned int* out, cudaStream_t st);
+
+bool axis_supported(int n);
+void set_error(const std::string& s);
+
+}  // namespace pft

@@ -1,0 +1,397 @@
+// pft_engine_impl.cuh -- one system's solve in working precision T (float: the
+// FP32-mixed path; double: the FP64 path).  Contour steps run through the pass
+// kernels of pft_passes.cuh; everything that accumulates (quadrature, reductions,
+// Hamiltonian, field update, Boltzmann exponentials) runs in double.
+#pragma once
+#include <math.h>
+
+#include <string>
+#include <vector>
+
+#include "pft_engine.h"
+#include "pft_passes.cuh"
+
+namespace pft {
+
+constexpr int PW_THREADS = 256;  // pointwise / reduction block size
+
+// ------------------------------------------------------------------ reductions
+// Block sum of K per-thread values into out[0..K) (ADD: out[j] += sum).
+template <int K, bool ADD = false>
+__device__ __forceinline__ void block_reduce_store(double (&v)[K], double* __restrict__ out) {
+  __shared__ double red[K][PW_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < K; j++) {
+    double s = v[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[j][wid] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int w = 0; w < PW_THREADS / 32; w++) s += red[threadIdx.x][w];
+    if (ADD) {
+      out[threadIdx.x] += s;
+    } else {
+      out[threadIdx.x] = s;
+    }
+  }
+}
+
+// Deterministic second stage: scal[off + j] = sum over blocks of partials[b*K + j].
+template <int K>
+__global__ void __launch_bounds__(PW_THREADS) k_reduce_final(const double* __restrict__ partials, int nblk,
+                                                             double* __restrict__ dst) {
+  double v[K];
+#pragma unroll
+  for (int j = 0; j < K; j++) v[j] = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += PW_THREADS) {
+#pragma unroll
+    for (int j = 0; j < K; j++) v[j] += partials[(long long)b * K + j];
+  }
+  block_reduce_store<K>(v, dst);
+}
+
+// --------------------------------------------------------------- small helpers
+__device__ __forceinline__ double2 cexp_d(double2 z) {
+  double s, c;
+  sincos(z.y, &s, &c);
+  const double e = exp(z.x);
+  return make_double2(e * c, e * s);
+}
+__device__ __forceinline__ double2 cmul_d(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv_d(double2 a, double2 b) {
+  const double den = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+template <typename T> __device__ __forceinline__ void store_w(T* p, long long i, double v) { p[i] = (T)v; }
+template <typename T> __device__ __forceinline__ void store_w(cpx<T>* p, long long i, double2 v) {
+  p[i] = mk<T>((T)v.x, (T)v.y);
+}
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies by
+// fixed odd constants, high halves xored with the other words and the round key;
+// the key advances by the two Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+  const unsigned int M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const unsigned int W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    const unsigned int lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    const unsigned int lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+// Four standard normals from one Philox block (Box-Muller on word pairs).
+__device__ __forceinline__ void philox_normal4(unsigned long long seed, unsigned long long instance,
+                                               unsigned long long step, int field, long long blk, double* z) {
+  const uint4 ctr = make_uint4((unsigned int)blk, (unsigned int)field, (unsigned int)step, (unsigned int)instance);
+  const uint2 key = make_uint2((unsigned int)(seed & 0xffffffffull), (unsigned int)(seed >> 32));
+  const uint4 x = philox4x32_10(ctr, key);
+  const double sc = 1.0 / 4294967296.0;
+  const double u0 = ((double)x.x + 0.5) * sc, u1 = ((double)x.y + 0.5) * sc;
+  const double u2 = ((double)x.z + 0.5) * sc, u3 = ((double)x.w + 0.5) * sc;
+  const double r1 = sqrt(-2.0 * log(u0)), r2 = sqrt(-2.0 * log(u2));
+  double s1, c1, s2, c2;
+  sincospi(2.0 * u1, &s1, &c1);
+  sincospi(2.0 * u3, &s2, &c2);
+  z[0] = r1 * c1;
+  z[1] = r1 * s1;
+  z[2] = r2 * c2;
+  z[3] = r2 * s2;
+}
+
+static __global__ void k_philox_normals(unsigned long long seed, unsigned long long instance, unsigned long long step,
+                                 int field, long long M, double* __restrict__ out) {
+  const long long nblk = (M + 3) / 4;
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < nblk;
+       b += (long long)gridDim.x * blockDim.x) {
+    double z[4];
+    philox_normal4(seed, instance, step, field, b, z);
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      if (4 * b + j < M) out[4 * b + j] = z[j];
+  }
+}
+
+static __global__ void k_philox_raw(uint4 c0, uint2 key, long long count, unsigned int* __restrict__ out) {
+  for (long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x; b < count;
+       b += (long long)gridDim.x * blockDim.x) {
+    uint4 c = c0;
+    c.x = c0.x + (unsigned int)b;
+    const uint4 r = philox4x32_10(c, key);
+    out[4 * b + 0] = r.x;
+    out[4 * b + 1] = r.y;
+    out[4 * b + 2] = r.z;
+    out[4 * b + 3] = r.w;
+  }
+}
+
+// ------------------------------------------------------------ pointwise kernels
+template <typename W> __device__ __forceinline__ W one_val();
+template <> __device__ __forceinline__ float one_val<float>() { return 1.f; }
+template <> __device__ __forceinline__ double one_val<double>() { return 1.0; }
+template <> __device__ __forceinline__ float2 one_val<float2>() { return make_float2(1.f, 0.f); }
+template <> __device__ __forceinline__ double2 one_val<double2>() { return make_double2(1.0, 0.0); }
+
+template <typename W> __global__ void k_fill_one(W* __restrict__ dst, long long M) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = one_val<W>();
+}
+
+// Boltzmann factors (Eq. 13) of real SCFT fields and the Eq. 3 field term.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_prepare_real(const double* __restrict__ wp, const double* __restrict__ wm,
+                                                             T* __restrict__ BA, T* __restrict__ BB, double ds, double chiN,
+                                                             long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double p = wp[i], m = wm[i];
+    BA[i] = (T)exp(-(p - m) * ds * 0.5);
+    BB[i] = (T)exp(-(p + m) * ds * 0.5);
+    acc[0] += m * m / chiN - p;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// Complex Langevin fields: wA = i w+ - w-, wB = i w+ + w-.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_prepare_cplx(const double2* __restrict__ wp, const double2* __restrict__ wm,
+                                                             cpx<T>* __restrict__ BA, cpx<T>* __restrict__ BB, double ds,
+                                                             double chiN, long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double2 p = wp[i], m = wm[i];
+    const double2 ip = make_double2(-p.y, p.x);
+    const double2 wA = make_double2(ip.x - m.x, ip.y - m.y);
+    const double2 wB = make_double2(ip.x + m.x, ip.y + m.y);
+    store_w<T>(BA, i, cexp_d(make_double2(-wA.x * ds * 0.5, -wA.y * ds * 0.5)));
+    store_w<T>(BB, i, cexp_d(make_double2(-wB.x * ds * 0.5, -wB.y * ds * 0.5)));
+    acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
+    acc[1] += 2.0 * m.x * m.y / chiN - p.x;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// Sum of q_Ns for Q (Eq. 4) and the m = 0 term of the quadrature (qd_0 = 1).
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_qsum_real(const T* __restrict__ q, double* __restrict__ accA,
+                                                          double* __restrict__ accB, double cA, double cB, long long M,
+                                                          double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)q[i];
+    acc[0] += v;
+    accA[i] = cA * v;
+    accB[i] = cB * v;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_qsum_cplx(const cpx<T>* __restrict__ q, double2* __restrict__ accA,
+                                                          double2* __restrict__ accB, double cA, double cB, long long M,
+                                                          double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double2 v = make_double2((double)q[i].x, (double)q[i].y);
+    acc[0] += v.x;
+    acc[1] += v.y;
+    accA[i] = make_double2(cA * v.x, cA * v.y);
+    accB[i] = make_double2(cB * v.x, cB * v.y);
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// Q, lnQ (principal branch) and H = C dV field_sum - C V lnQ (Eqs. 3, 4).
+static __global__ void k_observables(double* __restrict__ s, double M, double C) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double qr = s[S_QSUM] / M, qi = s[S_QSUM + 1] / M;
+  s[S_Q] = qr;
+  s[S_Q + 1] = qi;
+  double lr, li;
+  if (qi == 0.0) {
+    lr = log(fabs(qr));
+    li = (qr < 0.0) ? 3.14159265358979323846 : 0.0;
+  } else {
+    lr = 0.5 * log(qr * qr + qi * qi);
+    li = atan2(qi, qr);
+  }
+  s[S_LNQ] = lr;
+  s[S_LNQ + 1] = li;
+  const double V = s[S_VOL];
+  const double dV = V / M;
+  s[S_H] = C * dV * s[S_FIELD] - C * V * lr;
+  s[S_H + 1] = C * dV * s[S_FIELD + 1] - C * V * li;
+}
+
+// phi = ds * acc / Q (Eq. 8) in place, plus sums of phi and of the squared forces (Eq. 7).
+static __global__ void __launch_bounds__(PW_THREADS) k_finalize_real(double* __restrict__ accA, double* __restrict__ accB,
+                                                              const double* __restrict__ wm, const double* __restrict__ s,
+                                                              double ds, double chiN, long long M,
+                                                              double* __restrict__ partials) {
+  const double f = ds / s[S_Q];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double a = accA[i] * f, b = accB[i] * f;
+    accA[i] = a;
+    accB[i] = b;
+    const double fp = a + b - 1.0, fm = 2.0 * wm[i] / chiN + b - a;
+    acc[0] += a;
+    acc[2] += b;
+    acc[4] += fp * fp;
+    acc[5] += fm * fm;
+  }
+  block_reduce_store<6>(acc, partials + 6 * blockIdx.x);
+}
+
+static __global__ void __launch_bounds__(PW_THREADS) k_finalize_cplx(double2* __restrict__ accA, double2* __restrict__ accB,
+                                                              const double2* __restrict__ wm, const double* __restrict__ s,
+                                                              double ds, double chiN, long long M,
+                                                              double* __restrict__ partials) {
+  const double2 f = cdiv_d(make_double2(ds, 0.0), make_double2(s[S_Q], s[S_Q + 1]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = cmul_d(accA[i], f), b = cmul_d(accB[i], f);
+    accA[i] = a;
+    accB[i] = b;
+    const double2 fp = make_double2(a.x + b.x - 1.0, a.y + b.y);  // |i fp| = |fp|
+    const double2 m = wm[i];
+    const double2 fm = make_double2(2.0 * m.x / chiN + b.x - a.x, 2.0 * m.y / chiN + b.y - a.y);
+    acc[0] += a.x;
+    acc[1] += a.y;
+    acc[2] += b.x;
+    acc[3] += b.y;
+    acc[4] += fp.x * fp.x + fp.y * fp.y;
+    acc[5] += fm.x * fm.x + fm.y * fm.y;
+  }
+  block_reduce_store<6>(acc, partials + 6 * blockIdx.x);
+}
+
+// Explicit Euler SCFT relaxation (Eq. 9, no noise, Wick-rotated), then the new
+// Boltzmann factors and field term.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_step_scft(double* __restrict__ wp, double* __restrict__ wm,
+                                                          const double* __restrict__ phiA, const double* __restrict__ phiB,
+                                                          T* __restrict__ BA, T* __restrict__ BB, double lam, double ds,
+                                                          double chiN, long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double a = phiA[i], b = phiB[i];
+    double p = wp[i], m = wm[i];
+    const double fp = a + b - 1.0, fm = 2.0 * m / chiN + b - a;
+    p += lam * fp;
+    m -= lam * fm;
+    wp[i] = p;
+    wm[i] = m;
+    BA[i] = (T)exp(-(p - m) * ds * 0.5);
+    BB[i] = (T)exp(-(p + m) * ds * 0.5);
+    acc[0] += m * m / chiN - p;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// Euler-Maruyama complex Langevin step (Eq. 9 with the Eq. 7 forces per C and real
+// noise of variance 2 dt/(C dV)), four grid points per thread so that one Philox
+// block serves four consecutive points of each field.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp, double2* __restrict__ wm,
+                                                        const double2* __restrict__ phiA, const double2* __restrict__ phiB,
+                                                        cpx<T>* __restrict__ BA, cpx<T>* __restrict__ BB, double dt,
+                                                        double noise_std, const double* __restrict__ eta_p,
+                                                        const double* __restrict__ eta_m, unsigned long long seed,
+                                                        unsigned long long instance, unsigned long long step, double ds,
+                                                        double chiN, long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  const long long nblk = (M + 3) / 4;
+  for (long long bk = blockIdx.x * (long long)blockDim.x + threadIdx.x; bk < nblk;
+       bk += (long long)gridDim.x * blockDim.x) {
+    double zp[4], zm[4];
+    if (eta_p) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const long long i = 4 * bk + j;
+        zp[j] = (i < M) ? eta_p[i] : 0.0;
+        zm[j] = (i < M) ? eta_m[i] : 0.0;
+      }
+    } else {
+      philox_normal4(seed, instance, step, 0, bk, zp);
+      philox_normal4(seed, instance, step, 1, bk, zm);
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        zp[j] *= noise_std;
+        zm[j] *= noise_std;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const long long i = 4 * bk + j;
+      if (i >= M) break;
+      const double2 a = phiA[i], b = phiB[i];
+      double2 p = wp[i], m = wm[i];
+      // dH/dw+ per C = i (phiA + phiB - 1)
+      const double2 s = make_double2(a.x + b.x - 1.0, a.y + b.y);
+      const double2 fp = make_double2(-s.y, s.x);
+      const double2 fm = make_double2(2.0 * m.x / chiN + b.x - a.x, 2.0 * m.y / chiN + b.y - a.y);
+      p.x += -dt * fp.x + zp[j];
+      p.y += -dt * fp.y;
+      m.x += -dt * fm.x + zm[j];
+      m.y += -dt * fm.y;
+      wp[i] = p;
+      wm[i] = m;
+      const double2 ip = make_double2(-p.y, p.x);
+      const double2 wA = make_double2(ip.x - m.x, ip.y - m.y);
+      const double2 wB = make_double2(ip.x + m.x, ip.y + m.y);
+      store_w<T>(BA, i, cexp_d(make_double2(-wA.x * ds * 0.5, -wA.y * ds * 0.5)));
+      store_w<T>(BB, i, cexp_d(make_double2(-wB.x * ds * 0.5, -wB.y * ds * 0.5)));
+      acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
+      acc[1] += 2.0 * m.x * m.y / chiN - p.x;
+    }
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// Precision conversion of one slice (real or complex as 2 reals).
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = (B)src[i];
+}
+
+// Box derivative (stress) contraction for real fields: for one contour step,
+// sum over the half spectrum of w(kz) Re[conj(u^) v^] k_a^2 exp(-k^2 ds), a = x, y, z,
+// accumulated into per-block partials (same block -> same slots every step).
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_stress_real(const cpx<T>* __restrict__ u, const cpx<T>* __restrict__ v,
+                                                            const double* __restrict__ k2x, const double* __restrict__ k2y,
+                                                            const double* __restrict__ k2z, int nx, int ny, int nzh, int nz,
+                                                            double ds, double* __restrict__ partials) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  const long long Ms = (long long)nx * ny * nzh;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Ms; i += (long long)gridDim.x * blockDim.x) {
+    const int kz = (int)(i % nzh);
+    const long long r = i / nzh;
+    const int ky = (int)(r % ny), kx = (int)(r / ny);
+    const double wz = (kz == 0 || 2 * kz == nz) ? 1.0 : 2.0;
+    const cpx<T> a = u[i], b = v[i];
+    const double re = (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+    const double gx = k2x[kx], gy = k2y[ky], gz = k2z[kz];
+    const double w = wz * re * exp(-(gx + gy + gz) * ds);
+    acc[0] += w * gx;
+    acc[1] += w * gy;
+    acc[2] += w * gz;
+  }
+  block_reduce_store<3, true>(acc, partials + 3 * blockIdx.x);
+}
+
+}  // namespace pft

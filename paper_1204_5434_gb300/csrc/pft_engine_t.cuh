@@ -1,0 +1,375 @@
+// pft_engine_t.cuh -- EngineT<T>: launch sequences of one system in working
+// precision T.  Included once per precision (pft_engine_f32.cu, pft_engine_f64.cu).
+#pragma once
+#include <math.h>
+
+#include <vector>
+
+#include "pft_engine_impl.cuh"
+
+namespace pft {
+
+#define PFT_CASE(NV, ...) \
+  case NV: {              \
+    constexpr int N = NV; \
+    __VA_ARGS__;          \
+  } break;
+// FFT lengths of a grid axis
+#define PFT_DISPATCH_AXIS(n, ...)                                                                                  \
+  switch (n) {                                                                                                     \
+    PFT_CASE(4, __VA_ARGS__) PFT_CASE(6, __VA_ARGS__) PFT_CASE(8, __VA_ARGS__) PFT_CASE(12, __VA_ARGS__)           \
+    PFT_CASE(16, __VA_ARGS__) PFT_CASE(24, __VA_ARGS__) PFT_CASE(32, __VA_ARGS__) PFT_CASE(48, __VA_ARGS__)        \
+    PFT_CASE(64, __VA_ARGS__) PFT_CASE(96, __VA_ARGS__) PFT_CASE(128, __VA_ARGS__) PFT_CASE(192, __VA_ARGS__)      \
+    PFT_CASE(256, __VA_ARGS__)                                                                                     \
+    default: return cudaErrorInvalidValue;                                                                         \
+  }
+// half lengths nz/2 of the real-to-complex z transform
+#define PFT_DISPATCH_HALF(n, ...)                                                                                  \
+  switch (n) {                                                                                                     \
+    PFT_CASE(2, __VA_ARGS__) PFT_CASE(3, __VA_ARGS__) PFT_CASE(4, __VA_ARGS__) PFT_CASE(6, __VA_ARGS__)            \
+    PFT_CASE(8, __VA_ARGS__) PFT_CASE(12, __VA_ARGS__) PFT_CASE(16, __VA_ARGS__) PFT_CASE(24, __VA_ARGS__)         \
+    PFT_CASE(32, __VA_ARGS__) PFT_CASE(48, __VA_ARGS__) PFT_CASE(64, __VA_ARGS__) PFT_CASE(96, __VA_ARGS__)        \
+    PFT_CASE(128, __VA_ARGS__)                                                                                     \
+    default: return cudaErrorInvalidValue;                                                                         \
+  }
+
+// Quadrature weights of the contour integrals (Eq. 8): trapezoid rule on each block.
+inline void trapezoid_weight(int n, int Ns, int NsA, double* cA, double* cB) {
+  *cA = 0.0;
+  *cB = 0.0;
+  if (NsA > 0 && n <= NsA) *cA = (n == 0 || n == NsA) ? 0.5 : 1.0;
+  if (NsA < Ns && n >= NsA) *cB = (n == NsA || n == Ns) ? 0.5 : 1.0;
+}
+
+template <typename T>
+class EngineT : public Engine {
+ public:
+  using Z = cpx<T>;
+
+  size_t elem_bytes() const override { return sizeof(T); }
+
+  // ------------------------------------------------------------------ tables
+  cudaError_t upload_tables(CtxData& c) override {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const int nzc = (c.kind == PFT_SCFT_REAL) ? nz / 2 + 1 : nz;
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t off = 0;
+    const int twn[4] = {nx, ny, nz, nz / 2};
+    for (int a = 0; a < 4; a++) {
+      c.tw_off[a] = off;
+      off = al(off + sizeof(Z) * (size_t)twn[a]);
+    }
+    const int dn[3] = {nx, ny, nzc};
+    for (int a = 0; a < 3; a++) {
+      c.d_off[a] = off;
+      off = al(off + sizeof(T) * (size_t)dn[a]);
+    }
+    for (int a = 0; a < 3; a++) {
+      c.g_off[a] = off;
+      off = al(off + sizeof(double) * (size_t)dn[a]);
+    }
+    if (!c.tables) {
+      cudaError_t e = cudaMalloc(&c.tables, off);
+      if (e != cudaSuccess) return e;
+      c.tables_bytes = off;
+      c.bytes += off;
+    }
+    std::vector<unsigned char> h(off, 0);
+    for (int a = 0; a < 4; a++) {
+      Z* tw = reinterpret_cast<Z*>(h.data() + c.tw_off[a]);
+      for (int m = 0; m < twn[a]; m++) {
+        const double ang = -2.0 * M_PI * (double)m / (double)twn[a];
+        tw[m] = mk<T>((T)cos(ang), (T)sin(ang));
+      }
+    }
+    const double Md = (double)c.M;
+    for (int a = 0; a < 3; a++) {
+      const int na = c.n[a];
+      T* d = reinterpret_cast<T*>(h.data() + c.d_off[a]);
+      double* g = reinterpret_cast<double*>(h.data() + c.g_off[a]);
+      for (int m = 0; m < dn[a]; m++) {
+        const int mm = (m <= na / 2) ? m : m - na;
+        const double k = 2.0 * M_PI * (double)mm / c.L[a];
+        double dval = exp(-k * k * c.ds);
+        if (a == 0) dval /= Md;  // inverse-transform normalisation 1/M folded into D
+        d[m] = (T)dval;
+        g[m] = k * k;
+      }
+    }
+    return cudaMemcpyAsync(c.tables, h.data(), off, cudaMemcpyHostToDevice, c.stream);
+  }
+
+  cudaError_t fill_ones(CtxData& c, void* dst) override {
+    const int blocks = c.npart;
+    if (c.kind == PFT_SCFT_REAL) {
+      k_fill_one<T><<<blocks, PW_THREADS, 0, c.stream>>>(reinterpret_cast<T*>(dst), c.M);
+    } else {
+      k_fill_one<Z><<<blocks, PW_THREADS, 0, c.stream>>>(reinterpret_cast<Z*>(dst), c.M);
+    }
+    return cudaGetLastError();
+  }
+
+  // ---------------------------------------------------------------- a1: fields
+  cudaError_t prepare_fields(CtxData& c) override {
+    mark(c, KK_PREPARE);
+    if (c.kind == PFT_SCFT_REAL) {
+      k_prepare_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>(
+          (const double*)c.wp, (const double*)c.wm, (T*)c.BA, (T*)c.BB, c.ds, c.chiN, c.M, c.partials);
+    } else {
+      k_prepare_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>(
+          (const double2*)c.wp, (const double2*)c.wm, (Z*)c.BA, (Z*)c.BB, c.ds, c.chiN, c.M, c.partials);
+    }
+    k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
+    return cudaGetLastError();
+  }
+
+  // ------------------------------------------------------- one contour step
+  // out = B * F^-1[ D F[ B * in ] ]; epi 1 also accumulates the density sums.
+  cudaError_t contour_step(CtxData& c, const void* in, const void* B, void* out, int epi, const void* partner,
+                           double cA, double cB) {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const Z* twx = tab<Z>(c, c.tw_off[0]);
+    const Z* twy = tab<Z>(c, c.tw_off[1]);
+    const Z* twz = tab<Z>(c, c.tw_off[2]);
+    const Z* twh = tab<Z>(c, c.tw_off[3]);
+    const T* dx = tab<T>(c, c.d_off[0]);
+    const T* dy = tab<T>(c, c.d_off[1]);
+    const T* dz = tab<T>(c, c.d_off[2]);
+    Z* spec = (Z*)c.spec;
+    const long long npen = (long long)nx * ny;
+    const long long nzc = c.nzh;
+    cudaError_t e;
+    mark(c, KK_Z_FWD);
+    if (c.kind == PFT_SCFT_REAL) {
+      PFT_DISPATCH_HALF(nz / 2, e = launch_zf_r2c<N>(c, (const T*)in, (const T*)B, spec, npen, twh, twz));
+    } else {
+      PFT_DISPATCH_AXIS(nz, e = launch_zf_c2c<N>(c, (const Z*)in, (const Z*)B, spec, npen, twz));
+    }
+    if (e != cudaSuccess) return e;
+    mark(c, KK_Y_FWD);
+    PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 0>(c, spec, nx * nzc, nzc, ny * nzc, nzc, twy, dx, dy, dz, (int)nzc));
+    if (e != cudaSuccess) return e;
+    mark(c, KK_X_FUSED);
+    PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 2>(c, spec, ny * nzc, ny * nzc, 0, ny * nzc, twx, dx, dy, dz, (int)nzc));
+    if (e != cudaSuccess) return e;
+    mark(c, KK_Y_INV);
+    PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 1>(c, spec, nx * nzc, nzc, ny * nzc, nzc, twy, dx, dy, dz, (int)nzc));
+    if (e != cudaSuccess) return e;
+    mark(c, epi == 0 ? KK_Z_INV_FWD : KK_Z_INV_BWD);
+    if (c.kind == PFT_SCFT_REAL) {
+      if (epi == 0) {
+        PFT_DISPATCH_HALF(nz / 2, e = launch_zi_c2r<N, 0>(c, spec, (const T*)B, (T*)out, nullptr, nullptr, nullptr,
+                                                          0.0, 0.0, npen, twh, twz));
+      } else {
+        PFT_DISPATCH_HALF(nz / 2, e = launch_zi_c2r<N, 1>(c, spec, (const T*)B, (T*)out, (const T*)partner,
+                                                          (double*)c.accA, (double*)c.accB, cA, cB, npen, twh, twz));
+      }
+    } else {
+      if (epi == 0) {
+        PFT_DISPATCH_AXIS(nz, e = launch_zi_c2c<N, 0>(c, spec, (const Z*)B, (Z*)out, nullptr, nullptr, nullptr, 0.0,
+                                                      0.0, npen, twz));
+      } else {
+        PFT_DISPATCH_AXIS(nz, e = launch_zi_c2c<N, 1>(c, spec, (const Z*)B, (Z*)out, (const Z*)partner,
+                                                      (double2*)c.accA, (double2*)c.accB, cA, cB, npen, twz));
+      }
+    }
+    return e;
+  }
+
+  // ------------------------------------------------------------- a2 .. a6
+  cudaError_t record_solve(CtxData& c) {
+    const size_t slice = (size_t)c.M * (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
+    char* hist = (char*)c.hist;
+    cudaError_t e;
+    // forward march (Eqs. 5, 13)
+    for (int n = 1; n <= c.Ns; n++) {
+      const void* B = (n <= c.NsA) ? c.BA : c.BB;
+      e = contour_step(c, hist + (size_t)(n - 1) * slice, B, hist + (size_t)n * slice, 0, nullptr, 0.0, 0.0);
+      if (e != cudaSuccess) return e;
+    }
+    // Q (Eq. 4) and the qd_0 = 1 term of the quadrature
+    double cA, cB;
+    trapezoid_weight(c.Ns, c.Ns, c.NsA, &cA, &cB);
+    mark(c, KK_REDUCE);
+    if (c.kind == PFT_SCFT_REAL) {
+      k_qsum_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const T*)(hist + (size_t)c.Ns * slice), (double*)c.accA,
+                                                          (double*)c.accB, cA, cB, c.M, c.partials);
+    } else {
+      k_qsum_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)(hist + (size_t)c.Ns * slice), (double2*)c.accA,
+                                                          (double2*)c.accB, cA, cB, c.M, c.partials);
+    }
+    k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_QSUM);
+    k_observables<<<1, 32, 0, c.stream>>>(c.scal, (double)c.M, c.C);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // conjugate march with fused quadrature (Eq. 8)
+    for (int m = 1; m <= c.Ns; m++) {
+      const int nb = c.Ns + 1 - m;  // split step index of this qd step
+      const void* B = (nb <= c.NsA) ? c.BA : c.BB;
+      const void* in = (m == 1) ? c.qd0 : c.qd[(m - 1) & 1];
+      void* out = c.qd[m & 1];
+      const int pn = c.Ns - m;  // forward slice paired with qd_m
+      trapezoid_weight(pn, c.Ns, c.NsA, &cA, &cB);
+      e = contour_step(c, in, B, out, 1, hist + (size_t)pn * slice, cA, cB);
+      if (e != cudaSuccess) return e;
+    }
+    // densities and force norms
+    mark(c, KK_REDUCE);
+    if (c.kind == PFT_SCFT_REAL) {
+      k_finalize_real<<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.accA, (double*)c.accB, (const double*)c.wm,
+                                                            c.scal, c.ds, c.chiN, c.M, c.partials);
+    } else {
+      k_finalize_cplx<<<c.npart, PW_THREADS, 0, c.stream>>>((double2*)c.accA, (double2*)c.accB, (const double2*)c.wm,
+                                                            c.scal, c.ds, c.chiN, c.M, c.partials);
+    }
+    k_reduce_final<6><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_PHIA);
+    return cudaGetLastError();
+  }
+
+  cudaError_t enqueue_solve(CtxData& c) override {
+    if (!c.use_graph || c.profiling) return record_solve(c);
+    if (!c.graph_valid) {
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return e;
+      e = record_solve(c);
+      cudaError_t e2 = cudaStreamEndCapture(c.stream, &g);
+      if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return e;
+      }
+      if (e2 != cudaSuccess) return e2;
+      e = cudaGraphInstantiate(&c.graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return e;
+      c.graph_valid = true;
+    }
+    return cudaGraphLaunch(c.graph, c.stream);
+  }
+
+  // -------------------------------------------------------------- a7: step
+  cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p, const double* eta_m) override {
+    mark(c, KK_FIELD_STEP);
+    if (step_kind == PFT_STEP_SCFT_EULER) {
+      k_step_scft<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (double*)c.wm, (const double*)c.accA,
+                                                           (const double*)c.accB, (T*)c.BA, (T*)c.BB, lam, c.ds, c.chiN,
+                                                           c.M, c.partials);
+    } else {
+      const double dV = c.L[0] * c.L[1] * c.L[2] / (double)c.M;
+      const double std = sqrt(2.0 * lam / (c.C * dV));
+      k_step_cl<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double2*)c.wp, (double2*)c.wm, (const double2*)c.accA,
+                                                         (const double2*)c.accB, (Z*)c.BA, (Z*)c.BB, lam, std, eta_p,
+                                                         eta_m, c.seed, c.instance, (unsigned long long)c.step, c.ds,
+                                                         c.chiN, c.M, c.partials);
+    }
+    k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
+    return cudaGetLastError();
+  }
+
+  // ---------------------------------------------------------- test hook: FFT
+  cudaError_t fft3d(CtxData& c, void* data, int inverse) override {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const Z* twx = tab<Z>(c, c.tw_off[0]);
+    const Z* twy = tab<Z>(c, c.tw_off[1]);
+    const Z* twz = tab<Z>(c, c.tw_off[2]);
+    Z* d = (Z*)data;
+    const long long npen = (long long)nx * ny;
+    cudaError_t e;
+    if (!inverse) {
+      PFT_DISPATCH_AXIS(nz, e = launch_zf_c2c<N>(c, d, nullptr, d, npen, twz));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 0>(c, d, (long long)nx * nz, nz, (long long)ny * nz, nz, twy, nullptr,
+                                                     nullptr, nullptr, nz));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 0>(c, d, (long long)ny * nz, (long long)ny * nz, 0, (long long)ny * nz,
+                                                     twx, nullptr, nullptr, nullptr, nz));
+    } else {
+      PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 1>(c, d, (long long)ny * nz, (long long)ny * nz, 0, (long long)ny * nz,
+                                                     twx, nullptr, nullptr, nullptr, nz));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 1>(c, d, (long long)nx * nz, nz, (long long)ny * nz, nz, twy, nullptr,
+                                                     nullptr, nullptr, nz));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(nz, e = launch_zi_c2c<N, 2>(c, d, nullptr, d, nullptr, nullptr, nullptr, 0.0, 0.0, npen, twz));
+    }
+    return e;
+  }
+
+  cudaError_t gradients(CtxData& c, double* dwp, double* dwm) override {
+    (void)c;
+    (void)dwp;
+    (void)dwm;
+    return cudaErrorNotSupported;
+  }
+
+  cudaError_t to_f64(CtxData& c, const void* src, void* dst, long long cnt) override {
+    k_convert<T, double><<<c.npart, PW_THREADS, 0, c.stream>>>((const T*)src, (double*)dst, cnt);
+    return cudaGetLastError();
+  }
+  cudaError_t from_f64(CtxData& c, const void* src, void* dst, long long cnt) override {
+    k_convert<double, T><<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)src, (T*)dst, cnt);
+    return cudaGetLastError();
+  }
+
+ private:
+  template <typename P> static const P* tab(const CtxData& c, size_t off) {
+    return reinterpret_cast<const P*>(reinterpret_cast<const char*>(c.tables) + off);
+  }
+
+  template <int N, int MODE>
+  cudaError_t launch_strided(CtxData& c, Z* data, long long ncols, long long cin, long long s_outer, long long s_k,
+                             const Z* tw, const T* dk, const T* dy, const T* dz, int nzc) {
+    constexpr int C = Tile<T>::C;
+    const int threads = C * Plan<N>::TPC;
+    const size_t smem = (size_t)N * C * sizeof(Z);
+    const long long blocks = (ncols + C - 1) / C;
+    k_strided<T, N, MODE><<<(unsigned)blocks, threads, smem, c.stream>>>(data, ncols, cin, s_outer, s_k, tw, dk, dy, dz,
+                                                                         nzc);
+    return cudaGetLastError();
+  }
+
+  template <int N2>
+  cudaError_t launch_zf_r2c(CtxData& c, const T* q, const T* B, Z* spec, long long npen, const Z* twh, const Z* twf) {
+    constexpr int P = PencilsPerCta<T, N2>::v;
+    const int threads = P * Plan<N2>::TPC;
+    const size_t smem = (size_t)P * pencil_ld<T>(N2) * sizeof(Z);
+    const long long blocks = (npen + P - 1) / P;
+    k_zf_r2c<T, N2><<<(unsigned)blocks, threads, smem, c.stream>>>(q, B, spec, npen, twh, twf);
+    return cudaGetLastError();
+  }
+
+  template <int N2, int EPI>
+  cudaError_t launch_zi_c2r(CtxData& c, const Z* spec, const T* B, T* out, const T* partner, double* accA, double* accB,
+                            double cA, double cB, long long npen, const Z* twh, const Z* twf) {
+    constexpr int P = PencilsPerCta<T, N2>::v;
+    const int threads = P * Plan<N2>::TPC;
+    const size_t smem = (size_t)P * pencil_ld<T>(N2) * sizeof(Z);
+    const long long blocks = (npen + P - 1) / P;
+    k_zi_c2r<T, N2, EPI><<<(unsigned)blocks, threads, smem, c.stream>>>(spec, B, out, partner, accA, accB, cA, cB, npen,
+                                                                         twh, twf);
+    return cudaGetLastError();
+  }
+
+  template <int N>
+  cudaError_t launch_zf_c2c(CtxData& c, const Z* q, const Z* B, Z* spec, long long npen, const Z* tw) {
+    constexpr int P = PencilsPerCta<T, N>::v;
+    const int threads = P * Plan<N>::TPC;
+    const size_t smem = (size_t)P * pencil_ld<T>(N) * sizeof(Z);
+    const long long blocks = (npen + P - 1) / P;
+    k_zf_c2c<T, N><<<(unsigned)blocks, threads, smem, c.stream>>>(q, B, spec, npen, tw);
+    return cudaGetLastError();
+  }
+
+  template <int N, int EPI>
+  cudaError_t launch_zi_c2c(CtxData& c, const Z* spec, const Z* B, Z* out, const Z* partner, double2* accA,
+                            double2* accB, double cA, double cB, long long npen, const Z* tw) {
+    constexpr int P = PencilsPerCta<T, N>::v;
+    const int threads = P * Plan<N>::TPC;
+    const size_t smem = (size_t)P * pencil_ld<T>(N) * sizeof(Z);
+    const long long blocks = (npen + P - 1) / P;
+    k_zi_c2c<T, N, EPI><<<(unsigned)blocks, threads, smem, c.stream>>>(spec, B, out, partner, accA, accB, cA, cB, npen,
+                                                                        tw);
+    return cudaGetLastError();
+  }
+};
+
+}  // namespace pft

@@ -1,0 +1,307 @@
+// pft_passes.cuh -- the FFT pass kernels of one contour step
+//   q_n = B_n * F^-1[ D * F[ B_n * q_{n-1} ] ]        (operator splitting, Eq. 13)
+// on an [nx][ny][nz] grid (z contiguous).  One step is five passes over the
+// spectrum buffer, each a batch of 1D transforms held in registers:
+//   zf : z transform of B*q   (real->half spectrum in SCFT mode, complex in CL mode)
+//   yf : y transform
+//   x  : x transform, multiply by D(k)/M, inverse x transform   (fused)
+//   yi : inverse y transform
+//   zi : inverse z transform, multiply by B, store q_n; in the conjugate march
+//        also accumulate c_n q_n qd_{Ns-n} into the FP64 density sums (Eq. 8)
+#pragma once
+#include "pft_fft.cuh"
+
+namespace pft {
+
+// Shared-memory exchange for column-interleaved tiles [pos][LD] (strided passes:
+// consecutive threads own consecutive columns, so every access is conflict-free).
+template <typename T> struct XchCols {
+  cpx<T>* s;
+  int ld;
+  int c;
+  __device__ __forceinline__ void put(int pos, cpx<T> z) { s[pos * ld + c] = z; }
+  __device__ __forceinline__ cpx<T> get(int pos) const { return s[pos * ld + c]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+// Shared-memory exchange for pencil tiles [p][padded pos] (z passes: consecutive
+// threads own consecutive elements of one pencil).  One pad slot every 128 bytes
+// breaks the power-of-two strides of the Stockham scatter.
+template <typename T> struct XchPencil {
+  static constexpr int SH = (sizeof(cpx<T>) == 8) ? 4 : 3;
+  cpx<T>* s;  // start of this thread's pencil
+  __device__ __forceinline__ static int idx(int pos) { return pos + (pos >> SH); }
+  __device__ __forceinline__ void put(int pos, cpx<T> z) { s[idx(pos)] = z; }
+  __device__ __forceinline__ cpx<T> get(int pos) const { return s[idx(pos)]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+template <typename T> __host__ __device__ constexpr int pencil_ld(int n) {
+  return n + (n >> ((sizeof(cpx<T>) == 8) ? 4 : 3)) + 2;
+}
+
+// Columns per CTA of the strided passes and pencils per CTA of the z passes.
+template <typename T> struct Tile { static constexpr int C = (sizeof(T) == 4) ? 16 : 8; };
+// Pencils per CTA: about 256 threads, with the pencil tile inside the 48 KB of
+// dynamic shared memory a launch gets without an opt-in attribute.
+template <typename T, int N> struct PencilsPerCta {
+  static constexpr int by_threads = (Plan<N>::TPC >= 256) ? 1 : 256 / Plan<N>::TPC;
+  static constexpr int by_smem = (48 * 1024) / (pencil_ld<T>(N) * (int)sizeof(cpx<T>));
+  static constexpr int v = by_threads < by_smem ? by_threads : (by_smem > 0 ? by_smem : 1);
+};
+
+// ---------------------------------------------------------------- strided pass
+// MODE 0: forward transform; 1: inverse transform; 2: forward, multiply by
+// dk[k]*dy[ky]*dz[kz], inverse (the x pass of a contour step).
+// Column col in [0, ncols): element k at data[(col / cin) * s_outer + col % cin + k * s_k].
+template <typename T, int N, int MODE>
+__global__ void __launch_bounds__(Tile<T>::C * Plan<N>::TPC)
+k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s_outer, long long s_k,
+          const cpx<T>* __restrict__ tw, const T* __restrict__ dk, const T* __restrict__ dy,
+          const T* __restrict__ dz, int nzc) {
+  constexpr int C = Tile<T>::C;
+  constexpr int E = Plan<N>::E;
+  constexpr int TPC = Plan<N>::TPC;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
+  const int c = threadIdx.x % C;
+  const int t = threadIdx.x / C;
+  const long long col = (long long)blockIdx.x * C + c;
+  const bool valid = col < ncols;
+  const long long colc = valid ? col : 0;
+  const long long base = (colc / cin) * s_outer + (colc % cin);
+  cpx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    v[i] = valid ? data[base + (long long)(t + TPC * i) * s_k] : mk<T>(T(0), T(0));
+  }
+  XchCols<T> x{sm, C, c};
+  if (MODE == 1) {
+    fft<T, true, N>(v, t, tw, x);
+  } else {
+    fft<T, false, N>(v, t, tw, x);
+  }
+  if (MODE == 2) {
+    const long long ky = colc / nzc, kz = colc % nzc;
+    const T dyz = dy[ky] * dz[kz];
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], dk[t + TPC * i] * dyz);
+    // the forward transform ended with a barrier after its last shared-memory reads
+    fft<T, true, N>(v, t, tw, x);
+  }
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < E; i++) data[base + (long long)(t + TPC * i) * s_k] = v[i];
+  }
+}
+
+// ----------------------------------------------------------- z passes, real
+// Forward: pencil of nz = 2*N2 reals (times B) packed as N2 complex pairs, complex
+// transform of length N2, then the even/odd split into the nz/2+1 half spectrum.
+// twh: exp(-2 pi i m/N2); twf: exp(-2 pi i m/nz).
+template <typename T, int N2>
+__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
+k_zf_r2c(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
+         const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf) {
+  constexpr int P = PencilsPerCta<T, N2>::v;
+  constexpr int E = Plan<N2>::E;
+  constexpr int TPC = Plan<N2>::TPC;
+  constexpr int LD = pencil_ld<T>(N2);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long pen = (long long)blockIdx.x * P + p;
+  const bool valid = pen < npen;
+  const long long pc = valid ? pen : 0;
+  XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
+  const cpx<T>* q2 = reinterpret_cast<const cpx<T>*>(q) + pc * N2;
+  const cpx<T>* b2 = B ? reinterpret_cast<const cpx<T>*>(B) + pc * N2 : nullptr;
+  cpx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    cpx<T> z = valid ? q2[t + TPC * i] : mk<T>(T(0), T(0));
+    if (b2 && valid) {
+      const cpx<T> b = b2[t + TPC * i];
+      z.x *= b.x;
+      z.y *= b.y;
+    }
+    v[i] = z;
+  }
+  fft<T, false, N2>(v, t, twh, x);  // ends with a barrier after its last reads
+#pragma unroll
+  for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
+  __syncthreads();
+  const T h = T(0.5);
+  cpx<T>* out = spec + pc * (N2 + 1);
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const int k = t + TPC * i;
+    const cpx<T> zk = v[i];
+    const cpx<T> zc = cconj(x.get(k == 0 ? 0 : N2 - k));
+    const cpx<T> ev = cscale(cadd(zk, zc), h);
+    const cpx<T> od = cscale(rot90<false>(csub(zk, zc)), h);  // -i/2 (Zk - conj Z_{N2-k})
+    const cpx<T> X = cadd(ev, cmul(twf[k], od));
+    if (valid) out[k] = X;
+  }
+  if (valid && t == 0) {
+    const cpx<T> z0 = v[0];
+    out[N2] = mk<T>(z0.x - z0.y, T(0));
+  }
+}
+
+// Inverse: half spectrum -> N2 complex (even/odd merge, unnormalised) -> inverse
+// transform -> nz reals.  EPI 0: out = B*y; EPI 1: out = B*y and
+// accA += cA*out*partner, accB += cB*out*partner (FP64); EPI 2: out = y.
+template <typename T, int N2, int EPI>
+__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
+k_zi_c2r(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict__ qout,
+         const T* __restrict__ partner, double* __restrict__ accA, double* __restrict__ accB, double cA,
+         double cB, long long npen, const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf) {
+  constexpr int P = PencilsPerCta<T, N2>::v;
+  constexpr int E = Plan<N2>::E;
+  constexpr int TPC = Plan<N2>::TPC;
+  constexpr int LD = pencil_ld<T>(N2);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long pen = (long long)blockIdx.x * P + p;
+  const bool valid = pen < npen;
+  const long long pc = valid ? pen : 0;
+  XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
+  const cpx<T>* in = spec + pc * (N2 + 1);
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const int k = t + TPC * i;
+    x.put(k, valid ? in[k] : mk<T>(T(0), T(0)));
+  }
+  if (t == 0) x.put(N2, valid ? in[N2] : mk<T>(T(0), T(0)));
+  __syncthreads();
+  cpx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const int k = t + TPC * i;
+    const cpx<T> xk = x.get(k);
+    const cpx<T> xc = cconj(x.get(N2 - k));
+    // Z_k = (X_k + conj X_{N2-k}) + i e^{+2 pi i k/nz} (X_k - conj X_{N2-k})
+    const cpx<T> d = rot90<true>(cmulc(csub(xk, xc), twf[k]));
+    v[i] = cadd(cadd(xk, xc), d);
+  }
+  __syncthreads();
+  fft<T, true, N2>(v, t, twh, x);
+  if (!valid) return;
+  const long long o = pc * N2;
+  const cpx<T>* b2 = reinterpret_cast<const cpx<T>*>(B);
+  cpx<T>* q2 = reinterpret_cast<cpx<T>*>(qout);
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const long long m = o + t + TPC * i;
+    cpx<T> y = v[i];
+    if (EPI != 2) {
+      const cpx<T> b = b2[m];
+      y.x *= b.x;
+      y.y *= b.y;
+    }
+    q2[m] = y;
+    if (EPI == 1) {
+      const cpx<T> pp = reinterpret_cast<const cpx<T>*>(partner)[m];
+      const double p0 = (double)y.x * (double)pp.x;
+      const double p1 = (double)y.y * (double)pp.y;
+      if (cA != 0.0) {
+        double2* a = reinterpret_cast<double2*>(accA) + m;
+        double2 av = *a;
+        av.x += cA * p0;
+        av.y += cA * p1;
+        *a = av;
+      }
+      if (cB != 0.0) {
+        double2* a = reinterpret_cast<double2*>(accB) + m;
+        double2 av = *a;
+        av.x += cB * p0;
+        av.y += cB * p1;
+        *a = av;
+      }
+    }
+  }
+}
+
+// -------------------------------------------------------- z passes, complex
+// Forward: pencil of nz complex values times complex B, transform of length nz.
+template <typename T, int N>
+__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
+k_zf_c2c(const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
+         const cpx<T>* __restrict__ tw) {
+  constexpr int P = PencilsPerCta<T, N>::v;
+  constexpr int E = Plan<N>::E;
+  constexpr int TPC = Plan<N>::TPC;
+  constexpr int LD = pencil_ld<T>(N);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long pen = (long long)blockIdx.x * P + p;
+  const bool valid = pen < npen;
+  const long long o = (valid ? pen : 0) * N;
+  XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
+  cpx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    cpx<T> z = valid ? q[o + t + TPC * i] : mk<T>(T(0), T(0));
+    if (B && valid) z = cmul(z, B[o + t + TPC * i]);
+    v[i] = z;
+  }
+  fft<T, false, N>(v, t, tw, x);
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < E; i++) spec[o + t + TPC * i] = v[i];
+  }
+}
+
+// Inverse: transform of length nz, then the epilogue (EPI as for k_zi_c2r, complex
+// products, no conjugation: the density sums are bilinear in q and qd).
+template <typename T, int N, int EPI>
+__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
+k_zi_c2c(const cpx<T>* __restrict__ spec, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ qout,
+         const cpx<T>* __restrict__ partner, double2* __restrict__ accA, double2* __restrict__ accB, double cA,
+         double cB, long long npen, const cpx<T>* __restrict__ tw) {
+  constexpr int P = PencilsPerCta<T, N>::v;
+  constexpr int E = Plan<N>::E;
+  constexpr int TPC = Plan<N>::TPC;
+  constexpr int LD = pencil_ld<T>(N);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long pen = (long long)blockIdx.x * P + p;
+  const bool valid = pen < npen;
+  const long long o = (valid ? pen : 0) * N;
+  XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
+  cpx<T> v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = valid ? spec[o + t + TPC * i] : mk<T>(T(0), T(0));
+  fft<T, true, N>(v, t, tw, x);
+  if (!valid) return;
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const long long m = o + t + TPC * i;
+    cpx<T> y = v[i];
+    if (EPI != 2) y = cmul(y, B[m]);
+    qout[m] = y;
+    if (EPI == 1) {
+      const cpx<T> pp = partner[m];
+      double2 pr;
+      pr.x = (double)y.x * (double)pp.x - (double)y.y * (double)pp.y;
+      pr.y = (double)y.x * (double)pp.y + (double)y.y * (double)pp.x;
+      if (cA != 0.0) {
+        double2 a = accA[m];
+        a.x += cA * pr.x;
+        a.y += cA * pr.y;
+        accA[m] = a;
+      }
+      if (cB != 0.0) {
+        double2 a = accB[m];
+        a.x += cB * pr.x;
+        a.y += cB * pr.y;
+        accB[m] = a;
+      }
+    }
+  }
+}
+
+}  // namespace pft
