@@ -370,13 +370,36 @@ pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt, co
 
 pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[3], double dlnQ_dL[3],
                          pft_mem where) {
-  (void)dH_dwp;
-  (void)dH_dwm;
-  (void)dH_dL;
-  (void)dlnQ_dL;
-  (void)where;
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
-  return fail(PFT_ERR_UNSUPPORTED, "gradients are not built yet");
+  CtxData& d = ctx->d;
+  if (d.kind != PFT_SCFT_REAL) return fail(PFT_ERR_UNSUPPORTED, "gradients need real SCFT fields");
+  if (!d.solved) return fail(PFT_ERR_STATE, "pft_gradients needs a solve at the current fields");
+  double* gp = nullptr;
+  double* gm = nullptr;
+  if (where == PFT_HOST) {
+    gp = dH_dwp ? (double*)ctx->io : nullptr;
+    gm = dH_dwm ? (double*)ctx->io + d.M : nullptr;
+  } else {
+    gp = (double*)dH_dwp;
+    gm = (double*)dH_dwm;
+  }
+  PFT_CK(ctx->eng->gradients(d, gp, gm));
+  if (where == PFT_HOST) {
+    if (dH_dwp) PFT_CK(cudaMemcpyAsync(dH_dwp, gp, (size_t)d.M * 8, cudaMemcpyDeviceToHost, d.stream));
+    if (dH_dwm) PFT_CK(cudaMemcpyAsync(dH_dwm, gm, (size_t)d.M * 8, cudaMemcpyDeviceToHost, d.stream));
+  }
+  PFT_CK(cudaMemcpyAsync(d.scal_host, d.scal, pft::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  const double* s = d.scal_host;
+  const double Q = s[pft::S_Q], H = s[pft::S_H];
+  const double Md = (double)d.M;
+  const double V = d.L[0] * d.L[1] * d.L[2];
+  for (int a = 0; a < 3; a++) {
+    const double g = 2.0 * d.ds / (d.L[a] * Q * Md * Md) * s[pft::S_STRESS + a];
+    if (dlnQ_dL) dlnQ_dL[a] = g;
+    if (dH_dL) dH_dL[a] = H / d.L[a] - d.C * V * g;
+  }
+  return PFT_OK;
 }
 
 pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_profile* out) {

@@ -368,6 +368,20 @@ __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, long l
     dst[i] = (B)src[i];
 }
 
+// Exact gradients of the discrete H in the grid values of W+ and W- (Eq. 7 forces
+// times C dV).  Either output may be null.
+static __global__ void __launch_bounds__(PW_THREADS) k_grad_fields(const double* __restrict__ phiA,
+                                                                   const double* __restrict__ phiB,
+                                                                   const double* __restrict__ wm, double* __restrict__ gp,
+                                                                   double* __restrict__ gm, double cdv, double chiN,
+                                                                   long long M) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double a = phiA[i], b = phiB[i];
+    if (gp) gp[i] = cdv * (a + b - 1.0);
+    if (gm) gm[i] = cdv * (2.0 * wm[i] / chiN + b - a);
+  }
+}
+
 // Box derivative (stress) contraction for real fields: for one contour step,
 // sum over the half spectrum of w(kz) Re[conj(u^) v^] k_a^2 exp(-k^2 ds), a = x, y, z,
 // accumulated into per-block partials (same block -> same slots every step).

@@ -294,11 +294,64 @@ class EngineT : public Engine {
     return e;
   }
 
+  // ------------------------------------------------------- a8: gradients
+  // Field gradients from the densities of the last solve, and the box derivative of
+  // lnQ: the conjugate march is run again and, at every step, the forward spectra
+  // u^ = F[B_n qd_{Ns-n}] and v^ = F[B_n q_{n-1}] are contracted with
+  // k_a^2 exp(-k^2 ds) over the half spectrum (S_STRESS; the host applies
+  // 2 ds / (L_a Q M^2)).  Real SCFT fields only.
   cudaError_t gradients(CtxData& c, double* dwp, double* dwm) override {
-    (void)c;
-    (void)dwp;
-    (void)dwm;
-    return cudaErrorNotSupported;
+    if (c.kind != PFT_SCFT_REAL) return cudaErrorNotSupported;
+    const double dV = c.L[0] * c.L[1] * c.L[2] / (double)c.M;
+    if (dwp || dwm) {
+      k_grad_fields<<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.accA, (const double*)c.accB,
+                                                          (const double*)c.wm, dwp, dwm, c.C * dV, c.chiN, c.M);
+    }
+    cudaError_t e = cudaMemsetAsync(c.partials, 0, (size_t)c.npart * 3 * sizeof(double), c.stream);
+    if (e != cudaSuccess) return e;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const Z* twx = tab<Z>(c, c.tw_off[0]);
+    const Z* twy = tab<Z>(c, c.tw_off[1]);
+    const Z* twz = tab<Z>(c, c.tw_off[2]);
+    const Z* twh = tab<Z>(c, c.tw_off[3]);
+    const T* dx = tab<T>(c, c.d_off[0]);
+    const T* dy = tab<T>(c, c.d_off[1]);
+    const T* dz = tab<T>(c, c.d_off[2]);
+    const double* gx = tab<double>(c, c.g_off[0]);
+    const double* gy = tab<double>(c, c.g_off[1]);
+    const double* gz = tab<double>(c, c.g_off[2]);
+    Z* u = (Z*)c.spec;
+    Z* v = (Z*)c.spec2;
+    const long long npen = (long long)nx * ny;
+    const long long nzc = c.nzh;
+    const size_t slice = (size_t)c.M * sizeof(T);
+    const char* hist = (const char*)c.hist;
+    for (int m = 1; m <= c.Ns; m++) {
+      const int nb = c.Ns + 1 - m;
+      const T* B = (const T*)((nb <= c.NsA) ? c.BA : c.BB);
+      const T* in = (const T*)((m == 1) ? c.qd0 : c.qd[(m - 1) & 1]);
+      T* out = (T*)c.qd[m & 1];
+      const T* qprev = (const T*)(hist + (size_t)(nb - 1) * slice);
+      for (int w = 0; w < 2; w++) {
+        Z* sp = w ? v : u;
+        PFT_DISPATCH_HALF(nz / 2, e = launch_zf_r2c<N>(c, w ? qprev : in, B, sp, npen, twh, twz));
+        if (e != cudaSuccess) return e;
+        PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 0>(c, sp, nx * nzc, nzc, ny * nzc, nzc, twy, dx, dy, dz, (int)nzc));
+        if (e != cudaSuccess) return e;
+        PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 0>(c, sp, ny * nzc, ny * nzc, 0, ny * nzc, twx, dx, dy, dz, (int)nzc));
+        if (e != cudaSuccess) return e;
+      }
+      k_stress_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>(u, v, gx, gy, gz, nx, ny, (int)nzc, nz, c.ds, c.partials);
+      PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 3>(c, u, ny * nzc, ny * nzc, 0, ny * nzc, twx, dx, dy, dz, (int)nzc));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 1>(c, u, nx * nzc, nzc, ny * nzc, nzc, twy, dx, dy, dz, (int)nzc));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_HALF(nz / 2, e = launch_zi_c2r<N, 0>(c, u, B, out, nullptr, nullptr, nullptr, 0.0, 0.0, npen, twh,
+                                                        twz));
+      if (e != cudaSuccess) return e;
+    }
+    k_reduce_final<3><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_STRESS);
+    return cudaGetLastError();
   }
 
   cudaError_t to_f64(CtxData& c, const void* src, void* dst, long long cnt) override {

@@ -51,7 +51,8 @@ template <typename T, int N> struct PencilsPerCta {
 
 // ---------------------------------------------------------------- strided pass
 // MODE 0: forward transform; 1: inverse transform; 2: forward, multiply by
-// dk[k]*dy[ky]*dz[kz], inverse (the x pass of a contour step).
+// dk[k]*dy[ky]*dz[kz], inverse (the x pass of a contour step); 3: multiply by the
+// same factor, inverse (completes a step whose forward x transform already ran).
 // Column col in [0, ncols): element k at data[(col / cin) * s_outer + col % cin + k * s_k].
 template <typename T, int N, int MODE>
 __global__ void __launch_bounds__(Tile<T>::C * Plan<N>::TPC)
@@ -77,10 +78,10 @@ k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s
   XchCols<T> x{sm, C, c};
   if (MODE == 1) {
     fft<T, true, N>(v, t, tw, x);
-  } else {
+  } else if (MODE != 3) {
     fft<T, false, N>(v, t, tw, x);
   }
-  if (MODE == 2) {
+  if (MODE == 2 || MODE == 3) {
     const long long ky = colc / nzc, kz = colc % nzc;
     const T dyz = dy[ky] * dz[kz];
 #pragma unroll
