@@ -191,6 +191,29 @@ typedef struct {
  * Synchronises.  Errors: as pft_solve / pft_field_step. */
 pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_profile* out);
 
+/* One contour step that allocates no device memory, for callers that cannot call
+ * cudaMalloc (code running while another framework owns the device allocator, or a
+ * plug-in that may only use the memory it is handed).  The paper has no counterpart:
+ * it is this library's own addition.
+ *   q_out = B * F^-1[ D * F[ B * q_in ] ],  B = exp(-w/(2 Ns)),  D = exp(-k^2/Ns)
+ * in FP64 on real fields, with the library's context conventions (grid n[3], box
+ * L[3] in Rg, row-major [x][y][z]).  w, q_in, q_out: device float64 arrays of
+ * M = n[0]*n[1]*n[2] values owned by the caller; q_out may alias q_in; the call is
+ * asynchronous on `stream` (cudaStream_t or NULL for the legacy default stream).
+ * Scratch (Boltzmann factor, half spectrum, twiddle and diffusion tables) lives in
+ * one static device array of about 6.3 MB that every GPU loading the library keeps
+ * until the process exits; the limit is 64 points per axis (64^3 points).  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls share the array and each
+ * call overwrites every part of it that it reads, so nothing needs clearing between
+ * calls -- but calls whose work overlaps on the GPU (different streams or devices
+ * sharing a context without ordering) race on it.  Allocates nothing: no cudaMalloc,
+ * cudaFree or allocating library routine.
+ * Errors: PFT_ERR_ARG (NULL pointer, Ns < 1, non-positive L, any n[a] > 64),
+ * PFT_ERR_SHAPE (a size without an FFT plan), PFT_ERR_CUDA. */
+pft_status pft_contour_step_static(const int n[3], const double L[3], int Ns, const double* w,
+                                   const double* q_in, double* q_out, void* stream);
+
 /* Test hooks -------------------------------------------------------------- */
 
 /* 3D DFT of M complex128 values through the library's own FFT passes in the

@@ -102,6 +102,8 @@ _SIGS = {
     "pft_field_step": (ct.c_int, [_P, ct.c_int, ct.c_double, _P, _P, ct.c_int]),
     "pft_gradients": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int]),
     "pft_profile_step": (ct.c_int, [_P, ct.c_int, ct.c_double, ct.POINTER(pft_profile)]),
+    "pft_contour_step_static": (ct.c_int, [ct.POINTER(ct.c_int), ct.POINTER(ct.c_double), ct.c_int, _P, _P, _P,
+                                            _P]),
     "pft_fft3d": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int]),
     "pft_get_propagator": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, ct.c_int]),
     "pft_debug_set_q0": (ct.c_int, [_P, _P, ct.c_int]),
@@ -253,6 +255,16 @@ def pft_profile_step(h, step_kind=-1, lam_or_dt=0.0) -> dict:
     p = pft_profile()
     _check(_lib().pft_profile_step(h, int(step_kind), float(lam_or_dt), ct.byref(p)), "pft_profile_step")
     return p.as_dict()
+
+
+def pft_contour_step_static(n, L, Ns, w, q_in, q_out, stream=None):
+    """Device arrays only (torch CUDA tensors of float64)."""
+    ptrs = [_ptr(a) for a in (w, q_in, q_out)]
+    if any(wh != PFT_DEVICE for _, wh in ptrs):
+        raise ValueError("pft_contour_step_static takes device arrays")
+    _check(_lib().pft_contour_step_static((ct.c_int * 3)(*[int(v) for v in n]),
+                                          (ct.c_double * 3)(*[float(v) for v in L]), int(Ns),
+                                          ptrs[0][0], ptrs[1][0], ptrs[2][0], stream), "pft_contour_step_static")
 
 
 def pft_fft3d(h, x, out, inverse=False):
