@@ -60,6 +60,12 @@ typedef enum { PFT_SCFT_REAL = 0, PFT_CL_COMPLEX = 1 } pft_kind;
 typedef enum { PFT_FP64 = 0, PFT_FP32_MIXED = 1 } pft_precision;
 typedef enum { PFT_HOST = 0, PFT_DEVICE = 1 } pft_mem;
 typedef enum { PFT_STEP_SCFT_EULER = 0, PFT_STEP_CL_EULER_MARUYAMA = 1 } pft_step_kind;
+/* How the marches run: AUTO picks RESIDENT where it applies (FP32-mixed, real SCFT
+ * fields, cubic 64^3/96^3/128^3 grids) and PASSES elsewhere.  PASSES: five pass kernels
+ * per contour step, replayed as one CUDA graph per solve.  RESIDENT: one persistent
+ * cooperative launch per march, one CTA per x-plane keeping the Boltzmann factors and
+ * a spectrum plane in shared memory, two grid barriers per contour step. */
+typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1, PFT_MARCH_RESIDENT = 2 } pft_march;
 
 typedef struct { int n[3]; double L[3]; } pft_grid;          /* grid points and box (Rg) */
 typedef struct { int Ns; double fA; } pft_chain;              /* contour steps, A fraction */
@@ -71,6 +77,7 @@ typedef struct {
   void* stream;             /* cudaStream_t to run on; NULL: the library creates one */
   unsigned long long seed;  /* Philox key of the CL noise */
   unsigned long long instance; /* Philox counter word: independent replica streams */
+  pft_march march;          /* PFT_MARCH_RESIDENT where it does not apply: PFT_ERR_UNSUPPORTED */
 } pft_opts;
 
 /* Observables of the last solve.  Complex quantities are {re, im}; in SCFT mode the
@@ -171,6 +178,56 @@ pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt,
 pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[3],
                          double dlnQ_dL[3], pft_mem where);
 
+/* Batches of independent systems ------------------------------------------ */
+
+/* One member of a batch: its grid, chain and model, and the Philox key of its complex
+ * Langevin noise (the counter's instance word is the member index). */
+typedef struct {
+  pft_grid grid;
+  pft_chain chain;
+  pft_model model;
+  unsigned long long seed;
+} pft_instance_desc;
+
+typedef enum {
+  PFT_BATCH_GRAPHED = 0,      /* batched pass launches, one CUDA graph per field update */
+  PFT_BATCH_PER_INSTANCE = 1  /* one launch sequence per instance, instance after instance */
+} pft_batch_mode;
+
+typedef struct pft_batch pft_batch;
+
+/* Create `count` independent systems (SCFT and CL mixed; grid sizes up to 64 per axis
+ * from 4,6,8,12,16,24,32,48,64; any Ns and fA) in one precision.  Members with equal
+ * field kind and grid form a class; one field update of the whole batch runs each
+ * contour step of each class as five batched launches over the members still
+ * marching (members of a class sorted by Ns), then every member's reductions and
+ * field update.  stream: cudaStream_t or NULL (the batch creates one).
+ * Errors: PFT_ERR_ARG, PFT_ERR_SHAPE, PFT_ERR_OOM, PFT_ERR_CUDA. */
+pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc* descs,
+                            pft_precision precision, void* stream);
+pft_status pft_batch_destroy(pft_batch* b);
+
+/* Fields of member i (layout as pft_set_fields); resets its step counter. */
+pft_status pft_batch_set_fields(pft_batch* b, int i, const void* wp, const void* wm, pft_mem where);
+pft_status pft_batch_get_fields(pft_batch* b, int i, void* wp, void* wm, pft_mem where);
+
+/* `updates` field updates of every member: solve (Eqs. 3-5, 8, 13) then the field
+ * step of Eq. 9 -- explicit Euler with `lam` for SCFT members, Euler-Maruyama with
+ * `dt` and the library's Philox noise for CL members.  GRAPHED captures one update of
+ * the whole batch as a CUDA graph (recaptured when lam or dt change) and replays it.
+ * Asynchronous on the batch stream.  Error: PFT_ERR_STATE if a member has no fields. */
+pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_batch_mode mode);
+
+/* Observables and densities of member i's last solve (synchronises). */
+pft_status pft_batch_get_observables(pft_batch* b, int i, pft_obs* obs);
+pft_status pft_batch_get_densities(pft_batch* b, int i, void* phiA, void* phiB, pft_mem where);
+pft_status pft_batch_synchronize(pft_batch* b);
+
+/* Grid-point contour steps per field update (sum of 2 M Ns), number of classes, and
+ * kernel launches per captured update (0 before the first GRAPHED run). */
+pft_status pft_batch_info(const pft_batch* b, double* units_per_update, int* nclasses, long long* launches);
+pft_status pft_batch_get_stream(const pft_batch* b, void** stream);
+
 /* Per-kernel-class device times of one solve, for roofline reporting. */
 #define PFT_PROFILE_KINDS 16
 typedef struct {
@@ -228,6 +285,14 @@ pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem
 /* Replace the initial condition q_0 = qd_0 = 1 by a caller array (M values, float64
  * or complex128 by kind; NULL restores 1).  Used by the diffusion-only test. */
 pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
+
+/* Budget, in GPU clock cycles, of each bounded grid-barrier wait of the resident
+ * march (default 4e9, about 2 s).  A wait that runs out sets the context's error word:
+ * the march returns early and pft_get_observables reports PFT_ERR_TIMEOUT. */
+pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles);
+
+/* Which march the context uses: 1 = passes, 2 = resident. */
+pft_status pft_get_march(const pft_ctx* ctx, int* march);
 
 /* Standard normals of the device Philox stream (same layout as the CL noise) for
  * points 0..M-1 into a device float64 array, on `stream` (cudaStream_t or NULL). */

@@ -10,18 +10,22 @@
 using pft::CtxData;
 using pft::Engine;
 
-struct pft_ctx {
-  CtxData d;
-  Engine* eng = nullptr;
-  void* io = nullptr;   // [M] complex128 staging for conversions and host noise
-  bool have_obs = false;
-};
 
 namespace pft {
-const char* const kKernelKindNames[KK_COUNT] = {"z_fwd",  "y_fwd",   "x_fused",    "y_inv",  "z_inv_fwd",
-                                                "z_inv_bwd", "reduce", "field_step", "prepare"};
+const char* const kKernelKindNames[KK_COUNT] = {"z_fwd",      "y_fwd",   "x_fused",    "y_inv",
+                                                "z_inv_fwd",  "z_inv_bwd", "reduce",   "field_step",
+                                                "prepare",    "march_fwd", "march_bwd"};
 static thread_local std::string g_err;
 void set_error(const std::string& s) { g_err = s; }
+
+bool batch_axis_supported(int n) {
+  switch (n) {
+    case 4: case 6: case 8: case 12: case 16: case 24: case 32: case 48: case 64:
+      return true;
+    default:
+      return false;
+  }
+}
 
 bool axis_supported(int n) {
   switch (n) {
@@ -72,7 +76,7 @@ void free_all(pft_ctx* c) {
   if (d.graph) cudaGraphExecDestroy(d.graph);
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
-                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io};
+                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
@@ -173,6 +177,19 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
     d.own_stream = true;
   }
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
+  {
+    const bool can = c->eng->resident_supported(d);
+    if (opts->march == PFT_MARCH_RESIDENT && !can) {
+      free_all(c);
+      return fail(PFT_ERR_UNSUPPORTED,
+                  "resident march needs FP32-mixed precision, real SCFT fields and a 64^3, 96^3 or 128^3 grid");
+    }
+    if (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES && opts->march != PFT_MARCH_RESIDENT) {
+      free_all(c);
+      return fail(PFT_ERR_ARG, "unknown march");
+    }
+    d.march = (opts->march == PFT_MARCH_PASSES || !can) ? 1 : 2;
+  }
 
   const size_t M = (size_t)d.M;
   const size_t we = welem(d), fe = felem(d);
@@ -185,7 +202,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       {&d.hist, (size_t)(d.Ns + 1) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
       {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
       {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
-      {&c->io, M * 16},
+      {&c->io, M * 16}, {(void**)&d.sync, 4 * sizeof(unsigned)},
   };
   for (auto& a : plan) {
     e = dalloc(d, a.p, a.b);
@@ -201,6 +218,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
     e = cudaMemsetAsync(d.scal, 0, pft::S_COUNT * sizeof(double), d.stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(d.partials, 0, (size_t)d.npart * 8 * sizeof(double), d.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.sync, 0, 4 * sizeof(unsigned), d.stream);
   if (e == cudaSuccess) e = c->eng->upload_tables(d);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.hist);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.qd0);
@@ -301,11 +319,14 @@ pft_status pft_get_observables(pft_ctx* ctx, pft_obs* obs) {
   CtxData& d = ctx->d;
   if (!ctx->have_obs) return fail(PFT_ERR_STATE, "no solve since the fields were set");
   PFT_CK(cudaMemcpyAsync(d.scal_host, d.scal, pft::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+  unsigned syncw[4] = {0, 0, 0, 0};
+  if (d.march == 2) PFT_CK(cudaMemcpyAsync(syncw, d.sync, sizeof(syncw), cudaMemcpyDeviceToHost, d.stream));
   PFT_CK(cudaStreamSynchronize(d.stream));
   const double* s = d.scal_host;
   const double V = d.L[0] * d.L[1] * d.L[2];
   const double Md = (double)d.M;
   memset(obs, 0, sizeof(*obs));
+  if (syncw[2] != 0) return fail(PFT_ERR_TIMEOUT, "a grid barrier of the resident march ran out of its wait budget");
   for (int j = 0; j < 2; j++) {
     obs->Q[j] = s[pft::S_Q + j];
     obs->lnQ[j] = s[pft::S_LNQ + j];
@@ -454,9 +475,10 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   int iF = -1, iR1 = -1, iB = -1, iR2 = -1;
   for (int i = 0; i < d.ev_used; i++) {
     const int k = d.ev_kind[i];
-    if (iF < 0 && k == pft::KK_Z_FWD) iF = i;
+    const bool march_start = (k == pft::KK_Z_FWD || k == pft::KK_MARCH_FWD || k == pft::KK_MARCH_BWD);
+    if (iF < 0 && march_start) iF = i;
     else if (iF >= 0 && iR1 < 0 && k == pft::KK_REDUCE) iR1 = i;
-    else if (iR1 >= 0 && iB < 0 && k == pft::KK_Z_FWD) iB = i;
+    else if (iR1 >= 0 && iB < 0 && march_start) iB = i;
     else if (iB >= 0 && iR2 < 0 && k == pft::KK_REDUCE) iR2 = i;
   }
   if (iF >= 0 && iR1 > iF) {
@@ -480,6 +502,10 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   out->bytes_per_launch[pft::KK_Z_INV_BWD] = Ms * ze + 3 * M * we + 2 * M * fe;
   out->bytes_per_launch[pft::KK_FIELD_STEP] = 6 * M * fe + 2 * M * we;
   out->bytes_per_launch[pft::KK_PREPARE] = 2 * M * fe + 2 * M * we;
+  // one resident launch runs a whole march: per step the forward reads q_{n-1} and B
+  // and writes q_n, the conjugate one also reads the partner and updates an accumulator
+  out->bytes_per_launch[pft::KK_MARCH_FWD] = (double)d.Ns * (3 * M * we);
+  out->bytes_per_launch[pft::KK_MARCH_BWD] = (double)d.Ns * (4 * M * we + 2 * M * 8.0);
   return PFT_OK;
 }
 
@@ -523,6 +549,23 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where) {
     PFT_CK(ctx->eng->from_f64(d, ctx->io, d.qd0, cnt));
   }
   PFT_CK(cudaStreamSynchronize(d.stream));
+  return PFT_OK;
+}
+
+pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles) {
+  if (!ctx || cycles < 1) return fail(PFT_ERR_ARG, "bad argument");
+  ctx->d.spin_limit = cycles;
+  ctx->d.graph_valid = false;  // the budget is a launch argument captured in the graph
+  if (ctx->d.graph) {
+    cudaGraphExecDestroy(ctx->d.graph);
+    ctx->d.graph = nullptr;
+  }
+  return PFT_OK;
+}
+
+pft_status pft_get_march(const pft_ctx* ctx, int* march) {
+  if (!ctx || !march) return fail(PFT_ERR_ARG, "NULL argument");
+  *march = ctx->d.march;
   return PFT_OK;
 }
 

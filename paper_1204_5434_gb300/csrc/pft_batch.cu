@@ -1,0 +1,354 @@
+// pft_batch.cu -- many independent systems of uneven grid and contour sizes advanced
+// together.  Instances are grouped into classes of equal field kind and grid; within a
+// class the members are sorted by contour length, so at contour step s the instances
+// still marching are a prefix of the class and one launch per pass covers all of them
+// (blockIdx.y = instance).  One field update of every instance -- both marches of all
+// classes, each instance's reductions and its field step -- is captured once as a CUDA
+// graph and replayed.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "pft_batch.cuh"
+#include "pft_engine.h"
+
+namespace {
+
+struct BatchClass {
+  pft::BatchGeom g;
+  pft_kind kind;
+  std::vector<int> members;   // instance indices, Ns descending
+  int maxNs = 0;
+  std::vector<int> active;    // active[s-1]: members with Ns >= s
+  pft::BatchStep* d_fwd = nullptr;  // [maxNs][K]
+  pft::BatchStep* d_bwd = nullptr;
+};
+
+__global__ void k_batch_increment(unsigned long long* __restrict__ c, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] += 1ull;
+}
+
+pft_status bfail(pft_status s, const std::string& m) {
+  pft::set_error(m);
+  return s;
+}
+
+pft_status bcuda(cudaError_t e, const char* what) {
+  pft::set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  (void)cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? PFT_ERR_OOM : PFT_ERR_CUDA;
+}
+
+}  // namespace
+
+struct pft_batch {
+  std::vector<pft_ctx*> inst;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<BatchClass> classes;
+  unsigned long long* d_steps = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  double g_lam = -1.0, g_dt = -1.0;
+  long long launches = 0;
+  double units = 0.0;
+};
+
+namespace {
+
+void batch_free(pft_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  for (auto& c : b->classes) {
+    if (c.d_fwd) cudaFree(c.d_fwd);
+    if (c.d_bwd) cudaFree(c.d_bwd);
+  }
+  if (b->d_steps) cudaFree(b->d_steps);
+  for (pft_ctx* c : b->inst)
+    if (c) pft_destroy(c);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+// Per-instance step arguments of both marches.
+void fill_steps(const pft_ctx* c, int s, bool bwd, pft::BatchStep* st) {
+  const pft::CtxData& d = c->d;
+  const size_t we = (d.prec == PFT_FP64 ? 8 : 4) * (d.kind == PFT_SCFT_REAL ? 1 : 2);
+  const size_t slice = (size_t)d.M * we;
+  const char* hist = (const char*)d.hist;
+  memset(st, 0, sizeof(*st));
+  if (!bwd) {
+    st->in = hist + (size_t)(s - 1) * slice;
+    st->B = (s <= d.NsA) ? d.BA : d.BB;
+    st->out = (void*)(hist + (size_t)s * slice);
+  } else {
+    const int nb = d.Ns + 1 - s;
+    st->B = (nb <= d.NsA) ? d.BA : d.BB;
+    st->in = (s == 1) ? d.qd0 : d.qd[(s - 1) & 1];
+    st->out = d.qd[s & 1];
+    const int pn = d.Ns - s;
+    st->partner = hist + (size_t)pn * slice;
+    double cA = 0.0, cB = 0.0;
+    if (d.NsA > 0 && pn <= d.NsA) cA = (pn == 0 || pn == d.NsA) ? 0.5 : 1.0;
+    if (d.NsA < d.Ns && pn >= d.NsA) cB = (pn == d.NsA || pn == d.Ns) ? 0.5 : 1.0;
+    st->cA = cA;
+    st->cB = cB;
+    st->accA = d.accA;
+    st->accB = d.accB;
+  }
+  st->spec = d.spec;
+  const char* t = (const char*)d.tables;
+  for (int a = 0; a < 4; a++) st->tw[a] = t + d.tw_off[a];
+  for (int a = 0; a < 3; a++) st->d[a] = t + d.d_off[a];
+}
+
+// One field update of every instance, on b->stream.
+pft_status record_update(pft_batch* b, double lam, double dt) {
+  int maxNs = 0;
+  for (auto& c : b->classes) maxNs = std::max(maxNs, c.maxNs);
+  long long launches = 0;
+  for (int march = 0; march < 2; march++) {
+    for (int s = 1; s <= maxNs; s++) {
+      for (auto& c : b->classes) {
+        if (s > c.maxNs) continue;
+        const int K = (int)c.members.size();
+        const pft::BatchStep* st = (march ? c.d_bwd : c.d_fwd) + (size_t)(s - 1) * K;
+        pft::Engine* eng = b->inst[c.members[0]]->eng;
+        cudaError_t e = eng->batch_contour_step(c.g, st, c.active[s - 1], march, b->stream);
+        if (e != cudaSuccess) return bcuda(e, "batched contour step");
+        launches += 5;
+      }
+    }
+    for (pft_ctx* x : b->inst) {
+      cudaError_t e = march ? x->eng->solve_tail(x->d) : x->eng->solve_mid(x->d);
+      if (e != cudaSuccess) return bcuda(e, "batched reductions");
+      launches += march ? 2 : 3;
+    }
+  }
+  for (pft_ctx* x : b->inst) {
+    const bool scft = (x->d.kind == PFT_SCFT_REAL);
+    cudaError_t e = x->eng->field_step(x->d, scft ? PFT_STEP_SCFT_EULER : PFT_STEP_CL_EULER_MARUYAMA, scft ? lam : dt,
+                                       nullptr, nullptr);
+    if (e != cudaSuccess) return bcuda(e, "batched field step");
+    launches += 2;
+  }
+  const int n = (int)b->inst.size();
+  k_batch_increment<<<(n + 255) / 256, 256, 0, b->stream>>>(b->d_steps, n);
+  launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bcuda(e, "batched step counter");
+  b->launches = launches;
+  return PFT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc* descs, pft_precision precision,
+                            void* stream) {
+  if (!out) return bfail(PFT_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !descs) return bfail(PFT_ERR_ARG, "need at least one instance description");
+  for (int i = 0; i < count; i++)
+    for (int a = 0; a < 3; a++)
+      if (!pft::batch_axis_supported(descs[i].grid.n[a]))
+        return bfail(PFT_ERR_SHAPE, "batch instance " + std::to_string(i) + ": grid sizes must be one of " +
+                                        "4,6,8,12,16,24,32,48,64");
+  pft_batch* b = new pft_batch();
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete b;
+      return bcuda(e, "cudaStreamCreate");
+    }
+    b->own_stream = true;
+  }
+  b->inst.assign(count, nullptr);
+  for (int i = 0; i < count; i++) {
+    pft_opts o;
+    memset(&o, 0, sizeof(o));
+    o.precision = precision;
+    o.use_graph = 1;
+    o.stream = b->stream;
+    o.seed = descs[i].seed;
+    o.instance = (unsigned long long)i;
+    o.march = PFT_MARCH_PASSES;
+    pft_status s = pft_create(&b->inst[i], &descs[i].grid, &descs[i].chain, &descs[i].model, &o);
+    if (s != PFT_OK) {
+      std::string msg = pft_last_error();
+      batch_free(b);
+      return bfail(s, "batch instance " + std::to_string(i) + ": " + msg);
+    }
+    b->units += 2.0 * (double)b->inst[i]->d.M * b->inst[i]->d.Ns;
+  }
+  cudaError_t e = cudaMalloc(&b->d_steps, sizeof(unsigned long long) * count);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long) * count, b->stream);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return bcuda(e, "batch step counters");
+  }
+  for (int i = 0; i < count; i++) b->inst[i]->d.step_dev = b->d_steps + i;
+  // classes of equal kind and grid, members by descending contour length
+  std::map<std::tuple<int, int, int, int>, int> index;
+  for (int i = 0; i < count; i++) {
+    const pft::CtxData& d = b->inst[i]->d;
+    auto key = std::make_tuple((int)d.kind, d.n[0], d.n[1], d.n[2]);
+    auto it = index.find(key);
+    if (it == index.end()) {
+      BatchClass c;
+      for (int a = 0; a < 3; a++) c.g.n[a] = d.n[a];
+      c.g.kind = d.kind;
+      c.g.nzh = d.nzh;
+      c.kind = d.kind;
+      index[key] = (int)b->classes.size();
+      b->classes.push_back(c);
+      it = index.find(key);
+    }
+    b->classes[it->second].members.push_back(i);
+  }
+  for (auto& c : b->classes) {
+    std::stable_sort(c.members.begin(), c.members.end(),
+                     [&](int x, int y) { return b->inst[x]->d.Ns > b->inst[y]->d.Ns; });
+    const int K = (int)c.members.size();
+    c.maxNs = b->inst[c.members[0]]->d.Ns;
+    c.active.assign(c.maxNs, 0);
+    for (int s = 1; s <= c.maxNs; s++)
+      for (int k = 0; k < K; k++)
+        if (b->inst[c.members[k]]->d.Ns >= s) c.active[s - 1] = k + 1;
+    std::vector<pft::BatchStep> hf((size_t)c.maxNs * K), hb((size_t)c.maxNs * K);
+    for (int s = 1; s <= c.maxNs; s++)
+      for (int k = 0; k < c.active[s - 1]; k++) {
+        fill_steps(b->inst[c.members[k]], s, false, &hf[(size_t)(s - 1) * K + k]);
+        fill_steps(b->inst[c.members[k]], s, true, &hb[(size_t)(s - 1) * K + k]);
+      }
+    const size_t bytes = hf.size() * sizeof(pft::BatchStep);
+    e = cudaMalloc(&c.d_fwd, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_bwd, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_fwd, hf.data(), bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c.d_bwd, hb.data(), bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return bcuda(e, "batch step tables");
+    }
+  }
+  *out = b;
+  return PFT_OK;
+}
+
+pft_status pft_batch_destroy(pft_batch* b) {
+  if (!b) return PFT_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_free(b);
+  return PFT_OK;
+}
+
+pft_status pft_batch_set_fields(pft_batch* b, int i, const void* wp, const void* wm, pft_mem where) {
+  if (!b || i < 0 || i >= (int)b->inst.size()) return bfail(PFT_ERR_ARG, "bad batch or instance index");
+  pft_status s = pft_set_fields(b->inst[i], wp, wm, where);
+  if (s != PFT_OK) return s;
+  cudaError_t e = cudaMemsetAsync(b->d_steps + i, 0, sizeof(unsigned long long), b->stream);
+  return e == cudaSuccess ? PFT_OK : bcuda(e, "reset step counter");
+}
+
+pft_status pft_batch_get_fields(pft_batch* b, int i, void* wp, void* wm, pft_mem where) {
+  if (!b || i < 0 || i >= (int)b->inst.size()) return bfail(PFT_ERR_ARG, "bad batch or instance index");
+  return pft_get_fields(b->inst[i], wp, wm, where);
+}
+
+pft_status pft_batch_get_densities(pft_batch* b, int i, void* phiA, void* phiB, pft_mem where) {
+  if (!b || i < 0 || i >= (int)b->inst.size()) return bfail(PFT_ERR_ARG, "bad batch or instance index");
+  return pft_get_densities(b->inst[i], phiA, phiB, where);
+}
+
+pft_status pft_batch_get_observables(pft_batch* b, int i, pft_obs* obs) {
+  if (!b || i < 0 || i >= (int)b->inst.size()) return bfail(PFT_ERR_ARG, "bad batch or instance index");
+  return pft_get_observables(b->inst[i], obs);
+}
+
+pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_batch_mode mode) {
+  if (!b || updates < 0) return bfail(PFT_ERR_ARG, "bad argument");
+  if (!(lam > 0.0) || !(dt > 0.0) || !isfinite(lam) || !isfinite(dt))
+    return bfail(PFT_ERR_ARG, "lam and dt must be positive");
+  for (pft_ctx* x : b->inst)
+    if (!x->d.fields_set) return bfail(PFT_ERR_STATE, "every batch instance needs pft_batch_set_fields first");
+  if (mode == PFT_BATCH_GRAPHED) {
+    if (!b->graph || lam != b->g_lam || dt != b->g_dt) {
+      if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+      }
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return bcuda(e, "batch capture");
+      pft_status s = record_update(b, lam, dt);
+      e = cudaStreamEndCapture(b->stream, &g);
+      if (s != PFT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return s;
+      }
+      if (e != cudaSuccess) return bcuda(e, "batch capture end");
+      e = cudaGraphInstantiate(&b->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bcuda(e, "batch graph instantiate");
+      b->g_lam = lam;
+      b->g_dt = dt;
+    }
+    for (int u = 0; u < updates; u++) {
+      cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
+      if (e != cudaSuccess) return bcuda(e, "batch graph launch");
+    }
+  } else if (mode == PFT_BATCH_PER_INSTANCE) {
+    const int n = (int)b->inst.size();
+    for (int u = 0; u < updates; u++) {
+      for (pft_ctx* x : b->inst) {
+        const bool scft = (x->d.kind == PFT_SCFT_REAL);
+        cudaError_t e = x->eng->enqueue_solve(x->d);
+        if (e == cudaSuccess)
+          e = x->eng->field_step(x->d, scft ? PFT_STEP_SCFT_EULER : PFT_STEP_CL_EULER_MARUYAMA, scft ? lam : dt,
+                                 nullptr, nullptr);
+        if (e != cudaSuccess) return bcuda(e, "per-instance update");
+      }
+      k_batch_increment<<<(n + 255) / 256, 256, 0, b->stream>>>(b->d_steps, n);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return bcuda(e, "step counter");
+    }
+  } else {
+    return bfail(PFT_ERR_ARG, "unknown batch mode");
+  }
+  for (pft_ctx* x : b->inst) {
+    x->d.step += updates;
+    x->d.solved = false;
+    if (updates > 0) x->have_obs = true;
+  }
+  return PFT_OK;
+}
+
+pft_status pft_batch_synchronize(pft_batch* b) {
+  if (!b) return bfail(PFT_ERR_ARG, "NULL batch");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  return e == cudaSuccess ? PFT_OK : bcuda(e, "batch synchronize");
+}
+
+pft_status pft_batch_info(const pft_batch* b, double* units_per_update, int* nclasses, long long* launches) {
+  if (!b) return bfail(PFT_ERR_ARG, "NULL batch");
+  if (units_per_update) *units_per_update = b->units;
+  if (nclasses) *nclasses = (int)b->classes.size();
+  if (launches) *launches = b->launches;
+  return PFT_OK;
+}
+
+pft_status pft_batch_get_stream(const pft_batch* b, void** stream) {
+  if (!b || !stream) return bfail(PFT_ERR_ARG, "NULL argument");
+  *stream = (void*)b->stream;
+  return PFT_OK;
+}
+
+}  // extern "C"

@@ -72,6 +72,12 @@ struct CtxData {
   size_t tables_bytes = 0;
   int npart = 0;
   size_t bytes = 0;
+  // resident march: 1 = passes, 2 = resident; barrier words [count, gen, err, pad]
+  int march = 1;
+  unsigned* sync = nullptr;
+  long long spin_limit = 4000000000LL;
+  // optional device counter read by the CL field step instead of `step` (batches)
+  const unsigned long long* step_dev = nullptr;
   // profiling: an event recorded before every launch (eager solves only)
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
@@ -82,7 +88,7 @@ struct CtxData {
 // Kernel classes reported by pft_profile_step.
 enum KernelKind {
   KK_Z_FWD = 0, KK_Y_FWD, KK_X_FUSED, KK_Y_INV, KK_Z_INV_FWD, KK_Z_INV_BWD, KK_REDUCE, KK_FIELD_STEP,
-  KK_PREPARE, KK_COUNT
+  KK_PREPARE, KK_MARCH_FWD, KK_MARCH_BWD, KK_COUNT
 };
 extern const char* const kKernelKindNames[KK_COUNT];
 
@@ -94,14 +100,30 @@ inline void mark(CtxData& c, int kind) {
   c.ev_used++;
 }
 
+struct BatchStep;
+
+// Geometry shared by the members of one batch class.
+struct BatchGeom {
+  int n[3];
+  pft_kind kind;
+  int nzh;
+};
+
 class Engine {
  public:
   virtual ~Engine() {}
   virtual size_t elem_bytes() const = 0;      // working-precision real element
+  // Can this system run the resident march (and how much shared memory it needs)?
+  virtual bool resident_supported(const CtxData& c) const = 0;
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term
   virtual cudaError_t enqueue_solve(CtxData& c) = 0;    // marches, Q, densities, H
+  virtual cudaError_t solve_mid(CtxData& c) = 0;        // Q and the qd_0 quadrature term (after the forward march)
+  virtual cudaError_t solve_tail(CtxData& c) = 0;       // densities and force norms (after the conjugate march)
+  // One contour step of every active instance of a batch class (epi 0: forward, 1: conjugate).
+  virtual cudaError_t batch_contour_step(const BatchGeom& g, const BatchStep* d_steps, int nactive, int epi,
+                                         cudaStream_t st) = 0;
   virtual cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p,
                                  const double* eta_m) = 0;
   virtual cudaError_t fft3d(CtxData& c, void* data, int inverse) = 0;   // complex, in place
@@ -120,6 +142,15 @@ cudaError_t launch_philox_raw(const unsigned int ctr[4], const unsigned int key[
                               unsigned int* out, cudaStream_t st);
 
 bool axis_supported(int n);
+bool batch_axis_supported(int n);
 void set_error(const std::string& s);
 
 }  // namespace pft
+
+// The context object behind the opaque pft_ctx handle.
+struct pft_ctx {
+  pft::CtxData d;
+  pft::Engine* eng = nullptr;
+  void* io = nullptr;   // [M] complex128 staging for conversions and host noise
+  bool have_obs = false;
+};

@@ -310,9 +310,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
                                                         cpx<T>* __restrict__ BA, cpx<T>* __restrict__ BB, double dt,
                                                         double noise_std, const double* __restrict__ eta_p,
                                                         const double* __restrict__ eta_m, unsigned long long seed,
-                                                        unsigned long long instance, unsigned long long step, double ds,
+                                                        unsigned long long instance, unsigned long long step_arg,
+                                                        const unsigned long long* __restrict__ step_dev, double ds,
                                                         double chiN, long long M, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
+  const unsigned long long step = step_dev ? *step_dev : step_arg;
   const long long nblk = (M + 3) / 4;
   for (long long bk = blockIdx.x * (long long)blockDim.x + threadIdx.x; bk < nblk;
        bk += (long long)gridDim.x * blockDim.x) {
@@ -408,4 +410,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_stress_real(const cpx<T>* __rest
   block_reduce_store<3, true>(acc, partials + 3 * blockIdx.x);
 }
 
+}  // namespace pft
+
+namespace pft {
+static __global__ void k_increment_u64(unsigned long long* __restrict__ c, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] += 1ull;
+}
 }  // namespace pft

@@ -5,7 +5,11 @@
 
 #include <vector>
 
+#include <type_traits>
+
 #include "pft_engine_impl.cuh"
+#include "pft_batch.cuh"
+#include "pft_resident.cuh"
 
 namespace pft {
 
@@ -33,6 +37,22 @@ namespace pft {
     default: return cudaErrorInvalidValue;                                                                         \
   }
 
+// batch sizes (grid axes up to 64)
+#define PFT_BATCH_AXIS(n, ...)                                                                                     \
+  switch (n) {                                                                                                     \
+    PFT_CASE(4, __VA_ARGS__) PFT_CASE(6, __VA_ARGS__) PFT_CASE(8, __VA_ARGS__) PFT_CASE(12, __VA_ARGS__)           \
+    PFT_CASE(16, __VA_ARGS__) PFT_CASE(24, __VA_ARGS__) PFT_CASE(32, __VA_ARGS__) PFT_CASE(48, __VA_ARGS__)        \
+    PFT_CASE(64, __VA_ARGS__)                                                                                      \
+    default: return cudaErrorInvalidValue;                                                                         \
+  }
+#define PFT_BATCH_HALF(n, ...)                                                                                     \
+  switch (n) {                                                                                                     \
+    PFT_CASE(2, __VA_ARGS__) PFT_CASE(3, __VA_ARGS__) PFT_CASE(4, __VA_ARGS__) PFT_CASE(6, __VA_ARGS__)            \
+    PFT_CASE(8, __VA_ARGS__) PFT_CASE(12, __VA_ARGS__) PFT_CASE(16, __VA_ARGS__) PFT_CASE(24, __VA_ARGS__)         \
+    PFT_CASE(32, __VA_ARGS__)                                                                                      \
+    default: return cudaErrorInvalidValue;                                                                         \
+  }
+
 // Quadrature weights of the contour integrals (Eq. 8): trapezoid rule on each block.
 inline void trapezoid_weight(int n, int Ns, int NsA, double* cA, double* cB) {
   *cA = 0.0;
@@ -47,6 +67,89 @@ class EngineT : public Engine {
   using Z = cpx<T>;
 
   size_t elem_bytes() const override { return sizeof(T); }
+
+  // ------------------------------------------------------------ resident march
+  template <int NX, int NY, int NZ, bool BWD>
+  static cudaError_t launch_resident_n(CtxData& c, const ResArgs& a) {
+    using R = Res<NX, NY, NZ>;
+    auto kern = k_resident_march<NX, NY, NZ, BWD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(NX);
+    cfg.blockDim = dim3(R::THREADS);
+    cfg.dynamicSmemBytes = R::SMEM;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+  }
+
+  template <int NX, int NY, int NZ>
+  static bool resident_fits(const CtxData& c) {
+    using R = Res<NX, NY, NZ>;
+    int dev = c.device, smem_optin = 0, sms = 0;
+    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
+    return (size_t)smem_optin >= R::SMEM + 64 && NX <= sms;
+  }
+
+  bool resident_supported(const CtxData& c) const override {
+    if constexpr (!std::is_same<T, float>::value) {
+      return false;
+    } else {
+      if (c.kind != PFT_SCFT_REAL) return false;
+      if (c.n[0] != c.n[1] || c.n[1] != c.n[2]) return false;
+      switch (c.n[0]) {
+        case 64: return resident_fits<64, 64, 64>(c);
+        case 96: return resident_fits<96, 96, 96>(c);
+        case 128: return resident_fits<128, 128, 128>(c);
+        default: return false;
+      }
+    }
+  }
+
+  cudaError_t resident_march(CtxData& c, bool bwd) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      ResArgs a;
+      a.BA = (const float*)c.BA;
+      a.BB = (const float*)c.BB;
+      a.hist = (float*)c.hist;
+      a.qd0 = (const float*)c.qd0;
+      a.qd_out = (float*)c.qd[c.Ns & 1];
+      a.spec = (float2*)c.spec;
+      a.accA = (double*)c.accA;
+      a.accB = (double*)c.accB;
+      a.twx = tab<float2>(c, c.tw_off[0]);
+      a.twy = tab<float2>(c, c.tw_off[1]);
+      a.twz = tab<float2>(c, c.tw_off[2]);
+      a.twh = tab<float2>(c, c.tw_off[3]);
+      a.dx = tab<float>(c, c.d_off[0]);
+      a.dy = tab<float>(c, c.d_off[1]);
+      a.dz = tab<float>(c, c.d_off[2]);
+      a.Ns = c.Ns;
+      a.NsA = c.NsA;
+      a.bar = c.sync;
+      a.err = (int*)(c.sync + 2);
+      a.spin_limit = c.spin_limit;
+      // reset the arrival count and generation (a timed-out launch may leave them set)
+      cudaError_t e = cudaMemsetAsync(c.sync, 0, 2 * sizeof(unsigned), c.stream);
+      if (e != cudaSuccess) return e;
+      mark(c, bwd ? KK_MARCH_BWD : KK_MARCH_FWD);
+      switch (c.n[0]) {
+        case 64: return bwd ? launch_resident_n<64, 64, 64, true>(c, a) : launch_resident_n<64, 64, 64, false>(c, a);
+        case 96: return bwd ? launch_resident_n<96, 96, 96, true>(c, a) : launch_resident_n<96, 96, 96, false>(c, a);
+        case 128:
+          return bwd ? launch_resident_n<128, 128, 128, true>(c, a) : launch_resident_n<128, 128, 128, false>(c, a);
+        default: return cudaErrorNotSupported;
+      }
+    }
+  }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -181,13 +284,45 @@ class EngineT : public Engine {
     const size_t slice = (size_t)c.M * (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
     char* hist = (char*)c.hist;
     cudaError_t e;
+    const bool res = (c.march == 2);
+    if (res) {
+      // a fresh error word for this solve
+      if ((e = cudaMemsetAsync(c.sync, 0, 4 * sizeof(unsigned), c.stream)) != cudaSuccess) return e;
+    }
     // forward march (Eqs. 5, 13)
-    for (int n = 1; n <= c.Ns; n++) {
-      const void* B = (n <= c.NsA) ? c.BA : c.BB;
-      e = contour_step(c, hist + (size_t)(n - 1) * slice, B, hist + (size_t)n * slice, 0, nullptr, 0.0, 0.0);
-      if (e != cudaSuccess) return e;
+    if (res) {
+      if ((e = resident_march(c, false)) != cudaSuccess) return e;
+    } else {
+      for (int n = 1; n <= c.Ns; n++) {
+        const void* B = (n <= c.NsA) ? c.BA : c.BB;
+        e = contour_step(c, hist + (size_t)(n - 1) * slice, B, hist + (size_t)n * slice, 0, nullptr, 0.0, 0.0);
+        if (e != cudaSuccess) return e;
+      }
     }
     // Q (Eq. 4) and the qd_0 = 1 term of the quadrature
+    if ((e = solve_mid(c)) != cudaSuccess) return e;
+    double cA, cB;
+    // conjugate march with fused quadrature (Eq. 8)
+    if (res) {
+      if ((e = resident_march(c, true)) != cudaSuccess) return e;
+    }
+    for (int m = 1; m <= c.Ns && !res; m++) {
+      const int nb = c.Ns + 1 - m;  // split step index of this qd step
+      const void* B = (nb <= c.NsA) ? c.BA : c.BB;
+      const void* in = (m == 1) ? c.qd0 : c.qd[(m - 1) & 1];
+      void* out = c.qd[m & 1];
+      const int pn = c.Ns - m;  // forward slice paired with qd_m
+      trapezoid_weight(pn, c.Ns, c.NsA, &cA, &cB);
+      e = contour_step(c, in, B, out, 1, hist + (size_t)pn * slice, cA, cB);
+      if (e != cudaSuccess) return e;
+    }
+    // densities and force norms
+    return solve_tail(c);
+  }
+
+  cudaError_t solve_mid(CtxData& c) override {
+    const size_t slice = (size_t)c.M * (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
+    const char* hist = (const char*)c.hist;
     double cA, cB;
     trapezoid_weight(c.Ns, c.Ns, c.NsA, &cA, &cB);
     mark(c, KK_REDUCE);
@@ -200,19 +335,10 @@ class EngineT : public Engine {
     }
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_QSUM);
     k_observables<<<1, 32, 0, c.stream>>>(c.scal, (double)c.M, c.C);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // conjugate march with fused quadrature (Eq. 8)
-    for (int m = 1; m <= c.Ns; m++) {
-      const int nb = c.Ns + 1 - m;  // split step index of this qd step
-      const void* B = (nb <= c.NsA) ? c.BA : c.BB;
-      const void* in = (m == 1) ? c.qd0 : c.qd[(m - 1) & 1];
-      void* out = c.qd[m & 1];
-      const int pn = c.Ns - m;  // forward slice paired with qd_m
-      trapezoid_weight(pn, c.Ns, c.NsA, &cA, &cB);
-      e = contour_step(c, in, B, out, 1, hist + (size_t)pn * slice, cA, cB);
-      if (e != cudaSuccess) return e;
-    }
-    // densities and force norms
+    return cudaGetLastError();
+  }
+
+  cudaError_t solve_tail(CtxData& c) override {
     mark(c, KK_REDUCE);
     if (c.kind == PFT_SCFT_REAL) {
       k_finalize_real<<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.accA, (double*)c.accB, (const double*)c.wm,
@@ -225,8 +351,45 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
+  // ------------------------------------------------------------- a9: batches
+  cudaError_t batch_contour_step(const BatchGeom& g, const BatchStep* st, int nact, int epi,
+                                 cudaStream_t stream) override {
+    if (nact <= 0) return cudaSuccess;
+    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
+    const long long npen = (long long)nx * ny;
+    const long long nzc = g.nzh;
+    cudaError_t e = cudaSuccess;
+    if (g.kind == PFT_SCFT_REAL) {
+      PFT_BATCH_HALF(nz / 2, e = (bz_r2c<N>(st, npen, nact, stream)));
+    } else {
+      PFT_BATCH_AXIS(nz, e = (bz_c2c<N>(st, npen, nact, stream)));
+    }
+    if (e != cudaSuccess) return e;
+    PFT_BATCH_AXIS(ny, e = (bs<N, 0>(st, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, nact, stream)));
+    if (e != cudaSuccess) return e;
+    PFT_BATCH_AXIS(nx, e = (bs<N, 2>(st, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, nact, stream)));
+    if (e != cudaSuccess) return e;
+    PFT_BATCH_AXIS(ny, e = (bs<N, 1>(st, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, nact, stream)));
+    if (e != cudaSuccess) return e;
+    if (g.kind == PFT_SCFT_REAL) {
+      if (epi == 0) {
+        PFT_BATCH_HALF(nz / 2, e = (bzi_c2r<N, 0>(st, npen, nact, stream)));
+      } else {
+        PFT_BATCH_HALF(nz / 2, e = (bzi_c2r<N, 1>(st, npen, nact, stream)));
+      }
+    } else {
+      if (epi == 0) {
+        PFT_BATCH_AXIS(nz, e = (bzi_c2c<N, 0>(st, npen, nact, stream)));
+      } else {
+        PFT_BATCH_AXIS(nz, e = (bzi_c2c<N, 1>(st, npen, nact, stream)));
+      }
+    }
+    return e;
+  }
+
   cudaError_t enqueue_solve(CtxData& c) override {
-    if (!c.use_graph || c.profiling) return record_solve(c);
+    // the resident march is a handful of launches per solve: it runs without a graph
+    if (!c.use_graph || c.profiling || c.march == 2) return record_solve(c);
     if (!c.graph_valid) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
@@ -258,8 +421,8 @@ class EngineT : public Engine {
       const double std = sqrt(2.0 * lam / (c.C * dV));
       k_step_cl<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double2*)c.wp, (double2*)c.wm, (const double2*)c.accA,
                                                          (const double2*)c.accB, (Z*)c.BA, (Z*)c.BB, lam, std, eta_p,
-                                                         eta_m, c.seed, c.instance, (unsigned long long)c.step, c.ds,
-                                                         c.chiN, c.M, c.partials);
+                                                         eta_m, c.seed, c.instance, (unsigned long long)c.step,
+                                                         c.step_dev, c.ds, c.chiN, c.M, c.partials);
     }
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
     return cudaGetLastError();
@@ -364,6 +527,44 @@ class EngineT : public Engine {
   }
 
  private:
+  template <int N, int MODE>
+  static cudaError_t bs(const BatchStep* st, long long ncols, long long cin, long long s_outer, long long s_k, int nzc,
+                        int axis, int nact, cudaStream_t stream) {
+    constexpr int C = Tile<T>::C;
+    const dim3 grid((unsigned)((ncols + C - 1) / C), (unsigned)nact);
+    kb_strided<T, N, MODE><<<grid, C * Plan<N>::TPC, (size_t)N * C * sizeof(Z), stream>>>(st, ncols, cin, s_outer, s_k,
+                                                                                          nzc, axis);
+    return cudaGetLastError();
+  }
+  template <int N2>
+  static cudaError_t bz_r2c(const BatchStep* st, long long npen, int nact, cudaStream_t stream) {
+    constexpr int P = PencilsPerCta<T, N2>::v;
+    const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
+    kb_zf_r2c<T, N2><<<grid, P * Plan<N2>::TPC, (size_t)P * pencil_ld<T>(N2) * sizeof(Z), stream>>>(st, npen);
+    return cudaGetLastError();
+  }
+  template <int N2, int EPI>
+  static cudaError_t bzi_c2r(const BatchStep* st, long long npen, int nact, cudaStream_t stream) {
+    constexpr int P = PencilsPerCta<T, N2>::v;
+    const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
+    kb_zi_c2r<T, N2, EPI><<<grid, P * Plan<N2>::TPC, (size_t)P * pencil_ld<T>(N2) * sizeof(Z), stream>>>(st, npen);
+    return cudaGetLastError();
+  }
+  template <int N>
+  static cudaError_t bz_c2c(const BatchStep* st, long long npen, int nact, cudaStream_t stream) {
+    constexpr int P = PencilsPerCta<T, N>::v;
+    const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
+    kb_zf_c2c<T, N><<<grid, P * Plan<N>::TPC, (size_t)P * pencil_ld<T>(N) * sizeof(Z), stream>>>(st, npen);
+    return cudaGetLastError();
+  }
+  template <int N, int EPI>
+  static cudaError_t bzi_c2c(const BatchStep* st, long long npen, int nact, cudaStream_t stream) {
+    constexpr int P = PencilsPerCta<T, N>::v;
+    const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
+    kb_zi_c2c<T, N, EPI><<<grid, P * Plan<N>::TPC, (size_t)P * pencil_ld<T>(N) * sizeof(Z), stream>>>(st, npen);
+    return cudaGetLastError();
+  }
+
   template <typename P> static const P* tab(const CtxData& c, size_t off) {
     return reinterpret_cast<const P*>(reinterpret_cast<const char*>(c.tables) + off);
   }

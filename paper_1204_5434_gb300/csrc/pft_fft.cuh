@@ -105,17 +105,62 @@ template <bool INV, typename Z> struct Dft<8, INV, Z> {
   }
 };
 
+// 16-point DFT as 4 x 4: DFT-4 over n1 for each n2 (n = 4 n1 + n2), twiddle by
+// w16^(n2 k1), DFT-4 over n2 for each k1 (k = k1 + 4 k2).
+template <bool INV, typename Z> struct Dft<16, INV, Z> {
+  __device__ __forceinline__ static void run(Z* a) {
+    using S = decltype(a[0].x);
+    const S c1 = S(0.92387953251128675613), s1 = S(0.38268343236508977173);  // cos, sin(pi/8)
+    const S r2 = S(0.70710678118654752440);
+    Z b[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; n2++) {
+      Z t[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+      Dft<4, INV, Z>::run(t);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; k1++) b[n2][k1] = t[k1];
+    }
+    // twiddles w16^m, m = n2*k1 (forward: exp(-i pi m/8); inverse: conjugate)
+    const S sg = INV ? S(1) : S(-1);
+    auto tw = [&](Z z, S cr, S si) {  // z * (cr + i sg si)
+      Z r;
+      r.x = z.x * cr - z.y * sg * si;
+      r.y = z.x * sg * si + z.y * cr;
+      return r;
+    };
+    b[1][1] = tw(b[1][1], c1, s1);
+    b[1][2] = tw(b[1][2], r2, r2);
+    b[1][3] = tw(b[1][3], s1, c1);
+    b[2][1] = tw(b[2][1], r2, r2);
+    b[2][2] = rot90<INV>(b[2][2]);
+    b[2][3] = tw(b[2][3], -r2, r2);
+    b[3][1] = tw(b[3][1], s1, c1);
+    b[3][2] = tw(b[3][2], -r2, r2);
+    b[3][3] = tw(b[3][3], -c1, -s1);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; k1++) {
+      Z t[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
+      Dft<4, INV, Z>::run(t);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; k2++) a[k1 + 4 * k2] = t[k2];
+    }
+  }
+};
+
 // ------------------------------------------------------------------- FFT plans
 // Plan<N>: radices (applied first to last), elements per thread E (a multiple of
 // every radix), threads per column TPC = N/E.
 template <int... Rs> struct Radices {};
+// A plan: length N, E elements per thread, radices applied first to last.
+template <int N_, int E_, int... Rs> struct PlanX {
+  static constexpr int N = N_;
+  static constexpr int E = E_;
+  static constexpr int TPC = N_ / E_;
+  using R = Radices<Rs...>;
+};
 template <int N> struct Plan;
-#define PFT_PLAN(N_, E_, ...)                          \
-  template <> struct Plan<N_> {                         \
-    static constexpr int E = E_;                        \
-    static constexpr int TPC = N_ / E_;                 \
-    using R = Radices<__VA_ARGS__>;                     \
-  };
+#define PFT_PLAN(N_, E_, ...) \
+  template <> struct Plan<N_> : PlanX<N_, E_, __VA_ARGS__> {};
 PFT_PLAN(2, 2, 2)
 PFT_PLAN(3, 3, 3)
 PFT_PLAN(4, 4, 4)
@@ -174,21 +219,21 @@ __device__ __forceinline__ void fft_stages(cpx<T> (&v)[E], int t, const cpx<T>* 
   }
 }
 
-template <typename T, bool INV, int N, class X, int... Rs>
-__device__ __forceinline__ void fft_run(cpx<T> (&v)[Plan<N>::E], int t, const cpx<T>* __restrict__ tw, X& xch,
+template <typename T, bool INV, int N, int E, class X, int... Rs>
+__device__ __forceinline__ void fft_run(cpx<T> (&v)[E], int t, const cpx<T>* __restrict__ tw, X& xch,
                                         Radices<Rs...>) {
-  fft_stages<T, INV, N, Plan<N>::E, 1, X, Rs...>(v, t, tw, xch);
+  fft_stages<T, INV, N, E, 1, X, Rs...>(v, t, tw, xch);
 }
 
-// In-register transform of length N.  tw: exp(-2 pi i m / N), m = 0..N-1.
-template <typename T, bool INV, int N, class X>
-__device__ __forceinline__ void fft(cpx<T> (&v)[Plan<N>::E], int t, const cpx<T>* __restrict__ tw, X& xch) {
-  fft_run<T, INV, N, X>(v, t, tw, xch, typename Plan<N>::R{});
+// In-register transform of length N with plan PL.  tw: exp(-2 pi i m / N).
+template <typename T, bool INV, int N, class PL = Plan<N>, class X>
+__device__ __forceinline__ void fft(cpx<T> (&v)[PL::E], int t, const cpx<T>* __restrict__ tw, X& xch) {
+  static_assert(PL::N == N, "plan length");
+  fft_run<T, INV, N, PL::E, X>(v, t, tw, xch, typename PL::R{});
 }
 
 // Does the plan need exchanges (more than one stage)?
-template <int N> struct PlanStages;
-template <int N, int... Rs> __host__ __device__ constexpr int count_stages(Radices<Rs...>) { return sizeof...(Rs); }
-template <int N> __host__ __device__ constexpr int n_stages() { return count_stages<N>(typename Plan<N>::R{}); }
+template <int... Rs> __host__ __device__ constexpr int count_stages(Radices<Rs...>) { return sizeof...(Rs); }
+template <class PL> __host__ __device__ constexpr int n_stages() { return count_stages(typename PL::R{}); }
 
 }  // namespace pft

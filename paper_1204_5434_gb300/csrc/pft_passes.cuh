@@ -54,19 +54,17 @@ template <typename T, int N> struct PencilsPerCta {
 // dk[k]*dy[ky]*dz[kz], inverse (the x pass of a contour step); 3: multiply by the
 // same factor, inverse (completes a step whose forward x transform already ran).
 // Column col in [0, ncols): element k at data[(col / cin) * s_outer + col % cin + k * s_k].
-template <typename T, int N, int MODE>
-__global__ void __launch_bounds__(Tile<T>::C * Plan<N>::TPC)
-k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s_outer, long long s_k,
+template <typename T, int N, int MODE, class PL = Plan<N>, int C = Tile<T>::C>
+__device__ __forceinline__ void strided_body(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s_outer, long long s_k,
           const cpx<T>* __restrict__ tw, const T* __restrict__ dk, const T* __restrict__ dy,
-          const T* __restrict__ dz, int nzc) {
-  constexpr int C = Tile<T>::C;
-  constexpr int E = Plan<N>::E;
-  constexpr int TPC = Plan<N>::TPC;
+          const T* __restrict__ dz, int nzc, long long tile) {
+  constexpr int E = PL::E;
+  constexpr int TPC = PL::TPC;
   extern __shared__ __align__(16) unsigned char smraw[];
   cpx<T>* sm = reinterpret_cast<cpx<T>*>(smraw);
   const int c = threadIdx.x % C;
   const int t = threadIdx.x / C;
-  const long long col = (long long)blockIdx.x * C + c;
+  const long long col = (long long)tile * C + c;
   const bool valid = col < ncols;
   const long long colc = valid ? col : 0;
   const long long base = (colc / cin) * s_outer + (colc % cin);
@@ -77,9 +75,9 @@ k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s
   }
   XchCols<T> x{sm, C, c};
   if (MODE == 1) {
-    fft<T, true, N>(v, t, tw, x);
+    fft<T, true, N, PL>(v, t, tw, x);
   } else if (MODE != 3) {
-    fft<T, false, N>(v, t, tw, x);
+    fft<T, false, N, PL>(v, t, tw, x);
   }
   if (MODE == 2 || MODE == 3) {
     const long long ky = colc / nzc, kz = colc % nzc;
@@ -87,7 +85,7 @@ k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = cscale(v[i], dk[t + TPC * i] * dyz);
     // the forward transform ended with a barrier after its last shared-memory reads
-    fft<T, true, N>(v, t, tw, x);
+    fft<T, true, N, PL>(v, t, tw, x);
   }
   if (valid) {
 #pragma unroll
@@ -95,14 +93,21 @@ k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s
   }
 }
 
+template <typename T, int N, int MODE, class PL = Plan<N>, int C = Tile<T>::C>
+__global__ void __launch_bounds__(C * PL::TPC)
+k_strided(cpx<T>* __restrict__ data, long long ncols, long long cin, long long s_outer, long long s_k,
+          const cpx<T>* __restrict__ tw, const T* __restrict__ dk, const T* __restrict__ dy,
+          const T* __restrict__ dz, int nzc) {
+  strided_body<T, N, MODE, PL, C>(data, ncols, cin, s_outer, s_k, tw, dk, dy, dz, nzc, (long long)blockIdx.x);
+}
+
 // ----------------------------------------------------------- z passes, real
 // Forward: pencil of nz = 2*N2 reals (times B) packed as N2 complex pairs, complex
 // transform of length N2, then the even/odd split into the nz/2+1 half spectrum.
 // twh: exp(-2 pi i m/N2); twf: exp(-2 pi i m/nz).
 template <typename T, int N2>
-__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
-k_zf_r2c(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
-         const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf) {
+__device__ __forceinline__ void zf_r2c_body(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
+         const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf, long long tile) {
   constexpr int P = PencilsPerCta<T, N2>::v;
   constexpr int E = Plan<N2>::E;
   constexpr int TPC = Plan<N2>::TPC;
@@ -110,7 +115,7 @@ k_zf_r2c(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ 
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = threadIdx.x % TPC;
   const int p = threadIdx.x / TPC;
-  const long long pen = (long long)blockIdx.x * P + p;
+  const long long pen = (long long)tile * P + p;
   const bool valid = pen < npen;
   const long long pc = valid ? pen : 0;
   XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
@@ -149,14 +154,20 @@ k_zf_r2c(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ 
   }
 }
 
+template <typename T, int N2>
+__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
+k_zf_r2c(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
+         const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf) {
+  zf_r2c_body<T, N2>(q, B, spec, npen, twh, twf, (long long)blockIdx.x);
+}
+
 // Inverse: half spectrum -> N2 complex (even/odd merge, unnormalised) -> inverse
 // transform -> nz reals.  EPI 0: out = B*y; EPI 1: out = B*y and
 // accA += cA*out*partner, accB += cB*out*partner (FP64); EPI 2: out = y.
 template <typename T, int N2, int EPI>
-__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
-k_zi_c2r(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict__ qout,
+__device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict__ qout,
          const T* __restrict__ partner, double* __restrict__ accA, double* __restrict__ accB, double cA,
-         double cB, long long npen, const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf) {
+         double cB, long long npen, const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf, long long tile) {
   constexpr int P = PencilsPerCta<T, N2>::v;
   constexpr int E = Plan<N2>::E;
   constexpr int TPC = Plan<N2>::TPC;
@@ -164,7 +175,7 @@ k_zi_c2r(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = threadIdx.x % TPC;
   const int p = threadIdx.x / TPC;
-  const long long pen = (long long)blockIdx.x * P + p;
+  const long long pen = (long long)tile * P + p;
   const bool valid = pen < npen;
   const long long pc = valid ? pen : 0;
   XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
@@ -224,12 +235,19 @@ k_zi_c2r(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict
   }
 }
 
+template <typename T, int N2, int EPI>
+__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
+k_zi_c2r(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict__ qout,
+         const T* __restrict__ partner, double* __restrict__ accA, double* __restrict__ accB, double cA,
+         double cB, long long npen, const cpx<T>* __restrict__ twh, const cpx<T>* __restrict__ twf) {
+  zi_c2r_body<T, N2, EPI>(spec, B, qout, partner, accA, accB, cA, cB, npen, twh, twf, (long long)blockIdx.x);
+}
+
 // -------------------------------------------------------- z passes, complex
 // Forward: pencil of nz complex values times complex B, transform of length nz.
 template <typename T, int N>
-__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
-k_zf_c2c(const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
-         const cpx<T>* __restrict__ tw) {
+__device__ __forceinline__ void zf_c2c_body(const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
+         const cpx<T>* __restrict__ tw, long long tile) {
   constexpr int P = PencilsPerCta<T, N>::v;
   constexpr int E = Plan<N>::E;
   constexpr int TPC = Plan<N>::TPC;
@@ -237,7 +255,7 @@ k_zf_c2c(const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ B, cpx<T>* __r
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = threadIdx.x % TPC;
   const int p = threadIdx.x / TPC;
-  const long long pen = (long long)blockIdx.x * P + p;
+  const long long pen = (long long)tile * P + p;
   const bool valid = pen < npen;
   const long long o = (valid ? pen : 0) * N;
   XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
@@ -255,13 +273,19 @@ k_zf_c2c(const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ B, cpx<T>* __r
   }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
+k_zf_c2c(const cpx<T>* __restrict__ q, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ spec, long long npen,
+         const cpx<T>* __restrict__ tw) {
+  zf_c2c_body<T, N>(q, B, spec, npen, tw, (long long)blockIdx.x);
+}
+
 // Inverse: transform of length nz, then the epilogue (EPI as for k_zi_c2r, complex
 // products, no conjugation: the density sums are bilinear in q and qd).
 template <typename T, int N, int EPI>
-__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
-k_zi_c2c(const cpx<T>* __restrict__ spec, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ qout,
+__device__ __forceinline__ void zi_c2c_body(const cpx<T>* __restrict__ spec, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ qout,
          const cpx<T>* __restrict__ partner, double2* __restrict__ accA, double2* __restrict__ accB, double cA,
-         double cB, long long npen, const cpx<T>* __restrict__ tw) {
+         double cB, long long npen, const cpx<T>* __restrict__ tw, long long tile) {
   constexpr int P = PencilsPerCta<T, N>::v;
   constexpr int E = Plan<N>::E;
   constexpr int TPC = Plan<N>::TPC;
@@ -269,7 +293,7 @@ k_zi_c2c(const cpx<T>* __restrict__ spec, const cpx<T>* __restrict__ B, cpx<T>* 
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = threadIdx.x % TPC;
   const int p = threadIdx.x / TPC;
-  const long long pen = (long long)blockIdx.x * P + p;
+  const long long pen = (long long)tile * P + p;
   const bool valid = pen < npen;
   const long long o = (valid ? pen : 0) * N;
   XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
@@ -303,6 +327,14 @@ k_zi_c2c(const cpx<T>* __restrict__ spec, const cpx<T>* __restrict__ B, cpx<T>* 
       }
     }
   }
+}
+
+template <typename T, int N, int EPI>
+__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
+k_zi_c2c(const cpx<T>* __restrict__ spec, const cpx<T>* __restrict__ B, cpx<T>* __restrict__ qout,
+         const cpx<T>* __restrict__ partner, double2* __restrict__ accA, double2* __restrict__ accB, double cA,
+         double cB, long long npen, const cpx<T>* __restrict__ tw) {
+  zi_c2c_body<T, N, EPI>(spec, B, qout, partner, accA, accB, cA, cB, npen, tw, (long long)blockIdx.x);
 }
 
 }  // namespace pft

@@ -1,0 +1,430 @@
+// pft_resident.cuh -- the whole forward or conjugate march of a real-field (SCFT)
+// system in ONE persistent cooperative launch, FP32 propagators.
+//
+// One CTA per x-plane (grid = nx CTAs, one per SM).  Each CTA keeps, in shared memory
+// for the whole march, the two Boltzmann-factor planes B_A(p,:,:), B_B(p,:,:) and one
+// work plane.  A contour step (the split step of Eq. 13) is
+//   rows    : z inverse (C2R) of the previous step, x B_n, store q_n / accumulate
+//             the quadrature of Eq. 8, x B_{n+1}, z forward (R2C)   -- registers + smem
+//   columns : y forward transform of the plane                        -- smem
+//   store plane to the global spectrum, grid barrier
+//   x phase : this CTA's (ky,kz) columns: x forward, x D(k)/M, x inverse -- smem
+//   grid barrier, load plane, y inverse transform                     -- smem
+// so the only global traffic per step is the two spectrum transposes through L2 and the
+// q history (written by the forward march, read once by the conjugate march).
+// Grid barriers are bounded spin waits: on expiry the kernel sets an error word and
+// every CTA returns.
+#pragma once
+#include "pft_passes.cuh"
+
+namespace pft {
+
+struct ResArgs {
+  const float* BA;
+  const float* BB;
+  float* hist;          // (Ns+1) slices of M reals
+  const float* qd0;     // initial conjugate propagator
+  float* qd_out;        // last conjugate slice (conjugate march)
+  float2* spec;         // [nx][ny][nz/2+1]
+  double* accA;         // FP64 quadrature sums (conjugate march)
+  double* accB;
+  const float2* twx;
+  const float2* twy;
+  const float2* twz;    // length nz
+  const float2* twh;    // length nz/2
+  const float* dx;      // includes 1/M
+  const float* dy;
+  const float* dz;
+  int Ns;
+  int NsA;
+  unsigned* bar;        // [0] arrival count, [1] generation
+  int* err;             // [0] set on a barrier timeout
+  long long spin_limit; // clock64 cycles one barrier may wait
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier of nblk co-resident CTAs.  Returns false (in every thread) if the
+// wait exceeded its budget or another CTA already failed.
+__device__ __forceinline__ bool grid_barrier(const ResArgs& a, unsigned nblk, int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    const unsigned gen = ld_acquire_u32(a.bar + 1);
+    const unsigned old = atom_add_acq_rel_u32(a.bar, 1u);
+    if (old == nblk - 1) {
+      a.bar[0] = 0u;
+      st_release_u32(a.bar + 1, gen + 1u);
+    } else {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(a.bar + 1) == gen) {
+        if (*(volatile int*)a.err) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > a.spin_limit) {
+          atomicExch(a.err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+// Row exchange: the row region of the work plane, one pad slot every 16 complex.
+struct XRow {
+  float2* s;
+  __device__ __forceinline__ static int idx(int pos) { return pos + (pos >> 4); }
+  __device__ __forceinline__ void put(int pos, float2 z) { s[idx(pos)] = z; }
+  __device__ __forceinline__ float2 get(int pos) const { return s[idx(pos)]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+// Column exchange in the padded plane: element (pos, column) at pos*ld + off.
+struct XCol {
+  float2* s;
+  int ld;
+  int off;
+  __device__ __forceinline__ void put(int pos, float2 z) { s[pos * ld + off] = z; }
+  __device__ __forceinline__ float2 get(int pos) const { return s[pos * ld + off]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+
+template <int NX, int NY, int NZ>
+struct Res {
+  // 33 column groups of 16 threads at NY=128, so the 65 half-spectrum columns take
+  // two rounds in the y and x phases; 512 threads elsewhere.
+  static constexpr int THREADS = (NY == 128) ? 528 : 512;
+  static constexpr int N2 = NZ / 2;
+  static constexpr int NZH = NZ / 2 + 1;
+  static constexpr int LDP = N2 + (N2 >> 4) + 2;  // padded row of the work plane (complex)
+  static constexpr int ZT = Plan<N2>::TPC, ZE = Plan<N2>::E;
+  static constexpr int YT = Plan<NY>::TPC, YE = Plan<NY>::E;
+  static constexpr int XT = Plan<NX>::TPC, XE = Plan<NX>::E;
+  static constexpr int ROWS = THREADS / ZT;        // rows per round
+  static constexpr int YCOLS = THREADS / YT;       // y columns per round
+  static constexpr int XCPR = THREADS / XT;        // x columns per round
+  static constexpr int NCOL = NY * NZH;            // (ky,kz) columns of the x phase
+  static constexpr int XCOLS = (NCOL + NX - 1) / NX;  // x columns per CTA
+  static constexpr int PLANE_C = NY * LDP;
+  static constexpr int TILE_C = NX * XCOLS;
+  static constexpr int WORK_C = PLANE_C > TILE_C ? PLANE_C : TILE_C;
+  static constexpr size_t SMEM = (size_t)2 * NY * NZ * sizeof(float) + (size_t)WORK_C * sizeof(float2);
+  static constexpr int PLANE_E = NY * NZH;                      // spectrum plane elements
+  static constexpr int PLANE_K = (PLANE_E + THREADS - 1) / THREADS;  // per thread
+  static_assert(THREADS % ZT == 0, "row rounds");
+  static_assert(THREADS % YT == 0 && THREADS % XT == 0, "column rounds");
+};
+
+// ------------------------------------------------------------------- phases
+// Rows of the plane: [optional inverse z + epilogue] then [optional forward z].
+// MODE_IN 0: input row = q from global `qin` (first step); 1: input = inverse z
+// transform of the work-plane row.  Epilogue (when MODE_IN == 1): y = Bcur * z^-1[...],
+// stored to `qstore` (if non-null); if acc: accA += cA y partner, accB += cB y partner.
+// Forward (when Bnext != null): work-plane row <- half spectrum of Bnext * y.
+template <int NX, int NY, int NZ>
+__device__ __forceinline__ void row_phase(float2* __restrict__ W, int p, int mode_in, const float* __restrict__ qin,
+                                          const float* __restrict__ Bcur, float* __restrict__ qstore,
+                                          const float* __restrict__ partner, double* __restrict__ accA,
+                                          double* __restrict__ accB, double cA, double cB,
+                                          const float* __restrict__ Bnext, const ResArgs& a) {
+  using R = Res<NX, NY, NZ>;
+  constexpr int N2 = R::N2, E = R::ZE, TPC = R::ZT;
+  const int t = threadIdx.x % TPC;
+  const int rr = threadIdx.x / TPC;
+#pragma unroll 1
+  for (int r0 = 0; r0 < NY; r0 += R::ROWS) {
+    // threads past the last row repeat it: identical shared-memory values, and no
+    // global side effects (their stores and accumulations are skipped)
+    const bool dup = (r0 + rr >= NY);
+    const int y = dup ? NY - 1 : r0 + rr;
+    XRow x{W + y * R::LDP};
+    const long long rowoff = ((long long)p * NY + y) * NZ;  // first real of this row
+    float2 v[E];
+    if (mode_in == 0) {
+      const float2* q2 = reinterpret_cast<const float2*>(qin + rowoff);
+#pragma unroll
+      for (int i = 0; i < E; i++) v[i] = q2[t + TPC * i];
+    } else {
+      // partner slice of the quadrature: issue its loads before the transform
+      float2 pv[E];
+      const bool acc_on = (partner != nullptr) && !dup;
+      if (acc_on) {
+        const float2* pp = reinterpret_cast<const float2*>(partner + rowoff);
+#pragma unroll
+        for (int i = 0; i < E; i++) pv[i] = __ldcs(pp + t + TPC * i);
+      }
+      // half spectrum -> N2 complex (even/odd merge), inverse transform
+      float2 xk[E], xc[E];
+#pragma unroll
+      for (int i = 0; i < E; i++) {
+        const int k = t + TPC * i;
+        xk[i] = x.get(k);
+        xc[i] = cconj(x.get(N2 - k));
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < E; i++) {
+        const int k = t + TPC * i;
+        const float2 d = rot90<true>(cmulc(csub(xk[i], xc[i]), a.twz[k]));
+        v[i] = cadd(cadd(xk[i], xc[i]), d);
+      }
+      fft<float, true, N2>(v, t, a.twh, x);
+      const float2* b2 = reinterpret_cast<const float2*>(Bcur + (long long)y * NZ);
+      float2* qs = (qstore && !dup) ? reinterpret_cast<float2*>(qstore + rowoff) : nullptr;
+#pragma unroll
+      for (int i = 0; i < E; i++) {
+        const int m = t + TPC * i;
+        const float2 b = b2[m];
+        float2 yv = v[i];
+        yv.x *= b.x;
+        yv.y *= b.y;
+        v[i] = yv;
+        if (qs) __stcs(qs + m, yv);
+      }
+      if (acc_on) {
+        // one block is active except at the junction slice, where both get 1/2
+        for (int blk = 0; blk < 2; blk++) {
+          const double c = blk ? cB : cA;
+          if (c == 0.0) continue;
+          double2* acc = reinterpret_cast<double2*>((blk ? accB : accA) + rowoff);
+          double2 av[E];
+#pragma unroll
+          for (int i = 0; i < E; i++) av[i] = acc[t + TPC * i];
+#pragma unroll
+          for (int i = 0; i < E; i++) {
+            av[i].x += c * ((double)v[i].x * (double)pv[i].x);
+            av[i].y += c * ((double)v[i].y * (double)pv[i].y);
+            acc[t + TPC * i] = av[i];
+          }
+        }
+      }
+    }
+    if (Bnext) {
+      const float2* b2 = reinterpret_cast<const float2*>(Bnext + (long long)y * NZ);
+#pragma unroll
+      for (int i = 0; i < E; i++) {
+        const float2 b = b2[t + TPC * i];
+        v[i].x *= b.x;
+        v[i].y *= b.y;
+      }
+      if (mode_in == 1) __syncthreads();  // inverse transform's reads of this row are done
+      fft<float, false, N2>(v, t, a.twh, x);
+#pragma unroll
+      for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
+      __syncthreads();
+      float2 zc[E];
+#pragma unroll
+      for (int i = 0; i < E; i++) {
+        const int k = t + TPC * i;
+        zc[i] = cconj(x.get(k == 0 ? 0 : N2 - k));
+      }
+      __syncthreads();
+      const float h = 0.5f;
+#pragma unroll
+      for (int i = 0; i < E; i++) {
+        const int k = t + TPC * i;
+        const float2 ev = cscale(cadd(v[i], zc[i]), h);
+        const float2 od = cscale(rot90<false>(csub(v[i], zc[i])), h);
+        x.put(k, cadd(ev, cmul(a.twz[k], od)));
+      }
+      if (t == 0) x.put(N2, make_float2(v[0].x - v[0].y, 0.f));
+    }
+    __syncthreads();
+  }
+}
+
+// y transforms of all NZH columns of the work plane, in place.  Idle column groups of
+// the last round repeat the last column (identical values, identical writes).
+template <int NX, int NY, int NZ, bool INV>
+__device__ __forceinline__ void col_phase(float2* __restrict__ W, const ResArgs& a) {
+  using R = Res<NX, NY, NZ>;
+  constexpr int E = R::YE, TPC = R::YT;
+  const int c = threadIdx.x % R::YCOLS;
+  const int t = threadIdx.x / R::YCOLS;
+#pragma unroll 1
+  for (int c0 = 0; c0 < R::NZH; c0 += R::YCOLS) {
+    int kz = c0 + c;
+    if (kz >= R::NZH) kz = R::NZH - 1;
+    XCol x{W, R::LDP, XRow::idx(kz)};
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = x.get(t + TPC * i);
+    __syncthreads();
+    fft<float, INV, NY>(v, t, a.twy, x);
+#pragma unroll
+    for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
+    __syncthreads();
+  }
+}
+
+// Work plane <-> global spectrum plane p.  Loads are staged through registers so that
+// every load of the plane is in flight at once.
+template <int NX, int NY, int NZ, bool STORE>
+__device__ __forceinline__ void plane_copy(float2* __restrict__ W, float2* __restrict__ spec, int p) {
+  using R = Res<NX, NY, NZ>;
+  float2* g = spec + (long long)p * R::PLANE_E;
+  if (STORE) {
+#pragma unroll 4
+    for (int e = threadIdx.x; e < R::PLANE_E; e += R::THREADS) {
+      const int ky = e / R::NZH, kz = e - ky * R::NZH;
+      g[e] = W[ky * R::LDP + XRow::idx(kz)];
+    }
+  } else {
+    float2 r[R::PLANE_K];
+#pragma unroll
+    for (int k = 0; k < R::PLANE_K; k++) {
+      const int e = threadIdx.x + k * R::THREADS;
+      if (e < R::PLANE_E) r[k] = g[e];
+    }
+#pragma unroll
+    for (int k = 0; k < R::PLANE_K; k++) {
+      const int e = threadIdx.x + k * R::THREADS;
+      if (e < R::PLANE_E) {
+        const int ky = e / R::NZH, kz = e - ky * R::NZH;
+        W[ky * R::LDP + XRow::idx(kz)] = r[k];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// x phase: columns [cb, ce) of the flattened (ky,kz) index: load, forward x, x D/M,
+// inverse x, store.
+template <int NX, int NY, int NZ>
+__device__ __forceinline__ void x_phase(float2* __restrict__ W, int cta, const ResArgs& a) {
+  using R = Res<NX, NY, NZ>;
+  constexpr int E = R::XE, TPC = R::XT;
+  const int cb = cta * R::XCOLS;
+  const int ce = (cb + R::XCOLS < R::NCOL) ? cb + R::XCOLS : R::NCOL;
+  const int nc = ce - cb;
+  if (nc <= 0) return;  // uniform per CTA
+  {
+    constexpr int K = (NX * R::XCOLS + R::THREADS - 1) / R::THREADS;
+    float2 r[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const int e = threadIdx.x + k * R::THREADS;
+      const int x = e / R::XCOLS, j = e - x * R::XCOLS;
+      if (e < NX * R::XCOLS && j < nc) r[k] = a.spec[(long long)x * R::NCOL + cb + j];
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+      const int e = threadIdx.x + k * R::THREADS;
+      if (e < NX * R::XCOLS) W[e] = r[k];
+    }
+  }
+  __syncthreads();
+  const int c = threadIdx.x % R::XCPR;
+  const int t = threadIdx.x / R::XCPR;
+#pragma unroll 1
+  for (int j0 = 0; j0 < nc; j0 += R::XCPR) {
+    int j = j0 + c;
+    if (j >= nc) j = nc - 1;
+    XCol x{W, R::XCOLS, j};
+    float2 v[E];
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = x.get(t + TPC * i);
+    __syncthreads();
+    fft<float, false, NX>(v, t, a.twx, x);
+    const int col = cb + j;
+    const int ky = col / R::NZH, kz = col - ky * R::NZH;
+    const float dyz = a.dy[ky] * a.dz[kz];
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], a.dx[t + TPC * i] * dyz);
+    fft<float, true, NX>(v, t, a.twx, x);
+#pragma unroll
+    for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
+    __syncthreads();
+  }
+#pragma unroll 4
+  for (int e = threadIdx.x; e < NX * R::XCOLS; e += R::THREADS) {
+    const int x = e / R::XCOLS, j = e - x * R::XCOLS;
+    if (j < nc) a.spec[(long long)x * R::NCOL + cb + j] = W[e];
+  }
+}
+
+// Trapezoid weight of slice n on each block (the quadrature rule of Eq. 8 used here).
+__device__ __forceinline__ void res_weights(int n, int Ns, int NsA, double* cA, double* cB) {
+  *cA = 0.0;
+  *cB = 0.0;
+  if (NsA > 0 && n <= NsA) *cA = (n == 0 || n == NsA) ? 0.5 : 1.0;
+  if (NsA < Ns && n >= NsA) *cB = (n == NsA || n == Ns) ? 0.5 : 1.0;
+}
+
+// The march.  BWD = false: q_1..q_Ns into the history from q_0 = hist[0].
+// BWD = true: qd_1..qd_Ns from qd0 with the fused quadrature against the history.
+template <int NX, int NY, int NZ, bool BWD>
+__global__ void __launch_bounds__(Res<NX, NY, NZ>::THREADS, 1) k_resident_march(ResArgs a) {
+  using R = Res<NX, NY, NZ>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ int s_flag;
+  float* sBA = reinterpret_cast<float*>(smraw);
+  float* sBB = sBA + NY * NZ;
+  float2* W = reinterpret_cast<float2*>(sBB + NY * NZ);
+  const int p = blockIdx.x;
+  const long long M = (long long)NX * NY * NZ;
+  const long long poff = (long long)p * NY * NZ;
+  {
+    const float4* gA = reinterpret_cast<const float4*>(a.BA + poff);
+    const float4* gB = reinterpret_cast<const float4*>(a.BB + poff);
+    float4* tA = reinterpret_cast<float4*>(sBA);
+    float4* tB = reinterpret_cast<float4*>(sBB);
+    for (int e = threadIdx.x; e < NY * NZ / 4; e += R::THREADS) {
+      tA[e] = gA[e];
+      tB[e] = gB[e];
+    }
+    __syncthreads();
+  }
+  const int Ns = a.Ns, NsA = a.NsA;
+  // Split-step index of march step s (1..Ns): forward uses n = s, conjugate n = Ns+1-s.
+  auto Bof = [&](int s) -> const float* {
+    const int n = BWD ? Ns + 1 - s : s;
+    return (n <= NsA) ? sBA : sBB;
+  };
+  // first step: rows of the initial condition (global) times B, forward z
+  row_phase<NX, NY, NZ>(W, p, 0, BWD ? a.qd0 : a.hist, nullptr, nullptr, nullptr, nullptr, nullptr, 0.0, 0.0,
+                        Bof(1), a);
+#pragma unroll 1
+  for (int s = 1; s <= Ns; s++) {
+    col_phase<NX, NY, NZ, false>(W, a);
+    plane_copy<NX, NY, NZ, true>(W, a.spec, p);
+    if (!grid_barrier(a, gridDim.x, &s_flag)) return;
+    x_phase<NX, NY, NZ>(W, p, a);
+    if (!grid_barrier(a, gridDim.x, &s_flag)) return;
+    plane_copy<NX, NY, NZ, false>(W, a.spec, p);
+    col_phase<NX, NY, NZ, true>(W, a);
+    const float* Bn = Bof(s);
+    const float* Bnext = (s < Ns) ? Bof(s + 1) : nullptr;
+    if (!BWD) {
+      row_phase<NX, NY, NZ>(W, p, 1, nullptr, Bn, a.hist + (long long)s * M, nullptr, nullptr, nullptr, 0.0, 0.0,
+                            Bnext, a);
+    } else {
+      const int pn = Ns - s;  // forward slice paired with qd_s
+      double cA, cB;
+      res_weights(pn, Ns, NsA, &cA, &cB);
+      row_phase<NX, NY, NZ>(W, p, 1, nullptr, Bn, (s == Ns) ? a.qd_out : nullptr, a.hist + (long long)pn * M,
+                            a.accA, a.accB, cA, cB, Bnext, a);
+    }
+  }
+}
+
+}  // namespace pft

@@ -23,6 +23,8 @@ PFT_SCFT_REAL, PFT_CL_COMPLEX = 0, 1
 PFT_FP64, PFT_FP32_MIXED = 0, 1
 PFT_HOST, PFT_DEVICE = 0, 1
 PFT_STEP_SCFT_EULER, PFT_STEP_CL_EULER_MARUYAMA = 0, 1
+PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT = 0, 1, 2
+PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
 
 
 class pft_grid(ct.Structure):
@@ -39,7 +41,7 @@ class pft_model(ct.Structure):
 
 class pft_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("use_graph", ct.c_int), ("stream", ct.c_void_p),
-                ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong)]
+                ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong), ("march", ct.c_int)]
 
 
 class pft_obs(ct.Structure):
@@ -54,6 +56,10 @@ class pft_obs(ct.Structure):
                 "phiA_mean": z(self.phiA_mean), "phiB_mean": z(self.phiB_mean),
                 "force_p_rms": self.force_p_rms, "force_m_rms": self.force_m_rms,
                 "fA_eff": self.fA_eff, "NsA": self.NsA, "step": self.step}
+
+
+class pft_instance_desc(ct.Structure):
+    _fields_ = [("grid", pft_grid), ("chain", pft_chain), ("model", pft_model), ("seed", ct.c_ulonglong)]
 
 
 class pft_profile(ct.Structure):
@@ -101,12 +107,25 @@ _SIGS = {
     "pft_get_densities": (ct.c_int, [_P, _P, _P, ct.c_int]),
     "pft_field_step": (ct.c_int, [_P, ct.c_int, ct.c_double, _P, _P, ct.c_int]),
     "pft_gradients": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int]),
+    "pft_batch_create": (ct.c_int, [ct.POINTER(ct.c_void_p), ct.c_int, ct.POINTER(pft_instance_desc), ct.c_int,
+                                     _P]),
+    "pft_batch_destroy": (ct.c_int, [_P]),
+    "pft_batch_set_fields": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
+    "pft_batch_get_fields": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
+    "pft_batch_run": (ct.c_int, [_P, ct.c_int, ct.c_double, ct.c_double, ct.c_int]),
+    "pft_batch_get_observables": (ct.c_int, [_P, ct.c_int, ct.POINTER(pft_obs)]),
+    "pft_batch_get_densities": (ct.c_int, [_P, ct.c_int, _P, _P, ct.c_int]),
+    "pft_batch_synchronize": (ct.c_int, [_P]),
+    "pft_batch_info": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int), ct.POINTER(ct.c_longlong)]),
+    "pft_batch_get_stream": (ct.c_int, [_P, ct.POINTER(ct.c_void_p)]),
     "pft_profile_step": (ct.c_int, [_P, ct.c_int, ct.c_double, ct.POINTER(pft_profile)]),
     "pft_contour_step_static": (ct.c_int, [ct.POINTER(ct.c_int), ct.POINTER(ct.c_double), ct.c_int, _P, _P, _P,
                                             _P]),
     "pft_fft3d": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int]),
     "pft_get_propagator": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, ct.c_int]),
     "pft_debug_set_q0": (ct.c_int, [_P, _P, ct.c_int]),
+    "pft_debug_set_spin_limit": (ct.c_int, [_P, ct.c_longlong]),
+    "pft_get_march": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_philox_normals": (ct.c_int, [ct.c_ulonglong, ct.c_ulonglong, ct.c_ulonglong, ct.c_int, ct.c_longlong,
                                       _P, _P]),
     "pft_philox_raw": (ct.c_int, [ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint), ct.c_longlong, _P, _P]),
@@ -171,11 +190,12 @@ def pft_last_error() -> str:
 
 
 def pft_create(n, L, Ns, fA, chiN, C, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True, stream=None,
-               seed=0, instance=0):
+               seed=0, instance=0, march=PFT_MARCH_AUTO):
     g = pft_grid((ct.c_int * 3)(*[int(v) for v in n]), (ct.c_double * 3)(*[float(v) for v in L]))
     ch = pft_chain(int(Ns), float(fA))
     m = pft_model(float(chiN), float(C), int(kind))
-    o = pft_opts(int(precision), 1 if use_graph else 0, ct.c_void_p(stream or 0), int(seed), int(instance))
+    o = pft_opts(int(precision), 1 if use_graph else 0, ct.c_void_p(stream or 0), int(seed), int(instance),
+                 int(march))
     h = ct.c_void_p()
     _check(_lib().pft_create(ct.byref(h), ct.byref(g), ct.byref(ch), ct.byref(m), ct.byref(o)), "pft_create")
     return h
@@ -251,6 +271,67 @@ def pft_gradients(h, dH_dwp=None, dH_dwm=None):
     return tuple(dL), tuple(dq)
 
 
+def pft_batch_create(instances, precision=PFT_FP32_MIXED, stream=None):
+    """instances: list of dicts with n, L, Ns, fA, chiN, C, kind, seed."""
+    arr = (pft_instance_desc * len(instances))()
+    for i, d in enumerate(instances):
+        arr[i].grid = pft_grid((ct.c_int * 3)(*[int(v) for v in d["n"]]), (ct.c_double * 3)(*[float(v) for v in d["L"]]))
+        arr[i].chain = pft_chain(int(d["Ns"]), float(d["fA"]))
+        arr[i].model = pft_model(float(d["chiN"]), float(d["C"]), int(d["kind"]))
+        arr[i].seed = int(d.get("seed", 0))
+    h = ct.c_void_p()
+    _check(_lib().pft_batch_create(ct.byref(h), len(instances), arr, int(precision), stream), "pft_batch_create")
+    return h
+
+
+def pft_batch_destroy(b):
+    _check(_lib().pft_batch_destroy(b), "pft_batch_destroy")
+
+
+def pft_batch_set_fields(b, i, wp, wm):
+    w = _where(wp, wm)
+    _check(_lib().pft_batch_set_fields(b, int(i), _ptr(wp)[0], _ptr(wm)[0], w), "pft_batch_set_fields")
+
+
+def pft_batch_get_fields(b, i, wp, wm):
+    w = _where(wp, wm)
+    _check(_lib().pft_batch_get_fields(b, int(i), _ptr(wp, True)[0], _ptr(wm, True)[0], w), "pft_batch_get_fields")
+
+
+def pft_batch_run(b, updates, lam, dt, mode=PFT_BATCH_GRAPHED):
+    _check(_lib().pft_batch_run(b, int(updates), float(lam), float(dt), int(mode)), "pft_batch_run")
+
+
+def pft_batch_get_observables(b, i) -> dict:
+    o = pft_obs()
+    _check(_lib().pft_batch_get_observables(b, int(i), ct.byref(o)), "pft_batch_get_observables")
+    return o.as_dict()
+
+
+def pft_batch_get_densities(b, i, phiA, phiB):
+    w = _where(phiA, phiB)
+    _check(_lib().pft_batch_get_densities(b, int(i), _ptr(phiA, True)[0], _ptr(phiB, True)[0], w),
+           "pft_batch_get_densities")
+
+
+def pft_batch_synchronize(b):
+    _check(_lib().pft_batch_synchronize(b), "pft_batch_synchronize")
+
+
+def pft_batch_info(b):
+    u = ct.c_double()
+    c = ct.c_int()
+    n = ct.c_longlong()
+    _check(_lib().pft_batch_info(b, ct.byref(u), ct.byref(c), ct.byref(n)), "pft_batch_info")
+    return {"units_per_update": u.value, "classes": c.value, "launches": n.value}
+
+
+def pft_batch_get_stream(b) -> int:
+    s = ct.c_void_p()
+    _check(_lib().pft_batch_get_stream(b, ct.byref(s)), "pft_batch_get_stream")
+    return s.value or 0
+
+
 def pft_profile_step(h, step_kind=-1, lam_or_dt=0.0) -> dict:
     p = pft_profile()
     _check(_lib().pft_profile_step(h, int(step_kind), float(lam_or_dt), ct.byref(p)), "pft_profile_step")
@@ -281,6 +362,16 @@ def pft_debug_set_q0(h, q0=None):
     _check(_lib().pft_debug_set_q0(h, p, w), "pft_debug_set_q0")
 
 
+def pft_debug_set_spin_limit(h, cycles):
+    _check(_lib().pft_debug_set_spin_limit(h, int(cycles)), "pft_debug_set_spin_limit")
+
+
+def pft_get_march(h) -> int:
+    m = ct.c_int()
+    _check(_lib().pft_get_march(h, ct.byref(m)), "pft_get_march")
+    return m.value
+
+
 def pft_philox_normals(seed, instance, step, field, M, out_device, stream=None):
     p, w = _ptr(out_device, True)
     if w != PFT_DEVICE:
@@ -303,11 +394,12 @@ class System:
     """Owning wrapper of one context (pft_create / pft_destroy) with host-array helpers."""
 
     def __init__(self, n, L, Ns, fA, chiN, C=1.0, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True,
-                 stream=None, seed=0, instance=0):
+                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO):
         self.n = tuple(int(v) for v in n)
         self.kind = kind
         self.M = self.n[0] * self.n[1] * self.n[2]
-        self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance)
+        self.h = None
+        self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance, march)
 
     @property
     def dtype(self):

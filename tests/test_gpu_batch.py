@@ -1,0 +1,123 @@
+"""Batches of independent systems of uneven grid and contour sizes (SCFT and complex
+Langevin mixed), advanced by batched launches captured in one CUDA graph, against the
+FP64 oracle run instance by instance, and against the library's own one-launch-sequence-
+per-instance mode."""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1204_5434_gb300 import pft
+
+pytestmark = pytest.mark.gpu
+SCFT, CL = pft.PFT_SCFT_REAL, pft.PFT_CL_COMPLEX
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1204_5434_gb300 import build
+    build.build()
+
+
+DESCS = [
+    dict(n=(16, 16, 16), L=(3.0, 3.0, 3.0), Ns=10, fA=0.4, chiN=15.0, C=1.0, kind=SCFT, seed=11),
+    dict(n=(24, 24, 24), L=(4.0, 4.0, 4.0), Ns=14, fA=0.3, chiN=20.0, C=50.0, kind=CL, seed=12),
+    dict(n=(16, 16, 16), L=(3.0, 3.0, 3.0), Ns=20, fA=0.25, chiN=18.0, C=50.0, kind=CL, seed=13),
+    dict(n=(12, 12, 12), L=(2.0, 2.0, 2.0), Ns=7, fA=0.5, chiN=12.0, C=1.0, kind=SCFT, seed=14),
+    dict(n=(16, 16, 16), L=(3.0, 3.0, 3.0), Ns=15, fA=0.45, chiN=14.0, C=1.0, kind=SCFT, seed=15),
+    dict(n=(24, 24, 24), L=(4.0, 4.0, 4.0), Ns=9, fA=0.35, chiN=16.0, C=1.0, kind=SCFT, seed=16),
+    dict(n=(24, 24, 24), L=(4.0, 4.0, 4.0), Ns=11, fA=0.3, chiN=20.0, C=50.0, kind=CL, seed=17),
+]
+LAM, DT = 0.1, 0.01
+
+
+def _fields(d, seed):
+    rng = np.random.default_rng(seed)
+    n = d["n"]
+    wp = rng.normal(0, 0.2, n)
+    wm = rng.normal(0, 1.0, n)
+    if d["kind"] == CL:
+        return wp.astype(complex), (wm + d["chiN"] * (2 * d["fA"] - 1) / 2).astype(complex)
+    return wp, wm
+
+
+def _make(prec, descs=DESCS):
+    b = pft.pft_batch_create(descs, prec)
+    fields = []
+    for i, d in enumerate(descs):
+        wp, wm = _fields(d, 100 + i)
+        pft.pft_batch_set_fields(b, i, wp, wm)
+        fields.append((wp, wm))
+    return b, fields
+
+
+def _oracle_updates(d, i, wp, wm, updates):
+    kind = o.SCFT_REAL if d["kind"] == SCFT else o.CL_COMPLEX
+    M = int(np.prod(d["n"]))
+    dV = float(np.prod(d["L"])) / M
+    for u in range(updates):
+        s = o.solve(wp, wm, d["n"], d["L"], d["Ns"], d["fA"], kind)
+        H = o.hamiltonian(wp, wm, s.lnQ, d["chiN"], d["C"], d["n"], d["L"], kind)
+        if kind == o.SCFT_REAL:
+            wp, wm = o.scft_euler_step(wp, wm, s.phiA, s.phiB, d["chiN"], LAM)
+        else:
+            std = o.cl_noise_std(DT, d["C"], dV)
+            ep, em = o.cl_noise(d["seed"], i, u, M, std)
+            wp, wm = o.cl_euler_maruyama_step(wp, wm, s.phiA, s.phiB, d["chiN"], DT, ep.reshape(d["n"]),
+                                              em.reshape(d["n"]))
+    return wp, wm, s, H
+
+
+def test_batch_graphed_matches_oracle_fp64():
+    b, fields = _make(pft.PFT_FP64)
+    try:
+        pft.pft_batch_run(b, 2, LAM, DT, pft.PFT_BATCH_GRAPHED)
+        info = pft.pft_batch_info(b)
+        assert info["classes"] == 5
+        assert info["units_per_update"] == sum(2 * np.prod(d["n"]) * d["Ns"] for d in DESCS)
+        for i, d in enumerate(DESCS):
+            wp, wm, s, H = _oracle_updates(d, i, *fields[i], 2)
+            dt = np.float64 if d["kind"] == SCFT else np.complex128
+            gp = np.empty(d["n"], dt)
+            gm = np.empty(d["n"], dt)
+            pft.pft_batch_get_fields(b, i, gp, gm)
+            obs = pft.pft_batch_get_observables(b, i)
+            assert np.max(np.abs(gp - wp)) <= 1e-11 and np.max(np.abs(gm - wm)) <= 1e-11, i
+            Hg = obs["H"] if d["kind"] == CL else obs["H"].real
+            assert abs(Hg - H) <= 1e-11 * abs(H), (i, Hg, H)
+            assert obs["step"] == 2
+    finally:
+        pft.pft_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [pft.PFT_FP64, pft.PFT_FP32_MIXED])
+def test_batch_graphed_equals_per_instance(prec):
+    res = []
+    for mode in (pft.PFT_BATCH_GRAPHED, pft.PFT_BATCH_PER_INSTANCE):
+        b, _ = _make(prec)
+        try:
+            pft.pft_batch_run(b, 3, LAM, DT, mode)
+            out = []
+            for i, d in enumerate(DESCS):
+                dt = np.float64 if d["kind"] == SCFT else np.complex128
+                gp = np.empty(d["n"], dt)
+                gm = np.empty(d["n"], dt)
+                pft.pft_batch_get_fields(b, i, gp, gm)
+                out.append((gp, gm, pft.pft_batch_get_observables(b, i)["Q"]))
+            res.append(out)
+        finally:
+            pft.pft_batch_destroy(b)
+    for a, c in zip(*res):
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]) and a[2] == c[2]
+
+
+def test_batch_rejects_bad_members():
+    with pytest.raises(pft.PftError) as e:
+        pft.pft_batch_create([dict(n=(128, 16, 16), L=(1, 1, 1), Ns=4, fA=0.5, chiN=10.0, C=1.0, kind=SCFT)])
+    assert e.value.status == pft.PFT_ERR_SHAPE
+    b = pft.pft_batch_create(DESCS[:2])
+    try:
+        with pytest.raises(pft.PftError) as e:
+            pft.pft_batch_run(b, 1, LAM, DT)
+        assert e.value.status == pft.PFT_ERR_STATE
+    finally:
+        pft.pft_batch_destroy(b)

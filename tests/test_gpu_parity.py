@@ -326,3 +326,72 @@ def test_gyroid_128cubed_full_size(prec):
     print(f"\n128^3 prec={prec}: Q rel {eQ:.2e} H rel {eH:.2e} phi abs {ephi:.2e}")
     assert eQ <= t["Q"] and _check_H(obs["H"].real, Href, w.C, w.L, prec) and ephi <= t["phi"]
     assert abs(phiA.mean() - ref.NsA / w.Ns) <= (1e-12 if prec == FP64 else 1e-6)
+
+
+# ------------------------------------------------------------ resident march
+def _gyroid_like(n, L, seed):
+    x = [np.arange(n[a]) * L[a] / n[a] for a in range(3)]
+    X = (2 * np.pi * x[0] / L[0])[:, None, None]
+    Y = (2 * np.pi * x[1] / L[1])[None, :, None]
+    Z = (2 * np.pi * x[2] / L[2])[None, None, :]
+    G = np.sin(X) * np.cos(Y) + np.sin(Y) * np.cos(Z) + np.sin(Z) * np.cos(X)
+    rng = np.random.default_rng(seed)
+    return rng.normal(0, 0.1, n), 4.0 * G + rng.normal(0, 0.1, n)
+
+
+@pytest.mark.parametrize("nn", [64, 96, 128])
+def test_resident_march_matches_oracle_and_passes(nn):
+    """The persistent resident march (FP32) against the oracle and the pass-kernel path."""
+    n, L, Ns, fA, chiN = (nn, nn, nn), (8.0, 8.0, 8.0), 20, 0.35, 18.0
+    wp, wm = _gyroid_like(n, L, nn)
+    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, 1.0, n, L, o.SCFT_REAL)
+    out = {}
+    for march in (pft.PFT_MARCH_RESIDENT, pft.PFT_MARCH_PASSES):
+        with pft.System(n, L, Ns, fA, chiN, 1.0, SCFT, FP32, march=march) as s:
+            assert pft.pft_get_march(s.h) == (2 if march == pft.PFT_MARCH_RESIDENT else 1)
+            s.set_fields(wp, wm)
+            s.solve()
+            s.solve()
+            obs = s.observables()
+            phiA, phiB = s.densities()
+            q = s.propagator(0, Ns)
+            qd = s.propagator(1, 0)
+        eQ = _rel(obs["Q"].real, ref.Q)
+        ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+        print(f"\nresident={march} {nn}^3: Q rel {eQ:.2e} phi abs {ephi:.2e}")
+        assert eQ <= TOL[FP32]["Q"] and ephi <= TOL[FP32]["phi"]
+        assert _check_H(obs["H"].real, Href, 1.0, L, FP32)
+        assert np.max(np.abs(q - ref.q[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.q[Ns]))
+        assert np.max(np.abs(qd - ref.qd[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.qd[Ns]))
+        out[march] = (phiA, obs["Q"].real)
+    a, b = out[pft.PFT_MARCH_RESIDENT], out[pft.PFT_MARCH_PASSES]
+    assert abs(a[1] - b[1]) <= 1e-5 * abs(b[1]) and np.max(np.abs(a[0] - b[0])) <= 1e-5
+
+
+def test_resident_march_refuses_unsupported_configs():
+    with pytest.raises(pft.PftError) as e:
+        pft.System((32, 32, 32), (4, 4, 4), 10, 0.5, 15.0, 1.0, SCFT, FP32, march=pft.PFT_MARCH_RESIDENT)
+    assert e.value.status == pft.PFT_ERR_UNSUPPORTED
+    with pytest.raises(pft.PftError) as e:
+        pft.System((64, 64, 64), (4, 4, 4), 10, 0.5, 15.0, 1.0, SCFT, FP64, march=pft.PFT_MARCH_RESIDENT)
+    assert e.value.status == pft.PFT_ERR_UNSUPPORTED
+
+
+def test_resident_barrier_timeout_is_reported_and_recoverable():
+    """A barrier wait budget of one cycle makes the grid barriers give up: the march
+    returns early, the host sees PFT_ERR_TIMEOUT, and the context still works."""
+    n, L, Ns, fA = (64, 64, 64), (8.0, 8.0, 8.0), 8, 0.35
+    wp, wm = _gyroid_like(n, L, 5)
+    with pft.System(n, L, Ns, fA, 18.0, 1.0, SCFT, FP32, march=pft.PFT_MARCH_RESIDENT) as s:
+        s.set_fields(wp, wm)
+        pft.pft_debug_set_spin_limit(s.h, 1)
+        s.solve()
+        with pytest.raises(pft.PftError) as e:
+            s.observables()
+        assert e.value.status == pft.PFT_ERR_TIMEOUT
+        pft.pft_debug_set_spin_limit(s.h, 4_000_000_000)
+        s.solve()
+        obs = s.observables()
+    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    assert _rel(obs["Q"].real, ref.Q) <= TOL[FP32]["Q"]
