@@ -38,6 +38,16 @@ WORK = wl.GYR128
 # conjugate step also reads the partner q and reads+writes an FP64 accumulator
 # (3e+f+2a).  Mean (5e+2f+2a)/2 with e=f=4, a=8 (FP32-mixed) or e=f=a=8 (FP64), real fields.
 BYTES_PER_UNIT = {"fp32": 22.0, "fp64": 36.0}
+# FP64 is bound by the GB300 FP64 pipe (1.25 TFLOP/s nominal dense, 1.20 measured with
+# an FMA loop).  Flops per unit: a real-to-half-spectrum 3D transform costs
+# 2.5 log2(M) flops per point in the usual 5 N log2 N convention; one contour step does
+# a forward and an inverse one, plus about 6 pointwise flops (two Boltzmann multiplies,
+# the diffusion multiply, the quadrature update).
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_flops_per_unit(M):
+    return 5.0 * math.log2(M) + 6.0
 
 
 def _peaks():
@@ -166,6 +176,70 @@ def _time_device(pft, torch, h, stream, steps, warmup, units_per_step):
     return e0.elapsed_time(e1) / steps
 
 
+def _variable_cell(pft, torch, prec, steps, warmup, wpa, wma, lam_L=0.05):
+    """Variable-cell SCFT step of the same workload: solve, exact gradients (field
+    gradients from the densities, box derivative by one recompute march), explicit
+    Euler field update, cell update L_a += lam_L dlnQ/dL_a."""
+    s = pft.System(WORK.n, WORK.L, WORK.Ns, WORK.fA, WORK.chiN, WORK.C, pft.PFT_SCFT_REAL, prec)
+    h = s.h
+    pft.pft_set_fields(h, wpa, wma)
+    L = list(WORK.L)
+
+    def one():
+        pft.pft_solve(h)
+        _, dq = pft.pft_gradients(h)
+        pft.pft_field_step(h, pft.PFT_STEP_SCFT_EULER, WORK.lam)
+        for a in range(3):
+            L[a] += lam_L * dq[a]
+        pft.pft_set_box(h, L)
+    for _ in range(warmup):
+        one()
+    pft.pft_synchronize(h)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    pft.pft_synchronize(h)
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    s.close()
+    units = 3 * WORK.M * WORK.Ns  # forward, conjugate and the recompute march of the box derivative
+    return {"ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT, "units_per_step": units,
+            "step": "solve + gradients (field + box) + Euler field step + cell step (lam_L=0.05)",
+            "timing": "host wall clock around synchronised steps (the gradient call reads back 3 scalars)"}
+
+
+def _batch(pft, prec, updates=2):
+    """The uneven batch: 256 instances, grids {32,48,64}^3, Ns {50,100,200}, half SCFT
+    and half CL; graph-captured batched launches against one launch sequence per instance."""
+    descs = wl.batch_instances()
+    inst = [dict(n=d.n, L=d.L, Ns=d.Ns, fA=d.fA, chiN=d.chiN, C=d.C,
+                 kind=pft.PFT_SCFT_REAL if d.kind == wl.SCFT else pft.PFT_CL_COMPLEX, seed=d.seed) for d in descs]
+    out = {}
+    for mode_name, mode in (("graphed", pft.PFT_BATCH_GRAPHED), ("per_instance", pft.PFT_BATCH_PER_INSTANCE)):
+        b = pft.pft_batch_create(inst, prec)
+        try:
+            for i, d in enumerate(descs):
+                wp, wm = wl.sinusoid_fields(d)
+                pft.pft_batch_set_fields(b, i, wp, wm)
+            pft.pft_batch_run(b, 1, 0.1, 0.01, mode)
+            pft.pft_batch_synchronize(b)
+            t0 = time.perf_counter()
+            pft.pft_batch_run(b, updates, 0.1, 0.01, mode)
+            pft.pft_batch_synchronize(b)
+            ms = (time.perf_counter() - t0) * 1e3 / updates
+            info = pft.pft_batch_info(b)
+            out[mode_name] = {"ms_per_update": ms, "value": info["units_per_update"] / (ms * 1e-3)}
+            out["units_per_update"] = info["units_per_update"]
+            out["classes"] = info["classes"]
+            if mode == pft.PFT_BATCH_GRAPHED:
+                out["launches_per_update"] = info["launches"]
+        finally:
+            pft.pft_batch_destroy(b)
+    out["unit"] = UNIT
+    out["instances"] = len(descs)
+    out["graphed_over_per_instance"] = out["graphed"]["value"] / out["per_instance"]["value"]
+    return out
+
+
 def run(args):
     import torch
 
@@ -236,15 +310,27 @@ def run(args):
         del dwp, dwm
         torch.cuda.empty_cache()
         bpu = BYTES_PER_UNIT[prec_name]
-        step_ms = 0.5 * (prof["step_fwd_ms"] + prof["step_bwd_ms"])
+        # the contour step (five pass kernels) over the timed region: units/s from the
+        # event-timed graph replays, which include the ~3% of pointwise kernels
+        step_ms = ms / (2 * WORK.Ns)
         achieved = bpu * WORK.M / (step_ms * 1e-3) / 1e9
         top = max(prof["kinds"].items(), key=lambda kv: kv[1]["ms"])
+        if prec_name == "fp32":
+            roof = {"bound": "hbm", "kernel": "contour step (z_fwd, y_fwd, x_fused, y_inv, z_inv)",
+                    "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)", "bytes_per_unit": bpu,
+                    "units_per_launch": WORK.M, "step_us": step_ms * 1e3, "traffic": None}
+        else:
+            fpu = fp64_flops_per_unit(WORK.M)
+            tf = fpu * WORK.M / (step_ms * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": "contour step (z_fwd, y_fwd, x_fused, y_inv, z_inv), FP64 pipe",
+                    "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
+                    "peak_source": "nominal GB300 dense FP64 (1.20 measured by an FMA loop)",
+                    "flops_per_unit": fpu, "units_per_launch": WORK.M, "step_us": step_ms * 1e3,
+                    "hbm_achieved_GBps": achieved, "hbm_frac": achieved / peak, "traffic": None}
         res[prec_name] = {
             "value": value, "ms_per_step": ms, "clocks": ck, "launches_per_step": launches,
-            "roofline": {"bound": "hbm", "kernel": "contour step (z_fwd, y_fwd, x_fused, y_inv, z_inv)",
-                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "peak_source": f"{peak_src} hbm_gbs", "bytes_per_unit": bpu,
-                         "units_per_launch": WORK.M, "step_ms": step_ms, "traffic": None},
+            "roofline": roof,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                             "share": round(v["ms"] / prof["total_ms"], 4) if prof["total_ms"] else None,
                             "GBps": round(v["bytes_per_launch"] * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
@@ -254,6 +340,8 @@ def run(args):
             "e2e": {"value": ws * units_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * WORK.M * 8, "d2h_bytes_per_step": 2 * WORK.M * 8},
         }
+    vc = _variable_cell(pft, torch, pft.PFT_FP32_MIXED, max(2, args.steps // 3), 1, wpa, wma)
+    batch = _batch(pft, pft.PFT_FP32_MIXED)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -278,6 +366,8 @@ def run(args):
                  "kernels": fp64["kernels"], "e2e": fp64["e2e"], "clocks": fp64["clocks"],
                  "note": "FP64 FFTs are bound by the GB300 FP64 pipe (about 1.2 TFLOP/s measured)"},
         "fp32_over_fp64": main["value"] / fp64["value"],
+        "variable_cell": vc,
+        "batch": batch,
     }
     del fp64_flops_unit
     print(json.dumps(line), flush=True)

@@ -22,9 +22,10 @@
  *   - PFT_SCFT_REAL: fields are real float64 arrays W+ (= i*omega+) and W- (= omega-);
  *     PFT_CL_COMPLEX: fields are complex128 arrays omega+ and omega- (interleaved
  *     re, im).  All API-facing arrays are float64 / complex128 in either precision.
- *   - PFT_FP64 runs every step in double; PFT_FP32_MIXED runs the propagators and FFTs
- *     in float and the Boltzmann factors' exponentials, contour quadrature,
- *     reductions, Hamiltonian and field update in double.
+ *   - PFT_FP64 runs every step in double.  PFT_FP32_MIXED runs the propagators, FFTs
+ *     and Boltzmann factors in float (the integrand q*qd of the contour quadrature is
+ *     the float product of the two float propagators) and keeps the field update, the
+ *     contour quadrature sums, every spatial reduction, Q, lnQ and H in double.
  *   - Pointers marked "host or device" are read/written according to the pft_mem
  *     argument.  Device pointers must be readable on the context's stream when the
  *     call is made.  The library copies inputs; the caller keeps ownership of every
@@ -60,11 +61,11 @@ typedef enum { PFT_SCFT_REAL = 0, PFT_CL_COMPLEX = 1 } pft_kind;
 typedef enum { PFT_FP64 = 0, PFT_FP32_MIXED = 1 } pft_precision;
 typedef enum { PFT_HOST = 0, PFT_DEVICE = 1 } pft_mem;
 typedef enum { PFT_STEP_SCFT_EULER = 0, PFT_STEP_CL_EULER_MARUYAMA = 1 } pft_step_kind;
-/* How the marches run: AUTO picks RESIDENT where it applies (FP32-mixed, real SCFT
- * fields, cubic 64^3/96^3/128^3 grids) and PASSES elsewhere.  PASSES: five pass kernels
- * per contour step, replayed as one CUDA graph per solve.  RESIDENT: one persistent
- * cooperative launch per march, one CTA per x-plane keeping the Boltzmann factors and
- * a spectrum plane in shared memory, two grid barriers per contour step. */
+/* How the marches run.  PASSES: five pass kernels per contour step, replayed as one
+ * CUDA graph per solve.  RESIDENT (FP32-mixed, real SCFT fields, cubic 64^3/96^3/128^3
+ * grids only): one persistent cooperative launch per march, one CTA per x-plane keeping
+ * the Boltzmann factors and a spectrum plane in shared memory, two grid barriers per
+ * contour step.  AUTO picks the faster of the two on GB300 (currently PASSES). */
 typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1, PFT_MARCH_RESIDENT = 2 } pft_march;
 
 typedef struct { int n[3]; double L[3]; } pft_grid;          /* grid points and box (Rg) */

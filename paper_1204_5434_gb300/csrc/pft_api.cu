@@ -188,7 +188,9 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       free_all(c);
       return fail(PFT_ERR_ARG, "unknown march");
     }
-    d.march = (opts->march == PFT_MARCH_PASSES || !can) ? 1 : 2;
+    // AUTO takes the pass kernels: on GB300 they are currently faster than the
+    // resident march (see the profiles), which stays selectable explicitly.
+    d.march = (opts->march == PFT_MARCH_RESIDENT && can) ? 2 : 1;
   }
 
   const size_t M = (size_t)d.M;

@@ -74,6 +74,27 @@ template <typename T> __device__ __forceinline__ void store_w(cpx<T>* p, long lo
   p[i] = mk<T>((T)v.x, (T)v.y);
 }
 
+// Boltzmann factor exp(-w ds/2) in the propagators' precision: the exponent is formed in
+// double from the FP64 field, the exponential evaluated in T (for T = float the result is
+// stored as float anyway, and GB300's FP64 pipe is 1/64 of its FP32 rate).
+template <typename T> __device__ __forceinline__ T boltz(double w, double ds) {
+  return (T)exp(-w * ds * 0.5);
+}
+template <> __device__ __forceinline__ float boltz<float>(double w, double ds) {
+  return expf((float)(-w * ds * 0.5));
+}
+template <typename T> __device__ __forceinline__ cpx<T> boltz_c(double2 w, double ds) {
+  const double2 z = cexp_d(make_double2(-w.x * ds * 0.5, -w.y * ds * 0.5));
+  return mk<T>((T)z.x, (T)z.y);
+}
+template <> __device__ __forceinline__ float2 boltz_c<float>(double2 w, double ds) {
+  const float zr = (float)(-w.x * ds * 0.5), zi = (float)(-w.y * ds * 0.5);
+  float s, c;
+  sincosf(zi, &s, &c);
+  const float e = expf(zr);
+  return make_float2(e * c, e * s);
+}
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32->64 multiplies by
 // fixed odd constants, high halves xored with the other words and the round key;
@@ -157,8 +178,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_prepare_real(const double* __res
   double acc[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double p = wp[i], m = wm[i];
-    BA[i] = (T)exp(-(p - m) * ds * 0.5);
-    BB[i] = (T)exp(-(p + m) * ds * 0.5);
+    BA[i] = boltz<T>(p - m, ds);
+    BB[i] = boltz<T>(p + m, ds);
     acc[0] += m * m / chiN - p;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
@@ -175,8 +196,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_prepare_cplx(const double2* __re
     const double2 ip = make_double2(-p.y, p.x);
     const double2 wA = make_double2(ip.x - m.x, ip.y - m.y);
     const double2 wB = make_double2(ip.x + m.x, ip.y + m.y);
-    store_w<T>(BA, i, cexp_d(make_double2(-wA.x * ds * 0.5, -wA.y * ds * 0.5)));
-    store_w<T>(BB, i, cexp_d(make_double2(-wB.x * ds * 0.5, -wB.y * ds * 0.5)));
+    BA[i] = boltz_c<T>(wA, ds);
+    BB[i] = boltz_c<T>(wB, ds);
     acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
     acc[1] += 2.0 * m.x * m.y / chiN - p.x;
   }
@@ -294,8 +315,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_scft(double* __restrict__ w
     m -= lam * fm;
     wp[i] = p;
     wm[i] = m;
-    BA[i] = (T)exp(-(p - m) * ds * 0.5);
-    BB[i] = (T)exp(-(p + m) * ds * 0.5);
+    BA[i] = boltz<T>(p - m, ds);
+    BB[i] = boltz<T>(p + m, ds);
     acc[0] += m * m / chiN - p;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
@@ -354,8 +375,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
       const double2 ip = make_double2(-p.y, p.x);
       const double2 wA = make_double2(ip.x - m.x, ip.y - m.y);
       const double2 wB = make_double2(ip.x + m.x, ip.y + m.y);
-      store_w<T>(BA, i, cexp_d(make_double2(-wA.x * ds * 0.5, -wA.y * ds * 0.5)));
-      store_w<T>(BB, i, cexp_d(make_double2(-wB.x * ds * 0.5, -wB.y * ds * 0.5)));
+      BA[i] = boltz_c<T>(wA, ds);
+      BB[i] = boltz_c<T>(wB, ds);
       acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
       acc[1] += 2.0 * m.x * m.y / chiN - p.x;
     }

@@ -173,9 +173,9 @@ PFT_PLAN(32, 8, 8, 4)
 PFT_PLAN(48, 12, 3, 4, 4)
 PFT_PLAN(64, 8, 8, 8)
 PFT_PLAN(96, 12, 3, 4, 4, 2)
-PFT_PLAN(128, 8, 8, 4, 4)
+PFT_PLAN(128, 16, 16, 8)
 PFT_PLAN(192, 12, 3, 4, 4, 4)
-PFT_PLAN(256, 8, 8, 8, 4)
+PFT_PLAN(256, 16, 16, 16)
 #undef PFT_PLAN
 
 // ------------------------------------------------------------ Stockham stages

@@ -214,9 +214,10 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
     }
     q2[m] = y;
     if (EPI == 1) {
+      // integrand q qd in the propagators' precision, sum in FP64 (one DFMA each)
       const cpx<T> pp = reinterpret_cast<const cpx<T>*>(partner)[m];
-      const double p0 = (double)y.x * (double)pp.x;
-      const double p1 = (double)y.y * (double)pp.y;
+      const double p0 = (double)(y.x * pp.x);
+      const double p1 = (double)(y.y * pp.y);
       if (cA != 0.0) {
         double2* a = reinterpret_cast<double2*>(accA) + m;
         double2 av = *a;
@@ -309,10 +310,11 @@ __device__ __forceinline__ void zi_c2c_body(const cpx<T>* __restrict__ spec, con
     if (EPI != 2) y = cmul(y, B[m]);
     qout[m] = y;
     if (EPI == 1) {
-      const cpx<T> pp = partner[m];
+      // integrand q qd in the propagators' precision, sum in FP64
+      const cpx<T> pq = cmul(y, partner[m]);
       double2 pr;
-      pr.x = (double)y.x * (double)pp.x - (double)y.y * (double)pp.y;
-      pr.y = (double)y.x * (double)pp.y + (double)y.y * (double)pp.x;
+      pr.x = (double)pq.x;
+      pr.y = (double)pq.y;
       if (cA != 0.0) {
         double2 a = accA[m];
         a.x += cA * pr.x;

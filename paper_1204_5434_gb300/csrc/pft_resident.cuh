@@ -108,6 +108,12 @@ struct XCol {
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// Transform plans of the resident march: the pass kernels' radix-16 plan for N=128
+// needs more registers than one CTA of 528 threads per SM allows, so the march keeps
+// the radix 8-4-4 plan there.
+template <int N> struct ResPlan { using type = Plan<N>; };
+template <> struct ResPlan<128> { using type = PlanX<128, 8, 8, 4, 4>; };
+
 template <int NX, int NY, int NZ>
 struct Res {
   // 33 column groups of 16 threads at NY=128, so the 65 half-spectrum columns take
@@ -117,8 +123,10 @@ struct Res {
   static constexpr int NZH = NZ / 2 + 1;
   static constexpr int LDP = N2 + (N2 >> 4) + 2;  // padded row of the work plane (complex)
   static constexpr int ZT = Plan<N2>::TPC, ZE = Plan<N2>::E;
-  static constexpr int YT = Plan<NY>::TPC, YE = Plan<NY>::E;
-  static constexpr int XT = Plan<NX>::TPC, XE = Plan<NX>::E;
+  using YPL = typename ResPlan<NY>::type;
+  using XPL = typename ResPlan<NX>::type;
+  static constexpr int YT = YPL::TPC, YE = YPL::E;
+  static constexpr int XT = XPL::TPC, XE = XPL::E;
   static constexpr int ROWS = THREADS / ZT;        // rows per round
   static constexpr int YCOLS = THREADS / YT;       // y columns per round
   static constexpr int XCPR = THREADS / XT;        // x columns per round
@@ -211,8 +219,9 @@ __device__ __forceinline__ void row_phase(float2* __restrict__ W, int p, int mod
           for (int i = 0; i < E; i++) av[i] = acc[t + TPC * i];
 #pragma unroll
           for (int i = 0; i < E; i++) {
-            av[i].x += c * ((double)v[i].x * (double)pv[i].x);
-            av[i].y += c * ((double)v[i].y * (double)pv[i].y);
+            // FP32 integrand, FP64 sum (one DFMA per value)
+            av[i].x += c * (double)(v[i].x * pv[i].x);
+            av[i].y += c * (double)(v[i].y * pv[i].y);
             acc[t + TPC * i] = av[i];
           }
         }
@@ -269,7 +278,7 @@ __device__ __forceinline__ void col_phase(float2* __restrict__ W, const ResArgs&
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = x.get(t + TPC * i);
     __syncthreads();
-    fft<float, INV, NY>(v, t, a.twy, x);
+    fft<float, INV, NY, typename R::YPL>(v, t, a.twy, x);
 #pragma unroll
     for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
     __syncthreads();
@@ -344,13 +353,13 @@ __device__ __forceinline__ void x_phase(float2* __restrict__ W, int cta, const R
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = x.get(t + TPC * i);
     __syncthreads();
-    fft<float, false, NX>(v, t, a.twx, x);
+    fft<float, false, NX, typename R::XPL>(v, t, a.twx, x);
     const int col = cb + j;
     const int ky = col / R::NZH, kz = col - ky * R::NZH;
     const float dyz = a.dy[ky] * a.dz[kz];
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = cscale(v[i], a.dx[t + TPC * i] * dyz);
-    fft<float, true, NX>(v, t, a.twx, x);
+    fft<float, true, NX, typename R::XPL>(v, t, a.twx, x);
 #pragma unroll
     for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
     __syncthreads();
