@@ -65,8 +65,11 @@ typedef enum { PFT_STEP_SCFT_EULER = 0, PFT_STEP_CL_EULER_MARUYAMA = 1 } pft_ste
  * CUDA graph per solve.  RESIDENT (FP32-mixed, real SCFT fields, cubic 64^3/96^3/128^3
  * grids only): one persistent cooperative launch per march, one CTA per x-plane keeping
  * the Boltzmann factors and a spectrum plane in shared memory, two grid barriers per
- * contour step.  AUTO picks the faster of the two on GB300 (currently PASSES). */
-typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1, PFT_MARCH_RESIDENT = 2 } pft_march;
+ * contour step.  PERSISTENT (FP32-mixed, real SCFT fields, cubic 64^3/128^3/256^3):
+ * one cooperative launch per march over every SM (two CTAs per SM) running the pass
+ * tiles with bounded grid barriers in place of kernel boundaries, the z inverse of one
+ * step fused with the z forward of the next.  AUTO picks the fastest on GB300. */
+typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1, PFT_MARCH_RESIDENT = 2, PFT_MARCH_PERSISTENT = 3 } pft_march;
 
 typedef struct { int n[3]; double L[3]; } pft_grid;          /* grid points and box (Rg) */
 typedef struct { int Ns; double fA; } pft_chain;              /* contour steps, A fraction */
@@ -292,7 +295,7 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
  * the march returns early and pft_get_observables reports PFT_ERR_TIMEOUT. */
 pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles);
 
-/* Which march the context uses: 1 = passes, 2 = resident. */
+/* Which march the context uses: 1 = passes, 2 = resident, 3 = persistent. */
 pft_status pft_get_march(const pft_ctx* ctx, int* march);
 
 /* Standard normals of the device Philox stream (same layout as the CL noise) for

@@ -178,19 +178,30 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   }
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
   {
-    const bool can = c->eng->resident_supported(d);
-    if (opts->march == PFT_MARCH_RESIDENT && !can) {
+    const bool can_res = c->eng->resident_supported(d);
+    const bool can_per = c->eng->persist_supported(d);
+    if (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES && opts->march != PFT_MARCH_RESIDENT &&
+        opts->march != PFT_MARCH_PERSISTENT) {
+      free_all(c);
+      return fail(PFT_ERR_ARG, "unknown march");
+    }
+    if (opts->march == PFT_MARCH_RESIDENT && !can_res) {
       free_all(c);
       return fail(PFT_ERR_UNSUPPORTED,
                   "resident march needs FP32-mixed precision, real SCFT fields and a 64^3, 96^3 or 128^3 grid");
     }
-    if (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES && opts->march != PFT_MARCH_RESIDENT) {
+    if (opts->march == PFT_MARCH_PERSISTENT && !can_per) {
       free_all(c);
-      return fail(PFT_ERR_ARG, "unknown march");
+      return fail(PFT_ERR_UNSUPPORTED,
+                  "persistent march needs FP32-mixed precision, real SCFT fields and a 64^3, 128^3 or 256^3 grid");
     }
-    // AUTO takes the pass kernels: on GB300 they are currently faster than the
-    // resident march (see the profiles), which stays selectable explicitly.
-    d.march = (opts->march == PFT_MARCH_RESIDENT && can) ? 2 : 1;
+    if (opts->march == PFT_MARCH_RESIDENT) {
+      d.march = 2;
+    } else if (opts->march == PFT_MARCH_PERSISTENT) {
+      d.march = 3;
+    } else {
+      d.march = 1;  // AUTO: the pass kernels (see include/pft.h)
+    }
   }
 
   const size_t M = (size_t)d.M;
@@ -322,13 +333,13 @@ pft_status pft_get_observables(pft_ctx* ctx, pft_obs* obs) {
   if (!ctx->have_obs) return fail(PFT_ERR_STATE, "no solve since the fields were set");
   PFT_CK(cudaMemcpyAsync(d.scal_host, d.scal, pft::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
   unsigned syncw[4] = {0, 0, 0, 0};
-  if (d.march == 2) PFT_CK(cudaMemcpyAsync(syncw, d.sync, sizeof(syncw), cudaMemcpyDeviceToHost, d.stream));
+  if (d.march >= 2) PFT_CK(cudaMemcpyAsync(syncw, d.sync, sizeof(syncw), cudaMemcpyDeviceToHost, d.stream));
   PFT_CK(cudaStreamSynchronize(d.stream));
   const double* s = d.scal_host;
   const double V = d.L[0] * d.L[1] * d.L[2];
   const double Md = (double)d.M;
   memset(obs, 0, sizeof(*obs));
-  if (syncw[2] != 0) return fail(PFT_ERR_TIMEOUT, "a grid barrier of the resident march ran out of its wait budget");
+  if (syncw[2] != 0) return fail(PFT_ERR_TIMEOUT, "a grid barrier of the march ran out of its wait budget");
   for (int j = 0; j < 2; j++) {
     obs->Q[j] = s[pft::S_Q + j];
     obs->lnQ[j] = s[pft::S_LNQ + j];

@@ -72,7 +72,7 @@ struct CtxData {
   size_t tables_bytes = 0;
   int npart = 0;
   size_t bytes = 0;
-  // resident march: 1 = passes, 2 = resident; barrier words [count, gen, err, pad]
+  // march: 1 = passes, 2 = resident, 3 = persistent; barrier words [count, gen, err, pad]
   int march = 1;
   unsigned* sync = nullptr;
   long long spin_limit = 4000000000LL;
@@ -115,6 +115,7 @@ class Engine {
   virtual size_t elem_bytes() const = 0;      // working-precision real element
   // Can this system run the resident march (and how much shared memory it needs)?
   virtual bool resident_supported(const CtxData& c) const = 0;
+  virtual bool persist_supported(const CtxData& c) const = 0;
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

@@ -9,6 +9,7 @@
 
 #include "pft_engine_impl.cuh"
 #include "pft_batch.cuh"
+#include "pft_persist.cuh"
 #include "pft_resident.cuh"
 
 namespace pft {
@@ -108,6 +109,78 @@ class EngineT : public Engine {
         case 96: return resident_fits<96, 96, 96>(c);
         case 128: return resident_fits<128, 128, 128>(c);
         default: return false;
+      }
+    }
+  }
+
+  // ------------------------------------------------------------ persistent march
+  template <int N, bool BWD>
+  static cudaError_t launch_persist_n(CtxData& c, const PersistArgs& a) {
+    using R = Persist<N>;
+    auto kern = k_persist_march<N, BWD>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, R::THREADS, R::SMEM);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    if (per_sm > 2) per_sm = 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(per_sm * c.sms);
+    cfg.blockDim = dim3(R::THREADS);
+    cfg.dynamicSmemBytes = R::SMEM;
+    cfg.stream = c.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+  }
+
+  bool persist_supported(const CtxData& c) const override {
+    if constexpr (!std::is_same<T, float>::value) {
+      return false;
+    } else {
+      if (c.kind != PFT_SCFT_REAL) return false;
+      if (c.n[0] != c.n[1] || c.n[1] != c.n[2]) return false;
+      return c.n[0] == 64 || c.n[0] == 128 || c.n[0] == 256;
+    }
+  }
+
+  cudaError_t persist_march(CtxData& c, bool bwd) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      PersistArgs a;
+      a.BA = (const float*)c.BA;
+      a.BB = (const float*)c.BB;
+      a.hist = (float*)c.hist;
+      a.qd0 = (const float*)c.qd0;
+      a.qd_out = (float*)c.qd[c.Ns & 1];
+      a.spec = (float2*)c.spec;
+      a.accA = (double*)c.accA;
+      a.accB = (double*)c.accB;
+      a.twx = tab<float2>(c, c.tw_off[0]);
+      a.twy = tab<float2>(c, c.tw_off[1]);
+      a.twz = tab<float2>(c, c.tw_off[2]);
+      a.twh = tab<float2>(c, c.tw_off[3]);
+      a.dx = tab<float>(c, c.d_off[0]);
+      a.dy = tab<float>(c, c.d_off[1]);
+      a.dz = tab<float>(c, c.d_off[2]);
+      a.Ns = c.Ns;
+      a.NsA = c.NsA;
+      a.bar = c.sync;
+      a.err = (int*)(c.sync + 2);
+      a.spin_limit = c.spin_limit;
+      cudaError_t e = cudaMemsetAsync(c.sync, 0, 2 * sizeof(unsigned), c.stream);
+      if (e != cudaSuccess) return e;
+      mark(c, bwd ? KK_MARCH_BWD : KK_MARCH_FWD);
+      switch (c.n[0]) {
+        case 64: return bwd ? launch_persist_n<64, true>(c, a) : launch_persist_n<64, false>(c, a);
+        case 128: return bwd ? launch_persist_n<128, true>(c, a) : launch_persist_n<128, false>(c, a);
+        case 256: return bwd ? launch_persist_n<256, true>(c, a) : launch_persist_n<256, false>(c, a);
+        default: return cudaErrorNotSupported;
       }
     }
   }
@@ -284,14 +357,15 @@ class EngineT : public Engine {
     const size_t slice = (size_t)c.M * (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
     char* hist = (char*)c.hist;
     cudaError_t e;
-    const bool res = (c.march == 2);
+    const bool res = (c.march == 2 || c.march == 3);
     if (res) {
       // a fresh error word for this solve
       if ((e = cudaMemsetAsync(c.sync, 0, 4 * sizeof(unsigned), c.stream)) != cudaSuccess) return e;
     }
     // forward march (Eqs. 5, 13)
     if (res) {
-      if ((e = resident_march(c, false)) != cudaSuccess) return e;
+      e = (c.march == 2) ? resident_march(c, false) : persist_march(c, false);
+      if (e != cudaSuccess) return e;
     } else {
       for (int n = 1; n <= c.Ns; n++) {
         const void* B = (n <= c.NsA) ? c.BA : c.BB;
@@ -304,7 +378,8 @@ class EngineT : public Engine {
     double cA, cB;
     // conjugate march with fused quadrature (Eq. 8)
     if (res) {
-      if ((e = resident_march(c, true)) != cudaSuccess) return e;
+      e = (c.march == 2) ? resident_march(c, true) : persist_march(c, true);
+      if (e != cudaSuccess) return e;
     }
     for (int m = 1; m <= c.Ns && !res; m++) {
       const int nb = c.Ns + 1 - m;  // split step index of this qd step
@@ -389,7 +464,7 @@ class EngineT : public Engine {
 
   cudaError_t enqueue_solve(CtxData& c) override {
     // the resident march is a handful of launches per solve: it runs without a graph
-    if (!c.use_graph || c.profiling || c.march == 2) return record_solve(c);
+    if (!c.use_graph || c.profiling || c.march >= 2) return record_solve(c);
     if (!c.graph_valid) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);

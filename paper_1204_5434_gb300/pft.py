@@ -23,7 +23,7 @@ PFT_SCFT_REAL, PFT_CL_COMPLEX = 0, 1
 PFT_FP64, PFT_FP32_MIXED = 0, 1
 PFT_HOST, PFT_DEVICE = 0, 1
 PFT_STEP_SCFT_EULER, PFT_STEP_CL_EULER_MARUYAMA = 0, 1
-PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT = 0, 1, 2
+PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT, PFT_MARCH_PERSISTENT = 0, 1, 2, 3
 PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
 
 

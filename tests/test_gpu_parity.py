@@ -395,3 +395,51 @@ def test_resident_barrier_timeout_is_reported_and_recoverable():
         obs = s.observables()
     ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
     assert _rel(obs["Q"].real, ref.Q) <= TOL[FP32]["Q"]
+
+
+# ---------------------------------------------------------- persistent march
+@pytest.mark.parametrize("nn,Ns", [(64, 20), (128, 20), (256, 4)])
+def test_persistent_march_matches_oracle(nn, Ns):
+    """The persistent multi-pass march (FP32, one cooperative launch per march) against
+    the oracle and against the pass-kernel path."""
+    n, L, fA, chiN = (nn, nn, nn), (8.0, 8.0, 8.0), 0.35, 18.0
+    wp, wm = _gyroid_like(n, L, nn + 1)
+    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, 1.0, n, L, o.SCFT_REAL)
+    out = {}
+    for march in (pft.PFT_MARCH_PERSISTENT, pft.PFT_MARCH_PASSES):
+        with pft.System(n, L, Ns, fA, chiN, 1.0, SCFT, FP32, march=march) as s:
+            s.set_fields(wp, wm)
+            s.solve()
+            s.solve()
+            obs = s.observables()
+            phiA, phiB = s.densities()
+            q = s.propagator(0, Ns)
+            qd = s.propagator(1, 0)
+        eQ = _rel(obs["Q"].real, ref.Q)
+        ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+        print(f"\npersistent={march} {nn}^3: Q rel {eQ:.2e} phi abs {ephi:.2e}")
+        assert eQ <= TOL[FP32]["Q"] and ephi <= TOL[FP32]["phi"]
+        assert _check_H(obs["H"].real, Href, 1.0, L, FP32)
+        assert np.max(np.abs(q - ref.q[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.q[Ns]))
+        assert np.max(np.abs(qd - ref.qd[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.qd[Ns]))
+        out[march] = (phiA, obs["Q"].real)
+    a, b = out[pft.PFT_MARCH_PERSISTENT], out[pft.PFT_MARCH_PASSES]
+    assert abs(a[1] - b[1]) <= 1e-5 * abs(b[1]) and np.max(np.abs(a[0] - b[0])) <= 1e-5
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable():
+    n, L, Ns, fA = (64, 64, 64), (8.0, 8.0, 8.0), 8, 0.35
+    wp, wm = _gyroid_like(n, L, 6)
+    with pft.System(n, L, Ns, fA, 18.0, 1.0, SCFT, FP32, march=pft.PFT_MARCH_PERSISTENT) as s:
+        s.set_fields(wp, wm)
+        pft.pft_debug_set_spin_limit(s.h, 1)
+        s.solve()
+        with pytest.raises(pft.PftError) as e:
+            s.observables()
+        assert e.value.status == pft.PFT_ERR_TIMEOUT
+        pft.pft_debug_set_spin_limit(s.h, 4_000_000_000)
+        s.solve()
+        obs = s.observables()
+    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    assert _rel(obs["Q"].real, ref.Q) <= TOL[FP32]["Q"]
