@@ -12,9 +12,10 @@ using pft::Engine;
 
 
 namespace pft {
-const char* const kKernelKindNames[KK_COUNT] = {"z_fwd",      "y_fwd",   "x_fused",    "y_inv",
-                                                "z_inv_fwd",  "z_inv_bwd", "reduce",   "field_step",
-                                                "prepare",    "march_fwd", "march_bwd"};
+const char* const kKernelKindNames[KK_COUNT] = {"z_fwd",      "y_fwd",     "x_fused",   "y_inv",
+                                                "z_inv_fwd",  "z_inv_bwd", "reduce",    "field_step",
+                                                "prepare",    "march_fwd", "march_bwd", "pair_step",
+                                                "quadrature"};
 static thread_local std::string g_err;
 void set_error(const std::string& s) { g_err = s; }
 
@@ -76,7 +77,7 @@ void free_all(pft_ctx* c) {
   if (d.graph) cudaGraphExecDestroy(d.graph);
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
-                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync};
+                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync, d.qdh, d.steps2};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
@@ -494,6 +495,15 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
     else if (iR1 >= 0 && iB < 0 && march_start) iB = i;
     else if (iB >= 0 && iR2 < 0 && k == pft::KK_REDUCE) iR2 = i;
   }
+  {
+    // concurrent marches: each pair step advances both propagators by one contour step
+    double pair_ms = out->ms[pft::KK_PAIR_STEP];
+    if (out->launches[pft::KK_PAIR_STEP] > 0) {
+      out->step_fwd_ms = out->step_bwd_ms = pair_ms / (2.0 * out->launches[pft::KK_PAIR_STEP]);
+      iF = -1;
+      iB = -1;
+    }
+  }
   if (iF >= 0 && iR1 > iF) {
     float ms;
     PFT_CK(cudaEventElapsedTime(&ms, d.ev[iF], d.ev[iR1]));
@@ -519,6 +529,8 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   // and writes q_n, the conjugate one also reads the partner and updates an accumulator
   out->bytes_per_launch[pft::KK_MARCH_FWD] = (double)d.Ns * (3 * M * we);
   out->bytes_per_launch[pft::KK_MARCH_BWD] = (double)d.Ns * (4 * M * we + 2 * M * 8.0);
+  out->bytes_per_launch[pft::KK_PAIR_STEP] = 2 * (2 * M * we + Ms * ze) + 6 * (2 * Ms * ze) + 2 * (Ms * ze + 2 * M * we);
+  out->bytes_per_launch[pft::KK_QUADRATURE] = 2.0 * (d.Ns + 1) * M * we + 2 * M * fe;
   return PFT_OK;
 }
 
@@ -541,7 +553,9 @@ pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem
   if (which != 0 && which != 1) return fail(PFT_ERR_ARG, "which must be 0 (q) or 1 (qd)");
   if (which == 0 && (s < 0 || s > d.Ns)) return fail(PFT_ERR_ARG, "slice out of range");
   const size_t we = welem(d);
-  const void* src = (which == 0) ? (const void*)((const char*)d.hist + (size_t)s * d.M * we) : d.qd[d.Ns & 1];
+  const void* qd_last = (d.march == 1 && d.concurrent && d.qdh) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
+                                                                  : d.qd[d.Ns & 1];
+  const void* src = (which == 0) ? (const void*)((const char*)d.hist + (size_t)s * d.M * we) : qd_last;
   const long long cnt = d.M * (d.kind == PFT_SCFT_REAL ? 1 : 2);
   PFT_CK(ctx->eng->to_f64(d, src, ctx->io, cnt));
   PFT_CK(cudaMemcpyAsync(out, ctx->io, (size_t)cnt * 8, kind_out(where), d.stream));

@@ -188,6 +188,9 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
       return bfail(s, "batch instance " + std::to_string(i) + ": " + msg);
     }
     b->units += 2.0 * (double)b->inst[i]->d.M * b->inst[i]->d.Ns;
+    // members march one propagator at a time with the quadrature inside the conjugate
+    // march (the batched launches already fill the GPU), in both batch modes
+    b->inst[i]->d.concurrent = false;
   }
   cudaError_t e = cudaMalloc(&b->d_steps, sizeof(unsigned long long) * count);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long) * count, b->stream);

@@ -19,6 +19,7 @@ struct BatchStep {
   void* accB;
   const void* tw[4];    // twiddles x, y, z, z/2
   const void* d[3];     // diffusion tables
+  const void* Bnext;    // Boltzmann factor of the next split step (fused z passes), or null
 };
 
 template <typename T, int N, int MODE>
@@ -62,6 +63,122 @@ kb_zi_c2c(const BatchStep* __restrict__ st, long long npen) {
   zi_c2c_body<T, N, EPI>((const cpx<T>*)s.spec, (const cpx<T>*)s.B, (cpx<T>*)s.out, (const cpx<T>*)s.partner,
                          (double2*)s.accA, (double2*)s.accB, s.cA, s.cB, npen, (const cpx<T>*)s.tw[2],
                          (long long)blockIdx.x);
+}
+
+// Fused z passes of consecutive contour steps on the same pencils: inverse z of step s
+// (half spectrum -> nz reals), x B_s, store q_s; then x B_{s+1}, forward z of step s+1
+// back into the spectrum.  The C2R output and the R2C input share one thread
+// distribution, so q_s never leaves registers between the two transforms.
+template <typename T, int N2>
+__global__ void __launch_bounds__(PencilsPerCta<T, N2>::v * Plan<N2>::TPC)
+kb_zz_r2c(const BatchStep* __restrict__ st, long long npen) {
+  const BatchStep& s = st[blockIdx.y];
+  using Z = cpx<T>;
+  constexpr int P = PencilsPerCta<T, N2>::v;
+  constexpr int E = Plan<N2>::E;
+  constexpr int TPC = Plan<N2>::TPC;
+  constexpr int LD = pencil_ld<T>(N2);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long pen = (long long)blockIdx.x * P + p;
+  const bool valid = pen < npen;
+  const long long pc = valid ? pen : 0;
+  XchPencil<T> x{reinterpret_cast<Z*>(smraw) + p * LD};
+  Z* sp = (Z*)s.spec + pc * (N2 + 1);
+  const Z* twh = (const Z*)s.tw[3];
+  const Z* twf = (const Z*)s.tw[2];
+  const long long o = pc * N2;
+#pragma unroll
+  for (int i = 0; i < E; i++) x.put(t + TPC * i, valid ? sp[t + TPC * i] : mk<T>(T(0), T(0)));
+  if (t == 0) x.put(N2, valid ? sp[N2] : mk<T>(T(0), T(0)));
+  __syncthreads();
+  Z v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const int k = t + TPC * i;
+    const Z xk = x.get(k);
+    const Z xc = cconj(x.get(N2 - k));
+    const Z d = rot90<true>(cmulc(csub(xk, xc), twf[k]));
+    v[i] = cadd(cadd(xk, xc), d);
+  }
+  __syncthreads();
+  fft<T, true, N2>(v, t, twh, x);
+  const Z* b2 = reinterpret_cast<const Z*>(s.B) + o;
+  Z* q2 = reinterpret_cast<Z*>(s.out) + o;
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const int m = t + TPC * i;
+    const Z b = b2[m];
+    v[i].x *= b.x;
+    v[i].y *= b.y;
+    if (valid) q2[m] = v[i];
+  }
+  if (!s.Bnext) return;  // uniform per launch member
+  const Z* bn = reinterpret_cast<const Z*>(s.Bnext) + o;
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const Z b = bn[t + TPC * i];
+    v[i].x *= b.x;
+    v[i].y *= b.y;
+  }
+  fft<T, false, N2>(v, t, twh, x);  // the inverse ended with a barrier after its last reads
+#pragma unroll
+  for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
+  __syncthreads();
+  const T h = T(0.5);
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const int k = t + TPC * i;
+    const Z zc = cconj(x.get(k == 0 ? 0 : N2 - k));
+    const Z ev = cscale(cadd(v[i], zc), h);
+    const Z od = cscale(rot90<false>(csub(v[i], zc)), h);
+    if (valid) sp[k] = cadd(ev, cmul(twf[k], od));
+  }
+  if (valid && t == 0) sp[N2] = mk<T>(v[0].x - v[0].y, T(0));
+}
+
+// Complex fields: inverse z of step s, x B_s, store, x B_{s+1}, forward z of step s+1.
+template <typename T, int N>
+__global__ void __launch_bounds__(PencilsPerCta<T, N>::v * Plan<N>::TPC)
+kb_zz_c2c(const BatchStep* __restrict__ st, long long npen) {
+  const BatchStep& s = st[blockIdx.y];
+  using Z = cpx<T>;
+  constexpr int P = PencilsPerCta<T, N>::v;
+  constexpr int E = Plan<N>::E;
+  constexpr int TPC = Plan<N>::TPC;
+  constexpr int LD = pencil_ld<T>(N);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long pen = (long long)blockIdx.x * P + p;
+  const bool valid = pen < npen;
+  const long long o = (valid ? pen : 0) * N;
+  XchPencil<T> x{reinterpret_cast<Z*>(smraw) + p * LD};
+  Z* sp = (Z*)s.spec;
+  const Z* tw = (const Z*)s.tw[2];
+  Z v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = valid ? sp[o + t + TPC * i] : mk<T>(T(0), T(0));
+  fft<T, true, N>(v, t, tw, x);
+  const Z* B = (const Z*)s.B;
+  Z* q = (Z*)s.out;
+#pragma unroll
+  for (int i = 0; i < E; i++) {
+    const long long m = o + t + TPC * i;
+    v[i] = cmul(v[i], B[m]);
+    if (valid) q[m] = v[i];
+  }
+  if (!s.Bnext) return;
+  const Z* Bn = (const Z*)s.Bnext;
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = cmul(v[i], Bn[o + t + TPC * i]);
+  if (n_stages<Plan<N>>() > 1) __syncthreads();
+  fft<T, false, N>(v, t, tw, x);
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < E; i++) sp[o + t + TPC * i] = v[i];
+  }
 }
 
 }  // namespace pft

@@ -78,6 +78,11 @@ struct CtxData {
   long long spin_limit = 4000000000LL;
   // optional device counter read by the CL field step instead of `step` (batches)
   const unsigned long long* step_dev = nullptr;
+  // concurrent marches (pass kernels): q and qd advance together, two members per
+  // launch; the qd history is kept and the quadrature runs once over both histories
+  bool concurrent = true;
+  void* qdh = nullptr;      // [(Ns+1) * M] qd_0..qd_Ns (slice 0 unused: qd0 holds it)
+  void* steps2 = nullptr;   // [2 * Ns] BatchStep: forward and conjugate step s
   // profiling: an event recorded before every launch (eager solves only)
   bool profiling = false;
   std::vector<cudaEvent_t> ev;
@@ -88,7 +93,7 @@ struct CtxData {
 // Kernel classes reported by pft_profile_step.
 enum KernelKind {
   KK_Z_FWD = 0, KK_Y_FWD, KK_X_FUSED, KK_Y_INV, KK_Z_INV_FWD, KK_Z_INV_BWD, KK_REDUCE, KK_FIELD_STEP,
-  KK_PREPARE, KK_MARCH_FWD, KK_MARCH_BWD, KK_COUNT
+  KK_PREPARE, KK_MARCH_FWD, KK_MARCH_BWD, KK_PAIR_STEP, KK_QUADRATURE, KK_COUNT
 };
 extern const char* const kKernelKindNames[KK_COUNT];
 

@@ -234,6 +234,89 @@ __global__ void __launch_bounds__(PW_THREADS) k_qsum_cplx(const cpx<T>* __restri
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
+// Contour quadrature of Eq. 8 over the stored histories of both propagators:
+// accA = sum_n cA_n q_n qd_{Ns-n}, accB likewise (trapezoid weights on each block).  The
+// integrand is the product in the propagators' precision, the running sums are FP64.
+// Two grid points per thread (real) or one (complex).
+__device__ __forceinline__ void trap_w(int n, int Ns, int NsA, double* cA, double* cB) {
+  *cA = 0.0;
+  *cB = 0.0;
+  if (NsA > 0 && n <= NsA) *cA = (n == 0 || n == NsA) ? 0.5 : 1.0;
+  if (NsA < Ns && n >= NsA) *cB = (n == NsA || n == Ns) ? 0.5 : 1.0;
+}
+
+// Sum over n in [n0, n1] of w_n * q_n * qd_{Ns-n} for a pair of points, weights 1/2 at
+// both ends of the block (the block's trapezoid rule), FP64 running sums.
+template <typename T>
+__device__ __forceinline__ void quad_block(const T* __restrict__ hist, const T* __restrict__ qdh,
+                                           const T* __restrict__ qd0, long long M, int Ns, int n0, int n1,
+                                           long long i, double* s0, double* s1) {
+  double a0 = 0.0, a1 = 0.0;
+  if (n1 > n0) {
+#pragma unroll 4
+    for (int n = n0; n <= n1; n++) {
+      const int m = Ns - n;
+      const cpx<T> q = reinterpret_cast<const cpx<T>*>(hist + (long long)n * M)[i];
+      const cpx<T> d = reinterpret_cast<const cpx<T>*>(m == 0 ? qd0 : qdh + (long long)m * M)[i];
+      const double w = (n == n0 || n == n1) ? 0.5 : 1.0;
+      a0 = fma(w, widen(q.x * d.x), a0);
+      a1 = fma(w, widen(q.y * d.y), a1);
+    }
+  }
+  *s0 = a0;
+  *s1 = a1;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_quadrature_real(const T* __restrict__ hist, const T* __restrict__ qdh,
+                                                                const T* __restrict__ qd0, long long M, int Ns, int NsA,
+                                                                double* __restrict__ accA, double* __restrict__ accB) {
+  const long long M2 = M / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M2; i += (long long)gridDim.x * blockDim.x) {
+    double a0, a1, b0, b1;
+    quad_block<T>(hist, qdh, qd0, M, Ns, 0, NsA, i, &a0, &a1);
+    quad_block<T>(hist, qdh, qd0, M, Ns, NsA, Ns, i, &b0, &b1);
+    reinterpret_cast<double2*>(accA)[i] = make_double2(a0, a1);
+    reinterpret_cast<double2*>(accB)[i] = make_double2(b0, b1);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void quad_block_c(const cpx<T>* __restrict__ hist, const cpx<T>* __restrict__ qdh,
+                                             const cpx<T>* __restrict__ qd0, long long M, int Ns, int n0, int n1,
+                                             long long i, double* sr, double* si) {
+  double ar = 0.0, ai = 0.0;
+  if (n1 > n0) {
+#pragma unroll 4
+    for (int n = n0; n <= n1; n++) {
+      const int m = Ns - n;
+      const cpx<T> q = hist[(long long)n * M + i];
+      const cpx<T> d = (m == 0 ? qd0 : qdh + (long long)m * M)[i];
+      const cpx<T> pq = cmul(q, d);
+      const double w = (n == n0 || n == n1) ? 0.5 : 1.0;
+      ar = fma(w, widen(pq.x), ar);
+      ai = fma(w, widen(pq.y), ai);
+    }
+  }
+  *sr = ar;
+  *si = ai;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_quadrature_cplx(const cpx<T>* __restrict__ hist,
+                                                                const cpx<T>* __restrict__ qdh,
+                                                                const cpx<T>* __restrict__ qd0, long long M, int Ns,
+                                                                int NsA, double2* __restrict__ accA,
+                                                                double2* __restrict__ accB) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    double ar, ai, br, bi;
+    quad_block_c<T>(hist, qdh, qd0, M, Ns, 0, NsA, i, &ar, &ai);
+    quad_block_c<T>(hist, qdh, qd0, M, Ns, NsA, Ns, i, &br, &bi);
+    accA[i] = make_double2(ar, ai);
+    accB[i] = make_double2(br, bi);
+  }
+}
+
 // Q, lnQ (principal branch) and H = C dV field_sum - C V lnQ (Eqs. 3, 4).
 static __global__ void k_observables(double* __restrict__ s, double M, double C) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;

@@ -3,6 +3,8 @@
 #pragma once
 #include <math.h>
 
+#include <string.h>
+
 #include <vector>
 
 #include <type_traits>
@@ -38,21 +40,9 @@ namespace pft {
     default: return cudaErrorInvalidValue;                                                                         \
   }
 
-// batch sizes (grid axes up to 64)
-#define PFT_BATCH_AXIS(n, ...)                                                                                     \
-  switch (n) {                                                                                                     \
-    PFT_CASE(4, __VA_ARGS__) PFT_CASE(6, __VA_ARGS__) PFT_CASE(8, __VA_ARGS__) PFT_CASE(12, __VA_ARGS__)           \
-    PFT_CASE(16, __VA_ARGS__) PFT_CASE(24, __VA_ARGS__) PFT_CASE(32, __VA_ARGS__) PFT_CASE(48, __VA_ARGS__)        \
-    PFT_CASE(64, __VA_ARGS__)                                                                                      \
-    default: return cudaErrorInvalidValue;                                                                         \
-  }
-#define PFT_BATCH_HALF(n, ...)                                                                                     \
-  switch (n) {                                                                                                     \
-    PFT_CASE(2, __VA_ARGS__) PFT_CASE(3, __VA_ARGS__) PFT_CASE(4, __VA_ARGS__) PFT_CASE(6, __VA_ARGS__)            \
-    PFT_CASE(8, __VA_ARGS__) PFT_CASE(12, __VA_ARGS__) PFT_CASE(16, __VA_ARGS__) PFT_CASE(24, __VA_ARGS__)         \
-    PFT_CASE(32, __VA_ARGS__)                                                                                      \
-    default: return cudaErrorInvalidValue;                                                                         \
-  }
+// batched pass launches cover every compiled size
+#define PFT_BATCH_AXIS PFT_DISPATCH_AXIS
+#define PFT_BATCH_HALF PFT_DISPATCH_HALF
 
 // Quadrature weights of the contour integrals (Eq. 8): trapezoid rule on each block.
 inline void trapezoid_weight(int n, int Ns, int NsA, double* cA, double* cB) {
@@ -362,6 +352,7 @@ class EngineT : public Engine {
       // a fresh error word for this solve
       if ((e = cudaMemsetAsync(c.sync, 0, 4 * sizeof(unsigned), c.stream)) != cudaSuccess) return e;
     }
+    if (!res && c.concurrent) return record_solve_concurrent(c);
     // forward march (Eqs. 5, 13)
     if (res) {
       e = (c.march == 2) ? resident_march(c, false) : persist_march(c, false);
@@ -430,22 +421,52 @@ class EngineT : public Engine {
   cudaError_t batch_contour_step(const BatchGeom& g, const BatchStep* st, int nact, int epi,
                                  cudaStream_t stream) override {
     if (nact <= 0) return cudaSuccess;
-    const int nx = g.n[0], ny = g.n[1], nz = g.n[2];
-    const long long npen = (long long)nx * ny;
-    const long long nzc = g.nzh;
+    cudaError_t e = batch_zf(g, st, nact, stream);
+    if (e != cudaSuccess) return e;
+    if ((e = batch_mid(g, st, nact, stream)) != cudaSuccess) return e;
+    return batch_zi(g, st, nact, epi, stream);
+  }
+
+  cudaError_t batch_zf(const BatchGeom& g, const BatchStep* st, int nact, cudaStream_t stream) {
+    const long long npen = (long long)g.n[0] * g.n[1];
+    const int nz = g.n[2];
     cudaError_t e = cudaSuccess;
     if (g.kind == PFT_SCFT_REAL) {
       PFT_BATCH_HALF(nz / 2, e = (bz_r2c<N>(st, npen, nact, stream)));
     } else {
       PFT_BATCH_AXIS(nz, e = (bz_c2c<N>(st, npen, nact, stream)));
     }
-    if (e != cudaSuccess) return e;
+    return e;
+  }
+
+  cudaError_t batch_zz(const BatchGeom& g, const BatchStep* st, int nact, cudaStream_t stream) {
+    const long long npen = (long long)g.n[0] * g.n[1];
+    const int nz = g.n[2];
+    cudaError_t e = cudaSuccess;
+    if (g.kind == PFT_SCFT_REAL) {
+      PFT_BATCH_HALF(nz / 2, e = (bzz_r2c<N>(st, npen, nact, stream)));
+    } else {
+      PFT_BATCH_AXIS(nz, e = (bzz_c2c<N>(st, npen, nact, stream)));
+    }
+    return e;
+  }
+
+  cudaError_t batch_mid(const BatchGeom& g, const BatchStep* st, int nact, cudaStream_t stream) {
+    const int nx = g.n[0], ny = g.n[1];
+    const long long nzc = g.nzh;
+    cudaError_t e = cudaSuccess;
     PFT_BATCH_AXIS(ny, e = (bs<N, 0>(st, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, nact, stream)));
     if (e != cudaSuccess) return e;
     PFT_BATCH_AXIS(nx, e = (bs<N, 2>(st, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, nact, stream)));
     if (e != cudaSuccess) return e;
     PFT_BATCH_AXIS(ny, e = (bs<N, 1>(st, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, nact, stream)));
-    if (e != cudaSuccess) return e;
+    return e;
+  }
+
+  cudaError_t batch_zi(const BatchGeom& g, const BatchStep* st, int nact, int epi, cudaStream_t stream) {
+    const long long npen = (long long)g.n[0] * g.n[1];
+    const int nz = g.n[2];
+    cudaError_t e = cudaSuccess;
     if (g.kind == PFT_SCFT_REAL) {
       if (epi == 0) {
         PFT_BATCH_HALF(nz / 2, e = (bzi_c2r<N, 0>(st, npen, nact, stream)));
@@ -462,7 +483,89 @@ class EngineT : public Engine {
     return e;
   }
 
+  // Both marches at once (Eqs. 5, 13): step s of q and step s of qd in the same five
+  // launches (two members), then Q (Eq. 4), the quadrature of Eq. 8 over the two stored
+  // histories, densities and H.
+  cudaError_t prepare_concurrent(CtxData& c) {
+    const size_t we = (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
+    const size_t slice = (size_t)c.M * we;
+    cudaError_t e;
+    if (!c.qdh) {
+      e = cudaMalloc(&c.qdh, (size_t)(c.Ns + 1) * slice);
+      if (e != cudaSuccess) return e;
+      c.bytes += (size_t)(c.Ns + 1) * slice;
+    }
+    if (!c.steps2) {
+      std::vector<BatchStep> h((size_t)2 * c.Ns);
+      const char* hist = (const char*)c.hist;
+      char* qdh = (char*)c.qdh;
+      const char* t = (const char*)c.tables;
+      for (int s = 1; s <= c.Ns; s++) {
+        BatchStep& f = h[(size_t)2 * (s - 1)];
+        BatchStep& b = h[(size_t)2 * (s - 1) + 1];
+        memset(&f, 0, sizeof(f));
+        memset(&b, 0, sizeof(b));
+        f.in = hist + (size_t)(s - 1) * slice;
+        f.B = (s <= c.NsA) ? c.BA : c.BB;
+        f.out = (void*)(hist + (size_t)s * slice);
+        f.spec = c.spec;
+        const int nb = c.Ns + 1 - s;
+        b.in = (s == 1) ? c.qd0 : (const void*)(qdh + (size_t)(s - 1) * slice);
+        b.B = (nb <= c.NsA) ? c.BA : c.BB;
+        b.out = qdh + (size_t)s * slice;
+        b.spec = c.spec2;
+        if (s < c.Ns) {
+          f.Bnext = (s + 1 <= c.NsA) ? c.BA : c.BB;
+          b.Bnext = (nb - 1 <= c.NsA) ? c.BA : c.BB;
+        }
+        for (int a = 0; a < 4; a++) f.tw[a] = b.tw[a] = t + c.tw_off[a];
+        for (int a = 0; a < 3; a++) f.d[a] = b.d[a] = t + c.d_off[a];
+      }
+      e = cudaMalloc(&c.steps2, h.size() * sizeof(BatchStep));
+      if (e != cudaSuccess) return e;
+      c.bytes += h.size() * sizeof(BatchStep);
+      e = cudaMemcpy(c.steps2, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t record_solve_concurrent(CtxData& c) {
+    BatchGeom g;
+    for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
+    g.kind = c.kind;
+    g.nzh = c.nzh;
+    const BatchStep* st = (const BatchStep*)c.steps2;
+    cudaError_t e;
+    // z forward of step 1, then per step: y, x (D), y^-1, and the z inverse of step s
+    // fused with the z forward of step s+1
+    mark(c, KK_PAIR_STEP);
+    if ((e = batch_zf(g, st, 2, c.stream)) != cudaSuccess) return e;
+    for (int s = 1; s <= c.Ns; s++) {
+      mark(c, KK_PAIR_STEP);
+      const BatchStep* ss = st + (size_t)2 * (s - 1);
+      if ((e = batch_mid(g, ss, 2, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_zz(g, ss, 2, c.stream)) != cudaSuccess) return e;
+    }
+    if ((e = solve_mid(c)) != cudaSuccess) return e;
+    mark(c, KK_QUADRATURE);
+    const int blocks = c.sms * 8;
+    if (c.kind == PFT_SCFT_REAL) {
+      k_quadrature_real<T><<<blocks, PW_THREADS, 0, c.stream>>>((const T*)c.hist, (const T*)c.qdh, (const T*)c.qd0,
+                                                               c.M, c.Ns, c.NsA, (double*)c.accA, (double*)c.accB);
+    } else {
+      k_quadrature_cplx<T><<<blocks, PW_THREADS, 0, c.stream>>>((const Z*)c.hist, (const Z*)c.qdh, (const Z*)c.qd0, c.M,
+                                                               c.Ns, c.NsA, (double2*)c.accA, (double2*)c.accB);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return solve_tail(c);
+  }
+
   cudaError_t enqueue_solve(CtxData& c) override {
+    if (c.march == 1 && c.concurrent) {
+      cudaError_t e = prepare_concurrent(c);
+      if (e != cudaSuccess) return e;
+    }
     // the resident march is a handful of launches per solve: it runs without a graph
     if (!c.use_graph || c.profiling || c.march >= 2) return record_solve(c);
     if (!c.graph_valid) {
@@ -623,6 +726,20 @@ class EngineT : public Engine {
     constexpr int P = PencilsPerCta<T, N2>::v;
     const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
     kb_zi_c2r<T, N2, EPI><<<grid, P * Plan<N2>::TPC, (size_t)P * pencil_ld<T>(N2) * sizeof(Z), stream>>>(st, npen);
+    return cudaGetLastError();
+  }
+  template <int N2>
+  static cudaError_t bzz_r2c(const BatchStep* st, long long npen, int nact, cudaStream_t stream) {
+    constexpr int P = PencilsPerCta<T, N2>::v;
+    const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
+    kb_zz_r2c<T, N2><<<grid, P * Plan<N2>::TPC, (size_t)P * pencil_ld<T>(N2) * sizeof(Z), stream>>>(st, npen);
+    return cudaGetLastError();
+  }
+  template <int N>
+  static cudaError_t bzz_c2c(const BatchStep* st, long long npen, int nact, cudaStream_t stream) {
+    constexpr int P = PencilsPerCta<T, N>::v;
+    const dim3 grid((unsigned)((npen + P - 1) / P), (unsigned)nact);
+    kb_zz_c2c<T, N><<<grid, P * Plan<N>::TPC, (size_t)P * pencil_ld<T>(N) * sizeof(Z), stream>>>(st, npen);
     return cudaGetLastError();
   }
   template <int N>

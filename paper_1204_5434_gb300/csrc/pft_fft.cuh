@@ -40,6 +40,20 @@ template <bool INV, typename Z> __device__ __forceinline__ Z rot90(Z a) {
   return r;
 }
 
+// float -> double by bit manipulation on the integer pipe (exact for zero and normal
+// floats; the propagator products are never subnormal, infinite or NaN in a sane solve,
+// and a subnormal would only be flushed to zero): GB300 runs F2F.F64 on its 1/64-rate
+// FP64 pipe, which the quadrature needs for its one DFMA per term.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return (u & 0x80000000u) ? -0.0 : 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7fffffu) >> 3);
+  const unsigned lo = (u & 0x7u) << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // ------------------------------------------------------------ small DFT kernels
 // Forward: y_k = sum_n a_n exp(-2 pi i n k / R); inverse: exp(+...), unnormalised.
 template <int R, bool INV, typename Z> struct Dft;

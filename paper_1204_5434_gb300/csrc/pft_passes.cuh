@@ -216,8 +216,8 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
     if (EPI == 1) {
       // integrand q qd in the propagators' precision, sum in FP64 (one DFMA each)
       const cpx<T> pp = reinterpret_cast<const cpx<T>*>(partner)[m];
-      const double p0 = (double)(y.x * pp.x);
-      const double p1 = (double)(y.y * pp.y);
+      const double p0 = widen(y.x * pp.x);
+      const double p1 = widen(y.y * pp.y);
       if (cA != 0.0) {
         double2* a = reinterpret_cast<double2*>(accA) + m;
         double2 av = *a;
@@ -313,8 +313,8 @@ __device__ __forceinline__ void zi_c2c_body(const cpx<T>* __restrict__ spec, con
       // integrand q qd in the propagators' precision, sum in FP64
       const cpx<T> pq = cmul(y, partner[m]);
       double2 pr;
-      pr.x = (double)pq.x;
-      pr.y = (double)pq.y;
+      pr.x = widen(pq.x);
+      pr.y = widen(pq.y);
       if (cA != 0.0) {
         double2 a = accA[m];
         a.x += cA * pr.x;

@@ -156,8 +156,8 @@ __device__ __forceinline__ void zz_tile(const PersistArgs& a, long long tile, bo
         for (int i = 0; i < E; i++) av[i] = acc[t + TPC * i];
 #pragma unroll
         for (int i = 0; i < E; i++) {
-          av[i].x += c * (double)(v[i].x * pv[i].x);
-          av[i].y += c * (double)(v[i].y * pv[i].y);
+          av[i].x += c * widen(v[i].x * pv[i].x);
+          av[i].y += c * widen(v[i].y * pv[i].y);
           acc[t + TPC * i] = av[i];
         }
       }

@@ -220,8 +220,8 @@ __device__ __forceinline__ void row_phase(float2* __restrict__ W, int p, int mod
 #pragma unroll
           for (int i = 0; i < E; i++) {
             // FP32 integrand, FP64 sum (one DFMA per value)
-            av[i].x += c * (double)(v[i].x * pv[i].x);
-            av[i].y += c * (double)(v[i].y * pv[i].y);
+            av[i].x += c * widen(v[i].x * pv[i].x);
+            av[i].y += c * widen(v[i].y * pv[i].y);
             acc[t + TPC * i] = av[i];
           }
         }
