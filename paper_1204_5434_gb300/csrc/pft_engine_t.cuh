@@ -12,6 +12,7 @@
 #include "pft_engine_impl.cuh"
 #include "pft_batch.cuh"
 #include "pft_persist.cuh"
+#include "pft_plane.cuh"
 #include "pft_resident.cuh"
 
 namespace pft {
@@ -537,6 +538,22 @@ class EngineT : public Engine {
     g.nzh = c.nzh;
     const BatchStep* st = (const BatchStep*)c.steps2;
     cudaError_t e;
+    if (plane_supported(c)) {
+      // plane kernel (z and y of step 1), then per step: x pass, plane kernel
+      // (y^-1, z^-1 of step s fused with z of step s+1, y)
+      mark(c, KK_PAIR_STEP);
+      if ((e = batch_plane(c, st, 0)) != cudaSuccess) return e;
+      const int nx = c.n[0], ny = c.n[1];
+      const long long nzc = c.nzh;
+      for (int s = 1; s <= c.Ns; s++) {
+        mark(c, KK_PAIR_STEP);
+        const BatchStep* ss = st + (size_t)2 * (s - 1);
+        PFT_BATCH_AXIS(nx, e = (bs<N, 2>(ss, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 2, c.stream)));
+        if (e != cudaSuccess) return e;
+        if ((e = batch_plane(c, ss, 1)) != cudaSuccess) return e;
+      }
+      return finish_concurrent(c);
+    }
     // z forward of step 1, then per step: y, x (D), y^-1, and the z inverse of step s
     // fused with the z forward of step s+1
     mark(c, KK_PAIR_STEP);
@@ -547,6 +564,12 @@ class EngineT : public Engine {
       if ((e = batch_mid(g, ss, 2, c.stream)) != cudaSuccess) return e;
       if ((e = batch_zz(g, ss, 2, c.stream)) != cudaSuccess) return e;
     }
+    return finish_concurrent(c);
+  }
+
+  // Q, the quadrature over both histories, densities and H
+  cudaError_t finish_concurrent(CtxData& c) {
+    cudaError_t e;
     if ((e = solve_mid(c)) != cudaSuccess) return e;
     mark(c, KK_QUADRATURE);
     const int blocks = c.sms * 8;
@@ -559,6 +582,37 @@ class EngineT : public Engine {
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     return solve_tail(c);
+  }
+
+  // The plane kernel (y and z of a step in shared memory): FP32 real fields on 64^3 or
+  // 128^3 style grids (ny = nz in {64, 128}).
+  static bool plane_supported(const CtxData& c) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return false;
+    } else {
+      return c.kind == PFT_SCFT_REAL && c.n[1] == c.n[2] && (c.n[1] == 64 || c.n[1] == 128);
+    }
+  }
+
+  template <int NY, int MODE>
+  static cudaError_t launch_plane(const BatchStep* st, int nx, cudaStream_t stream) {
+    using R = PlaneCfg<NY, NY>;
+    auto kern = kb_plane_r2c<NY, NY, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)nx, 2u), R::THREADS, R::SMEM, stream>>>(st, nx);
+    return cudaGetLastError();
+  }
+
+  cudaError_t batch_plane(CtxData& c, const BatchStep* st, int mode) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      const int nx = c.n[0];
+      if (c.n[1] == 64) return mode ? launch_plane<64, 1>(st, nx, c.stream) : launch_plane<64, 0>(st, nx, c.stream);
+      if (c.n[1] == 128) return mode ? launch_plane<128, 1>(st, nx, c.stream) : launch_plane<128, 0>(st, nx, c.stream);
+      return cudaErrorNotSupported;
+    }
   }
 
   cudaError_t enqueue_solve(CtxData& c) override {
