@@ -207,6 +207,40 @@ def _variable_cell(pft, torch, prec, steps, warmup, wpa, wma, lam_L=0.05):
             "timing": "host wall clock around synchronised steps (the gradient call reads back 3 scalars)"}
 
 
+def _cl(pft, torch, w, prec, steps, warmup=1):
+    """Complex Langevin field updates (solve + Euler-Maruyama step with the device Philox
+    noise) of a complex-field workload, timed with CUDA events on the context stream."""
+    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, pft.PFT_CL_COMPLEX, prec, seed=w.seed)
+    h = s.h
+    wp, wm = wl.fields(w)
+    pft.pft_set_fields(h, wp, wm)
+
+    def one():
+        pft.pft_solve(h)
+        pft.pft_field_step(h, pft.PFT_STEP_CL_EULER_MARUYAMA, w.dt)
+    for _ in range(warmup):
+        one()
+    pft.pft_synchronize(h)
+    st = torch.cuda.ExternalStream(pft.pft_get_stream(h))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        one()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    obs = pft.pft_get_observables(h)
+    mem = pft.pft_memory_bytes(h)
+    s.close()
+    units = 2 * w.M * w.Ns
+    bpu = 44.0 if prec == pft.PFT_FP32_MIXED else 72.0
+    peak, _ = _peaks()
+    return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
+            "hbm_roofline_frac": bpu * units / (ms * 1e-3) / 1e9 / peak, "bytes_per_unit": bpu,
+            "device_bytes": mem, "H_last": [obs["H"].real, obs["H"].imag]}
+
+
 def _batch(pft, prec, updates=2):
     """The uneven batch: 256 instances, grids {32,48,64}^3, Ns {50,100,200}, half SCFT
     and half CL; graph-captured batched launches against one launch sequence per instance."""
@@ -341,6 +375,11 @@ def run(args):
                     "h2d_bytes_per_step": 2 * WORK.M * 8, "d2h_bytes_per_step": 2 * WORK.M * 8},
         }
     vc = _variable_cell(pft, torch, pft.PFT_FP32_MIXED, max(2, args.steps // 3), 1, wpa, wma)
+    cl = {"cl64_fp32": _cl(pft, torch, wl.CL64, pft.PFT_FP32_MIXED, 10),
+          "cl64_fp64": _cl(pft, torch, wl.CL64, pft.PFT_FP64, 3),
+          "cl256_fp32": _cl(pft, torch, wl.CL256, pft.PFT_FP32_MIXED, 3),
+          "cl256_fp64": _cl(pft, torch, wl.CL256, pft.PFT_FP64, 1)}
+    torch.cuda.empty_cache()
     batch = _batch(pft, pft.PFT_FP32_MIXED)
     if rank != 0:
         if ws > 1:
@@ -368,6 +407,7 @@ def run(args):
         "fp32_over_fp64": main["value"] / fp64["value"],
         "variable_cell": vc,
         "batch": batch,
+        "complex_langevin": cl,
     }
     del fp64_flops_unit
     print(json.dumps(line), flush=True)

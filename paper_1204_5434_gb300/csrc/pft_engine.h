@@ -83,6 +83,7 @@ struct CtxData {
   bool concurrent = true;
   void* qdh = nullptr;      // [(Ns+1) * M] qd_0..qd_Ns (slice 0 unused: qd0 holds it)
   void* steps2 = nullptr;   // [2 * Ns] BatchStep: forward and conjugate step s
+  void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
   // profiling: an event recorded before every launch (eager solves only)
   bool profiling = false;
   std::vector<cudaEvent_t> ev;

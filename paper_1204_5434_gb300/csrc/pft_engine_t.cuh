@@ -704,6 +704,7 @@ class EngineT : public Engine {
     }
     cudaError_t e = cudaMemsetAsync(c.partials, 0, (size_t)c.npart * 3 * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
+    if (c.march == 1 && c.concurrent && c.qdh) return gradients_from_histories(c);
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const Z* twx = tab<Z>(c, c.tw_off[0]);
     const Z* twy = tab<Z>(c, c.tw_off[1]);
@@ -744,6 +745,61 @@ class EngineT : public Engine {
       PFT_DISPATCH_HALF(nz / 2, e = launch_zi_c2r<N, 0>(c, u, B, out, nullptr, nullptr, nullptr, 0.0, 0.0, npen, twh,
                                                         twz));
       if (e != cudaSuccess) return e;
+    }
+    k_reduce_final<3><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_STRESS);
+    return cudaGetLastError();
+  }
+
+  // Box derivative from the two stored histories of the last (concurrent) solve: for each
+  // split step n the forward spectra of B_n qd_{Ns-n} and B_n q_{n-1} (two members of
+  // batched z, y and x forward passes), then the contraction.
+  cudaError_t gradients_from_histories(CtxData& c) {
+    const size_t slice = (size_t)c.M * sizeof(T);
+    cudaError_t e;
+    if (!c.stepsg) {
+      std::vector<BatchStep> h((size_t)2 * c.Ns);
+      const char* hist = (const char*)c.hist;
+      const char* qdh = (const char*)c.qdh;
+      const char* t = (const char*)c.tables;
+      for (int n = 1; n <= c.Ns; n++) {
+        BatchStep& u = h[(size_t)2 * (n - 1)];
+        BatchStep& v = h[(size_t)2 * (n - 1) + 1];
+        memset(&u, 0, sizeof(u));
+        memset(&v, 0, sizeof(v));
+        const int m = c.Ns - n;
+        u.in = (m == 0) ? c.qd0 : (const void*)(qdh + (size_t)m * slice);
+        v.in = hist + (size_t)(n - 1) * slice;
+        u.B = v.B = (n <= c.NsA) ? c.BA : c.BB;
+        u.spec = c.spec;
+        v.spec = c.spec2;
+        for (int a = 0; a < 4; a++) u.tw[a] = v.tw[a] = t + c.tw_off[a];
+        for (int a = 0; a < 3; a++) u.d[a] = v.d[a] = t + c.d_off[a];
+      }
+      e = cudaMalloc(&c.stepsg, h.size() * sizeof(BatchStep));
+      if (e != cudaSuccess) return e;
+      c.bytes += h.size() * sizeof(BatchStep);
+      e = cudaMemcpy(c.stepsg, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+    BatchGeom g;
+    for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
+    g.kind = c.kind;
+    g.nzh = c.nzh;
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const long long nzc = c.nzh;
+    const double* gx = tab<double>(c, c.g_off[0]);
+    const double* gy = tab<double>(c, c.g_off[1]);
+    const double* gz = tab<double>(c, c.g_off[2]);
+    const BatchStep* st = (const BatchStep*)c.stepsg;
+    for (int n = 1; n <= c.Ns; n++) {
+      const BatchStep* ss = st + (size_t)2 * (n - 1);
+      if ((e = batch_zf(g, ss, 2, c.stream)) != cudaSuccess) return e;
+      PFT_BATCH_AXIS(ny, e = (bs<N, 0>(ss, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, 2, c.stream)));
+      if (e != cudaSuccess) return e;
+      PFT_BATCH_AXIS(nx, e = (bs<N, 0>(ss, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 2, c.stream)));
+      if (e != cudaSuccess) return e;
+      k_stress_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)c.spec, (const Z*)c.spec2, gx, gy, gz, nx, ny,
+                                                            (int)nzc, nz, c.ds, c.partials);
     }
     k_reduce_final<3><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_STRESS);
     return cudaGetLastError();

@@ -370,3 +370,80 @@ def test_cl_noise_variance():
     assert abs(std ** 2 - 2 * 0.01 / (50.0 * 0.5)) < 1e-18
     ep, em = o.cl_noise(1, 0, 0, 200000, std)
     assert abs(ep.var() / std ** 2 - 1) < 0.02 and abs(em.var() / std ** 2 - 1) < 0.02
+
+
+# ------------------------------------------------------------ RQM4 (Eq. 13)
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_rqm4_uniform_fields_exact(kind):
+    """Uniform fields: every split step multiplies by exp(-w h) exactly, so the
+    Richardson combination (4 e^{-w h} - e^{-w h})/3 is exact too."""
+    n, L, Ns, fA = (4, 6, 4), (2.0, 3.0, 2.0), 14, 0.4
+    fa = o.n_A_steps(Ns, fA) / Ns
+    if kind == o.SCFT_REAL:
+        wp, wm = np.full(n, 0.3), np.full(n, -0.9)
+        wA, wB = 1.2, -0.6
+    else:
+        wp, wm = np.full(n, 0.2 + 0.1j), np.full(n, -0.5 + 0.2j)
+        wA, wB = 1j * (0.2 + 0.1j) + 0.5 - 0.2j, 1j * (0.2 + 0.1j) - 0.5 + 0.2j
+    s = o.solve(wp, wm, n, L, Ns, fA, kind, scheme=o.RQM4)
+    Qx = np.exp(-(fa * wA + (1 - fa) * wB))
+    assert abs(s.Q - Qx) <= 1e-13 * abs(Qx)
+    assert np.max(np.abs(s.phiA - fa)) < 1e-13
+
+
+def test_simpson_weights_exact_for_cubics():
+    """The composite rule (Simpson, 3/8 for an odd tail, trapezoid for one interval)
+    integrates cubics exactly on any block [n0, n1]."""
+    Ns = 17
+    s = np.arange(Ns + 1) / Ns
+    for n0, n1 in [(0, 17), (0, 6), (6, 17), (3, 4), (5, 5), (2, 9)]:
+        c = o.simpson_weights(n0, n1, Ns + 1)
+        a, b = n0 / Ns, n1 / Ns
+        f = 1.0 + 2.0 * s - 3.0 * s ** 2 + 5.0 * s ** 3
+        exact = (b - a) + (b ** 2 - a ** 2) - (b ** 3 - a ** 3) + 1.25 * (b ** 4 - a ** 4)
+        if n1 - n0 == 1:
+            continue  # the trapezoid fallback is exact only for linear functions
+        assert abs(np.sum(c * f) / Ns - exact) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_rqm4_slice_invariance_and_sum_rules(kind):
+    """The RQM4 step is a combination of symmetric operators, hence symmetric: Q is the
+    same at every cut, and with a rule exact on constants <phiA> = fA_eff exactly."""
+    n, L, Ns, fA = (6, 4, 4), (3.0, 2.0, 2.0), 15, 0.4
+    wp, wm = _rand_fields(n, kind, 31)
+    s = o.solve(wp, wm, n, L, Ns, fA, kind, scheme=o.RQM4)
+    Qn = o.slice_partition_functions(s)
+    assert np.max(np.abs(Qn - s.Q)) <= 1e-13 * abs(s.Q)
+    assert abs(s.phiA.mean() - o.n_A_steps(Ns, fA) / Ns) < 1e-13
+    assert abs((s.phiA + s.phiB).mean() - 1.0) < 1e-13
+
+
+def test_rqm4_fourth_order_convergence_to_continuum():
+    """Q(Ns) from the scheme of Eq. 13 converges to the exact-in-s answer (dense expm)
+    as ds^4: error ratios for Ns = 8 .. 128 rise towards 16 (14.0, 15.0, 15.5, 15.7)."""
+    n, L = (8, 4, 4), (4.0, 2.0, 2.0)
+    xs = np.arange(8) * 4.0 / 8
+    wm = np.broadcast_to(1.5 * np.cos(2 * np.pi * xs / 4.0)[:, None, None], n).copy()
+    wp = 0.3 * np.broadcast_to(np.sin(2 * np.pi * xs / 4.0)[:, None, None], n).copy()
+    wA, wB = o.species_fields(wp, wm, o.SCFT_REAL)
+    Qs = o.continuum_Q(wA, wB, n, L, 0.25)
+    errs = [o.solve(wp, wm, n, L, Ns, 0.25, o.SCFT_REAL, scheme=o.RQM4).Q - Qs for Ns in (8, 16, 32, 64, 128)]
+    ratios = [errs[i] / errs[i + 1] for i in range(4)]
+    assert all(13.5 < r < 16.5 for r in ratios), ratios
+    assert ratios[-1] > 15.5 and all(ratios[i] < ratios[i + 1] for i in range(3)), ratios
+    assert abs(errs[-1]) < 1e-9 * abs(Qs)
+
+
+def test_rqm4_densities_are_fourth_order_gradients():
+    """With RQM4 and Simpson weights phi is the lnQ gradient up to O(ds^4): the mismatch
+    against a finite difference falls by ~16 when Ns doubles."""
+    n, L, fA = (6, 4, 4), (3.0, 2.0, 2.0), 0.5
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 32, amp_p=0.2, amp_m=0.6)
+    idx = (1, 2, 3)
+    mism = []
+    for Ns in (64, 128):
+        s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL, scheme=o.RQM4)
+        fd = fd5(lambda h: o.solve(wp, _perturbed(wm, idx, h), n, L, Ns, fA, o.SCFT_REAL, scheme=o.RQM4).lnQ)
+        mism.append(abs(fd - (s.phiA - s.phiB)[idx] / wp.size))
+    assert mism[1] < mism[0] / 12.0, mism
