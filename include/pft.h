@@ -71,6 +71,13 @@ typedef enum { PFT_STEP_SCFT_EULER = 0, PFT_STEP_CL_EULER_MARUYAMA = 1 } pft_ste
  * step fused with the z forward of the next.  AUTO picks the fastest on GB300. */
 typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1, PFT_MARCH_RESIDENT = 2, PFT_MARCH_PERSISTENT = 3 } pft_march;
 
+/* Contour scheme.  SPLIT2: the 2nd-order split step A(ds) of Eq. 13 with the trapezoid
+ * rule per block for Eq. 8.  RQM4: the 4th-order Richardson combination of Eq. 13,
+ * q(s+ds) = -(1/3)[A(ds) - 4 A(ds/2) A(ds/2)] q, with composite Simpson weights per
+ * block (Simpson 3/8 on the last three intervals of an odd block, the trapezoid rule
+ * for a one-interval block); PASSES march only, no gradients. */
+typedef enum { PFT_SCHEME_SPLIT2 = 0, PFT_SCHEME_RQM4 = 1 } pft_scheme;
+
 typedef struct { int n[3]; double L[3]; } pft_grid;          /* grid points and box (Rg) */
 typedef struct { int Ns; double fA; } pft_chain;              /* contour steps, A fraction */
 typedef struct { double chiN; double C; pft_kind kind; } pft_model;
@@ -82,6 +89,7 @@ typedef struct {
   unsigned long long seed;  /* Philox key of the CL noise */
   unsigned long long instance; /* Philox counter word: independent replica streams */
   pft_march march;          /* PFT_MARCH_RESIDENT where it does not apply: PFT_ERR_UNSUPPORTED */
+  pft_scheme scheme;        /* PFT_SCHEME_SPLIT2 (0) or PFT_SCHEME_RQM4 */
 } pft_opts;
 
 /* Observables of the last solve.  Complex quantities are {re, im}; in SCFT mode the

@@ -77,7 +77,8 @@ void free_all(pft_ctx* c) {
   if (d.graph) cudaGraphExecDestroy(d.graph);
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
-                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync, d.qdh, d.steps2, d.stepsg};
+                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync, d.qdh, d.steps2, d.stepsg,
+                  d.BAh, d.BBh, d.rq, d.qw};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
@@ -136,6 +137,9 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   if (!(model->chiN > 0.0) || !(model->C > 0.0)) return fail(PFT_ERR_ARG, "chiN and C must be positive");
   if (model->kind != PFT_SCFT_REAL && model->kind != PFT_CL_COMPLEX) return fail(PFT_ERR_ARG, "unknown model kind");
   if (opts->precision != PFT_FP64 && opts->precision != PFT_FP32_MIXED) return fail(PFT_ERR_ARG, "unknown precision");
+  if (opts->scheme != PFT_SCHEME_SPLIT2 && opts->scheme != PFT_SCHEME_RQM4) return fail(PFT_ERR_ARG, "unknown scheme");
+  if (opts->scheme == PFT_SCHEME_RQM4 && opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES)
+    return fail(PFT_ERR_UNSUPPORTED, "the 4th-order scheme runs on the pass kernels only");
 
   pft_ctx* c = new pft_ctx();
   CtxData& d = c->d;
@@ -196,6 +200,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       return fail(PFT_ERR_UNSUPPORTED,
                   "persistent march needs FP32-mixed precision, real SCFT fields and a 64^3, 128^3 or 256^3 grid");
     }
+    d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
     if (opts->march == PFT_MARCH_RESIDENT) {
       d.march = 2;
     } else if (opts->march == PFT_MARCH_PERSISTENT) {
@@ -217,8 +222,11 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
       {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
       {&c->io, M * 16}, {(void**)&d.sync, 4 * sizeof(unsigned)},
+      // quarter-step Boltzmann factors of the 4th-order scheme
+      {d.scheme ? &d.BAh : nullptr, M * we}, {d.scheme ? &d.BBh : nullptr, M * we},
   };
   for (auto& a : plan) {
+    if (!a.p) continue;
     e = dalloc(d, a.p, a.b);
     if (e != cudaSuccess) {
       pft_status s = cuda_fail(e, "device allocation");
@@ -408,6 +416,8 @@ pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
   if (d.kind != PFT_SCFT_REAL) return fail(PFT_ERR_UNSUPPORTED, "gradients need real SCFT fields");
+  if (d.scheme != 0)
+    return fail(PFT_ERR_UNSUPPORTED, "gradients are the exact derivatives of the 2nd-order scheme only");
   if (!d.solved) return fail(PFT_ERR_STATE, "pft_gradients needs a solve at the current fields");
   double* gp = nullptr;
   double* gm = nullptr;
@@ -530,6 +540,13 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   out->bytes_per_launch[pft::KK_MARCH_FWD] = (double)d.Ns * (3 * M * we);
   out->bytes_per_launch[pft::KK_MARCH_BWD] = (double)d.Ns * (4 * M * we + 2 * M * 8.0);
   out->bytes_per_launch[pft::KK_PAIR_STEP] = 2 * (2 * M * we + Ms * ze) + 6 * (2 * Ms * ze) + 2 * (Ms * ze + 2 * M * we);
+  if (d.scheme == 1) {
+    // 4th-order step of both propagators: four z forwards, 18 strided passes, two z
+    // inverses, two fused z passes (B, out, Bnext), two combining z inverses (B, full, out)
+    out->bytes_per_launch[pft::KK_PAIR_STEP] = 4 * (2 * M * we + Ms * ze) + 18 * (2 * Ms * ze) +
+                                                2 * (Ms * ze + 2 * M * we) + 2 * (2 * Ms * ze + 3 * M * we) +
+                                                2 * (Ms * ze + 3 * M * we);
+  }
   out->bytes_per_launch[pft::KK_QUADRATURE] = 2.0 * (d.Ns + 1) * M * we + 2 * M * fe;
   return PFT_OK;
 }

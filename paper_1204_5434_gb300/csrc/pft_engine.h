@@ -84,6 +84,14 @@ struct CtxData {
   void* qdh = nullptr;      // [(Ns+1) * M] qd_0..qd_Ns (slice 0 unused: qd0 holds it)
   void* steps2 = nullptr;   // [2 * Ns] BatchStep: forward and conjugate step s
   void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
+  // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
+  // scratch slices for the full and the two half steps, quadrature weight tables
+  int scheme = 0;
+  void* BAh = nullptr;
+  void* BBh = nullptr;
+  size_t dh_off[3] = {0, 0, 0};
+  void* rq = nullptr;       // [3 * M]
+  double* qw = nullptr;     // [2 * (Ns+1)] weights of the A and B blocks
   // profiling: an event recorded before every launch (eager solves only)
   bool profiling = false;
   std::vector<cudaEvent_t> ev;

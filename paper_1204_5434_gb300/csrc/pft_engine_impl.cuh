@@ -204,6 +204,31 @@ __global__ void __launch_bounds__(PW_THREADS) k_prepare_cplx(const double2* __re
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
+// Half-step Boltzmann factors exp(-w ds/4) of the 4th-order scheme (the two A(ds/2)
+// blocks of Eq. 13), real SCFT fields and complex Langevin fields.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_half_boltz_real(const double* __restrict__ wp,
+                                                                const double* __restrict__ wm, T* __restrict__ BA,
+                                                                T* __restrict__ BB, double hds, long long M) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double p = wp[i], m = wm[i];
+    BA[i] = boltz<T>(p - m, hds);
+    BB[i] = boltz<T>(p + m, hds);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_half_boltz_cplx(const double2* __restrict__ wp,
+                                                                const double2* __restrict__ wm, cpx<T>* __restrict__ BA,
+                                                                cpx<T>* __restrict__ BB, double hds, long long M) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double2 p = wp[i], m = wm[i];
+    const double2 ip = make_double2(-p.y, p.x);
+    BA[i] = boltz_c<T>(make_double2(ip.x - m.x, ip.y - m.y), hds);
+    BB[i] = boltz_c<T>(make_double2(ip.x + m.x, ip.y + m.y), hds);
+  }
+}
+
 // Sum of q_Ns for Q (Eq. 4) and the m = 0 term of the quadrature (qd_0 = 1).
 template <typename T>
 __global__ void __launch_bounds__(PW_THREADS) k_qsum_real(const T* __restrict__ q, double* __restrict__ accA,
@@ -312,6 +337,60 @@ __global__ void __launch_bounds__(PW_THREADS) k_quadrature_cplx(const cpx<T>* __
     double ar, ai, br, bi;
     quad_block_c<T>(hist, qdh, qd0, M, Ns, 0, NsA, i, &ar, &ai);
     quad_block_c<T>(hist, qdh, qd0, M, Ns, NsA, Ns, i, &br, &bi);
+    accA[i] = make_double2(ar, ai);
+    accB[i] = make_double2(br, bi);
+  }
+}
+
+// Contour quadrature of Eq. 8 with a weight table: accA = sum_n w[n] q_n qd_{Ns-n},
+// accB = sum_n w[Ns+1+n] q_n qd_{Ns-n} (composite Simpson weights of the 4th-order
+// scheme).  Integrand in the propagators' precision, FP64 sums; two grid points per
+// thread (real) or one (complex).
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_quadrature_w_real(const T* __restrict__ hist, const T* __restrict__ qdh,
+                                                                  const T* __restrict__ qd0, long long M, int Ns,
+                                                                  const double* __restrict__ w,
+                                                                  double* __restrict__ accA, double* __restrict__ accB) {
+  const long long M2 = M / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M2; i += (long long)gridDim.x * blockDim.x) {
+    double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+#pragma unroll 2
+    for (int n = 0; n <= Ns; n++) {
+      const int m = Ns - n;
+      const cpx<T> q = reinterpret_cast<const cpx<T>*>(hist + (long long)n * M)[i];
+      const cpx<T> d = reinterpret_cast<const cpx<T>*>(m == 0 ? qd0 : qdh + (long long)m * M)[i];
+      const double p0 = widen(q.x * d.x), p1 = widen(q.y * d.y);
+      const double wa = w[n], wb = w[Ns + 1 + n];
+      a0 = fma(wa, p0, a0);
+      a1 = fma(wa, p1, a1);
+      b0 = fma(wb, p0, b0);
+      b1 = fma(wb, p1, b1);
+    }
+    reinterpret_cast<double2*>(accA)[i] = make_double2(a0, a1);
+    reinterpret_cast<double2*>(accB)[i] = make_double2(b0, b1);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_quadrature_w_cplx(const cpx<T>* __restrict__ hist,
+                                                                  const cpx<T>* __restrict__ qdh,
+                                                                  const cpx<T>* __restrict__ qd0, long long M, int Ns,
+                                                                  const double* __restrict__ w,
+                                                                  double2* __restrict__ accA,
+                                                                  double2* __restrict__ accB) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    double ar = 0.0, ai = 0.0, br = 0.0, bi = 0.0;
+#pragma unroll 2
+    for (int n = 0; n <= Ns; n++) {
+      const int m = Ns - n;
+      const cpx<T> pq = cmul(hist[(long long)n * M + i], (m == 0 ? qd0 : qdh + (long long)m * M)[i]);
+      const double pr = widen(pq.x), pi = widen(pq.y);
+      const double wa = w[n], wb = w[Ns + 1 + n];
+      ar = fma(wa, pr, ar);
+      ai = fma(wa, pi, ai);
+      br = fma(wb, pr, br);
+      bi = fma(wb, pi, bi);
+    }
     accA[i] = make_double2(ar, ai);
     accB[i] = make_double2(br, bi);
   }

@@ -41,6 +41,31 @@ namespace pft {
     default: return cudaErrorInvalidValue;                                                                         \
   }
 
+// Composite Simpson weights (in units of ds) of the slices n0..n1, added into w[n0..n1]:
+// 1/3, 4/3, 1/3 on each pair of intervals; with an odd interval count of at least three
+// the last three intervals take Simpson's 3/8 rule (3/8, 9/8, 9/8, 3/8); a block of one
+// interval takes the trapezoid rule.  Exact for cubics, the order of the 4th-order
+// scheme of Eq. 13.
+inline void simpson_block(int n0, int n1, double* w) {
+  const int len = n1 - n0;
+  if (len <= 0) return;
+  if (len == 1) {
+    w[n0] += 0.5;
+    w[n1] += 0.5;
+    return;
+  }
+  const int pairs_end = (len % 2 == 0) ? n1 : n1 - 3;
+  for (int a = n0; a < pairs_end; a += 2) {
+    w[a] += 1.0 / 3.0;
+    w[a + 1] += 4.0 / 3.0;
+    w[a + 2] += 1.0 / 3.0;
+  }
+  if (len % 2 == 1) {
+    const double e[4] = {3.0 / 8.0, 9.0 / 8.0, 9.0 / 8.0, 3.0 / 8.0};
+    for (int j = 0; j < 4; j++) w[pairs_end + j] += e[j];
+  }
+}
+
 // batched pass launches cover every compiled size
 #define PFT_BATCH_AXIS PFT_DISPATCH_AXIS
 #define PFT_BATCH_HALF PFT_DISPATCH_HALF
@@ -235,6 +260,11 @@ class EngineT : public Engine {
       c.g_off[a] = off;
       off = al(off + sizeof(double) * (size_t)dn[a]);
     }
+    // half-step diffusion tables exp(-k^2 ds/2) of the 4th-order scheme
+    for (int a = 0; a < 3; a++) {
+      c.dh_off[a] = off;
+      off = al(off + sizeof(T) * (size_t)dn[a]);
+    }
     if (!c.tables) {
       cudaError_t e = cudaMalloc(&c.tables, off);
       if (e != cudaSuccess) return e;
@@ -258,8 +288,13 @@ class EngineT : public Engine {
         const int mm = (m <= na / 2) ? m : m - na;
         const double k = 2.0 * M_PI * (double)mm / c.L[a];
         double dval = exp(-k * k * c.ds);
-        if (a == 0) dval /= Md;  // inverse-transform normalisation 1/M folded into D
+        double hval = exp(-k * k * c.ds * 0.5);
+        if (a == 0) {  // inverse-transform normalisation 1/M folded into D
+          dval /= Md;
+          hval /= Md;
+        }
         d[m] = (T)dval;
+        reinterpret_cast<T*>(h.data() + c.dh_off[a])[m] = (T)hval;
         g[m] = k * k;
       }
     }
@@ -287,6 +322,19 @@ class EngineT : public Engine {
           (const double2*)c.wp, (const double2*)c.wm, (Z*)c.BA, (Z*)c.BB, c.ds, c.chiN, c.M, c.partials);
     }
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
+    return half_boltz(c);
+  }
+
+  // quarter-step factors exp(-w ds/4) of the 4th-order scheme (nothing for SPLIT2)
+  cudaError_t half_boltz(CtxData& c) {
+    if (c.scheme != 1) return cudaGetLastError();
+    if (c.kind == PFT_SCFT_REAL) {
+      k_half_boltz_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.wp, (const double*)c.wm, (T*)c.BAh,
+                                                                 (T*)c.BBh, 0.5 * c.ds, c.M);
+    } else {
+      k_half_boltz_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const double2*)c.wp, (const double2*)c.wm, (Z*)c.BAh,
+                                                                 (Z*)c.BBh, 0.5 * c.ds, c.M);
+    }
     return cudaGetLastError();
   }
 
@@ -353,6 +401,7 @@ class EngineT : public Engine {
       // a fresh error word for this solve
       if ((e = cudaMemsetAsync(c.sync, 0, 4 * sizeof(unsigned), c.stream)) != cudaSuccess) return e;
     }
+    if (c.scheme == 1) return record_solve_rqm4(c);
     if (!res && c.concurrent) return record_solve_concurrent(c);
     // forward march (Eqs. 5, 13)
     if (res) {
@@ -471,14 +520,18 @@ class EngineT : public Engine {
     if (g.kind == PFT_SCFT_REAL) {
       if (epi == 0) {
         PFT_BATCH_HALF(nz / 2, e = (bzi_c2r<N, 0>(st, npen, nact, stream)));
-      } else {
+      } else if (epi == 1) {
         PFT_BATCH_HALF(nz / 2, e = (bzi_c2r<N, 1>(st, npen, nact, stream)));
+      } else {
+        PFT_BATCH_HALF(nz / 2, e = (bzi_c2r<N, 3>(st, npen, nact, stream)));
       }
     } else {
       if (epi == 0) {
         PFT_BATCH_AXIS(nz, e = (bzi_c2c<N, 0>(st, npen, nact, stream)));
-      } else {
+      } else if (epi == 1) {
         PFT_BATCH_AXIS(nz, e = (bzi_c2c<N, 1>(st, npen, nact, stream)));
+      } else {
+        PFT_BATCH_AXIS(nz, e = (bzi_c2c<N, 3>(st, npen, nact, stream)));
       }
     }
     return e;
@@ -584,6 +637,121 @@ class EngineT : public Engine {
     return solve_tail(c);
   }
 
+  // ------------------------------------------------------ 4th-order scheme
+  // One contour step of Eq. 13 for both propagators, six members per step:
+  //   0, 1  A(ds) q_{s-1} and A(ds) qd_{s-1}                  -> rq[0], rq[1]
+  //   2, 3  first A(ds/2) of each (z inverse fused with the z forward of the second)
+  //   4, 5  second A(ds/2), stored as (4 A(ds/2)A(ds/2) q - A(ds) q) / 3 -> q_s, qd_s
+  // Launches per step: z forward, y, x (D), y inverse of members 0-3; z inverse of 0-1;
+  // fused z inverse / z forward of 2-3; y, x (D/2), y inverse and z inverse of 4-5.
+  cudaError_t prepare_rqm4(CtxData& c) {
+    const size_t we = (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
+    const size_t slice = (size_t)c.M * we;
+    const size_t spec_b = (size_t)c.M * sizeof(Z);
+    cudaError_t e;
+    if (!c.qdh) {
+      if ((e = cudaMalloc(&c.qdh, (size_t)(c.Ns + 1) * slice)) != cudaSuccess) return e;
+      c.bytes += (size_t)(c.Ns + 1) * slice;
+    }
+    if (!c.rq) {
+      // four propagator slices, then two spectra
+      const size_t b = 4 * slice + 2 * spec_b;
+      if ((e = cudaMalloc(&c.rq, b)) != cudaSuccess) return e;
+      c.bytes += b;
+    }
+    if (!c.qw) {
+      std::vector<double> w((size_t)2 * (c.Ns + 1), 0.0);
+      simpson_block(0, c.NsA, w.data());
+      simpson_block(c.NsA, c.Ns, w.data() + (c.Ns + 1));
+      if ((e = cudaMalloc(&c.qw, w.size() * sizeof(double))) != cudaSuccess) return e;
+      c.bytes += w.size() * sizeof(double);
+      if ((e = cudaMemcpy(c.qw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    }
+    if (!c.steps2) {
+      char* rq = (char*)c.rq;
+      void* rqs[4] = {rq, rq + slice, rq + 2 * slice, rq + 3 * slice};
+      void* spec3 = rq + 4 * slice;
+      void* spec4 = rq + 4 * slice + spec_b;
+      std::vector<BatchStep> h((size_t)6 * c.Ns);
+      const char* hist = (const char*)c.hist;
+      char* qdh = (char*)c.qdh;
+      const char* t = (const char*)c.tables;
+      for (int s = 1; s <= c.Ns; s++) {
+        BatchStep* e6 = &h[(size_t)6 * (s - 1)];
+        memset(e6, 0, 6 * sizeof(BatchStep));
+        const int nb = c.Ns + 1 - s;  // block index of the conjugate march's step
+        const void* in[2] = {hist + (size_t)(s - 1) * slice,
+                             (s == 1) ? c.qd0 : (const void*)(qdh + (size_t)(s - 1) * slice)};
+        void* out[2] = {(void*)(hist + (size_t)s * slice), qdh + (size_t)s * slice};
+        const bool inA[2] = {s <= c.NsA, nb <= c.NsA};
+        void* full_spec[2] = {c.spec, c.spec2};
+        void* half_spec[2] = {spec3, spec4};
+        for (int p = 0; p < 2; p++) {
+          const void* Bf = inA[p] ? c.BA : c.BB;
+          const void* Bh = inA[p] ? c.BAh : c.BBh;
+          BatchStep& f = e6[p];
+          BatchStep& h1 = e6[2 + p];
+          BatchStep& h2 = e6[4 + p];
+          f.in = in[p];
+          f.B = Bf;
+          f.out = rqs[p];
+          f.spec = full_spec[p];
+          h1.in = in[p];
+          h1.B = Bh;
+          h1.out = rqs[2 + p];
+          h1.spec = half_spec[p];
+          h1.Bnext = Bh;
+          h2.B = Bh;
+          h2.out = out[p];
+          h2.partner = rqs[p];
+          h2.spec = half_spec[p];
+          for (BatchStep* b : {&f, &h1, &h2})
+            for (int a = 0; a < 4; a++) b->tw[a] = t + c.tw_off[a];
+          for (int a = 0; a < 3; a++) {
+            f.d[a] = t + c.d_off[a];
+            h1.d[a] = h2.d[a] = t + c.dh_off[a];
+          }
+        }
+      }
+      if ((e = cudaMalloc(&c.steps2, h.size() * sizeof(BatchStep))) != cudaSuccess) return e;
+      c.bytes += h.size() * sizeof(BatchStep);
+      e = cudaMemcpy(c.steps2, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  cudaError_t record_solve_rqm4(CtxData& c) {
+    BatchGeom g;
+    for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
+    g.kind = c.kind;
+    g.nzh = c.nzh;
+    const BatchStep* st = (const BatchStep*)c.steps2;
+    cudaError_t e;
+    for (int s = 1; s <= c.Ns; s++) {
+      mark(c, KK_PAIR_STEP);
+      const BatchStep* e6 = st + (size_t)6 * (s - 1);
+      if ((e = batch_zf(g, e6, 4, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_mid(g, e6, 4, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_zi(g, e6, 2, 0, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_zz(g, e6 + 2, 2, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_mid(g, e6 + 4, 2, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_zi(g, e6 + 4, 2, 3, c.stream)) != cudaSuccess) return e;
+    }
+    if ((e = solve_mid(c)) != cudaSuccess) return e;
+    mark(c, KK_QUADRATURE);
+    const int blocks = c.sms * 8;
+    if (c.kind == PFT_SCFT_REAL) {
+      k_quadrature_w_real<T><<<blocks, PW_THREADS, 0, c.stream>>>((const T*)c.hist, (const T*)c.qdh, (const T*)c.qd0,
+                                                                 c.M, c.Ns, c.qw, (double*)c.accA, (double*)c.accB);
+    } else {
+      k_quadrature_w_cplx<T><<<blocks, PW_THREADS, 0, c.stream>>>((const Z*)c.hist, (const Z*)c.qdh, (const Z*)c.qd0,
+                                                                 c.M, c.Ns, c.qw, (double2*)c.accA, (double2*)c.accB);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return solve_tail(c);
+  }
+
   // The plane kernel (y and z of a step in shared memory): FP32 real fields on 64^3 or
   // 128^3 style grids (ny = nz in {64, 128}).
   static bool plane_supported(const CtxData& c) {
@@ -616,7 +784,10 @@ class EngineT : public Engine {
   }
 
   cudaError_t enqueue_solve(CtxData& c) override {
-    if (c.march == 1 && c.concurrent) {
+    if (c.scheme == 1) {
+      cudaError_t e = prepare_rqm4(c);
+      if (e != cudaSuccess) return e;
+    } else if (c.march == 1 && c.concurrent) {
       cudaError_t e = prepare_concurrent(c);
       if (e != cudaSuccess) return e;
     }
@@ -657,7 +828,7 @@ class EngineT : public Engine {
                                                          c.step_dev, c.ds, c.chiN, c.M, c.partials);
     }
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
-    return cudaGetLastError();
+    return half_boltz(c);
   }
 
   // ---------------------------------------------------------- test hook: FFT
@@ -696,7 +867,7 @@ class EngineT : public Engine {
   // k_a^2 exp(-k^2 ds) over the half spectrum (S_STRESS; the host applies
   // 2 ds / (L_a Q M^2)).  Real SCFT fields only.
   cudaError_t gradients(CtxData& c, double* dwp, double* dwm) override {
-    if (c.kind != PFT_SCFT_REAL) return cudaErrorNotSupported;
+    if (c.kind != PFT_SCFT_REAL || c.scheme != 0) return cudaErrorNotSupported;
     const double dV = c.L[0] * c.L[1] * c.L[2] / (double)c.M;
     if (dwp || dwm) {
       k_grad_fields<<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.accA, (const double*)c.accB,

@@ -163,7 +163,9 @@ k_zf_r2c(const T* __restrict__ q, const T* __restrict__ B, cpx<T>* __restrict__ 
 
 // Inverse: half spectrum -> N2 complex (even/odd merge, unnormalised) -> inverse
 // transform -> nz reals.  EPI 0: out = B*y; EPI 1: out = B*y and
-// accA += cA*out*partner, accB += cB*out*partner (FP64); EPI 2: out = y.
+// accA += cA*out*partner, accB += cB*out*partner (FP64); EPI 2: out = y;
+// EPI 3: out = (4 B*y - partner) / 3, the Richardson combination of Eq. 13 (B*y the two
+// half steps, partner the full step).
 template <typename T, int N2, int EPI>
 __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, const T* __restrict__ B, T* __restrict__ qout,
          const T* __restrict__ partner, double* __restrict__ accA, double* __restrict__ accB, double cA,
@@ -211,6 +213,11 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
       const cpx<T> b = b2[m];
       y.x *= b.x;
       y.y *= b.y;
+    }
+    if (EPI == 3) {
+      const cpx<T> f = reinterpret_cast<const cpx<T>*>(partner)[m];
+      y.x = (T(4) * y.x - f.x) / T(3);
+      y.y = (T(4) * y.y - f.y) / T(3);
     }
     q2[m] = y;
     if (EPI == 1) {
@@ -308,6 +315,11 @@ __device__ __forceinline__ void zi_c2c_body(const cpx<T>* __restrict__ spec, con
     const long long m = o + t + TPC * i;
     cpx<T> y = v[i];
     if (EPI != 2) y = cmul(y, B[m]);
+    if (EPI == 3) {
+      const cpx<T> f = partner[m];
+      y.x = (T(4) * y.x - f.x) / T(3);
+      y.y = (T(4) * y.y - f.y) / T(3);
+    }
     qout[m] = y;
     if (EPI == 1) {
       // integrand q qd in the propagators' precision, sum in FP64

@@ -25,6 +25,7 @@ PFT_HOST, PFT_DEVICE = 0, 1
 PFT_STEP_SCFT_EULER, PFT_STEP_CL_EULER_MARUYAMA = 0, 1
 PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT, PFT_MARCH_PERSISTENT = 0, 1, 2, 3
 PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
+PFT_SCHEME_SPLIT2, PFT_SCHEME_RQM4 = 0, 1
 
 
 class pft_grid(ct.Structure):
@@ -41,7 +42,7 @@ class pft_model(ct.Structure):
 
 class pft_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("use_graph", ct.c_int), ("stream", ct.c_void_p),
-                ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong), ("march", ct.c_int)]
+                ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong), ("march", ct.c_int), ("scheme", ct.c_int)]
 
 
 class pft_obs(ct.Structure):
@@ -190,12 +191,12 @@ def pft_last_error() -> str:
 
 
 def pft_create(n, L, Ns, fA, chiN, C, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True, stream=None,
-               seed=0, instance=0, march=PFT_MARCH_AUTO):
+               seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2):
     g = pft_grid((ct.c_int * 3)(*[int(v) for v in n]), (ct.c_double * 3)(*[float(v) for v in L]))
     ch = pft_chain(int(Ns), float(fA))
     m = pft_model(float(chiN), float(C), int(kind))
     o = pft_opts(int(precision), 1 if use_graph else 0, ct.c_void_p(stream or 0), int(seed), int(instance),
-                 int(march))
+                 int(march), int(scheme))
     h = ct.c_void_p()
     _check(_lib().pft_create(ct.byref(h), ct.byref(g), ct.byref(ch), ct.byref(m), ct.byref(o)), "pft_create")
     return h
@@ -394,12 +395,13 @@ class System:
     """Owning wrapper of one context (pft_create / pft_destroy) with host-array helpers."""
 
     def __init__(self, n, L, Ns, fA, chiN, C=1.0, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True,
-                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO):
+                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2):
         self.n = tuple(int(v) for v in n)
         self.kind = kind
         self.M = self.n[0] * self.n[1] * self.n[2]
         self.h = None
-        self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance, march)
+        self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance, march,
+                            scheme)
 
     @property
     def dtype(self):

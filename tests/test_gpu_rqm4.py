@@ -1,0 +1,241 @@
+"""GPU parity of the 4th-order contour scheme (Eq. 13) against the oracle's RQM4 solve.
+
+Each contour step is the Richardson combination (4 A(ds/2) A(ds/2) - A(ds)) / 3 of the
+split operator A(h) = exp(-w h/2) exp(laplacian h) exp(-w h/2), and the contour
+integrals of Eq. 8 take composite Simpson weights per block.  Tolerances: FP64 as for
+the 2nd-order path (relative 1e-12 on Q and H, 1e-10 absolute on phi, 1e-12 relative on
+propagator slices).  FP32-mixed: 4e-5, derived as for the 2nd-order path (unit roundoff
+6e-8 x log2(M) ~ 21 per transform) with three transforms per step (x sqrt 3) and the
+combination (4a - b)/3 (gain 5/3 on the rounding of a and b): ~3.6e-6 per step, a random
+walk over 2 Ns <= 80 steps -> ~3.2e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle as o
+from paper_1204_5434_gb300 import pft
+from paper_1204_5434_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+FP64, FP32 = pft.PFT_FP64, pft.PFT_FP32_MIXED
+SCFT, CL = pft.PFT_SCFT_REAL, pft.PFT_CL_COMPLEX
+OKIND = {SCFT: o.SCFT_REAL, CL: o.CL_COMPLEX}
+RQM4 = pft.PFT_SCHEME_RQM4
+TOL = {FP64: dict(Q=1e-12, H=1e-12, phi=1e-10, q=1e-12), FP32: dict(Q=4e-5, h=4e-5, phi=4e-5, q=4e-5)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1204_5434_gb300 import build
+    build.build()
+
+
+def _fields(n, kind, seed, amp_p=0.3, amp_m=1.0):
+    rng = np.random.default_rng(seed)
+    wp = rng.normal(0, amp_p, n)
+    wm = rng.normal(0, amp_m, n)
+    if kind == CL:
+        wp = wp + 1j * rng.normal(0, amp_p, n)
+        wm = wm + 1j * rng.normal(0, 0.3 * amp_m, n)
+    return wp, wm
+
+
+def _rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+# NsA = floor(fA Ns + 1/2): the cases cover even and odd block lengths (Simpson with and
+# without the 3/8 tail), one-interval blocks (trapezoid) and empty blocks.
+CASES = [
+    ((16, 12, 8), (4.0, 3.0, 2.0), 20, 0.35),     # A 7 (odd), B 13 (odd)
+    ((12, 12, 12), (3.0, 3.0, 3.0), 13, 0.5),     # A 7, B 6; ragged tiles
+    ((8, 6, 24), (2.0, 1.5, 6.0), 8, 0.25),       # A 2, B 6
+    ((48, 4, 6), (6.0, 1.0, 1.5), 10, 0.6),       # A 6, B 4; radix-3 lengths
+    ((8, 8, 8), (3.0, 3.0, 3.0), 2, 0.5),         # A 1, B 1: trapezoid blocks
+    ((8, 8, 8), (3.0, 3.0, 3.0), 1, 0.5),         # A 1, B 0
+    ((8, 8, 8), (3.0, 3.0, 3.0), 6, 0.0),         # pure B
+    ((8, 8, 8), (3.0, 3.0, 3.0), 9, 1.0),         # pure A, odd
+]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("kind", [SCFT, CL])
+@pytest.mark.parametrize("case", CASES)
+def test_rqm4_solve_matches_oracle(case, kind, prec):
+    n, L, Ns, fA = case
+    chiN, C = 17.0, 3.0
+    wp, wm = _fields(n, kind, 31 + Ns)
+    ref = o.solve(wp, wm, n, L, Ns, fA, OKIND[kind], scheme=o.RQM4)
+    Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, C, n, L, OKIND[kind])
+    t = TOL[prec]
+    with pft.System(n, L, Ns, fA, chiN, C, kind, prec, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        s.solve()
+        obs = s.observables()
+        phiA, phiB = s.densities()
+        Q = obs["Q"] if kind == CL else obs["Q"].real
+        H = obs["H"] if kind == CL else obs["H"].real
+        eQ = _rel(Q, ref.Q)
+        ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+        print(f"\nrqm4 {n} Ns={Ns} fA={fA} kind={kind} prec={prec}: Q rel {eQ:.2e} phi abs {ephi:.2e}")
+        assert eQ <= t["Q"], (Q, ref.Q)
+        if prec == FP64:
+            assert _rel(H, Href) <= t["H"], (H, Href)
+        else:
+            assert abs(H - Href) / (C * float(np.prod(L))) <= t["h"], (H, Href)
+        assert ephi <= t["phi"]
+        for k in sorted({0, 1, ref.NsA, Ns}):
+            q = s.propagator(0, k)
+            assert np.max(np.abs(q - ref.q[k])) <= t["q"] * np.max(np.abs(ref.q[k])), k
+        qd = s.propagator(1, 0)
+        assert np.max(np.abs(qd - ref.qd[Ns])) <= t["q"] * np.max(np.abs(ref.qd[Ns]))
+
+
+def test_rqm4_uniform_fields_are_exact():
+    """Uniform fields: every step is the exact exp(-w ds) on the k = 0 mode, so Q is the
+    closed form and phi_A the A fraction, as in the 2nd-order scheme."""
+    n, L, Ns, fA = (8, 12, 16), (2.0, 3.0, 4.0), 20, 0.35
+    fa = o.n_A_steps(Ns, fA) / Ns
+    with pft.System(n, L, Ns, fA, 15.0, 1.0, SCFT, FP64, scheme=RQM4) as s:
+        s.set_fields(np.full(n, 0.7), np.full(n, -1.3))
+        s.solve()
+        obs = s.observables()
+        phiA, phiB = s.densities()
+    Qx = np.exp(-(fa * 2.0 + (1 - fa) * (-0.6)))
+    assert _rel(obs["Q"].real, Qx) <= 1e-13
+    assert np.max(np.abs(phiA - fa)) <= 1e-13 and np.max(np.abs(phiB - (1 - fa))) <= 1e-13
+
+
+def test_rqm4_converges_at_fourth_order_on_the_gpu():
+    """Property at any size: with fixed smooth fields (a gyroid level set, one period per
+    box, and a smooth W+), halving ds cuts the error of Q and of the densities ~16x
+    (reference: the same path at Ns = 512).  Fields with grid-scale noise are not in the
+    asymptotic range at these ds: their stiff high-k modes dominate the splitting error."""
+    n, L, fA = (32, 32, 32), (4.0, 4.0, 4.0), 0.5
+    x = np.arange(32) * (2 * np.pi / 32)
+    X, Y, Z = x[:, None, None], x[None, :, None], x[None, None, :]
+    wm = 1.5 * (np.sin(X) * np.cos(Y) + np.sin(Y) * np.cos(Z) + np.sin(Z) * np.cos(X))
+    wp = 0.3 * np.cos(X + 2 * Y) * np.sin(Z)
+    Qs = {}
+    phis = {}
+    for Ns in (16, 32, 64, 512):
+        with pft.System(n, L, Ns, fA, 15.0, 1.0, SCFT, FP64, scheme=RQM4) as s:
+            s.set_fields(wp, wm)
+            s.solve()
+            Qs[Ns] = s.observables()["Q"].real
+            phis[Ns] = s.densities()[0]
+    e = [abs(Qs[Ns] - Qs[512]) for Ns in (16, 32, 64)]
+    r = [e[0] / e[1], e[1] / e[2]]
+    ep = [np.max(np.abs(phis[Ns] - phis[512])) for Ns in (16, 32, 64)]
+    rp = [ep[0] / ep[1], ep[1] / ep[2]]
+    print(f"\nrqm4 Q error ratios {r}, phi error ratios {rp}")
+    assert all(12.0 < x < 20.0 for x in r), r
+    assert all(12.0 < x < 20.0 for x in rp), rp
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_rqm4_scft_relaxation_matches_oracle(prec):
+    """Euler steps of Eq. 9 from RQM4 densities: the quarter-step Boltzmann factors are
+    rebuilt from the updated fields at every step."""
+    n, L, Ns, fA, chiN, lam = (16, 12, 8), (4.0, 3.0, 2.0), 16, 0.4, 15.0, 0.1
+    wp, wm = _fields(n, SCFT, 21)
+    with pft.System(n, L, Ns, fA, chiN, 1.0, SCFT, prec, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        for it in range(4):
+            s.solve()
+            obs = s.observables()
+            ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL, scheme=o.RQM4)
+            Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, 1.0, n, L, o.SCFT_REAL)
+            if prec == FP64:
+                assert _rel(obs["H"].real, Href) <= 1e-12
+            else:
+                assert abs(obs["H"].real - Href) / float(np.prod(L)) <= TOL[FP32]["h"]
+            s.field_step(lam)
+            wp, wm = o.scft_euler_step(wp, wm, ref.phiA, ref.phiB, chiN, lam)
+            gp, gm = s.get_fields()
+            tol = 1e-12 if prec == FP64 else 1e-5
+            assert np.max(np.abs(gp - wp)) <= tol and np.max(np.abs(gm - wm)) <= tol * 10
+
+
+def test_rqm4_cl_steps_with_supplied_noise_match_oracle():
+    n, L, Ns, fA, chiN, C, dt = (16, 8, 12), (4.0, 2.0, 3.0), 12, 0.3, 20.0, 50.0, 0.01
+    wp, wm = _fields(n, CL, 22, 0.05, 0.2)
+    wm = wm + chiN * (2 * fA - 1) / 2
+    dV = np.prod(L) / np.prod(n)
+    std = o.cl_noise_std(dt, C, dV)
+    rng = np.random.default_rng(6)
+    with pft.System(n, L, Ns, fA, chiN, C, CL, FP64, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        for it in range(3):
+            s.solve()
+            ref = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX, scheme=o.RQM4)
+            obs = s.observables()
+            Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, C, n, L, o.CL_COMPLEX)
+            assert _rel(obs["H"], Href) <= 1e-12
+            ep = std * rng.normal(size=n)
+            em = std * rng.normal(size=n)
+            s.field_step(dt, ep, em)
+            wp, wm = o.cl_euler_maruyama_step(wp, wm, ref.phiA, ref.phiB, chiN, dt, ep, em)
+            gp, gm = s.get_fields()
+            assert np.max(np.abs(gp - wp)) <= 1e-10 and np.max(np.abs(gm - wm)) <= 1e-10
+
+
+def test_rqm4_after_set_box_uses_the_new_tables():
+    """pft_set_box rebuilds the full- and half-step diffusion tables."""
+    n, Ns, fA = (16, 16, 16), 12, 0.4
+    wp, wm = _fields(n, SCFT, 51)
+    L0, L1 = (4.0, 4.0, 4.0), (4.4, 3.8, 4.1)
+    ref = o.solve(wp, wm, n, L1, Ns, fA, o.SCFT_REAL, scheme=o.RQM4)
+    with pft.System(n, L0, Ns, fA, 15.0, 1.0, SCFT, FP64, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        s.solve()
+        s.set_box(L1)
+        s.set_fields(wp, wm)
+        s.solve()
+        Q = s.observables()["Q"].real
+    assert _rel(Q, ref.Q) <= 1e-12
+
+
+def test_rqm4_refuses_gradients_and_other_marches():
+    n = (16, 16, 16)
+    wp, wm = _fields(n, SCFT, 52)
+    with pft.System(n, (4.0, 4.0, 4.0), 8, 0.5, 15.0, 1.0, SCFT, FP64, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        s.solve()
+        with pytest.raises(pft.PftError) as ei:
+            s.gradients()
+        assert ei.value.status == pft.PFT_ERR_UNSUPPORTED
+    for march in (pft.PFT_MARCH_RESIDENT, pft.PFT_MARCH_PERSISTENT):
+        with pytest.raises(pft.PftError) as ei:
+            pft.System((64, 64, 64), (8.0, 8.0, 8.0), 8, 0.5, 15.0, 1.0, SCFT, FP32, march=march, scheme=RQM4)
+        assert ei.value.status == pft.PFT_ERR_UNSUPPORTED
+    with pytest.raises(pft.PftError) as ei:
+        pft.System(n, (4.0, 4.0, 4.0), 8, 0.5, 15.0, 1.0, SCFT, FP64, scheme=7)
+    assert ei.value.status == pft.PFT_ERR_ARG
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+def test_rqm4_gyroid_128cubed(prec):
+    """The 128^3 gyroid-seeded SCFT fields (fA = 0.35, chiN = 18) with Ns = 40 under the
+    4th-order scheme: Q, H and phi at 4096 sampled points against the oracle."""
+    w = wl.GYR128.with_(Ns=40)
+    wp, wm = wl.fields(w)
+    ref = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL, scheme=o.RQM4)
+    Href = o.hamiltonian(wp, wm, ref.lnQ, w.chiN, w.C, w.n, w.L, o.SCFT_REAL)
+    with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        s.solve()
+        obs = s.observables()
+        phiA, phiB = s.densities()
+    idx = np.random.default_rng(1).choice(phiA.size, 4096, replace=False)
+    t = TOL[prec]
+    eQ = _rel(obs["Q"].real, ref.Q)
+    ephi = max(np.max(np.abs(phiA.ravel()[idx] - ref.phiA.ravel()[idx])),
+               np.max(np.abs(phiB.ravel()[idx] - ref.phiB.ravel()[idx])))
+    print(f"\nrqm4 128^3 prec={prec}: Q rel {eQ:.2e} phi abs {ephi:.2e}")
+    assert eQ <= t["Q"] and ephi <= t["phi"]
+    if prec == FP64:
+        assert _rel(obs["H"].real, Href) <= t["H"]
+    else:
+        assert abs(obs["H"].real - Href) / (w.C * float(np.prod(w.L))) <= t["h"]
