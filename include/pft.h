@@ -90,6 +90,12 @@ typedef struct {
   unsigned long long instance; /* Philox counter word: independent replica streams */
   pft_march march;          /* PFT_MARCH_RESIDENT where it does not apply: PFT_ERR_UNSUPPORTED */
   pft_scheme scheme;        /* PFT_SCHEME_SPLIT2 (0) or PFT_SCHEME_RQM4 */
+  int checkpoint;           /* q history: 0 = AUTO (every slice when the two histories fit in
+                               60% of the free device memory, else every ceil(sqrt(Ns))-th),
+                               1 = every slice, K >= 2 = every K-th slice (clamped to Ns): the
+                               conjugate march recomputes each segment of K-1 slices from its
+                               checkpoint (one extra forward march).  K >= 2 needs the pass
+                               march and the SPLIT2 scheme (else PFT_ERR_UNSUPPORTED). */
 } pft_opts;
 
 /* Observables of the last solve.  Complex quantities are {re, im}; in SCFT mode the
@@ -305,6 +311,18 @@ pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles);
 
 /* Which march the context uses: 1 = passes, 2 = resident, 3 = persistent. */
 pft_status pft_get_march(const pft_ctx* ctx, int* march);
+
+/* History interval in use: 1 = every slice of q is kept, K >= 2 = every K-th slice (see
+ * pft_opts.checkpoint).  Errors: PFT_ERR_ARG for NULL arguments. */
+pft_status pft_get_checkpoint(const pft_ctx* ctx, int* K);
+
+/* Kernel launches of this library per call, for accounting (no counterpart in the
+ * paper).  *solve: the kernel nodes of the CUDA graph one pft_solve replays, counted
+ * when the graph was captured; -1 before the first graphed solve and for contexts that
+ * solve without a graph (use_graph = 0, resident or persistent march).  *field_step:
+ * the kernels one pft_field_step launches.  Either pointer may be NULL.
+ * Errors: PFT_ERR_ARG for a NULL ctx. */
+pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* field_step);
 
 /* Standard normals of the device Philox stream (same layout as the CL noise) for
  * points 0..M-1 into a device float64 array, on `stream` (cudaStream_t or NULL). */

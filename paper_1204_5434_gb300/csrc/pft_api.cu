@@ -140,6 +140,10 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   if (opts->scheme != PFT_SCHEME_SPLIT2 && opts->scheme != PFT_SCHEME_RQM4) return fail(PFT_ERR_ARG, "unknown scheme");
   if (opts->scheme == PFT_SCHEME_RQM4 && opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES)
     return fail(PFT_ERR_UNSUPPORTED, "the 4th-order scheme runs on the pass kernels only");
+  if (opts->checkpoint < 0) return fail(PFT_ERR_ARG, "checkpoint interval must be >= 0");
+  if (opts->checkpoint >= 2 && (opts->scheme != PFT_SCHEME_SPLIT2 || (opts->march != PFT_MARCH_AUTO &&
+                                                                      opts->march != PFT_MARCH_PASSES)))
+    return fail(PFT_ERR_UNSUPPORTED, "a checkpointed history needs the pass march and the SPLIT2 scheme");
 
   pft_ctx* c = new pft_ctx();
   CtxData& d = c->d;
@@ -213,12 +217,28 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   const size_t M = (size_t)d.M;
   const size_t we = welem(d), fe = felem(d);
   const size_t ze = 2 * c->eng->elem_bytes();  // working-precision complex
+  {
+    // history interval: every slice, or every K-th with segment recomputation
+    int K = opts->checkpoint;
+    if (K == 0) {
+      size_t free_b = 0, total_b = 0;
+      K = 1;
+      if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) {
+        const double need = 2.0 * (double)(d.Ns + 1) * (double)(M * we);  // q and qd histories
+        if (need > 0.6 * (double)free_b) K = (int)ceil(sqrt((double)d.Ns));
+      }
+    }
+    if (K > d.Ns) K = d.Ns;
+    if (K < 2 || d.march != 1 || d.scheme != 0) K = 1;
+    d.ckK = K;
+    d.nck = (K > 1) ? d.Ns / K + 1 : 0;
+  }
   struct {
     void** p;
     size_t b;
   } plan[] = {
       {&d.wp, M * fe},   {&d.wm, M * fe},    {&d.BA, M * we},     {&d.BB, M * we},
-      {&d.hist, (size_t)(d.Ns + 1) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
+      {&d.hist, (size_t)pft::q_slots(d) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
       {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
       {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
       {&c->io, M * 16}, {(void**)&d.sync, 4 * sizeof(unsigned)},
@@ -570,9 +590,11 @@ pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem
   if (which != 0 && which != 1) return fail(PFT_ERR_ARG, "which must be 0 (q) or 1 (qd)");
   if (which == 0 && (s < 0 || s > d.Ns)) return fail(PFT_ERR_ARG, "slice out of range");
   const size_t we = welem(d);
-  const void* qd_last = (d.march == 1 && d.concurrent && d.qdh) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
+  const void* qd_last = (d.march == 1 && d.concurrent && d.qdh && d.ckK == 1) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
                                                                   : d.qd[d.Ns & 1];
-  const void* src = (which == 0) ? (const void*)((const char*)d.hist + (size_t)s * d.M * we) : qd_last;
+  if (which == 0 && !pft::q_kept(d, s))
+    return fail(PFT_ERR_UNSUPPORTED, "slice " + std::to_string(s) + " is not kept by the checkpointed history");
+  const void* src = (which == 0) ? (const void*)((const char*)d.hist + (size_t)pft::q_slot(d, s) * d.M * we) : qd_last;
   const long long cnt = d.M * (d.kind == PFT_SCFT_REAL ? 1 : 2);
   PFT_CK(ctx->eng->to_f64(d, src, ctx->io, cnt));
   PFT_CK(cudaMemcpyAsync(out, ctx->io, (size_t)cnt * 8, kind_out(where), d.stream));
@@ -604,6 +626,21 @@ pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles) {
     cudaGraphExecDestroy(ctx->d.graph);
     ctx->d.graph = nullptr;
   }
+  return PFT_OK;
+}
+
+pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* field_step) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  const CtxData& d = ctx->d;
+  if (solve) *solve = (d.use_graph && d.march == 1 && d.graph_valid) ? d.graph_kernels : -1;
+  // the update kernel and its final reduction, plus the quarter-step factors of RQM4
+  if (field_step) *field_step = 2 + (d.scheme == 1 ? 1 : 0);
+  return PFT_OK;
+}
+
+pft_status pft_get_checkpoint(const pft_ctx* ctx, int* K) {
+  if (!ctx || !K) return fail(PFT_ERR_ARG, "NULL argument");
+  *K = ctx->d.ckK;
   return PFT_OK;
 }
 

@@ -181,6 +181,7 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
     o.seed = descs[i].seed;
     o.instance = (unsigned long long)i;
     o.march = PFT_MARCH_PASSES;
+    o.checkpoint = 1;
     pft_status s = pft_create(&b->inst[i], &descs[i].grid, &descs[i].chain, &descs[i].model, &o);
     if (s != PFT_OK) {
       std::string msg = pft_last_error();

@@ -46,6 +46,7 @@ struct CtxData {
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;
   bool graph_valid = false;
+  long long graph_kernels = -1;  // kernel nodes of the captured solve graph
   unsigned long long seed = 0, instance = 0;
   long long step = 0;
   bool fields_set = false, solved = false;
@@ -87,6 +88,11 @@ struct CtxData {
   // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
   // scratch slices for the full and the two half steps, quadrature weight tables
   int scheme = 0;
+  // q history: ckK = 1 keeps every slice in hist; ckK = K >= 2 keeps q_{cK} in slots
+  // 0..nck-1 (nck = Ns/K + 1), q_Ns in slot nck when K does not divide Ns, and the
+  // segment q_{cK+j} (j = 1..K-1) being recomputed in slots nck+j
+  int ckK = 1;
+  int nck = 0;
   void* BAh = nullptr;
   void* BBh = nullptr;
   size_t dh_off[3] = {0, 0, 0};
@@ -113,6 +119,22 @@ inline void mark(CtxData& c, int kind) {
   c.ev_kind[c.ev_used] = kind;
   c.ev_used++;
 }
+
+// Bytes of one propagator slice in the working precision.
+inline size_t slice_bytes(const CtxData& c, size_t elem) {
+  return (size_t)c.M * (c.kind == PFT_SCFT_REAL ? elem : 2 * elem);
+}
+// History slot holding q_n (see CtxData::ckK).
+inline int q_slot(const CtxData& c, int n) {
+  if (c.ckK <= 1) return n;
+  if (n % c.ckK == 0) return n / c.ckK;
+  if (n == c.Ns) return c.nck;
+  return c.nck + n % c.ckK;
+}
+// Slots the history needs.
+inline int q_slots(const CtxData& c) { return c.ckK <= 1 ? c.Ns + 1 : c.nck + c.ckK; }
+// Is q_n kept after a solve (a checkpoint, q_Ns, or every slice)?
+inline bool q_kept(const CtxData& c, int n) { return c.ckK <= 1 || n % c.ckK == 0 || n == c.Ns; }
 
 struct BatchStep;
 

@@ -392,9 +392,27 @@ class EngineT : public Engine {
   }
 
   // ------------------------------------------------------------- a2 .. a6
+  // q_n of the history (every slice, or checkpoint / segment slots)
+  void* q_at(const CtxData& c, int n) const {
+    return (char*)c.hist + (size_t)q_slot(c, n) * slice_bytes(c, sizeof(T));
+  }
+
+  // With a checkpointed history: before the conjugate step paired with q_n, recompute
+  // the segment q_{cK+1} .. q_n (c = n / K) from its checkpoint when n is the top of
+  // its segment (one forward split step per slice, Eq. 13).
+  cudaError_t recompute_segment(CtxData& c, int n) {
+    const int K = c.ckK;
+    if (K <= 1 || n % K == 0) return cudaSuccess;
+    if (n != c.Ns - 1 && (n + 1) % K != 0) return cudaSuccess;
+    for (int j = n - n % K + 1; j <= n; j++) {
+      const void* B = (j <= c.NsA) ? c.BA : c.BB;
+      cudaError_t e = contour_step(c, q_at(c, j - 1), B, q_at(c, j), 0, nullptr, 0.0, 0.0);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
   cudaError_t record_solve(CtxData& c) {
-    const size_t slice = (size_t)c.M * (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
-    char* hist = (char*)c.hist;
     cudaError_t e;
     const bool res = (c.march == 2 || c.march == 3);
     if (res) {
@@ -402,15 +420,15 @@ class EngineT : public Engine {
       if ((e = cudaMemsetAsync(c.sync, 0, 4 * sizeof(unsigned), c.stream)) != cudaSuccess) return e;
     }
     if (c.scheme == 1) return record_solve_rqm4(c);
-    if (!res && c.concurrent) return record_solve_concurrent(c);
-    // forward march (Eqs. 5, 13)
+    if (!res && c.concurrent && c.ckK == 1) return record_solve_concurrent(c);
+    // forward march (Eqs. 5, 13); a checkpointed history keeps every K-th slice and q_Ns
     if (res) {
       e = (c.march == 2) ? resident_march(c, false) : persist_march(c, false);
       if (e != cudaSuccess) return e;
     } else {
       for (int n = 1; n <= c.Ns; n++) {
         const void* B = (n <= c.NsA) ? c.BA : c.BB;
-        e = contour_step(c, hist + (size_t)(n - 1) * slice, B, hist + (size_t)n * slice, 0, nullptr, 0.0, 0.0);
+        e = contour_step(c, q_at(c, n - 1), B, q_at(c, n), 0, nullptr, 0.0, 0.0);
         if (e != cudaSuccess) return e;
       }
     }
@@ -429,7 +447,8 @@ class EngineT : public Engine {
       void* out = c.qd[m & 1];
       const int pn = c.Ns - m;  // forward slice paired with qd_m
       trapezoid_weight(pn, c.Ns, c.NsA, &cA, &cB);
-      e = contour_step(c, in, B, out, 1, hist + (size_t)pn * slice, cA, cB);
+      if ((e = recompute_segment(c, pn)) != cudaSuccess) return e;
+      e = contour_step(c, in, B, out, 1, q_at(c, pn), cA, cB);
       if (e != cudaSuccess) return e;
     }
     // densities and force norms
@@ -437,16 +456,14 @@ class EngineT : public Engine {
   }
 
   cudaError_t solve_mid(CtxData& c) override {
-    const size_t slice = (size_t)c.M * (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
-    const char* hist = (const char*)c.hist;
     double cA, cB;
     trapezoid_weight(c.Ns, c.Ns, c.NsA, &cA, &cB);
     mark(c, KK_REDUCE);
     if (c.kind == PFT_SCFT_REAL) {
-      k_qsum_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const T*)(hist + (size_t)c.Ns * slice), (double*)c.accA,
+      k_qsum_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const T*)q_at(c, c.Ns), (double*)c.accA,
                                                           (double*)c.accB, cA, cB, c.M, c.partials);
     } else {
-      k_qsum_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)(hist + (size_t)c.Ns * slice), (double2*)c.accA,
+      k_qsum_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)q_at(c, c.Ns), (double2*)c.accA,
                                                           (double2*)c.accB, cA, cB, c.M, c.partials);
     }
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_QSUM);
@@ -768,7 +785,7 @@ class EngineT : public Engine {
     auto kern = kb_plane_r2c<NY, NY, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<dim3((unsigned)nx, 2u), R::THREADS, R::SMEM, stream>>>(st, nx);
+    kern<<<dim3((unsigned)nx, 2u), R::THREADS, R::SMEM, stream>>>(st);
     return cudaGetLastError();
   }
 
@@ -787,7 +804,7 @@ class EngineT : public Engine {
     if (c.scheme == 1) {
       cudaError_t e = prepare_rqm4(c);
       if (e != cudaSuccess) return e;
-    } else if (c.march == 1 && c.concurrent) {
+    } else if (c.march == 1 && c.concurrent && c.ckK == 1) {
       cudaError_t e = prepare_concurrent(c);
       if (e != cudaSuccess) return e;
     }
@@ -804,6 +821,22 @@ class EngineT : public Engine {
         return e;
       }
       if (e2 != cudaSuccess) return e2;
+      size_t nn = 0;
+      if ((e = cudaGraphGetNodes(g, nullptr, &nn)) == cudaSuccess) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        e = cudaGraphGetNodes(g, nodes.data(), &nn);
+        long long k = 0;
+        for (size_t i = 0; i < nn && e == cudaSuccess; i++) {
+          cudaGraphNodeType ty;
+          e = cudaGraphNodeGetType(nodes[i], &ty);
+          if (ty == cudaGraphNodeTypeKernel) k++;
+        }
+        c.graph_kernels = k;
+      }
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        return e;
+      }
       e = cudaGraphInstantiate(&c.graph, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return e;
@@ -875,7 +908,7 @@ class EngineT : public Engine {
     }
     cudaError_t e = cudaMemsetAsync(c.partials, 0, (size_t)c.npart * 3 * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
-    if (c.march == 1 && c.concurrent && c.qdh) return gradients_from_histories(c);
+    if (c.march == 1 && c.concurrent && c.qdh && c.ckK == 1) return gradients_from_histories(c);
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const Z* twx = tab<Z>(c, c.tw_off[0]);
     const Z* twy = tab<Z>(c, c.tw_off[1]);
@@ -891,14 +924,13 @@ class EngineT : public Engine {
     Z* v = (Z*)c.spec2;
     const long long npen = (long long)nx * ny;
     const long long nzc = c.nzh;
-    const size_t slice = (size_t)c.M * sizeof(T);
-    const char* hist = (const char*)c.hist;
     for (int m = 1; m <= c.Ns; m++) {
       const int nb = c.Ns + 1 - m;
       const T* B = (const T*)((nb <= c.NsA) ? c.BA : c.BB);
       const T* in = (const T*)((m == 1) ? c.qd0 : c.qd[(m - 1) & 1]);
       T* out = (T*)c.qd[m & 1];
-      const T* qprev = (const T*)(hist + (size_t)(nb - 1) * slice);
+      if ((e = recompute_segment(c, nb - 1)) != cudaSuccess) return e;
+      const T* qprev = (const T*)q_at(c, nb - 1);
       for (int w = 0; w < 2; w++) {
         Z* sp = w ? v : u;
         PFT_DISPATCH_HALF(nz / 2, e = launch_zf_r2c<N>(c, w ? qprev : in, B, sp, npen, twh, twz));

@@ -42,7 +42,8 @@ class pft_model(ct.Structure):
 
 class pft_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("use_graph", ct.c_int), ("stream", ct.c_void_p),
-                ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong), ("march", ct.c_int), ("scheme", ct.c_int)]
+                ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong), ("march", ct.c_int), ("scheme", ct.c_int),
+                ("checkpoint", ct.c_int)]
 
 
 class pft_obs(ct.Structure):
@@ -127,6 +128,8 @@ _SIGS = {
     "pft_debug_set_q0": (ct.c_int, [_P, _P, ct.c_int]),
     "pft_debug_set_spin_limit": (ct.c_int, [_P, ct.c_longlong]),
     "pft_get_march": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
+    "pft_launch_counts": (ct.c_int, [_P, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
+    "pft_get_checkpoint": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_philox_normals": (ct.c_int, [ct.c_ulonglong, ct.c_ulonglong, ct.c_ulonglong, ct.c_int, ct.c_longlong,
                                       _P, _P]),
     "pft_philox_raw": (ct.c_int, [ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint), ct.c_longlong, _P, _P]),
@@ -191,12 +194,12 @@ def pft_last_error() -> str:
 
 
 def pft_create(n, L, Ns, fA, chiN, C, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True, stream=None,
-               seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2):
+               seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0):
     g = pft_grid((ct.c_int * 3)(*[int(v) for v in n]), (ct.c_double * 3)(*[float(v) for v in L]))
     ch = pft_chain(int(Ns), float(fA))
     m = pft_model(float(chiN), float(C), int(kind))
     o = pft_opts(int(precision), 1 if use_graph else 0, ct.c_void_p(stream or 0), int(seed), int(instance),
-                 int(march), int(scheme))
+                 int(march), int(scheme), int(checkpoint))
     h = ct.c_void_p()
     _check(_lib().pft_create(ct.byref(h), ct.byref(g), ct.byref(ch), ct.byref(m), ct.byref(o)), "pft_create")
     return h
@@ -373,6 +376,21 @@ def pft_get_march(h) -> int:
     return m.value
 
 
+def pft_get_checkpoint(h) -> int:
+    """History interval in use: 1 = every slice, K >= 2 = every K-th slice."""
+    k = ct.c_int()
+    _check(_lib().pft_get_checkpoint(h, ct.byref(k)), "pft_get_checkpoint")
+    return k.value
+
+
+def pft_launch_counts(h):
+    """(kernels per graphed pft_solve or -1, kernels per pft_field_step)."""
+    a = ct.c_longlong()
+    b = ct.c_longlong()
+    _check(_lib().pft_launch_counts(h, ct.byref(a), ct.byref(b)), "pft_launch_counts")
+    return a.value, b.value
+
+
 def pft_philox_normals(seed, instance, step, field, M, out_device, stream=None):
     p, w = _ptr(out_device, True)
     if w != PFT_DEVICE:
@@ -395,13 +413,13 @@ class System:
     """Owning wrapper of one context (pft_create / pft_destroy) with host-array helpers."""
 
     def __init__(self, n, L, Ns, fA, chiN, C=1.0, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True,
-                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2):
+                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0):
         self.n = tuple(int(v) for v in n)
         self.kind = kind
         self.M = self.n[0] * self.n[1] * self.n[2]
         self.h = None
         self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance, march,
-                            scheme)
+                            scheme, checkpoint)
 
     @property
     def dtype(self):

@@ -61,6 +61,12 @@ def test_shape_and_argument_validation(lib):
         pft.pft_create((8, 8, 8), (1, 1, 1), 10, 0.5, 10, 1, scheme=5)
     assert e.value.status == pft.PFT_ERR_ARG
     with pytest.raises(pft.PftError) as e:
+        pft.pft_create((8, 8, 8), (1, 1, 1), 10, 0.5, 10, 1, checkpoint=-1)
+    assert e.value.status == pft.PFT_ERR_ARG
+    with pytest.raises(pft.PftError) as e:
+        pft.pft_create((8, 8, 8), (1, 1, 1), 10, 0.5, 10, 1, checkpoint=3, scheme=pft.PFT_SCHEME_RQM4)
+    assert e.value.status == pft.PFT_ERR_UNSUPPORTED
+    with pytest.raises(pft.PftError) as e:
         pft.pft_create((64, 64, 64), (1, 1, 1), 10, 0.5, 10, 1, precision=pft.PFT_FP32_MIXED,
                        march=pft.PFT_MARCH_RESIDENT, scheme=pft.PFT_SCHEME_RQM4)
     assert e.value.status == pft.PFT_ERR_UNSUPPORTED
@@ -83,7 +89,7 @@ int main(void) {
   S(pft_chain) F(pft_chain, fA)
   S(pft_model) F(pft_model, C) F(pft_model, kind)
   S(pft_opts) F(pft_opts, use_graph) F(pft_opts, stream) F(pft_opts, seed) F(pft_opts, instance)
-  F(pft_opts, march) F(pft_opts, scheme)
+  F(pft_opts, march) F(pft_opts, scheme) F(pft_opts, checkpoint)
   S(pft_obs) F(pft_obs, lnQ) F(pft_obs, H) F(pft_obs, h) F(pft_obs, phiA_mean) F(pft_obs, phiB_mean)
   F(pft_obs, force_p_rms) F(pft_obs, force_m_rms) F(pft_obs, fA_eff) F(pft_obs, NsA) F(pft_obs, step)
   S(pft_instance_desc) F(pft_instance_desc, chain) F(pft_instance_desc, model) F(pft_instance_desc, seed)
