@@ -207,10 +207,11 @@ def _variable_cell(pft, torch, prec, steps, warmup, wpa, wma, lam_L=0.05):
             "timing": "host wall clock around synchronised steps (the gradient call reads back 3 scalars)"}
 
 
-def _cl(pft, torch, w, prec, steps, warmup=1):
+def _cl(pft, torch, w, prec, steps, warmup=1, checkpoint=0):
     """Complex Langevin field updates (solve + Euler-Maruyama step with the device Philox
-    noise) of a complex-field workload, timed with CUDA events on the context stream."""
-    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, pft.PFT_CL_COMPLEX, prec, seed=w.seed)
+    noise) of a complex-field workload, timed with CUDA events on the context stream.
+    checkpoint K >= 2 keeps every K-th q slice and recomputes segments (one extra march)."""
+    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, pft.PFT_CL_COMPLEX, prec, seed=w.seed, checkpoint=checkpoint)
     h = s.h
     wp, wm = wl.fields(w)
     pft.pft_set_fields(h, wp, wm)
@@ -232,13 +233,79 @@ def _cl(pft, torch, w, prec, steps, warmup=1):
     ms = e0.elapsed_time(e1) / steps
     obs = pft.pft_get_observables(h)
     mem = pft.pft_memory_bytes(h)
+    hist_k = pft.pft_get_checkpoint(h)
     s.close()
     units = 2 * w.M * w.Ns
     bpu = 44.0 if prec == pft.PFT_FP32_MIXED else 72.0
     peak, _ = _peaks()
     return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
             "hbm_roofline_frac": bpu * units / (ms * 1e-3) / 1e9 / peak, "bytes_per_unit": bpu,
-            "device_bytes": mem, "H_last": [obs["H"].real, obs["H"].imag]}
+            "device_bytes": mem, "history_interval": hist_k,
+            "H_last": [obs["H"].real, obs["H"].imag]}
+
+
+def _library_fft_step(torch, wpa, wma, steps=3, warmup=1):
+    """Comparison arm (not the product path): the same field update written with
+    torch.fft (cuFFT) R2C/C2R transforms and separate elementwise kernels, eager launches,
+    FP32 propagators and FP64 quadrature/update, on the headline workload."""
+    w = WORK
+    dev = torch.device("cuda")
+    n = tuple(w.n)
+    Ns = w.Ns
+    ds = 1.0 / Ns
+    NsA = int(math.floor(w.fA * Ns + 0.5))
+    f64 = torch.float64
+    kx = 2 * math.pi * torch.fft.fftfreq(n[0], d=w.L[0] / n[0], device=dev, dtype=f64)
+    ky = 2 * math.pi * torch.fft.fftfreq(n[1], d=w.L[1] / n[1], device=dev, dtype=f64)
+    kz = 2 * math.pi * torch.fft.rfftfreq(n[2], d=w.L[2] / n[2], device=dev, dtype=f64)
+    k2 = kx[:, None, None] ** 2 + ky[None, :, None] ** 2 + kz[None, None, :] ** 2
+    D = torch.exp(-k2 * ds).to(torch.float32)
+    wp = torch.from_numpy(wpa).to(dev)
+    wm = torch.from_numpy(wma).to(dev)
+    q = torch.empty((Ns + 1,) + n, device=dev, dtype=torch.float32)
+
+    def step(wp, wm):
+        BA = torch.exp(-(wp - wm) * (ds / 2)).float()
+        BB = torch.exp(-(wp + wm) * (ds / 2)).float()
+        q[0].fill_(1.0)
+        for s in range(1, Ns + 1):
+            B = BA if s <= NsA else BB
+            q[s] = B * torch.fft.irfftn(D * torch.fft.rfftn(B * q[s - 1]), s=n)
+        Q = q[Ns].double().mean()
+        accA = torch.zeros(n, device=dev, dtype=f64)
+        accB = torch.zeros(n, device=dev, dtype=f64)
+        qd = torch.ones(n, device=dev, dtype=torch.float32)
+        for m in range(0, Ns + 1):
+            if m > 0:
+                nb = Ns + 1 - m
+                B = BA if nb <= NsA else BB
+                qd = B * torch.fft.irfftn(D * torch.fft.rfftn(B * qd), s=n)
+            k = Ns - m
+            prod = (q[k] * qd).double()
+            if NsA > 0 and k <= NsA:
+                accA += (0.5 if k in (0, NsA) else 1.0) * prod
+            if NsA < Ns and k >= NsA:
+                accB += (0.5 if k in (NsA, Ns) else 1.0) * prod
+        phiA = accA * (ds / Q)
+        phiB = accB * (ds / Q)
+        wp2 = wp + w.lam * (phiA + phiB - 1.0)
+        wm2 = wm - w.lam * (2.0 * wm / w.chiN + phiB - phiA)
+        return wp2, wm2, Q
+
+    for _ in range(warmup):
+        step(wp, wm)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        wp, wm, Q = step(wp, wm)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    units = 2 * w.M * Ns
+    return {"kind": "torch.fft (cuFFT) + elementwise kernels, eager", "ms_per_step": ms,
+            "value": units / (ms * 1e-3), "unit": UNIT, "Q_last": float(Q)}
 
 
 def _batch(pft, prec, updates=2):
@@ -380,7 +447,10 @@ def run(args):
     cl = {"cl64_fp32": _cl(pft, torch, wl.CL64, pft.PFT_FP32_MIXED, 10),
           "cl64_fp64": _cl(pft, torch, wl.CL64, pft.PFT_FP64, 3),
           "cl256_fp32": _cl(pft, torch, wl.CL256, pft.PFT_FP32_MIXED, 3),
-          "cl256_fp64": _cl(pft, torch, wl.CL256, pft.PFT_FP64, 1)}
+          "cl256_fp64": _cl(pft, torch, wl.CL256, pft.PFT_FP64, 1),
+          "cl256_fp32_checkpoint14": _cl(pft, torch, wl.CL256, pft.PFT_FP32_MIXED, 2, checkpoint=14)}
+    torch.cuda.empty_cache()
+    lib_fft = _library_fft_step(torch, wpa, wma)
     torch.cuda.empty_cache()
     batch = _batch(pft, pft.PFT_FP32_MIXED)
     if rank != 0:
@@ -411,6 +481,7 @@ def run(args):
         "variable_cell": vc,
         "batch": batch,
         "complex_langevin": cl,
+        "library_fft_comparison": dict(lib_fft, ours_over_library=main["value"] / lib_fft["value"]),
     }
     print(json.dumps(line), flush=True)
     if ws > 1:

@@ -83,6 +83,9 @@ void free_all(pft_ctx* c) {
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
   if (d.own_stream && d.stream) cudaStreamDestroy(d.stream);
+  if (d.stream2) cudaStreamDestroy(d.stream2);
+  if (d.fork_ev) cudaEventDestroy(d.fork_ev);
+  if (d.join_ev) cudaEventDestroy(d.join_ev);
   delete c->eng;
   delete c;
 }
@@ -184,6 +187,14 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       return s;
     }
     d.own_stream = true;
+  }
+  e = cudaStreamCreateWithFlags(&d.stream2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d.join_ev, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    pft_status s = cuda_fail(e, "second stream");
+    free_all(c);
+    return s;
   }
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
   {

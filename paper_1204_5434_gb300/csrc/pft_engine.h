@@ -42,6 +42,11 @@ struct CtxData {
   // runtime
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // the concurrent marches run one chain per propagator: member 0 on `stream`, member 1
+  // on `stream2`, forked from and joined back into `stream` (graph branches when captured)
+  cudaStream_t stream2 = nullptr;
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev = nullptr;
   int device = 0;
   bool use_graph = true;
   cudaGraphExec_t graph = nullptr;

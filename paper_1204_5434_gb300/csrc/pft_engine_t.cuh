@@ -608,11 +608,24 @@ class EngineT : public Engine {
     g.nzh = c.nzh;
     const BatchStep* st = (const BatchStep*)c.steps2;
     cudaError_t e;
+    if (!c.profiling) {
+      // one chain per propagator on two streams: the two marches are independent until
+      // the quadrature, and their kernels fill each other's idle SMs
+      if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(c.stream2, c.fork_ev, 0)) != cudaSuccess) return e;
+      for (int m = 0; m < 2; m++) {
+        cudaStream_t sm = m ? c.stream2 : c.stream;
+        if ((e = march_chain(c, g, st + m, sm)) != cudaSuccess) return e;
+      }
+      if ((e = cudaEventRecord(c.join_ev, c.stream2)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
+      return finish_concurrent(c);
+    }
     if (plane_supported(c)) {
       // plane kernel (z and y of step 1), then per step: x pass, plane kernel
       // (y^-1, z^-1 of step s fused with z of step s+1, y)
       mark(c, KK_PAIR_STEP);
-      if ((e = batch_plane(c, st, 0)) != cudaSuccess) return e;
+      if ((e = batch_plane(c, st, 0, 2, c.stream)) != cudaSuccess) return e;
       const int nx = c.n[0], ny = c.n[1];
       const long long nzc = c.nzh;
       for (int s = 1; s <= c.Ns; s++) {
@@ -620,7 +633,7 @@ class EngineT : public Engine {
         const BatchStep* ss = st + (size_t)2 * (s - 1);
         PFT_BATCH_AXIS(nx, e = (bs<N, 2>(ss, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 2, c.stream)));
         if (e != cudaSuccess) return e;
-        if ((e = batch_plane(c, ss, 1)) != cudaSuccess) return e;
+        if ((e = batch_plane(c, ss, 1, 2, c.stream)) != cudaSuccess) return e;
       }
       return finish_concurrent(c);
     }
@@ -635,6 +648,31 @@ class EngineT : public Engine {
       if ((e = batch_zz(g, ss, 2, c.stream)) != cudaSuccess) return e;
     }
     return finish_concurrent(c);
+  }
+
+  // All Ns steps of one propagator on `sm`: st points at the member's entry of step 1
+  // (entries of consecutive steps are two apart).
+  cudaError_t march_chain(CtxData& c, const BatchGeom& g, const BatchStep* st, cudaStream_t sm) {
+    cudaError_t e;
+    if (plane_supported(c)) {
+      if ((e = batch_plane(c, st, 0, 1, sm)) != cudaSuccess) return e;
+      const int nx = c.n[0], ny = c.n[1];
+      const long long nzc = c.nzh;
+      for (int s = 1; s <= c.Ns; s++) {
+        const BatchStep* ss = st + (size_t)2 * (s - 1);
+        PFT_BATCH_AXIS(nx, e = (bs<N, 2>(ss, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 1, sm)));
+        if (e != cudaSuccess) return e;
+        if ((e = batch_plane(c, ss, 1, 1, sm)) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    }
+    if ((e = batch_zf(g, st, 1, sm)) != cudaSuccess) return e;
+    for (int s = 1; s <= c.Ns; s++) {
+      const BatchStep* ss = st + (size_t)2 * (s - 1);
+      if ((e = batch_mid(g, ss, 1, sm)) != cudaSuccess) return e;
+      if ((e = batch_zz(g, ss, 1, sm)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
   }
 
   // Q, the quadrature over both histories, densities and H
@@ -780,22 +818,25 @@ class EngineT : public Engine {
   }
 
   template <int NY, int MODE>
-  static cudaError_t launch_plane(const BatchStep* st, int nx, cudaStream_t stream) {
+  static cudaError_t launch_plane(const BatchStep* st, int nx, int members, cudaStream_t stream) {
     using R = PlaneCfg<NY, NY>;
     auto kern = kb_plane_r2c<NY, NY, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e != cudaSuccess) return e;
-    kern<<<dim3((unsigned)nx, 2u), R::THREADS, R::SMEM, stream>>>(st);
+    kern<<<dim3((unsigned)nx, (unsigned)members), R::THREADS, R::SMEM, stream>>>(st);
     return cudaGetLastError();
   }
 
-  cudaError_t batch_plane(CtxData& c, const BatchStep* st, int mode) {
+  // the plane kernel over `members` consecutive entries of st
+  cudaError_t batch_plane(CtxData& c, const BatchStep* st, int mode, int members, cudaStream_t sm) {
     if constexpr (!std::is_same<T, float>::value) {
       return cudaErrorNotSupported;
     } else {
       const int nx = c.n[0];
-      if (c.n[1] == 64) return mode ? launch_plane<64, 1>(st, nx, c.stream) : launch_plane<64, 0>(st, nx, c.stream);
-      if (c.n[1] == 128) return mode ? launch_plane<128, 1>(st, nx, c.stream) : launch_plane<128, 0>(st, nx, c.stream);
+      if (c.n[1] == 64)
+        return mode ? launch_plane<64, 1>(st, nx, members, sm) : launch_plane<64, 0>(st, nx, members, sm);
+      if (c.n[1] == 128)
+        return mode ? launch_plane<128, 1>(st, nx, members, sm) : launch_plane<128, 0>(st, nx, members, sm);
       return cudaErrorNotSupported;
     }
   }

@@ -75,8 +75,8 @@ template <class R> __device__ __forceinline__ void col_role(int round, int& kz, 
 // MODE 0: first step (rows from q_0 = st.in, x B, z forward, y forward to HBM).
 // MODE 1: a full step (y inverse from HBM, rows: z inverse, x B, store q, then if
 //         st.Bnext: x Bnext, z forward; y forward to HBM).
-template <int NY, int NZ, int MODE, int YC = PlaneCfg<NY, NZ>::YC, class YPL = Plan<NY>>
-__global__ void __launch_bounds__(PlaneCfg<NY, NZ, YC, YPL>::THREADS)
+template <int NY, int NZ, int MODE, int YC = PlaneCfg<NY, NZ>::YC, class YPL = Plan<NY>, int MINB = 1>
+__global__ void __launch_bounds__(PlaneCfg<NY, NZ, YC, YPL>::THREADS, MINB)
 kb_plane_r2c(const BatchStep* __restrict__ st) {
   using R = PlaneCfg<NY, NZ, YC, YPL>;
   constexpr int N2 = R::N2, NZH = R::NZH;
