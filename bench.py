@@ -81,7 +81,7 @@ class Clocks:
         try:
             self.f = open(self.path, "w")
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "25"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -138,6 +138,14 @@ def _oracle_sample(seconds_target=15.0, nsteps=None):
     return units / dt, f"oracle forward march, {nsteps} contour steps of the 128^3 grid ({dt:.1f} s)", 1
 
 
+def _config(ws):
+    return {"workload": WORK.name, "grid": list(WORK.n), "L": list(WORK.L), "Ns": WORK.Ns, "fA": WORK.fA,
+            "chiN": WORK.chiN, "step": "solve + SCFT Euler field update (lambda=0.1)",
+            "units_per_step": 2 * WORK.M * WORK.Ns, "parallelism": f"replicas x{ws}",
+            "l2": "q and q-dagger histories of 101 slices each (2 x 850 MB f32) stream through HBM every step; "
+                  "no flush"}
+
+
 def run_reference(args):
     ws, rank = _dist()
     if rank != 0:
@@ -151,7 +159,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORK.name, "grid": list(WORK.n), "Ns": WORK.Ns},
+            "config": _config(1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -465,10 +473,7 @@ def run(args):
         "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "precision": "f32 propagators/FFTs, f64 quadrature/reductions/update",
         "data": "synthetic",
-        "config": {"workload": WORK.name, "grid": list(WORK.n), "L": list(WORK.L), "Ns": WORK.Ns, "fA": WORK.fA,
-                   "chiN": WORK.chiN, "step": "solve + SCFT Euler field update (lambda=0.1)",
-                   "units_per_step": units_per_step, "parallelism": f"replicas x{ws}",
-                   "l2": "q history of 101 slices (850 MB f32) streams through HBM every step; no flush"},
+        "config": _config(ws),
         "roofline": main["roofline"], "kernels": main["kernels"],
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_sample},
         "e2e": main["e2e"],
