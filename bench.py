@@ -44,6 +44,23 @@ BYTES_PER_UNIT = {"fp32": 22.0, "fp64": 36.0}
 # a forward and an inverse one, plus about 6 pointwise flops (two Boltzmann multiplies,
 # the diffusion multiply, the quadrature update).
 FP64_PEAK_TFLOPS = 1.25
+# DRAM traffic of one contour step of one propagator on the FP32 128^3 path (plane kernel
+# + x pass, steady state inside a block), dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture (profiles/plane_kernel_and_x_pass_fp32_128cubed_ncu.md).  Valid only for
+# the kernel sources it was taken on: reported as null once any of them changes.
+TRAFFIC_FP32 = {"bytes_per_contour_step": 16.944128e6 + 8.543744e6,
+                "sources": ("paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
+                            "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_fft.cuh"),
+                "sha256": "466c5ea1d96e7515eeb6dc38c7c684c845850e52804166667f26ab0a3e276865"}
+
+
+def _traffic_fp32():
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_FP32["sources"]:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC_FP32["bytes_per_contour_step"] if h.hexdigest() == TRAFFIC_FP32["sha256"] else None
 
 
 def fp64_flops_per_unit(M):
@@ -430,7 +447,9 @@ def run(args):
             roof = {"bound": "hbm", "kernel": "pair step (both propagators): plane kernel (y, z in shared memory) + batched x pass",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)", "bytes_per_unit": bpu,
-                    "units_per_launch": WORK.M, "step_us": step_ms * 1e3, "traffic": None}
+                    "units_per_launch": WORK.M, "step_us": step_ms * 1e3, "traffic": _traffic_fp32(),
+                    "traffic_note": "ncu dram bytes of one contour step (plane kernel + x pass) of one "
+                                    "propagator, cold cache; q writes leave L2 after the kernel"}
         else:
             fpu = fp64_flops_per_unit(WORK.M)
             tf = fpu * WORK.M / (step_ms * 1e-3) / 1e12
