@@ -48,6 +48,7 @@ __all__ = [
     "dlnQ_dL", "dH_dL", "dH_dfields", "dft_matrix", "dft3_bruteforce",
     "dense_propagator_matrix", "forward_march_dense", "continuum_Q", "debye_g",
     "variable_cell_step", "rqm4_step", "simpson_weights", "SPLIT2", "RQM4",
+    "debye_chain", "scft_sis_step", "cl_sis_step",
 ]
 
 SPLIT2 = "split2"   # 2nd-order operator splitting, the A(ds) block of Eq. 13
@@ -305,6 +306,46 @@ def cl_euler_maruyama_step(wp, wm, phiA, phiB, chiN: float, dt: float, eta_p, et
     real noise eta (already scaled to its standard deviation), force per C."""
     fp, fm = mean_field_forces(wp, wm, phiA, phiB, chiN, CL_COMPLEX)
     return wp - lam * dt * fp + eta_p, wm - lam * dt * fm + eta_m
+
+
+def debye_chain(x):
+    """Debye function of the whole chain (ideal homopolymer of the full contour length),
+    g_D(x) = 2 (e^{-x} + x - 1) / x^2 at x = k^2 Rg^2, with g_D(0) = 1.  Below x = 0.1,
+    where the closed form cancels, the Taylor series 2 sum_{m>=2} (-x)^(m-2) / m! through
+    x^9 (truncation below 1e-16)."""
+    x = np.asarray(x, dtype=float)
+    small = x < 0.1
+    xs = np.where(small, 1.0, x)
+    g = 2.0 * (np.exp(-xs) + xs - 1.0) / xs ** 2
+    ser = np.zeros_like(x)
+    for m in range(11, 1, -1):  # Horner on the coefficients 2 (-1)^(m-2) / m!
+        ser = ser * x + 2.0 * (-1.0) ** (m - 2) / math.factorial(m)
+    return np.where(small, ser, g)
+
+
+def scft_sis_step(wp, wm, phiA, phiB, chiN: float, lam: float, n, L):
+    """Semi-implicit SCFT relaxation (Eq. 11 without noise, Wick-rotated).  W+: the
+    linear density response to W+, -g_D(k) W+, is taken at the new time, which gives the
+    wavevector-dependent step W+^ += lam F+^ / (1 + lam g_D(k)).  W-: the explicit linear
+    term 2 W-/chiN is taken fully implicitly, the density difference explicitly:
+    W- <- (W- - lam (phiB - phiA)) / (1 + 2 lam/chiN)."""
+    fp = phiA + phiB - 1.0
+    gD = debye_chain(k_squared(n, L))
+    wp_new = wp + np.fft.ifftn(np.fft.fftn(lam * fp) / (1.0 + lam * gD)).real
+    wm_new = (wm - lam * (phiB - phiA)) / (1.0 + 2.0 * lam / chiN)
+    return wp_new, wm_new
+
+
+def cl_sis_step(wp, wm, phiA, phiB, chiN: float, dt: float, eta_p, eta_m, n, L):
+    """Semi-implicit complex Langevin step (Eq. 11 with lam = 1): the linear part of the
+    omega+ force, g_D(k) omega+, at the new time, so the force and the noise are divided
+    by 1 + dt g_D(k) in reciprocal space; the 2 omega-/chiN term fully implicit:
+    omega- <- (omega- - dt (phiB - phiA) + eta-) / (1 + 2 dt/chiN)."""
+    fp = 1j * (phiA + phiB - 1.0)
+    gD = debye_chain(k_squared(n, L))
+    wp_new = wp + np.fft.ifftn(np.fft.fftn(-dt * fp + eta_p) / (1.0 + dt * gD))
+    wm_new = (wm - dt * (phiB - phiA) + eta_m) / (1.0 + 2.0 * dt / chiN)
+    return wp_new, wm_new
 
 
 def cl_noise(seed: int, instance: int, step: int, M: int, std: float):

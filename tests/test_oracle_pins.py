@@ -447,3 +447,95 @@ def test_rqm4_densities_are_fourth_order_gradients():
         fd = fd5(lambda h: o.solve(wp, _perturbed(wm, idx, h), n, L, Ns, fA, o.SCFT_REAL, scheme=o.RQM4).lnQ)
         mism.append(abs(fd - (s.phiA - s.phiB)[idx] / wp.size))
     assert mism[1] < mism[0] / 12.0, mism
+
+
+# ------------------------------------------------------------ SIS (Eq. 11)
+def test_debye_chain_is_the_sum_of_the_block_functions():
+    """g_D = g_AA + 2 g_AB + g_BB for any block split (the whole chain's Debye function)
+    where the block closed forms are accurate (x >= 0.01), and the closed form evaluated
+    in 50-digit arithmetic across the series/closed-form switch at small x."""
+    for x in (0.01, 0.3, 2.0, 17.0):
+        for f in (0.2, 0.5, 0.65):
+            gAA, gBB, gAB = o.debye_g(x, f)
+            assert abs(float(o.debye_chain(x)) - (gAA + 2 * gAB + gBB)) < 1e-10, (x, f)
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    for x in (1e-6, 1e-3, 0.0999, 0.1001, 0.5):
+        X = mpmath.mpf(x)
+        ref = float(2 * (mpmath.exp(-X) + X - 1) / X ** 2)
+        assert abs(float(o.debye_chain(x)) - ref) < 1e-13, x
+    assert float(o.debye_chain(0.0)) == 1.0
+
+
+def _cos_field(eps, n, L, k_index=1):
+    x = np.arange(n[0]) * L[0] / n[0]
+    k = 2 * np.pi * k_index / L[0]
+    return np.broadcast_to(eps * np.cos(k * x)[:, None, None], n).copy(), x, k
+
+
+@pytest.mark.parametrize("lam", [0.5, 4.0])
+def test_sis_linear_response_is_the_wavevector_dependent_step(lam):
+    """W+ = eps cos(k x), W- = 0, fA = 1/2: the linearised force is -g_D(k) W+, so one
+    SIS step leaves the amplitude eps / (1 + lam g_D(k)) up to O(eps^2) + O(ds^2) (error
+    4e-7 at Ns = 128, falling 4x per halving of ds); the explicit Euler step leaves
+    eps (1 - lam g_D(k)), which grows for lam g_D > 2."""
+    eps = 1e-4
+    n, L = (16, 2, 2), (5.0, 1.0, 1.0)
+    wp, x, k = _cos_field(eps, n, L)
+    wm = np.zeros(n)
+    gD = float(o.debye_chain(k * k))
+    errs = []
+    for Ns in (64, 128):
+        s = o.solve(wp, wm, n, L, Ns, 0.5, o.SCFT_REAL)
+        wpn, wmn = o.scft_sis_step(wp, wm, s.phiA, s.phiB, 15.0, lam, n, L)
+        amp = 2 * np.mean(wpn[:, 0, 0] * np.cos(k * x)) / eps
+        errs.append(abs(amp * (1 + lam * gD) - 1))
+        assert np.max(np.abs(wmn)) < 1e-12  # fA = 1/2: no exchange-field response to W+
+        wpe, _ = o.scft_euler_step(wp, wm, s.phiA, s.phiB, 15.0, lam)
+        ampe = 2 * np.mean(wpe[:, 0, 0] * np.cos(k * x)) / eps
+        assert abs(ampe - (1 - lam * gD)) < 1e-5
+    assert errs[1] < 1e-6 and 3.0 < errs[0] / errs[1] < 5.0, errs
+    if lam * gD > 2:
+        assert abs(1 - lam * gD) > 1 > 1 / (1 + lam * gD)
+
+
+def test_sis_leaves_the_homogeneous_saddle_fixed():
+    """At the homogeneous saddle (W+ uniform, W- = chiN (2 fA_eff - 1)/2) both forces
+    vanish and the SIS step changes nothing (SCFT and CL forms)."""
+    n, L, Ns, fA, chiN = (6, 4, 8), (3.0, 2.0, 4.0), 20, 0.35, 12.0
+    fa = o.n_A_steps(Ns, fA) / Ns
+    wp = np.full(n, 0.4)
+    wm = np.full(n, chiN * (2 * fa - 1) / 2)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    wpn, wmn = o.scft_sis_step(wp, wm, s.phiA, s.phiB, chiN, 0.7, n, L)
+    assert np.max(np.abs(wpn - wp)) < 1e-13 and np.max(np.abs(wmn - wm)) < 1e-13
+    z = np.zeros(n)
+    cpn, cmn = o.cl_sis_step(-1j * wp, wm.astype(complex), s.phiA, s.phiB, chiN, 0.7, z, z, n, L)
+    assert np.max(np.abs(cpn + 1j * wp)) < 1e-13 and np.max(np.abs(cmn - wm)) < 1e-13
+
+
+def test_cl_sis_without_noise_is_the_wick_rotated_scft_sis():
+    """With omega+ = -i W+ (purely imaginary), real omega- and no noise, the CL SIS step
+    with dt = lam is the SCFT SIS step rotated back (W+ = i omega+)."""
+    n, L, Ns, fA, chiN, lam = (6, 4, 8), (3.0, 2.0, 4.0), 12, 0.4, 14.0, 0.3
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 41)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    wpn, wmn = o.scft_sis_step(wp, wm, s.phiA, s.phiB, chiN, lam, n, L)
+    z = np.zeros(n)
+    cpn, cmn = o.cl_sis_step(-1j * wp, wm.astype(complex), s.phiA, s.phiB, chiN, lam, z, z, n, L)
+    assert np.max(np.abs(1j * cpn - wpn)) < 1e-13 and np.max(np.abs(cmn - wmn)) < 1e-13
+
+
+def test_cl_sis_filters_the_noise_with_the_same_factor():
+    """Eq. 11 puts the noise on the same side as the force, so at a saddle a plane-wave
+    noise eta+ = a cos(k x) moves omega+ by a cos(k x) / (1 + dt g_D(k)), and eta- moves
+    omega- by eta- / (1 + 2 dt/chiN)."""
+    n, L, Ns, fA, chiN, dt = (16, 2, 2), (5.0, 1.0, 1.0), 16, 0.5, 10.0, 0.8
+    wp = np.zeros(n, complex)
+    wm = np.zeros(n, complex)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    eta, x, k = _cos_field(0.3, n, L, k_index=2)
+    gD = float(o.debye_chain(k * k))
+    cpn, cmn = o.cl_sis_step(wp, wm, s.phiA, s.phiB, chiN, dt, eta, eta, n, L)
+    assert np.max(np.abs(cpn - eta / (1 + dt * gD))) < 1e-13
+    assert np.max(np.abs(cmn - eta / (1 + 2 * dt / chiN))) < 1e-13
