@@ -60,7 +60,12 @@ typedef enum {
 typedef enum { PFT_SCFT_REAL = 0, PFT_CL_COMPLEX = 1 } pft_kind;
 typedef enum { PFT_FP64 = 0, PFT_FP32_MIXED = 1 } pft_precision;
 typedef enum { PFT_HOST = 0, PFT_DEVICE = 1 } pft_mem;
-typedef enum { PFT_STEP_SCFT_EULER = 0, PFT_STEP_CL_EULER_MARUYAMA = 1 } pft_step_kind;
+typedef enum {
+  PFT_STEP_SCFT_EULER = 0,
+  PFT_STEP_CL_EULER_MARUYAMA = 1,
+  PFT_STEP_SCFT_SIS = 2,
+  PFT_STEP_CL_SIS = 3
+} pft_step_kind;
 /* How the marches run.  PASSES: five pass kernels per contour step, replayed as one
  * CUDA graph per solve.  RESIDENT (FP32-mixed, real SCFT fields, cubic 64^3/96^3/128^3
  * grids only): one persistent cooperative launch per march, one CTA per x-plane keeping
@@ -175,6 +180,15 @@ pft_status pft_get_densities(pft_ctx* ctx, void* phiA, void* phiB, pft_mem where
  *                                     W- -= lam (2 W-/chiN + phiB - phiA)
  *   PFT_STEP_CL_EULER_MARUYAMA (CL):  w+ += -dt i (phiA+phiB-1) + eta+;
  *                                     w- += -dt (2 w-/chiN + phiB - phiA) + eta-
+ * and the semi-implicit steps of Eq. 11 (the linear part of the force at the new time):
+ *   PFT_STEP_SCFT_SIS (SCFT mode):    W+^(k) += lam F+^(k) / (1 + lam g_D(k));
+ *                                     W- = (W- - lam (phiB - phiA)) / (1 + 2 lam/chiN)
+ *   PFT_STEP_CL_SIS (CL):             w+^(k) += (-dt i F^(k) + eta+^(k)) / (1 + dt g_D(k)),
+ *                                     F = phiA+phiB-1;
+ *                                     w- = (w- - dt (phiB - phiA) + eta-) / (1 + 2 dt/chiN)
+ * with g_D(k) = 2 (e^{-x} + x - 1)/x^2, x = k^2 (the whole chain's Debye function, Rg = 1)
+ * and ^ the discrete Fourier transform (one forward and one inverse FP64 transform of the
+ * w+ increment per step).
  * eta+/- are real Gaussian with variance 2 dt/(C dV) (below Eq. 10).  If eta_p and
  * eta_m are NULL the library draws them from its Philox4x32-10 stream (key = seed,
  * counter = (point/4, field, step, instance)); otherwise they are caller arrays of M

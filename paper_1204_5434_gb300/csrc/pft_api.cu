@@ -78,7 +78,7 @@ void free_all(pft_ctx* c) {
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
                   d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync, d.qdh, d.steps2, d.stepsg,
-                  d.BAh, d.BBh, d.rq, d.qw};
+                  d.BAh, d.BBh, d.rq, d.qw, d.sis};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
@@ -414,16 +414,17 @@ pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt, co
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
   if (!d.solved) return fail(PFT_ERR_STATE, "pft_field_step needs a solve at the current fields");
-  if (kind == PFT_STEP_SCFT_EULER && d.kind != PFT_SCFT_REAL)
-    return fail(PFT_ERR_ARG, "SCFT Euler step needs real SCFT fields");
-  if (kind == PFT_STEP_CL_EULER_MARUYAMA && d.kind != PFT_CL_COMPLEX)
-    return fail(PFT_ERR_ARG, "complex Langevin step needs complex fields");
-  if (kind != PFT_STEP_SCFT_EULER && kind != PFT_STEP_CL_EULER_MARUYAMA) return fail(PFT_ERR_ARG, "unknown step kind");
+  if (kind != PFT_STEP_SCFT_EULER && kind != PFT_STEP_CL_EULER_MARUYAMA && kind != PFT_STEP_SCFT_SIS &&
+      kind != PFT_STEP_CL_SIS)
+    return fail(PFT_ERR_ARG, "unknown step kind");
+  const bool scft_step = (kind == PFT_STEP_SCFT_EULER || kind == PFT_STEP_SCFT_SIS);
+  if (scft_step && d.kind != PFT_SCFT_REAL) return fail(PFT_ERR_ARG, "SCFT step needs real SCFT fields");
+  if (!scft_step && d.kind != PFT_CL_COMPLEX) return fail(PFT_ERR_ARG, "complex Langevin step needs complex fields");
   if (!isfinite(lam_or_dt) || !(lam_or_dt > 0.0)) return fail(PFT_ERR_ARG, "step size must be positive");
   if ((eta_p == nullptr) != (eta_m == nullptr)) return fail(PFT_ERR_ARG, "give both noise arrays or neither");
   const double* ep = nullptr;
   const double* em = nullptr;
-  if (eta_p && kind == PFT_STEP_CL_EULER_MARUYAMA) {
+  if (eta_p && !scft_step) {
     if (where == PFT_HOST) {
       double* io = (double*)ctx->io;
       PFT_CK(cudaMemcpyAsync(io, eta_p, (size_t)d.M * 8, cudaMemcpyHostToDevice, d.stream));
@@ -483,8 +484,8 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   CtxData& d = ctx->d;
   if (!d.fields_set) return fail(PFT_ERR_STATE, "pft_profile_step before pft_set_fields");
   if (step_kind >= 0) {
-    if ((step_kind == PFT_STEP_SCFT_EULER) != (d.kind == PFT_SCFT_REAL) ||
-        (step_kind != PFT_STEP_SCFT_EULER && step_kind != PFT_STEP_CL_EULER_MARUYAMA))
+    const bool scft_step = (step_kind == PFT_STEP_SCFT_EULER || step_kind == PFT_STEP_SCFT_SIS);
+    if (step_kind > PFT_STEP_CL_SIS || scft_step != (d.kind == PFT_SCFT_REAL))
       return fail(PFT_ERR_ARG, "step kind does not match the model kind");
     if (!isfinite(lam_or_dt) || !(lam_or_dt > 0.0)) return fail(PFT_ERR_ARG, "step size must be positive");
   }

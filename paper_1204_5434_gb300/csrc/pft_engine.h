@@ -74,7 +74,9 @@ struct CtxData {
   void* tables = nullptr;      // twiddles + diffusion factors
   size_t tw_off[4] = {0, 0, 0, 0};  // x, y, z (full nz), z half (nz/2): byte offsets
   size_t d_off[3] = {0, 0, 0};      // dx (with 1/M), dy, dz
-  size_t g_off[3] = {0, 0, 0};      // box-derivative weights 2 ds k_a^2 / L_a per axis
+  size_t g_off[3] = {0, 0, 0};      // k_a^2 per axis (FP64): box derivative, SIS Debye factor
+  size_t t64_off[3] = {0, 0, 0};    // FP64 twiddles x, y, z (full nz) for the SIS transforms
+  void* sis = nullptr;              // [M] complex FP64 scratch of the semi-implicit step
   size_t tables_bytes = 0;
   int npart = 0;
   size_t bytes = 0;

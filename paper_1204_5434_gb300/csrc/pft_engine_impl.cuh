@@ -546,6 +546,143 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
+// ------------------------------------------------- semi-implicit step (Eq. 11)
+// Debye function of the whole chain, g_D(x) = 2 (e^{-x} + x - 1) / x^2 at x = k^2 (Rg = 1):
+// the closed form from x = 0.1 up, below it the Taylor series 2 sum_{j>=0} (-x)^j / (j+2)!
+// through x^9 (the closed form loses digits to cancellation there).
+__device__ __forceinline__ double debye_chain(double x) {
+  if (x >= 0.1) return 2.0 * (exp(-x) + x - 1.0) / (x * x);
+  const double c[10] = {1.0,          -2.0 / 6.0,      2.0 / 24.0,      -2.0 / 120.0,      2.0 / 720.0,
+                        -2.0 / 5040.0, 2.0 / 40320.0, -2.0 / 362880.0, 2.0 / 3628800.0, -2.0 / 39916800.0};
+  double r = c[9];
+#pragma unroll
+  for (int j = 8; j >= 0; j--) r = fma(r, x, c[j]);
+  return r;
+}
+
+// SCFT: G = lam (phiA + phiB - 1) as a complex array for the transform, and the
+// exchange field with its linear term implicit: W- = (W- - lam (phiB - phiA)) / (1 + 2 lam/chiN).
+static __global__ void __launch_bounds__(PW_THREADS) k_sis_force_real(const double* __restrict__ phiA,
+                                                               const double* __restrict__ phiB,
+                                                               double* __restrict__ wm, double2* __restrict__ G,
+                                                               double lam, double chiN, long long M) {
+  const double inv = 1.0 / (1.0 + 2.0 * lam / chiN);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double a = phiA[i], b = phiB[i];
+    G[i] = make_double2(lam * (a + b - 1.0), 0.0);
+    wm[i] = (wm[i] - lam * (b - a)) * inv;
+  }
+}
+
+// CL: G = -dt i (phiA + phiB - 1) + eta+ and w- = (w- - dt (phiB - phiA) + eta-) / (1 + 2 dt/chiN),
+// the noise from the Philox stream (same counters as the Euler-Maruyama step) or the caller.
+static __global__ void __launch_bounds__(PW_THREADS) k_sis_force_cplx(const double2* __restrict__ phiA,
+                                                               const double2* __restrict__ phiB,
+                                                               double2* __restrict__ wm, double2* __restrict__ G,
+                                                               double dt, double noise_std,
+                                                               const double* __restrict__ eta_p,
+                                                               const double* __restrict__ eta_m,
+                                                               unsigned long long seed, unsigned long long instance,
+                                                               unsigned long long step_arg,
+                                                               const unsigned long long* __restrict__ step_dev,
+                                                               double chiN, long long M) {
+  const unsigned long long step = step_dev ? *step_dev : step_arg;
+  const double inv = 1.0 / (1.0 + 2.0 * dt / chiN);
+  const long long nblk = (M + 3) / 4;
+  for (long long bk = blockIdx.x * (long long)blockDim.x + threadIdx.x; bk < nblk;
+       bk += (long long)gridDim.x * blockDim.x) {
+    double zp[4], zm[4];
+    if (eta_p) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const long long i = 4 * bk + j;
+        zp[j] = (i < M) ? eta_p[i] : 0.0;
+        zm[j] = (i < M) ? eta_m[i] : 0.0;
+      }
+    } else {
+      philox_normal4(seed, instance, step, 0, bk, zp);
+      philox_normal4(seed, instance, step, 1, bk, zm);
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        zp[j] *= noise_std;
+        zm[j] *= noise_std;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const long long i = 4 * bk + j;
+      if (i >= M) break;
+      const double2 a = phiA[i], b = phiB[i];
+      // -dt i (s - 1) with s = phiA + phiB
+      const double sr = a.x + b.x - 1.0, si = a.y + b.y;
+      G[i] = make_double2(dt * si + zp[j], -dt * sr);
+      double2 m = wm[i];
+      m.x = (m.x - dt * (b.x - a.x) + zm[j]) * inv;
+      m.y = (m.y - dt * (b.y - a.y)) * inv;
+      wm[i] = m;
+    }
+  }
+}
+
+// G^(k) /= 1 + a g_D(k^2) on the full (nx, ny, nz) complex grid; k^2 from the per-axis
+// tables (the z table may hold only kz <= nz/2: k^2 is even in kz).
+static __global__ void __launch_bounds__(PW_THREADS) k_sis_scale(double2* __restrict__ G, const double* __restrict__ gx,
+                                                          const double* __restrict__ gy, const double* __restrict__ gz,
+                                                          int ny, int nz, double a, long long M) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const int kz = (int)(i % nz);
+    const long long r = i / nz;
+    const int ky = (int)(r % ny);
+    const int kx = (int)(r / ny);
+    const int kzz = kz <= nz - kz ? kz : nz - kz;
+    const double k2 = gx[kx] + gy[ky] + gz[kzz];
+    const double f = 1.0 / (1.0 + a * debye_chain(k2));
+    double2 g = G[i];
+    g.x *= f;
+    g.y *= f;
+    G[i] = g;
+  }
+}
+
+// W+ += Re(G)/M (the unnormalised inverse transform), then the Boltzmann factors of the
+// new fields and the field term of Eq. 3.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_sis_apply_real(double* __restrict__ wp, const double* __restrict__ wm,
+                                                               const double2* __restrict__ G, T* __restrict__ BA,
+                                                               T* __restrict__ BB, double invM, double ds, double chiN,
+                                                               long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double p = wp[i] + G[i].x * invM, m = wm[i];
+    wp[i] = p;
+    BA[i] = boltz<T>(p - m, ds);
+    BB[i] = boltz<T>(p + m, ds);
+    acc[0] += m * m / chiN - p;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_sis_apply_cplx(double2* __restrict__ wp, const double2* __restrict__ wm,
+                                                               const double2* __restrict__ G, cpx<T>* __restrict__ BA,
+                                                               cpx<T>* __restrict__ BB, double invM, double ds,
+                                                               double chiN, long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    double2 p = wp[i];
+    const double2 g = G[i], m = wm[i];
+    p.x += g.x * invM;
+    p.y += g.y * invM;
+    wp[i] = p;
+    const double2 ip = make_double2(-p.y, p.x);
+    BA[i] = boltz_c<T>(make_double2(ip.x - m.x, ip.y - m.y), ds);
+    BB[i] = boltz_c<T>(make_double2(ip.x + m.x, ip.y + m.y), ds);
+    acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
+    acc[1] += 2.0 * m.x * m.y / chiN - p.x;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
 // Precision conversion of one slice (real or complex as 2 reals).
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, long long n) {

@@ -265,6 +265,11 @@ class EngineT : public Engine {
       c.dh_off[a] = off;
       off = al(off + sizeof(T) * (size_t)dn[a]);
     }
+    // FP64 twiddles of the full x, y, z lengths (the transforms of the semi-implicit step)
+    for (int a = 0; a < 3; a++) {
+      c.t64_off[a] = off;
+      off = al(off + sizeof(double2) * (size_t)twn[a]);
+    }
     if (!c.tables) {
       cudaError_t e = cudaMalloc(&c.tables, off);
       if (e != cudaSuccess) return e;
@@ -277,6 +282,13 @@ class EngineT : public Engine {
       for (int m = 0; m < twn[a]; m++) {
         const double ang = -2.0 * M_PI * (double)m / (double)twn[a];
         tw[m] = mk<T>((T)cos(ang), (T)sin(ang));
+      }
+    }
+    for (int a = 0; a < 3; a++) {
+      double2* tw = reinterpret_cast<double2*>(h.data() + c.t64_off[a]);
+      for (int m = 0; m < twn[a]; m++) {
+        const double ang = -2.0 * M_PI * (double)m / (double)twn[a];
+        tw[m] = make_double2(cos(ang), sin(ang));
       }
     }
     const double Md = (double)c.M;
@@ -889,6 +901,7 @@ class EngineT : public Engine {
   // -------------------------------------------------------------- a7: step
   cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p, const double* eta_m) override {
     mark(c, KK_FIELD_STEP);
+    if (step_kind == PFT_STEP_SCFT_SIS || step_kind == PFT_STEP_CL_SIS) return sis_step(c, step_kind, lam, eta_p, eta_m);
     if (step_kind == PFT_STEP_SCFT_EULER) {
       k_step_scft<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (double*)c.wm, (const double*)c.accA,
                                                            (const double*)c.accB, (T*)c.BA, (T*)c.BB, lam, c.ds, c.chiN,
@@ -903,6 +916,69 @@ class EngineT : public Engine {
     }
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
     return half_boltz(c);
+  }
+
+  // ------------------------------------------- semi-implicit step (Eq. 11)
+  // Force and exchange-field update, FP64 transform of the W+ increment, division by
+  // 1 + a g_D(k), inverse transform, W+ update with the new Boltzmann factors.
+  cudaError_t sis_step(CtxData& c, int step_kind, double a, const double* eta_p, const double* eta_m) {
+    cudaError_t e;
+    if (!c.sis) {
+      if ((e = cudaMalloc(&c.sis, (size_t)c.M * sizeof(double2))) != cudaSuccess) return e;
+      c.bytes += (size_t)c.M * sizeof(double2);
+    }
+    double2* G = (double2*)c.sis;
+    if (step_kind == PFT_STEP_SCFT_SIS) {
+      k_sis_force_real<<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.accA, (const double*)c.accB,
+                                                             (double*)c.wm, G, a, c.chiN, c.M);
+    } else {
+      const double dV = c.L[0] * c.L[1] * c.L[2] / (double)c.M;
+      const double std = sqrt(2.0 * a / (c.C * dV));
+      k_sis_force_cplx<<<c.npart, PW_THREADS, 0, c.stream>>>((const double2*)c.accA, (const double2*)c.accB,
+                                                             (double2*)c.wm, G, a, std, eta_p, eta_m, c.seed,
+                                                             c.instance, (unsigned long long)c.step, c.step_dev,
+                                                             c.chiN, c.M);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = fft3d_f64(c, G, false)) != cudaSuccess) return e;
+    k_sis_scale<<<c.npart, PW_THREADS, 0, c.stream>>>(G, tab<double>(c, c.g_off[0]), tab<double>(c, c.g_off[1]),
+                                                      tab<double>(c, c.g_off[2]), c.n[1], c.n[2], a, c.M);
+    if ((e = fft3d_f64(c, G, true)) != cudaSuccess) return e;
+    if (c.kind == PFT_SCFT_REAL) {
+      k_sis_apply_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (const double*)c.wm, G, (T*)c.BA,
+                                                                (T*)c.BB, 1.0 / (double)c.M, c.ds, c.chiN, c.M,
+                                                                c.partials);
+    } else {
+      k_sis_apply_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double2*)c.wp, (const double2*)c.wm, G, (Z*)c.BA,
+                                                                (Z*)c.BB, 1.0 / (double)c.M, c.ds, c.chiN, c.M,
+                                                                c.partials);
+    }
+    k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
+    return half_boltz(c);
+  }
+
+  // Complex FP64 3D transform in place (unnormalised both ways) with the FP64 twiddles.
+  cudaError_t fft3d_f64(CtxData& c, double2* d, bool inverse) {
+    const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
+    const double2* twx = tab<double2>(c, c.t64_off[0]);
+    const double2* twy = tab<double2>(c, c.t64_off[1]);
+    const double2* twz = tab<double2>(c, c.t64_off[2]);
+    const long long npen = (long long)nx * ny;
+    cudaError_t e;
+    if (!inverse) {
+      PFT_DISPATCH_AXIS(nz, e = (d_zf_c2c<N>(c, d, npen, twz)));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(ny, e = (d_strided<N, 0>(c, d, (long long)nx * nz, nz, (long long)ny * nz, nz, twy)));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(nx, e = (d_strided<N, 0>(c, d, (long long)ny * nz, (long long)ny * nz, 0, (long long)ny * nz, twx)));
+    } else {
+      PFT_DISPATCH_AXIS(nx, e = (d_strided<N, 1>(c, d, (long long)ny * nz, (long long)ny * nz, 0, (long long)ny * nz, twx)));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(ny, e = (d_strided<N, 1>(c, d, (long long)nx * nz, nz, (long long)ny * nz, nz, twy)));
+      if (e != cudaSuccess) return e;
+      PFT_DISPATCH_AXIS(nz, e = (d_zi_c2c<N>(c, d, npen, twz)));
+    }
+    return e;
   }
 
   // ---------------------------------------------------------- test hook: FFT
@@ -1059,6 +1135,32 @@ class EngineT : public Engine {
   }
 
  private:
+  // FP64 complex transform launches (independent of the working precision T)
+  template <int N, int MODE>
+  static cudaError_t d_strided(CtxData& c, double2* data, long long ncols, long long cin, long long s_outer,
+                               long long s_k, const double2* tw) {
+    constexpr int C = Tile<double>::C;
+    const long long blocks = (ncols + C - 1) / C;
+    k_strided<double, N, MODE><<<(unsigned)blocks, C * Plan<N>::TPC, (size_t)N * C * sizeof(double2), c.stream>>>(
+        data, ncols, cin, s_outer, s_k, tw, nullptr, nullptr, nullptr, 1);
+    return cudaGetLastError();
+  }
+  template <int N>
+  static cudaError_t d_zf_c2c(CtxData& c, double2* d, long long npen, const double2* tw) {
+    constexpr int P = PencilsPerCta<double, N>::v;
+    k_zf_c2c<double, N><<<(unsigned)((npen + P - 1) / P), P * Plan<N>::TPC, (size_t)P * pencil_ld<double>(N) * sizeof(double2),
+                          c.stream>>>(d, nullptr, d, npen, tw);
+    return cudaGetLastError();
+  }
+  template <int N>
+  static cudaError_t d_zi_c2c(CtxData& c, double2* d, long long npen, const double2* tw) {
+    constexpr int P = PencilsPerCta<double, N>::v;
+    k_zi_c2c<double, N, 2><<<(unsigned)((npen + P - 1) / P), P * Plan<N>::TPC,
+                             (size_t)P * pencil_ld<double>(N) * sizeof(double2), c.stream>>>(
+        d, nullptr, d, nullptr, nullptr, nullptr, 0.0, 0.0, npen, tw);
+    return cudaGetLastError();
+  }
+
   template <int N, int MODE>
   static cudaError_t bs(const BatchStep* st, long long ncols, long long cin, long long s_outer, long long s_k, int nzc,
                         int axis, int nact, cudaStream_t stream) {

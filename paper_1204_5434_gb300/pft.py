@@ -26,6 +26,7 @@ PFT_STEP_SCFT_EULER, PFT_STEP_CL_EULER_MARUYAMA = 0, 1
 PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT, PFT_MARCH_PERSISTENT = 0, 1, 2, 3
 PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
 PFT_SCHEME_SPLIT2, PFT_SCHEME_RQM4 = 0, 1
+PFT_STEP_SCFT_SIS, PFT_STEP_CL_SIS = 2, 3
 
 
 class pft_grid(ct.Structure):
@@ -466,8 +467,11 @@ class System:
         pft_get_densities(self.h, a, b)
         return a, b
 
-    def field_step(self, lam_or_dt, eta_p=None, eta_m=None):
-        kind = PFT_STEP_SCFT_EULER if self.kind == PFT_SCFT_REAL else PFT_STEP_CL_EULER_MARUYAMA
+    def field_step(self, lam_or_dt, eta_p=None, eta_m=None, semi_implicit=False):
+        if self.kind == PFT_SCFT_REAL:
+            kind = PFT_STEP_SCFT_SIS if semi_implicit else PFT_STEP_SCFT_EULER
+        else:
+            kind = PFT_STEP_CL_SIS if semi_implicit else PFT_STEP_CL_EULER_MARUYAMA
         if isinstance(eta_p, np.ndarray):
             eta_p = np.ascontiguousarray(eta_p, dtype=np.float64)
             eta_m = np.ascontiguousarray(eta_m, dtype=np.float64)
