@@ -269,6 +269,39 @@ def _cl(pft, torch, w, prec, steps, warmup=1, checkpoint=0):
             "H_last": [obs["H"].real, obs["H"].imag]}
 
 
+def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, step_size=None):
+    """Field updates of a workload with another contour scheme or field-step kind, timed
+    with CUDA events on the context stream (fields resident on the device)."""
+    kind = pft.PFT_SCFT_REAL if w.kind == wl.SCFT else pft.PFT_CL_COMPLEX
+    if step_kind is None:
+        step_kind = pft.PFT_STEP_SCFT_EULER if kind == pft.PFT_SCFT_REAL else pft.PFT_STEP_CL_EULER_MARUYAMA
+    if step_size is None:
+        step_size = w.lam if kind == pft.PFT_SCFT_REAL else w.dt
+    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, kind, prec, seed=w.seed, scheme=scheme)
+    h = s.h
+    wp, wm = wl.fields(w)
+    pft.pft_set_fields(h, wp, wm)
+
+    def one():
+        pft.pft_solve(h)
+        pft.pft_field_step(h, step_kind, step_size)
+    for _ in range(warmup):
+        one()
+    pft.pft_synchronize(h)
+    st = torch.cuda.ExternalStream(pft.pft_get_stream(h))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        one()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    s.close()
+    units = 2 * w.M * w.Ns
+    return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+
+
 def _library_fft_step(torch, wpa, wma, steps=3, warmup=1):
     """Comparison arm (not the product path): the same field update written with
     torch.fft (cuFFT) R2C/C2R transforms and separate elementwise kernels, eager launches,
@@ -477,6 +510,20 @@ def run(args):
           "cl256_fp64": _cl(pft, torch, wl.CL256, pft.PFT_FP64, 1),
           "cl256_fp32_checkpoint14": _cl(pft, torch, wl.CL256, pft.PFT_FP32_MIXED, 2, checkpoint=14)}
     torch.cuda.empty_cache()
+    variants = {
+        # the paper's 4th-order scheme (three split steps per contour step): units are
+        # 4th-order contour steps
+        "rqm4_fp32": dict(_variant(pft, torch, WORK, pft.PFT_FP32_MIXED, 5, scheme=pft.PFT_SCHEME_RQM4),
+                          scheme="RQM4 (Eq. 13), Simpson quadrature"),
+        "rqm4_fp64": dict(_variant(pft, torch, WORK, pft.PFT_FP64, 2, scheme=pft.PFT_SCHEME_RQM4),
+                          scheme="RQM4 (Eq. 13), Simpson quadrature"),
+        # semi-implicit field steps (Eq. 11): one FP64 transform pair per update on top
+        "sis_scft_fp32": dict(_variant(pft, torch, WORK, pft.PFT_FP32_MIXED, 10, step_kind=pft.PFT_STEP_SCFT_SIS),
+                              step="solve + semi-implicit SCFT step (lambda=0.1)"),
+        "sis_cl64_fp32": dict(_variant(pft, torch, wl.CL64, pft.PFT_FP32_MIXED, 10, step_kind=pft.PFT_STEP_CL_SIS),
+                              step="solve + semi-implicit complex Langevin step"),
+    }
+    torch.cuda.empty_cache()
     lib_fft = _library_fft_step(torch, wpa, wma)
     torch.cuda.empty_cache()
     batch = _batch(pft, pft.PFT_FP32_MIXED)
@@ -506,6 +553,7 @@ def run(args):
         "batch": batch,
         "complex_langevin": cl,
         "library_fft_comparison": dict(lib_fft, ours_over_library=main["value"] / lib_fft["value"]),
+        "variants": variants,
     }
     print(json.dumps(line), flush=True)
     if ws > 1:
