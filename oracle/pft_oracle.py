@@ -48,7 +48,8 @@ __all__ = [
     "dlnQ_dL", "dH_dL", "dH_dfields", "dft_matrix", "dft3_bruteforce",
     "dense_propagator_matrix", "forward_march_dense", "continuum_Q", "debye_g",
     "variable_cell_step", "rqm4_step", "simpson_weights", "SPLIT2", "RQM4",
-    "debye_chain", "scft_sis_step", "cl_sis_step",
+    "debye_chain", "scft_sis_step", "cl_sis_step", "EdwardsSolution", "edwards_field", "edwards_solve",
+    "edwards_hamiltonian", "edwards_scft_step", "edwards_cl_step",
 ]
 
 SPLIT2 = "split2"   # 2nd-order operator splitting, the A(ds) block of Eq. 13
@@ -354,6 +355,63 @@ def cl_noise(seed: int, instance: int, step: int, M: int, std: float):
     eta_p = std * philox_normals(seed, instance, step, 0, M)
     eta_m = std * philox_normals(seed, instance, step, 1, M)
     return eta_p, eta_m
+
+
+# ----------------------------------------------------------------------------
+# Edwards model of homopolymers in implicit solvent (Eq. 2): one field omega entering
+# Q as i omega; the chain is reversible, so q-dagger = q and half of the march is needed
+# ----------------------------------------------------------------------------
+@dataclass
+class EdwardsSolution:
+    Q: complex
+    lnQ: complex
+    phi: np.ndarray
+    q: np.ndarray
+
+
+def edwards_field(w, kind: str):
+    """Field felt by every segment: W = i omega is stored directly in SCFT mode (Wick
+    rotation of the pressure-like field), i omega in CL mode."""
+    return w if kind == SCFT_REAL else 1j * w
+
+
+def edwards_solve(w, n, L, Ns: int, kind: str, q0=None) -> EdwardsSolution:
+    """q from Eqs. 5 and 13 with one field for the whole chain, Q (Eq. 4), and the
+    segment density phi = (1/Q) int_0^1 ds q(s) q(1-s) (q-dagger = q for a homopolymer;
+    trapezoid rule over the whole contour)."""
+    ds = 1.0 / Ns
+    B = boltzmann_factor(edwards_field(w, kind), ds)
+    D = diffusion_factor(n, L, ds)
+    q = forward_march(B, B, D, Ns, Ns, q0)
+    Q = q[Ns].mean()
+    c = np.ones(Ns + 1)
+    c[0] = c[Ns] = 0.5
+    acc = np.zeros(q.shape[1:], q.dtype)
+    for k in range(Ns + 1):
+        acc = acc + c[k] * q[k] * q[Ns - k]
+    phi = ds * acc / Q
+    lnQ = np.log(Q) if np.iscomplexobj(Q) else math.log(Q)
+    return EdwardsSolution(Q=Q, lnQ=lnQ, phi=phi, q=q)
+
+
+def edwards_hamiltonian(w, lnQ, B: float, C: float, n, L, kind: str):
+    """H = (B/2) int dx omega^2 - C V lnQ (Eq. 2); in SCFT mode omega^2 = -W^2."""
+    M = int(np.prod(n))
+    V = float(np.prod(L))
+    w2 = -w * w if kind == SCFT_REAL else w * w
+    return 0.5 * B * (V / M) * w2.sum() - C * V * lnQ
+
+
+def edwards_scft_step(W, phi, B: float, C: float, lam: float):
+    """Relaxation of the Wick-rotated field towards the saddle W = (C/B) phi, ascent on
+    the pressure-like field with the force per C: W += lam (phi - (B/C) W)."""
+    return W + lam * (phi - (B / C) * W)
+
+
+def edwards_cl_step(w, phi, B: float, C: float, dt: float, eta):
+    """Euler-Maruyama complex Langevin step with the force per C,
+    dH/domega / C = (B/C) omega + i phi, and real noise eta of variance 2 dt/(C dV)."""
+    return w - dt * ((B / C) * w + 1j * phi) + eta
 
 
 # ----------------------------------------------------------------------------

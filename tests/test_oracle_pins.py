@@ -539,3 +539,80 @@ def test_cl_sis_filters_the_noise_with_the_same_factor():
     cpn, cmn = o.cl_sis_step(wp, wm, s.phiA, s.phiB, chiN, dt, eta, eta, n, L)
     assert np.max(np.abs(cpn - eta / (1 + dt * gD))) < 1e-13
     assert np.max(np.abs(cmn - eta / (1 + 2 * dt / chiN))) < 1e-13
+
+
+# ------------------------------------------------------- Edwards homopolymer (Eq. 2)
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_edwards_uniform_field_closed_form(kind):
+    """Uniform field: q_n = exp(-w n ds), Q = exp(-w), phi = 1 exactly."""
+    n, L, Ns = (4, 6, 4), (2.0, 3.0, 2.0), 14
+    w = np.full(n, 0.7) if kind == o.SCFT_REAL else np.full(n, 0.3 - 0.2j)
+    s = o.edwards_solve(w, n, L, Ns, kind)
+    wf = o.edwards_field(w, kind).flat[0]
+    assert abs(s.Q - np.exp(-wf)) <= 1e-14 * abs(np.exp(-wf))
+    for k in (1, 5, Ns):
+        assert np.max(np.abs(s.q[k] - np.exp(-wf * k / Ns))) < 1e-14
+    assert np.max(np.abs(s.phi - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_edwards_equals_the_diblock_path_with_one_block(kind):
+    """A homopolymer is a diblock with fA = 1 and no exchange field: the diblock path, which
+    marches q-dagger separately, gives the same Q and phi_A = phi (pins q-dagger = q)."""
+    n, L, Ns = (6, 4, 8), (3.0, 2.0, 4.0), 17
+    rng = np.random.default_rng(50)
+    w = rng.normal(0, 0.5, n)
+    if kind == o.CL_COMPLEX:
+        w = w + 1j * rng.normal(0, 0.3, n)
+    e = o.edwards_solve(w, n, L, Ns, kind)
+    d = o.solve(w, np.zeros(n, w.dtype), n, L, Ns, 1.0, kind)
+    assert abs(e.Q - d.Q) <= 1e-13 * abs(d.Q)
+    assert np.max(np.abs(e.phi - d.phiA)) < 1e-13 and np.max(np.abs(d.phiB)) == 0.0
+
+
+@pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
+def test_edwards_force_is_the_gradient_of_H(kind):
+    """dH/dW_j = C dV (phi_j - (B/C) W_j) for the discrete H of SCFT mode (5-point finite
+    differences, 1e-8), and dH/domega_j = C dV ((B/C) omega_j + i phi_j) in CL mode."""
+    n, L, Ns, B, C = (6, 4, 4), (3.0, 2.0, 2.0), 12, 2.0, 5.0
+    rng = np.random.default_rng(51)
+    w = rng.normal(0, 0.4, n)
+    if kind == o.CL_COMPLEX:
+        w = w + 1j * rng.normal(0, 0.2, n)
+    s = o.edwards_solve(w, n, L, Ns, kind)
+    dV = np.prod(L) / np.prod(n)
+    if kind == o.SCFT_REAL:
+        g = C * dV * (s.phi - (B / C) * w)
+    else:
+        g = C * dV * ((B / C) * w + 1j * s.phi)
+    for idx in [(1, 2, 3), (4, 0, 1)]:
+        def H(h, idx=idx):
+            ww = w.copy()
+            ww[idx] += h
+            return o.edwards_hamiltonian(ww, o.edwards_solve(ww, n, L, Ns, kind).lnQ, B, C, n, L, kind)
+        fd = fd5(H)
+        assert abs(fd - g[idx]) <= 1e-8 * max(1.0, abs(g[idx])), (idx, fd, g[idx])
+
+
+def test_edwards_debye_response_and_saddle():
+    """W = W0 + eps cos(k x): the k-mode of phi is -eps g_D(k) (whole-chain Debye function)
+    up to O(eps^2) and O(ds^2) (Richardson over Ns = 64, 128, 256); the homogeneous
+    saddle W = C/B is a fixed point of the SCFT step."""
+    eps = 1e-4
+    n, L = (16, 2, 2), (5.0, 1.0, 1.0)
+    x = np.arange(16) * 5.0 / 16
+    k = 2 * np.pi / 5.0
+    W = 0.3 + np.broadcast_to(eps * np.cos(k * x)[:, None, None], n).copy()
+    amps = []
+    for Ns in (64, 128, 256):
+        s = o.edwards_solve(W, n, L, Ns, o.SCFT_REAL)
+        amps.append(2 * np.mean(s.phi[:, 0, 0] * np.cos(k * x)))
+    r1 = (4 * amps[1] - amps[0]) / 3
+    r2 = (4 * amps[2] - amps[1]) / 3
+    rr = (16 * r2 - r1) / 15
+    ex = -eps * float(o.debye_chain(k * k))
+    assert abs(rr - ex) <= 1e-6 * abs(ex), (rr, ex)
+    B, C = 2.0, 5.0
+    W0 = np.full((4, 4, 4), C / B)
+    s = o.edwards_solve(W0, (4, 4, 4), (2.0, 2.0, 2.0), 10, o.SCFT_REAL)
+    assert np.max(np.abs(o.edwards_scft_step(W0, s.phi, B, C, 0.5) - W0)) < 1e-13
