@@ -85,7 +85,23 @@ typedef enum { PFT_SCHEME_SPLIT2 = 0, PFT_SCHEME_RQM4 = 1 } pft_scheme;
 
 typedef struct { int n[3]; double L[3]; } pft_grid;          /* grid points and box (Rg) */
 typedef struct { int Ns; double fA; } pft_chain;              /* contour steps, A fraction */
-typedef struct { double chiN; double C; pft_kind kind; } pft_model;
+/* Chain model.  DIBLOCK: incompressible AB diblock melt (Eq. 3), fields W+/W- (SCFT) or
+ * omega+/omega- (CL).  EDWARDS: homopolymers in implicit solvent (Eq. 2),
+ * H = (B/2) int omega^2 - C V lnQ[i omega]: one field (the first field argument; the
+ * second is ignored and may be NULL), stored Wick-rotated as W = i omega in SCFT mode and
+ * as omega in CL mode; the chain is reversible, so q-dagger = q and one march is run;
+ * phi = (1/Q) int ds q(s) q(1-s) is returned as phiA (phiB = 0); chiN and fA are unused.
+ * EDWARDS runs the SPLIT2 scheme on the pass march with the full history, Euler or
+ * Euler-Maruyama steps; other options give PFT_ERR_UNSUPPORTED. */
+typedef enum { PFT_ARCH_DIBLOCK = 0, PFT_ARCH_EDWARDS = 1 } pft_arch;
+
+typedef struct {
+  double chiN;     /* chi_AB N (diblock) */
+  double C;        /* chains per Rg^3 (both models) */
+  pft_kind kind;   /* real SCFT or complex Langevin fields */
+  pft_arch arch;   /* 0 (memset) = DIBLOCK */
+  double B;        /* excluded-volume parameter of the Edwards model (>= 0) */
+} pft_model;
 
 typedef struct {
   pft_precision precision;
@@ -180,7 +196,9 @@ pft_status pft_get_densities(pft_ctx* ctx, void* phiA, void* phiB, pft_mem where
  *                                     W- -= lam (2 W-/chiN + phiB - phiA)
  *   PFT_STEP_CL_EULER_MARUYAMA (CL):  w+ += -dt i (phiA+phiB-1) + eta+;
  *                                     w- += -dt (2 w-/chiN + phiB - phiA) + eta-
- * and the semi-implicit steps of Eq. 11 (the linear part of the force at the new time):
+ * Edwards model (force per C, b = B/C): SCFT W += lam (phi - b W); CL
+ * omega += -dt (b omega + i phi) + eta (eta_m unused; Philox field 0);
+ * and the semi-implicit steps (diblock only) of Eq. 11 (the linear part of the force at the new time):
  *   PFT_STEP_SCFT_SIS (SCFT mode):    W+^(k) += lam F+^(k) / (1 + lam g_D(k));
  *                                     W- = (W- - lam (phiB - phiA)) / (1 + 2 lam/chiN)
  *   PFT_STEP_CL_SIS (CL):             w+^(k) += (-dt i F^(k) + eta+^(k)) / (1 + dt g_D(k)),

@@ -137,7 +137,14 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   }
   if (chain->Ns < 1 || chain->Ns > 100000) return fail(PFT_ERR_ARG, "Ns out of range [1, 100000]");
   if (!(chain->fA >= 0.0 && chain->fA <= 1.0)) return fail(PFT_ERR_ARG, "fA out of [0, 1]");
-  if (!(model->chiN > 0.0) || !(model->C > 0.0)) return fail(PFT_ERR_ARG, "chiN and C must be positive");
+  if (model->arch != PFT_ARCH_DIBLOCK && model->arch != PFT_ARCH_EDWARDS) return fail(PFT_ERR_ARG, "unknown chain model");
+  const bool edw = (model->arch == PFT_ARCH_EDWARDS);
+  if (!(model->C > 0.0) || !isfinite(model->C)) return fail(PFT_ERR_ARG, "C must be positive");
+  if (!edw && !(model->chiN > 0.0)) return fail(PFT_ERR_ARG, "chiN must be positive");
+  if (edw && !(model->B >= 0.0 && isfinite(model->B))) return fail(PFT_ERR_ARG, "B must be finite and >= 0");
+  if (edw && (opts->scheme != PFT_SCHEME_SPLIT2 || opts->checkpoint >= 2 ||
+              (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES)))
+    return fail(PFT_ERR_UNSUPPORTED, "the Edwards model runs SPLIT2 on the pass march with the full history");
   if (model->kind != PFT_SCFT_REAL && model->kind != PFT_CL_COMPLEX) return fail(PFT_ERR_ARG, "unknown model kind");
   if (opts->precision != PFT_FP64 && opts->precision != PFT_FP32_MIXED) return fail(PFT_ERR_ARG, "unknown precision");
   if (opts->scheme != PFT_SCHEME_SPLIT2 && opts->scheme != PFT_SCHEME_RQM4) return fail(PFT_ERR_ARG, "unknown scheme");
@@ -158,7 +165,13 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   d.fA = chain->fA;
   d.NsA = (int)floor(chain->fA * chain->Ns + 0.5);
   d.ds = 1.0 / chain->Ns;
-  d.chiN = model->chiN;
+  d.chiN = edw ? 1.0 : model->chiN;
+  d.edw = edw;
+  d.bC = edw ? model->B / model->C : 0.0;
+  if (edw) {  // one block: the whole chain feels the one field
+    d.fA = 1.0;
+    d.NsA = d.Ns;
+  }
   d.C = model->C;
   d.kind = model->kind;
   d.prec = opts->precision;
@@ -240,7 +253,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       }
     }
     if (K > d.Ns) K = d.Ns;
-    if (K < 2 || d.march != 1 || d.scheme != 0) K = 1;
+    if (K < 2 || d.march != 1 || d.scheme != 0 || d.edw) K = 1;
     d.ckK = K;
     d.nck = (K > 1) ? d.Ns / K + 1 : 0;
   }
@@ -316,11 +329,15 @@ pft_status pft_synchronize(pft_ctx* ctx) {
 }
 
 pft_status pft_set_fields(pft_ctx* ctx, const void* wp, const void* wm, pft_mem where) {
-  if (!ctx || !wp || !wm) return fail(PFT_ERR_ARG, "NULL argument");
+  if (!ctx || !wp || (!wm && !ctx->d.edw)) return fail(PFT_ERR_ARG, "NULL argument");
   CtxData& d = ctx->d;
   const size_t b = (size_t)d.M * felem(d);
   PFT_CK(cudaMemcpyAsync(d.wp, wp, b, kind_in(where), d.stream));
-  PFT_CK(cudaMemcpyAsync(d.wm, wm, b, kind_in(where), d.stream));
+  if (d.edw) {
+    PFT_CK(cudaMemsetAsync(d.wm, 0, b, d.stream));  // the one-field model keeps the second field at 0
+  } else {
+    PFT_CK(cudaMemcpyAsync(d.wm, wm, b, kind_in(where), d.stream));
+  }
   PFT_CK(ctx->eng->prepare_fields(d));
   if (where == PFT_HOST) PFT_CK(cudaStreamSynchronize(d.stream));
   d.fields_set = true;
@@ -331,12 +348,12 @@ pft_status pft_set_fields(pft_ctx* ctx, const void* wp, const void* wm, pft_mem 
 }
 
 pft_status pft_get_fields(pft_ctx* ctx, void* wp, void* wm, pft_mem where) {
-  if (!ctx || !wp || !wm) return fail(PFT_ERR_ARG, "NULL argument");
+  if (!ctx || !wp || (!wm && !ctx->d.edw)) return fail(PFT_ERR_ARG, "NULL argument");
   CtxData& d = ctx->d;
   if (!d.fields_set) return fail(PFT_ERR_STATE, "fields not set");
   const size_t b = (size_t)d.M * felem(d);
   PFT_CK(cudaMemcpyAsync(wp, d.wp, b, kind_out(where), d.stream));
-  PFT_CK(cudaMemcpyAsync(wm, d.wm, b, kind_out(where), d.stream));
+  if (wm) PFT_CK(cudaMemcpyAsync(wm, d.wm, b, kind_out(where), d.stream));
   if (where == PFT_HOST) PFT_CK(cudaStreamSynchronize(d.stream));
   return PFT_OK;
 }
@@ -420,6 +437,8 @@ pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt, co
   const bool scft_step = (kind == PFT_STEP_SCFT_EULER || kind == PFT_STEP_SCFT_SIS);
   if (scft_step && d.kind != PFT_SCFT_REAL) return fail(PFT_ERR_ARG, "SCFT step needs real SCFT fields");
   if (!scft_step && d.kind != PFT_CL_COMPLEX) return fail(PFT_ERR_ARG, "complex Langevin step needs complex fields");
+  if (d.edw && (kind == PFT_STEP_SCFT_SIS || kind == PFT_STEP_CL_SIS))
+    return fail(PFT_ERR_UNSUPPORTED, "semi-implicit steps are implemented for the diblock model");
   if (!isfinite(lam_or_dt) || !(lam_or_dt > 0.0)) return fail(PFT_ERR_ARG, "step size must be positive");
   if ((eta_p == nullptr) != (eta_m == nullptr)) return fail(PFT_ERR_ARG, "give both noise arrays or neither");
   const double* ep = nullptr;
@@ -448,6 +467,7 @@ pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
   if (d.kind != PFT_SCFT_REAL) return fail(PFT_ERR_UNSUPPORTED, "gradients need real SCFT fields");
+  if (d.edw) return fail(PFT_ERR_UNSUPPORTED, "gradients are implemented for the diblock model");
   if (d.scheme != 0)
     return fail(PFT_ERR_UNSUPPORTED, "gradients are the exact derivatives of the 2nd-order scheme only");
   if (!d.solved) return fail(PFT_ERR_STATE, "pft_gradients needs a solve at the current fields");
@@ -602,7 +622,8 @@ pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem
   if (which != 0 && which != 1) return fail(PFT_ERR_ARG, "which must be 0 (q) or 1 (qd)");
   if (which == 0 && (s < 0 || s > d.Ns)) return fail(PFT_ERR_ARG, "slice out of range");
   const size_t we = welem(d);
-  const void* qd_last = (d.march == 1 && d.concurrent && d.qdh && d.ckK == 1) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
+  const void* qd_last = d.edw ? (const void*)((const char*)d.hist + (size_t)d.Ns * d.M * we) :  // qd = q
+                        (d.march == 1 && d.concurrent && d.qdh && d.ckK == 1) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
                                                                   : d.qd[d.Ns & 1];
   if (which == 0 && !pft::q_kept(d, s))
     return fail(PFT_ERR_UNSUPPORTED, "slice " + std::to_string(s) + " is not kept by the checkpointed history");

@@ -156,6 +156,9 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
   *out = nullptr;
   if (count < 1 || !descs) return bfail(PFT_ERR_ARG, "need at least one instance description");
   for (int i = 0; i < count; i++)
+    if (descs[i].model.arch != PFT_ARCH_DIBLOCK)
+      return bfail(PFT_ERR_UNSUPPORTED, "batch instance " + std::to_string(i) + ": batches hold diblock systems");
+  for (int i = 0; i < count; i++)
     for (int a = 0; a < 3; a++)
       if (!pft::batch_axis_supported(descs[i].grid.n[a]))
         return bfail(PFT_ERR_SHAPE, "batch instance " + std::to_string(i) + ": grid sizes must be one of " +

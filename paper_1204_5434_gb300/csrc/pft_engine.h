@@ -94,6 +94,8 @@ struct CtxData {
   void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
   // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
   // scratch slices for the full and the two half steps, quadrature weight tables
+  bool edw = false;   // Edwards homopolymer model: one field, q-dagger = q
+  double bC = 0.0;    // its B / C
   int scheme = 0;
   // q history: ckK = 1 keeps every slice in hist; ckK = K >= 2 keeps q_{cK} in slots
   // 0..nck-1 (nck = Ns/K + 1), q_Ns in slot nck when K does not divide Ns, and the

@@ -546,6 +546,139 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
+// ------------------------------------------------ Edwards homopolymer model (Eq. 2)
+// Boltzmann factor of the one field (W = i omega stored in SCFT mode, omega in CL mode)
+// and the field term of H per C: -(b/2) W^2 (SCFT) or (b/2) omega^2 (CL), b = B/C.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_prepare_edw_real(const double* __restrict__ W, T* __restrict__ BA,
+                                                                 double ds, double b, long long M,
+                                                                 double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double w = W[i];
+    BA[i] = boltz<T>(w, ds);
+    acc[0] -= 0.5 * b * w * w;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_prepare_edw_cplx(const double2* __restrict__ w, cpx<T>* __restrict__ BA,
+                                                                 double ds, double b, long long M,
+                                                                 double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double2 o = w[i];
+    BA[i] = boltz_c<T>(make_double2(-o.y, o.x), ds);  // the chain feels i omega
+    acc[0] += 0.5 * b * (o.x * o.x - o.y * o.y);
+    acc[1] += b * o.x * o.y;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// phi = ds acc / Q in place (accB cleared), plus the sum of phi and of |force per C|^2:
+// phi - b W (SCFT) or b omega + i phi (CL).
+static __global__ void __launch_bounds__(PW_THREADS) k_finalize_edw_real(double* __restrict__ accA,
+                                                                         double* __restrict__ accB,
+                                                                         const double* __restrict__ W,
+                                                                         const double* __restrict__ s, double ds,
+                                                                         double b, long long M,
+                                                                         double* __restrict__ partials) {
+  const double f = ds / s[S_Q];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double p = accA[i] * f;
+    accA[i] = p;
+    accB[i] = 0.0;
+    const double F = p - b * W[i];
+    acc[0] += p;
+    acc[4] += F * F;
+  }
+  block_reduce_store<6>(acc, partials + 6 * blockIdx.x);
+}
+
+static __global__ void __launch_bounds__(PW_THREADS) k_finalize_edw_cplx(double2* __restrict__ accA,
+                                                                         double2* __restrict__ accB,
+                                                                         const double2* __restrict__ w,
+                                                                         const double* __restrict__ s, double ds,
+                                                                         double b, long long M,
+                                                                         double* __restrict__ partials) {
+  const double2 f = cdiv_d(make_double2(ds, 0.0), make_double2(s[S_Q], s[S_Q + 1]));
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double2 p = cmul_d(accA[i], f);
+    accA[i] = p;
+    accB[i] = make_double2(0.0, 0.0);
+    const double2 o = w[i];
+    const double2 F = make_double2(b * o.x - p.y, b * o.y + p.x);  // b omega + i phi
+    acc[0] += p.x;
+    acc[1] += p.y;
+    acc[4] += F.x * F.x + F.y * F.y;
+  }
+  block_reduce_store<6>(acc, partials + 6 * blockIdx.x);
+}
+
+// SCFT relaxation of the Wick-rotated field, ascent with the force per C:
+// W += lam (phi - b W); then its Boltzmann factor and field term.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_step_edw_scft(double* __restrict__ W, const double* __restrict__ phi,
+                                                              T* __restrict__ BA, double lam, double ds, double b,
+                                                              long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    double w = W[i];
+    w += lam * (phi[i] - b * w);
+    W[i] = w;
+    BA[i] = boltz<T>(w, ds);
+    acc[0] -= 0.5 * b * w * w;
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// Euler-Maruyama complex Langevin step: omega += -dt (b omega + i phi) + eta, real eta of
+// variance 2 dt/(C dV) from the Philox stream (field 0) or the caller.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_step_edw_cl(double2* __restrict__ w, const double2* __restrict__ phi,
+                                                            cpx<T>* __restrict__ BA, double dt, double noise_std,
+                                                            const double* __restrict__ eta,
+                                                            unsigned long long seed, unsigned long long instance,
+                                                            unsigned long long step_arg,
+                                                            const unsigned long long* __restrict__ step_dev, double ds,
+                                                            double b, long long M, double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  const unsigned long long step = step_dev ? *step_dev : step_arg;
+  const long long nblk = (M + 3) / 4;
+  for (long long bk = blockIdx.x * (long long)blockDim.x + threadIdx.x; bk < nblk;
+       bk += (long long)gridDim.x * blockDim.x) {
+    double z[4];
+    if (eta) {
+#pragma unroll
+      for (int j = 0; j < 4; j++) {
+        const long long i = 4 * bk + j;
+        z[j] = (i < M) ? eta[i] : 0.0;
+      }
+    } else {
+      philox_normal4(seed, instance, step, 0, bk, z);
+#pragma unroll
+      for (int j = 0; j < 4; j++) z[j] *= noise_std;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const long long i = 4 * bk + j;
+      if (i >= M) break;
+      double2 o = w[i];
+      const double2 p = phi[i];
+      o.x += -dt * (b * o.x - p.y) + z[j];
+      o.y += -dt * (b * o.y + p.x);
+      w[i] = o;
+      BA[i] = boltz_c<T>(make_double2(-o.y, o.x), ds);
+      acc[0] += 0.5 * b * (o.x * o.x - o.y * o.y);
+      acc[1] += b * o.x * o.y;
+    }
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
 // ------------------------------------------------- semi-implicit step (Eq. 11)
 // Debye function of the whole chain, g_D(x) = 2 (e^{-x} + x - 1) / x^2 at x = k^2 (Rg = 1):
 // the closed form from x = 0.1 up, below it the Taylor series 2 sum_{j>=0} (-x)^j / (j+2)!

@@ -326,7 +326,15 @@ class EngineT : public Engine {
   // ---------------------------------------------------------------- a1: fields
   cudaError_t prepare_fields(CtxData& c) override {
     mark(c, KK_PREPARE);
-    if (c.kind == PFT_SCFT_REAL) {
+    if (c.edw) {
+      if (c.kind == PFT_SCFT_REAL) {
+        k_prepare_edw_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.wp, (T*)c.BA, c.ds, c.bC, c.M,
+                                                                    c.partials);
+      } else {
+        k_prepare_edw_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const double2*)c.wp, (Z*)c.BA, c.ds, c.bC, c.M,
+                                                                    c.partials);
+      }
+    } else if (c.kind == PFT_SCFT_REAL) {
       k_prepare_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>(
           (const double*)c.wp, (const double*)c.wm, (T*)c.BA, (T*)c.BB, c.ds, c.chiN, c.M, c.partials);
     } else {
@@ -485,7 +493,16 @@ class EngineT : public Engine {
 
   cudaError_t solve_tail(CtxData& c) override {
     mark(c, KK_REDUCE);
-    if (c.kind == PFT_SCFT_REAL) {
+    if (c.edw) {
+      if (c.kind == PFT_SCFT_REAL) {
+        k_finalize_edw_real<<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.accA, (double*)c.accB, (const double*)c.wp,
+                                                                  c.scal, c.ds, c.bC, c.M, c.partials);
+      } else {
+        k_finalize_edw_cplx<<<c.npart, PW_THREADS, 0, c.stream>>>((double2*)c.accA, (double2*)c.accB,
+                                                                  (const double2*)c.wp, c.scal, c.ds, c.bC, c.M,
+                                                                  c.partials);
+      }
+    } else if (c.kind == PFT_SCFT_REAL) {
       k_finalize_real<<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.accA, (double*)c.accB, (const double*)c.wm,
                                                             c.scal, c.ds, c.chiN, c.M, c.partials);
     } else {
@@ -573,7 +590,7 @@ class EngineT : public Engine {
     const size_t we = (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
     const size_t slice = (size_t)c.M * we;
     cudaError_t e;
-    if (!c.qdh) {
+    if (!c.qdh && !c.edw) {  // the Edwards chain is reversible: qd = q, one history
       e = cudaMalloc(&c.qdh, (size_t)(c.Ns + 1) * slice);
       if (e != cudaSuccess) return e;
       c.bytes += (size_t)(c.Ns + 1) * slice;
@@ -593,13 +610,13 @@ class EngineT : public Engine {
         f.out = (void*)(hist + (size_t)s * slice);
         f.spec = c.spec;
         const int nb = c.Ns + 1 - s;
-        b.in = (s == 1) ? c.qd0 : (const void*)(qdh + (size_t)(s - 1) * slice);
-        b.B = (nb <= c.NsA) ? c.BA : c.BB;
-        b.out = qdh + (size_t)s * slice;
-        b.spec = c.spec2;
-        if (s < c.Ns) {
-          f.Bnext = (s + 1 <= c.NsA) ? c.BA : c.BB;
-          b.Bnext = (nb - 1 <= c.NsA) ? c.BA : c.BB;
+        if (s < c.Ns) f.Bnext = (s + 1 <= c.NsA) ? c.BA : c.BB;
+        if (qdh) {
+          b.in = (s == 1) ? c.qd0 : (const void*)(qdh + (size_t)(s - 1) * slice);
+          b.B = (nb <= c.NsA) ? c.BA : c.BB;
+          b.out = qdh + (size_t)s * slice;
+          b.spec = c.spec2;
+          if (s < c.Ns) b.Bnext = (nb - 1 <= c.NsA) ? c.BA : c.BB;
         }
         for (int a = 0; a < 4; a++) f.tw[a] = b.tw[a] = t + c.tw_off[a];
         for (int a = 0; a < 3; a++) f.d[a] = b.d[a] = t + c.d_off[a];
@@ -620,6 +637,10 @@ class EngineT : public Engine {
     g.nzh = c.nzh;
     const BatchStep* st = (const BatchStep*)c.steps2;
     cudaError_t e;
+    if (c.edw) {  // one reversible chain: the forward march is the whole solve
+      if ((e = march_chain(c, g, st, c.stream)) != cudaSuccess) return e;
+      return finish_concurrent(c);
+    }
     if (!c.profiling) {
       // one chain per propagator on two streams: the two marches are independent until
       // the quadrature, and their kernels fill each other's idle SMs
@@ -693,11 +714,14 @@ class EngineT : public Engine {
     if ((e = solve_mid(c)) != cudaSuccess) return e;
     mark(c, KK_QUADRATURE);
     const int blocks = c.sms * 8;
+    // qd = q for the reversible Edwards chain (its q_0 is the qd_0 of the pairing)
+    const void* qdh = c.edw ? c.hist : c.qdh;
+    const void* qd0 = c.edw ? c.hist : c.qd0;
     if (c.kind == PFT_SCFT_REAL) {
-      k_quadrature_real<T><<<blocks, PW_THREADS, 0, c.stream>>>((const T*)c.hist, (const T*)c.qdh, (const T*)c.qd0,
-                                                               c.M, c.Ns, c.NsA, (double*)c.accA, (double*)c.accB);
+      k_quadrature_real<T><<<blocks, PW_THREADS, 0, c.stream>>>((const T*)c.hist, (const T*)qdh, (const T*)qd0, c.M,
+                                                               c.Ns, c.NsA, (double*)c.accA, (double*)c.accB);
     } else {
-      k_quadrature_cplx<T><<<blocks, PW_THREADS, 0, c.stream>>>((const Z*)c.hist, (const Z*)c.qdh, (const Z*)c.qd0, c.M,
+      k_quadrature_cplx<T><<<blocks, PW_THREADS, 0, c.stream>>>((const Z*)c.hist, (const Z*)qdh, (const Z*)qd0, c.M,
                                                                c.Ns, c.NsA, (double2*)c.accA, (double2*)c.accB);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -902,6 +926,20 @@ class EngineT : public Engine {
   cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p, const double* eta_m) override {
     mark(c, KK_FIELD_STEP);
     if (step_kind == PFT_STEP_SCFT_SIS || step_kind == PFT_STEP_CL_SIS) return sis_step(c, step_kind, lam, eta_p, eta_m);
+    if (c.edw) {
+      if (step_kind == PFT_STEP_SCFT_EULER) {
+        k_step_edw_scft<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (const double*)c.accA, (T*)c.BA, lam,
+                                                                 c.ds, c.bC, c.M, c.partials);
+      } else {
+        const double dV = c.L[0] * c.L[1] * c.L[2] / (double)c.M;
+        const double std = sqrt(2.0 * lam / (c.C * dV));
+        k_step_edw_cl<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double2*)c.wp, (const double2*)c.accA, (Z*)c.BA, lam, std,
+                                                               eta_p, c.seed, c.instance, (unsigned long long)c.step,
+                                                               c.step_dev, c.ds, c.bC, c.M, c.partials);
+      }
+      k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_FIELD);
+      return cudaGetLastError();
+    }
     if (step_kind == PFT_STEP_SCFT_EULER) {
       k_step_scft<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (double*)c.wm, (const double*)c.accA,
                                                            (const double*)c.accB, (T*)c.BA, (T*)c.BB, lam, c.ds, c.chiN,

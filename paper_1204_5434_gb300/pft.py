@@ -27,6 +27,7 @@ PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT, PFT_MARCH_PERSISTENT = 0, 
 PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
 PFT_SCHEME_SPLIT2, PFT_SCHEME_RQM4 = 0, 1
 PFT_STEP_SCFT_SIS, PFT_STEP_CL_SIS = 2, 3
+PFT_ARCH_DIBLOCK, PFT_ARCH_EDWARDS = 0, 1
 
 
 class pft_grid(ct.Structure):
@@ -38,7 +39,8 @@ class pft_chain(ct.Structure):
 
 
 class pft_model(ct.Structure):
-    _fields_ = [("chiN", ct.c_double), ("C", ct.c_double), ("kind", ct.c_int)]
+    _fields_ = [("chiN", ct.c_double), ("C", ct.c_double), ("kind", ct.c_int), ("arch", ct.c_int),
+                ("B", ct.c_double)]
 
 
 class pft_opts(ct.Structure):
@@ -195,10 +197,11 @@ def pft_last_error() -> str:
 
 
 def pft_create(n, L, Ns, fA, chiN, C, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True, stream=None,
-               seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0):
+               seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0,
+               arch=PFT_ARCH_DIBLOCK, B=0.0):
     g = pft_grid((ct.c_int * 3)(*[int(v) for v in n]), (ct.c_double * 3)(*[float(v) for v in L]))
     ch = pft_chain(int(Ns), float(fA))
-    m = pft_model(float(chiN), float(C), int(kind))
+    m = pft_model(float(chiN), float(C), int(kind), int(arch), float(B))
     o = pft_opts(int(precision), 1 if use_graph else 0, ct.c_void_p(stream or 0), int(seed), int(instance),
                  int(march), int(scheme), int(checkpoint))
     h = ct.c_void_p()
@@ -414,13 +417,15 @@ class System:
     """Owning wrapper of one context (pft_create / pft_destroy) with host-array helpers."""
 
     def __init__(self, n, L, Ns, fA, chiN, C=1.0, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True,
-                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0):
+                 stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0,
+                 arch=PFT_ARCH_DIBLOCK, B=0.0):
         self.n = tuple(int(v) for v in n)
         self.kind = kind
         self.M = self.n[0] * self.n[1] * self.n[2]
         self.h = None
+        self.arch = arch
         self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance, march,
-                            scheme, checkpoint)
+                            scheme, checkpoint, arch, B)
 
     @property
     def dtype(self):
@@ -443,10 +448,12 @@ class System:
     def __exit__(self, *a):
         self.close()
 
-    def set_fields(self, wp, wm):
+    def set_fields(self, wp, wm=None):
+        """wm may be None for the one-field Edwards model."""
         if isinstance(wp, np.ndarray):
             wp = np.ascontiguousarray(wp, dtype=self.dtype)
-            wm = np.ascontiguousarray(wm, dtype=self.dtype)
+            if wm is not None:
+                wm = np.ascontiguousarray(wm, dtype=self.dtype)
         pft_set_fields(self.h, wp, wm)
 
     def get_fields(self):

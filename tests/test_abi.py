@@ -87,7 +87,7 @@ _LAYOUT_PROBE = r"""
 int main(void) {
   S(pft_grid) F(pft_grid, L)
   S(pft_chain) F(pft_chain, fA)
-  S(pft_model) F(pft_model, C) F(pft_model, kind)
+  S(pft_model) F(pft_model, C) F(pft_model, kind) F(pft_model, arch) F(pft_model, B)
   S(pft_opts) F(pft_opts, use_graph) F(pft_opts, stream) F(pft_opts, seed) F(pft_opts, instance)
   F(pft_opts, march) F(pft_opts, scheme) F(pft_opts, checkpoint)
   S(pft_obs) F(pft_obs, lnQ) F(pft_obs, H) F(pft_obs, h) F(pft_obs, phiA_mean) F(pft_obs, phiB_mean)
