@@ -277,7 +277,8 @@ def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, ste
         step_kind = pft.PFT_STEP_SCFT_EULER if kind == pft.PFT_SCFT_REAL else pft.PFT_STEP_CL_EULER_MARUYAMA
     if step_size is None:
         step_size = w.lam if kind == pft.PFT_SCFT_REAL else w.dt
-    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, kind, prec, seed=w.seed, scheme=scheme)
+    arch = pft.PFT_ARCH_EDWARDS if w.arch == "edwards" else pft.PFT_ARCH_DIBLOCK
+    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, kind, prec, seed=w.seed, scheme=scheme, arch=arch, B=w.B)
     h = s.h
     wp, wm = wl.fields(w)
     pft.pft_set_fields(h, wp, wm)
@@ -298,7 +299,7 @@ def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, ste
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     s.close()
-    units = 2 * w.M * w.Ns
+    units = (1 if arch == pft.PFT_ARCH_EDWARDS else 2) * w.M * w.Ns  # propagators marched
     return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
 
 
@@ -522,6 +523,9 @@ def run(args):
                               step="solve + semi-implicit SCFT step (lambda=0.1)"),
         "sis_cl64_fp32": dict(_variant(pft, torch, wl.CL64, pft.PFT_FP32_MIXED, 10, step_kind=pft.PFT_STEP_CL_SIS),
                               step="solve + semi-implicit complex Langevin step"),
+        # Edwards homopolymer model: one reversible chain (q-dagger = q), one march per solve
+        "edwards_scft128_fp32": _variant(pft, torch, wl.EDW128, pft.PFT_FP32_MIXED, 10),
+        "edwards_cl128_fp32": _variant(pft, torch, wl.EDWCL128, pft.PFT_FP32_MIXED, 10),
     }
     torch.cuda.empty_cache()
     lib_fft = _library_fft_step(torch, wpa, wma)

@@ -45,8 +45,9 @@ def main(argv=None) -> int:
     step_kind = pft.PFT_STEP_SCFT_EULER if kind == pft.PFT_SCFT_REAL else pft.PFT_STEP_CL_EULER_MARUYAMA
     step_size = w.lam if kind == pft.PFT_SCFT_REAL else w.dt
     wp, wm = wl.fields(w)
+    arch = pft.PFT_ARCH_EDWARDS if w.arch == "edwards" else pft.PFT_ARCH_DIBLOCK
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, kind, _PREC[a.precision], use_graph=not a.no_graph,
-                    seed=w.seed, march=_MARCH[a.march], scheme=_SCHEME[a.scheme]) as s:
+                    seed=w.seed, march=_MARCH[a.march], scheme=_SCHEME[a.scheme], arch=arch, B=w.B) as s:
         s.set_fields(wp, wm)
         h = s.h
         for _ in range(a.warmup):
@@ -73,7 +74,7 @@ def main(argv=None) -> int:
         pft.pft_solve(h)
         obs = s.observables()
         n_solve, n_field = pft.pft_launch_counts(h)
-    units = 2 * w.M * w.Ns
+    units = (1 if arch == pft.PFT_ARCH_EDWARDS else 2) * w.M * w.Ns  # propagators marched
     out = {"workload": w.name, "precision": a.precision, "scheme": a.scheme, "Ns": w.Ns, "steps": a.steps,
            "ms_per_update": ms, "units_per_s": (units / (ms * 1e-3)) if ms else None,
            "kernels_per_solve": n_solve, "kernels_per_field_step": n_field,

@@ -35,6 +35,8 @@ class Workload:
     lam: float = 0.1     # SCFT relaxation step
     dt: float = 0.01     # CL time step
     steps: int = 1
+    arch: str = "diblock"  # "diblock" or "edwards" (homopolymer in implicit solvent, one field)
+    B: float = 0.0       # Edwards excluded-volume parameter
 
     @property
     def M(self) -> int:
@@ -68,6 +70,13 @@ def fields(wl: Workload):
         # homogeneous melt start: omega- at chiN (2 fA - 1)/2, omega+ at 0, plus noise
         wp = rng.normal(0.0, wl.noise, n)
         wm = wl.chiN * (2 * wl.fA - 1) / 2 + rng.normal(0.0, wl.noise, n)
+    elif wl.seed_kind == "edwards_saddle":
+        # homogeneous mean-field saddle of the Edwards model, W = i omega = C/B, plus noise;
+        # the second field is unused (zeros)
+        wp = wl.C / wl.B + rng.normal(0.0, wl.noise, n)
+        wm = np.zeros(n)
+        if wl.kind == CL:
+            return (-1j * wp).astype(np.complex128), wm.astype(np.complex128)
     elif wl.seed_kind == "random":
         wp = rng.normal(0.0, wl.noise, n)
         wm = rng.normal(0.0, wl.amp, n)
@@ -90,7 +99,13 @@ CL256 = Workload("complex Langevin 256^3, L=16, Ns=200, fA=0.5, chiN=14, C=100",
                  200, 0.5, 14.0, 100.0, CL, 5, "homogeneous", 0.0, 0.05, dt=0.005, steps=200)
 CL128 = CL64.with_(name="complex Langevin 128^3, L=8, Ns=100, fA=0.3, chiN=20, C=50", n=(128, 128, 128))
 
-ALL = {"lam32": LAM32, "cl64": CL64, "gyr64": GYR64, "gyr128": GYR128, "cl128": CL128, "cl256": CL256}
+# Edwards homopolymer solution (Eq. 2): SCFT and complex Langevin around the homogeneous saddle
+EDW128 = Workload("Edwards homopolymer SCFT 128^3, L=8, Ns=100, B=1, C=20", (128, 128, 128), (8.0, 8.0, 8.0),
+                  100, 1.0, 1.0, 20.0, SCFT, 6, "edwards_saddle", 0.0, 0.1, lam=0.1, arch="edwards", B=1.0)
+EDWCL128 = EDW128.with_(name="Edwards homopolymer CL 128^3, L=8, Ns=100, B=1, C=20", kind=CL, dt=0.01)
+
+ALL = {"lam32": LAM32, "cl64": CL64, "gyr64": GYR64, "gyr128": GYR128, "cl128": CL128, "cl256": CL256,
+       "edw128": EDW128, "edwcl128": EDWCL128}
 
 
 def batch_instances(count: int = 256, seed: int = 3):
