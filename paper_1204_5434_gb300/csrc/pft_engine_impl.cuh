@@ -176,11 +176,12 @@ __global__ void __launch_bounds__(PW_THREADS) k_prepare_real(const double* __res
                                                              T* __restrict__ BA, T* __restrict__ BB, double ds, double chiN,
                                                              long long M, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double p = wp[i], m = wm[i];
     BA[i] = boltz<T>(p - m, ds);
     BB[i] = boltz<T>(p + m, ds);
-    acc[0] += m * m / chiN - p;
+    acc[0] += m * m * ichiN - p;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
@@ -191,6 +192,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_prepare_cplx(const double2* __re
                                                              cpx<T>* __restrict__ BA, cpx<T>* __restrict__ BB, double ds,
                                                              double chiN, long long M, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double2 p = wp[i], m = wm[i];
     const double2 ip = make_double2(-p.y, p.x);
@@ -198,8 +200,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_prepare_cplx(const double2* __re
     const double2 wB = make_double2(ip.x + m.x, ip.y + m.y);
     BA[i] = boltz_c<T>(wA, ds);
     BB[i] = boltz_c<T>(wB, ds);
-    acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
-    acc[1] += 2.0 * m.x * m.y / chiN - p.x;
+    acc[0] += (m.x * m.x - m.y * m.y) * ichiN + p.y;
+    acc[1] += 2.0 * m.x * m.y * ichiN - p.x;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
@@ -425,11 +427,12 @@ static __global__ void __launch_bounds__(PW_THREADS) k_finalize_real(double* __r
                                                               double* __restrict__ partials) {
   const double f = ds / s[S_Q];
   double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double a = accA[i] * f, b = accB[i] * f;
     accA[i] = a;
     accB[i] = b;
-    const double fp = a + b - 1.0, fm = 2.0 * wm[i] / chiN + b - a;
+    const double fp = a + b - 1.0, fm = 2.0 * wm[i] * ichiN + b - a;
     acc[0] += a;
     acc[2] += b;
     acc[4] += fp * fp;
@@ -444,13 +447,14 @@ static __global__ void __launch_bounds__(PW_THREADS) k_finalize_cplx(double2* __
                                                               double* __restrict__ partials) {
   const double2 f = cdiv_d(make_double2(ds, 0.0), make_double2(s[S_Q], s[S_Q + 1]));
   double acc[6] = {0, 0, 0, 0, 0, 0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double2 a = cmul_d(accA[i], f), b = cmul_d(accB[i], f);
     accA[i] = a;
     accB[i] = b;
     const double2 fp = make_double2(a.x + b.x - 1.0, a.y + b.y);  // |i fp| = |fp|
     const double2 m = wm[i];
-    const double2 fm = make_double2(2.0 * m.x / chiN + b.x - a.x, 2.0 * m.y / chiN + b.y - a.y);
+    const double2 fm = make_double2(2.0 * m.x * ichiN + b.x - a.x, 2.0 * m.y * ichiN + b.y - a.y);
     acc[0] += a.x;
     acc[1] += a.y;
     acc[2] += b.x;
@@ -469,17 +473,18 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_scft(double* __restrict__ w
                                                           T* __restrict__ BA, T* __restrict__ BB, double lam, double ds,
                                                           double chiN, long long M, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double a = phiA[i], b = phiB[i];
     double p = wp[i], m = wm[i];
-    const double fp = a + b - 1.0, fm = 2.0 * m / chiN + b - a;
+    const double fp = a + b - 1.0, fm = 2.0 * m * ichiN + b - a;
     p += lam * fp;
     m -= lam * fm;
     wp[i] = p;
     wm[i] = m;
     BA[i] = boltz<T>(p - m, ds);
     BB[i] = boltz<T>(p + m, ds);
-    acc[0] += m * m / chiN - p;
+    acc[0] += m * m * ichiN - p;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
@@ -496,6 +501,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
                                                         unsigned long long instance, unsigned long long step_arg,
                                                         const unsigned long long* __restrict__ step_dev, double ds,
                                                         double chiN, long long M, double* __restrict__ partials) {
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   double acc[2] = {0.0, 0.0};
   const unsigned long long step = step_dev ? *step_dev : step_arg;
   const long long nblk = (M + 3) / 4;
@@ -527,7 +533,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
       // dH/dw+ per C = i (phiA + phiB - 1)
       const double2 s = make_double2(a.x + b.x - 1.0, a.y + b.y);
       const double2 fp = make_double2(-s.y, s.x);
-      const double2 fm = make_double2(2.0 * m.x / chiN + b.x - a.x, 2.0 * m.y / chiN + b.y - a.y);
+      const double2 fm = make_double2(2.0 * m.x * ichiN + b.x - a.x, 2.0 * m.y * ichiN + b.y - a.y);
       p.x += -dt * fp.x + zp[j];
       p.y += -dt * fp.y;
       m.x += -dt * fm.x + zm[j];
@@ -539,8 +545,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
       const double2 wB = make_double2(ip.x + m.x, ip.y + m.y);
       BA[i] = boltz_c<T>(wA, ds);
       BB[i] = boltz_c<T>(wB, ds);
-      acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
-      acc[1] += 2.0 * m.x * m.y / chiN - p.x;
+      acc[0] += (m.x * m.x - m.y * m.y) * ichiN + p.y;
+      acc[1] += 2.0 * m.x * m.y * ichiN - p.x;
     }
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
@@ -785,12 +791,13 @@ __global__ void __launch_bounds__(PW_THREADS) k_sis_apply_real(double* __restric
                                                                T* __restrict__ BB, double invM, double ds, double chiN,
                                                                long long M, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double p = wp[i] + G[i].x * invM, m = wm[i];
     wp[i] = p;
     BA[i] = boltz<T>(p - m, ds);
     BB[i] = boltz<T>(p + m, ds);
-    acc[0] += m * m / chiN - p;
+    acc[0] += m * m * ichiN - p;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
@@ -801,6 +808,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_sis_apply_cplx(double2* __restri
                                                                cpx<T>* __restrict__ BB, double invM, double ds,
                                                                double chiN, long long M, double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     double2 p = wp[i];
     const double2 g = G[i], m = wm[i];
@@ -810,8 +818,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_sis_apply_cplx(double2* __restri
     const double2 ip = make_double2(-p.y, p.x);
     BA[i] = boltz_c<T>(make_double2(ip.x - m.x, ip.y - m.y), ds);
     BB[i] = boltz_c<T>(make_double2(ip.x + m.x, ip.y + m.y), ds);
-    acc[0] += (m.x * m.x - m.y * m.y) / chiN + p.y;
-    acc[1] += 2.0 * m.x * m.y / chiN - p.x;
+    acc[0] += (m.x * m.x - m.y * m.y) * ichiN + p.y;
+    acc[1] += 2.0 * m.x * m.y * ichiN - p.x;
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
@@ -830,10 +838,11 @@ static __global__ void __launch_bounds__(PW_THREADS) k_grad_fields(const double*
                                                                    const double* __restrict__ wm, double* __restrict__ gp,
                                                                    double* __restrict__ gm, double cdv, double chiN,
                                                                    long long M) {
+  const double ichiN = 1.0 / chiN;  // one division per thread, not per point
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double a = phiA[i], b = phiB[i];
     if (gp) gp[i] = cdv * (a + b - 1.0);
-    if (gm) gm[i] = cdv * (2.0 * wm[i] / chiN + b - a);
+    if (gm) gm[i] = cdv * (2.0 * wm[i] * ichiN + b - a);
   }
 }
 
