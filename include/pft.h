@@ -117,6 +117,13 @@ typedef struct {
                                conjugate march recomputes each segment of K-1 slices from its
                                checkpoint (one extra forward march).  K >= 2 needs the pass
                                march and the SPLIT2 scheme (else PFT_ERR_UNSUPPORTED). */
+  int autotune;             /* 1: at the first solve, time the plans of the pass march (plane
+                               kernel or pencil passes; two propagator chains on two streams or
+                               two-member launches) on the context's own data and keep the
+                               fastest; cached per (grid, field kind, precision, Ns) in memory and,
+                               if the environment variable PFT_AUTOTUNE_CACHE names a file, in
+                               that file (read at the first lookup, appended after tuning).
+                               0: the fixed plan (plane kernel where it applies, two chains). */
 } pft_opts;
 
 /* Observables of the last solve.  Complex quantities are {re, im}; in SCFT mode the
@@ -343,6 +350,11 @@ pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles);
 
 /* Which march the context uses: 1 = passes, 2 = resident, 3 = persistent. */
 pft_status pft_get_march(const pft_ctx* ctx, int* march);
+
+/* Plan of the pass march in use: *plane = 1 if the y/z plane kernel runs the steps (FP32
+ * real 64^3/128^3 grids), *streams = 1 if the two propagators run as two chains on two
+ * streams.  Either pointer may be NULL.  Errors: PFT_ERR_ARG for a NULL ctx. */
+pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams);
 
 /* History interval in use: 1 = every slice of q is kept, K >= 2 = every K-th slice (see
  * pft_opts.checkpoint).  Errors: PFT_ERR_ARG for NULL arguments. */

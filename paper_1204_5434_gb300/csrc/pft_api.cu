@@ -3,6 +3,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
 #include <string>
 
 #include "pft_engine.h"
@@ -26,6 +28,47 @@ bool batch_axis_supported(int n) {
     default:
       return false;
   }
+}
+
+namespace {
+std::mutex g_plan_mu;
+std::map<std::string, std::pair<int, int>> g_plans;
+bool g_plans_loaded = false;
+
+void load_plan_file() {
+  g_plans_loaded = true;
+  const char* path = getenv("PFT_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[256];
+  int plane = 0, streams = 0;
+  double ms = 0.0;
+  while (fscanf(f, "%255s %d %d %lf", key, &plane, &streams, &ms) == 4) g_plans[key] = {plane, streams};
+  fclose(f);
+}
+}  // namespace
+
+bool plan_cache_lookup(const std::string& key, int* plane, int* streams) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (!g_plans_loaded) load_plan_file();
+  auto it = g_plans.find(key);
+  if (it == g_plans.end()) return false;
+  *plane = it->second.first;
+  *streams = it->second.second;
+  return true;
+}
+
+void plan_cache_store(const std::string& key, int plane, int streams, double ms) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (!g_plans_loaded) load_plan_file();
+  g_plans[key] = {plane, streams};
+  const char* path = getenv("PFT_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %.6f\n", key.c_str(), plane, streams, ms);
+  fclose(f);
 }
 
 bool axis_supported(int n) {
@@ -229,6 +272,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
                   "persistent march needs FP32-mixed precision, real SCFT fields and a 64^3, 128^3 or 256^3 grid");
     }
     d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
+  d.autotune = opts->autotune != 0;
     if (opts->march == PFT_MARCH_RESIDENT) {
       d.march = 2;
     } else if (opts->march == PFT_MARCH_PERSISTENT) {
@@ -668,6 +712,13 @@ pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* fi
   if (solve) *solve = (d.use_graph && d.march == 1 && d.graph_valid) ? d.graph_kernels : -1;
   // the update kernel and its final reduction, plus the quarter-step factors of RQM4
   if (field_step) *field_step = 2 + (d.scheme == 1 ? 1 : 0);
+  return PFT_OK;
+}
+
+pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  if (plane) *plane = ctx->d.plan_plane;
+  if (streams) *streams = ctx->d.plan_streams;
   return PFT_OK;
 }
 

@@ -94,6 +94,13 @@ struct CtxData {
   void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
   // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
   // scratch slices for the full and the two half steps, quadrature weight tables
+  // plan of the concurrent pass march: plane kernel (1) or pencil passes (0) where the
+  // plane kernel applies, two propagator chains on two streams (1) or two-member launches
+  // on one stream (0); chosen by timing at the first solve when `autotune` is set
+  int plan_plane = 1;
+  int plan_streams = 1;
+  bool autotune = false;
+  bool tuned = false;
   bool edw = false;   // Edwards homopolymer model: one field, q-dagger = q
   double bC = 0.0;    // its B / C
   int scheme = 0;
@@ -190,6 +197,11 @@ cudaError_t launch_philox_raw(const unsigned int ctr[4], const unsigned int key[
 bool axis_supported(int n);
 bool batch_axis_supported(int n);
 void set_error(const std::string& s);
+
+// Plan cache of the autotuner: in memory, and in the text file named by the environment
+// variable PFT_AUTOTUNE_CACHE (one line per entry: key plane streams ms) when it is set.
+bool plan_cache_lookup(const std::string& key, int* plane, int* streams);
+void plan_cache_store(const std::string& key, int plane, int streams, double ms);
 
 }  // namespace pft
 

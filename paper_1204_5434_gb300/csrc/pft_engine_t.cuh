@@ -3,6 +3,7 @@
 #pragma once
 #include <math.h>
 
+#include <stdio.h>
 #include <string.h>
 
 #include <vector>
@@ -641,7 +642,7 @@ class EngineT : public Engine {
       if ((e = march_chain(c, g, st, c.stream)) != cudaSuccess) return e;
       return finish_concurrent(c);
     }
-    if (!c.profiling) {
+    if (!c.profiling && c.plan_streams) {
       // one chain per propagator on two streams: the two marches are independent until
       // the quadrature, and their kernels fill each other's idle SMs
       if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
@@ -654,7 +655,7 @@ class EngineT : public Engine {
       if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
       return finish_concurrent(c);
     }
-    if (plane_supported(c)) {
+    if (plane_supported(c) && c.plan_plane) {
       // plane kernel (z and y of step 1), then per step: x pass, plane kernel
       // (y^-1, z^-1 of step s fused with z of step s+1, y)
       mark(c, KK_PAIR_STEP);
@@ -687,7 +688,7 @@ class EngineT : public Engine {
   // (entries of consecutive steps are two apart).
   cudaError_t march_chain(CtxData& c, const BatchGeom& g, const BatchStep* st, cudaStream_t sm) {
     cudaError_t e;
-    if (plane_supported(c)) {
+    if (plane_supported(c) && c.plan_plane) {
       if ((e = batch_plane(c, st, 0, 1, sm)) != cudaSuccess) return e;
       const int nx = c.n[0], ny = c.n[1];
       const long long nzc = c.nzh;
@@ -705,6 +706,53 @@ class EngineT : public Engine {
       if ((e = batch_mid(g, ss, 1, sm)) != cudaSuccess) return e;
       if ((e = batch_zz(g, ss, 1, sm)) != cudaSuccess) return e;
     }
+    return cudaSuccess;
+  }
+
+  // Autotuner of the pass march: one timed eager solve (after a warm-up solve) for each
+  // plan -- plane kernel or pencil passes where the plane kernel applies, two chains on
+  // two streams or two-member launches -- on the context's own fields; the fastest is
+  // kept and cached per (grid, field kind, precision, Ns).
+  cudaError_t tune_plan(CtxData& c) {
+    c.tuned = true;
+    char key[160];
+    snprintf(key, sizeof(key), "%dx%dx%d/%s/%s/Ns%d", c.n[0], c.n[1], c.n[2],
+             c.kind == PFT_SCFT_REAL ? "real" : "complex", sizeof(T) == 4 ? "fp32" : "fp64", c.Ns);
+    int pl = 0, sm = 0;
+    if (plan_cache_lookup(key, &pl, &sm)) {
+      c.plan_plane = (pl && plane_supported(c)) ? 1 : 0;
+      c.plan_streams = sm ? 1 : 0;
+      return cudaSuccess;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    float best = -1.f;
+    int bpl = c.plan_plane, bsm = c.plan_streams;
+    for (int cand = 0; cand < 4 && e == cudaSuccess; cand++) {
+      const int cpl = (cand >> 1) & 1 ? 0 : 1, csm = (cand & 1) ? 0 : 1;
+      if (cpl && !plane_supported(c)) continue;
+      c.plan_plane = cpl;
+      c.plan_streams = csm;
+      if ((e = record_solve(c)) != cudaSuccess) break;  // warm-up
+      if ((e = cudaEventRecord(e0, c.stream)) != cudaSuccess) break;
+      if ((e = record_solve(c)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e1, c.stream)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) break;
+      if (best < 0.f || ms < best) {
+        best = ms;
+        bpl = cpl;
+        bsm = csm;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    c.plan_plane = bpl;
+    c.plan_streams = bsm;
+    if (e != cudaSuccess) return e;
+    plan_cache_store(key, bpl, bsm, (double)best);
     return cudaSuccess;
   }
 
@@ -878,12 +926,16 @@ class EngineT : public Engine {
   }
 
   cudaError_t enqueue_solve(CtxData& c) override {
+    if (!plane_supported(c)) c.plan_plane = 0;
     if (c.scheme == 1) {
       cudaError_t e = prepare_rqm4(c);
       if (e != cudaSuccess) return e;
     } else if (c.march == 1 && c.concurrent && c.ckK == 1) {
       cudaError_t e = prepare_concurrent(c);
       if (e != cudaSuccess) return e;
+      if (c.autotune && !c.tuned && !c.edw && !c.profiling) {
+        if ((e = tune_plan(c)) != cudaSuccess) return e;
+      }
     }
     // the resident march is a handful of launches per solve: it runs without a graph
     if (!c.use_graph || c.profiling || c.march >= 2) return record_solve(c);

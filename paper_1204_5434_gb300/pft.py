@@ -46,7 +46,7 @@ class pft_model(ct.Structure):
 class pft_opts(ct.Structure):
     _fields_ = [("precision", ct.c_int), ("use_graph", ct.c_int), ("stream", ct.c_void_p),
                 ("seed", ct.c_ulonglong), ("instance", ct.c_ulonglong), ("march", ct.c_int), ("scheme", ct.c_int),
-                ("checkpoint", ct.c_int)]
+                ("checkpoint", ct.c_int), ("autotune", ct.c_int)]
 
 
 class pft_obs(ct.Structure):
@@ -133,6 +133,7 @@ _SIGS = {
     "pft_get_march": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_launch_counts": (ct.c_int, [_P, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     "pft_get_checkpoint": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
+    "pft_get_plan": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pft_philox_normals": (ct.c_int, [ct.c_ulonglong, ct.c_ulonglong, ct.c_ulonglong, ct.c_int, ct.c_longlong,
                                       _P, _P]),
     "pft_philox_raw": (ct.c_int, [ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint), ct.c_longlong, _P, _P]),
@@ -198,12 +199,12 @@ def pft_last_error() -> str:
 
 def pft_create(n, L, Ns, fA, chiN, C, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True, stream=None,
                seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0,
-               arch=PFT_ARCH_DIBLOCK, B=0.0):
+               arch=PFT_ARCH_DIBLOCK, B=0.0, autotune=0):
     g = pft_grid((ct.c_int * 3)(*[int(v) for v in n]), (ct.c_double * 3)(*[float(v) for v in L]))
     ch = pft_chain(int(Ns), float(fA))
     m = pft_model(float(chiN), float(C), int(kind), int(arch), float(B))
     o = pft_opts(int(precision), 1 if use_graph else 0, ct.c_void_p(stream or 0), int(seed), int(instance),
-                 int(march), int(scheme), int(checkpoint))
+                 int(march), int(scheme), int(checkpoint), int(autotune))
     h = ct.c_void_p()
     _check(_lib().pft_create(ct.byref(h), ct.byref(g), ct.byref(ch), ct.byref(m), ct.byref(o)), "pft_create")
     return h
@@ -380,6 +381,14 @@ def pft_get_march(h) -> int:
     return m.value
 
 
+def pft_get_plan(h):
+    """(plane kernel in use, two chains on two streams) of the pass march."""
+    a = ct.c_int()
+    b = ct.c_int()
+    _check(_lib().pft_get_plan(h, ct.byref(a), ct.byref(b)), "pft_get_plan")
+    return a.value, b.value
+
+
 def pft_get_checkpoint(h) -> int:
     """History interval in use: 1 = every slice, K >= 2 = every K-th slice."""
     k = ct.c_int()
@@ -418,14 +427,14 @@ class System:
 
     def __init__(self, n, L, Ns, fA, chiN, C=1.0, kind=PFT_SCFT_REAL, precision=PFT_FP64, use_graph=True,
                  stream=None, seed=0, instance=0, march=PFT_MARCH_AUTO, scheme=PFT_SCHEME_SPLIT2, checkpoint=0,
-                 arch=PFT_ARCH_DIBLOCK, B=0.0):
+                 arch=PFT_ARCH_DIBLOCK, B=0.0, autotune=0):
         self.n = tuple(int(v) for v in n)
         self.kind = kind
         self.M = self.n[0] * self.n[1] * self.n[2]
         self.h = None
         self.arch = arch
         self.h = pft_create(n, L, Ns, fA, chiN, C, kind, precision, use_graph, stream, seed, instance, march,
-                            scheme, checkpoint, arch, B)
+                            scheme, checkpoint, arch, B, autotune)
 
     @property
     def dtype(self):

@@ -90,6 +90,7 @@ int main(void) {
   S(pft_model) F(pft_model, C) F(pft_model, kind) F(pft_model, arch) F(pft_model, B)
   S(pft_opts) F(pft_opts, use_graph) F(pft_opts, stream) F(pft_opts, seed) F(pft_opts, instance)
   F(pft_opts, march) F(pft_opts, scheme) F(pft_opts, checkpoint)
+  F(pft_opts, autotune)
   S(pft_obs) F(pft_obs, lnQ) F(pft_obs, H) F(pft_obs, h) F(pft_obs, phiA_mean) F(pft_obs, phiB_mean)
   F(pft_obs, force_p_rms) F(pft_obs, force_m_rms) F(pft_obs, fA_eff) F(pft_obs, NsA) F(pft_obs, step)
   S(pft_instance_desc) F(pft_instance_desc, chain) F(pft_instance_desc, model) F(pft_instance_desc, seed)
