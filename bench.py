@@ -374,12 +374,16 @@ def _batch(pft, prec, updates=2):
     inst = [dict(n=d.n, L=d.L, Ns=d.Ns, fA=d.fA, chiN=d.chiN, C=d.C,
                  kind=pft.PFT_SCFT_REAL if d.kind == wl.SCFT else pft.PFT_CL_COMPLEX, seed=d.seed) for d in descs]
     out = {}
-    for mode_name, mode in (("graphed", pft.PFT_BATCH_GRAPHED), ("per_instance", pft.PFT_BATCH_PER_INSTANCE)):
+    for mode_name, mode in (("graphed", pft.PFT_BATCH_GRAPHED), ("per_instance", pft.PFT_BATCH_PER_INSTANCE),
+                            ("graphed_autotuned", pft.PFT_BATCH_GRAPHED)):
         b = pft.pft_batch_create(inst, prec)
         try:
             for i, d in enumerate(descs):
                 wp, wm = wl.sinusoid_fields(d)
                 pft.pft_batch_set_fields(b, i, wp, wm)
+            if mode_name == "graphed_autotuned":
+                pft.pft_batch_autotune(b)
+                out["plans"] = [pft.pft_batch_class_info(b, k) for k in range(pft.pft_batch_info(b)["classes"])]
             pft.pft_batch_run(b, 1, 0.1, 0.01, mode)
             pft.pft_batch_synchronize(b)
             t0 = time.perf_counter()
@@ -391,7 +395,7 @@ def _batch(pft, prec, updates=2):
             out["units_per_update"] = info["units_per_update"]
             out["classes"] = info["classes"]
             if mode == pft.PFT_BATCH_GRAPHED:
-                out["launches_per_update"] = info["launches"]
+                out[mode_name]["launches_per_update"] = info["launches"]
         finally:
             pft.pft_batch_destroy(b)
     out["unit"] = UNIT

@@ -275,6 +275,25 @@ pft_status pft_batch_get_fields(pft_batch* b, int i, void* wp, void* wm, pft_mem
  * Asynchronous on the batch stream.  Error: PFT_ERR_STATE if a member has no fields. */
 pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_batch_mode mode);
 
+/* Per-class plan autotuner of a batch (uses the instances' current fields): for every class
+ * of equal field kind and grid, time the class's two marches and densities under plan 0
+ * (one march after the other, the quadrature fused into the conjugate march) and plan 1
+ * (both marches in the same launches, fused z passes of consecutive steps, the quadrature
+ * after the marches over both histories; one extra q-dagger history per instance) and keep
+ * the faster; the next graphed run captures the chosen plans.  Plan 1 is the default.
+ * Errors: PFT_ERR_STATE if an instance has no fields; PFT_ERR_OOM. */
+pft_status pft_batch_autotune(pft_batch* batch);
+
+/* Set the plan (0 or 1, as for pft_batch_autotune) of class `cls`, or of every class for
+ * cls = -1.  Errors: PFT_ERR_ARG for a bad index or plan. */
+pft_status pft_batch_set_plan(pft_batch* batch, int cls, int plan);
+
+/* Class `cls` (0 .. classes-1 of pft_batch_info): grid n[3], field kind, member count, plan
+ * in use and the autotuner's timings of plans 0 and 1 in ms (-1 if not tuned).  Any output
+ * pointer may be NULL.  Errors: PFT_ERR_ARG for a bad index. */
+pft_status pft_batch_class_info(const pft_batch* batch, int cls, int n[3], int* kind, int* members, int* plan,
+                                float tuned_ms[2]);
+
 /* Observables and densities of member i's last solve (synchronises). */
 pft_status pft_batch_get_observables(pft_batch* b, int i, pft_obs* obs);
 pft_status pft_batch_get_densities(pft_batch* b, int i, void* phiA, void* phiB, pft_mem where);

@@ -27,6 +27,12 @@ struct BatchClass {
   std::vector<int> active;    // active[s-1]: members with Ns >= s
   pft::BatchStep* d_fwd = nullptr;  // [maxNs][K]
   pft::BatchStep* d_bwd = nullptr;
+  // plan 0: one march after the other, the quadrature fused into the conjugate march;
+  // plan 1: both marches in the same launches (entries 2k / 2k+1 of a step), the z passes
+  // of consecutive steps fused, the quadrature after the marches over both histories
+  int plan = 1;
+  pft::BatchStep* d_conc = nullptr;  // [maxNs][2K]
+  float tuned_ms[2] = {-1.f, -1.f};   // autotuner timings of the two plans
 };
 
 __global__ void k_batch_increment(unsigned long long* __restrict__ c, int n) {
@@ -67,6 +73,7 @@ void batch_free(pft_batch* b) {
   for (auto& c : b->classes) {
     if (c.d_fwd) cudaFree(c.d_fwd);
     if (c.d_bwd) cudaFree(c.d_bwd);
+    if (c.d_conc) cudaFree(c.d_conc);
   }
   if (b->d_steps) cudaFree(b->d_steps);
   for (pft_ctx* c : b->inst)
@@ -107,28 +114,102 @@ void fill_steps(const pft_ctx* c, int s, bool bwd, pft::BatchStep* st) {
   for (int a = 0; a < 3; a++) st->d[a] = t + d.d_off[a];
 }
 
-// One field update of every instance, on b->stream.
-pft_status record_update(pft_batch* b, double lam, double dt) {
-  int maxNs = 0;
-  for (auto& c : b->classes) maxNs = std::max(maxNs, c.maxNs);
-  long long launches = 0;
-  for (int march = 0; march < 2; march++) {
-    for (int s = 1; s <= maxNs; s++) {
-      for (auto& c : b->classes) {
-        if (s > c.maxNs) continue;
-        const int K = (int)c.members.size();
-        const pft::BatchStep* st = (march ? c.d_bwd : c.d_fwd) + (size_t)(s - 1) * K;
-        pft::Engine* eng = b->inst[c.members[0]]->eng;
-        cudaError_t e = eng->batch_contour_step(c.g, st, c.active[s - 1], march, b->stream);
-        if (e != cudaSuccess) return bcuda(e, "batched contour step");
-        launches += 5;
-      }
+// Entries of step s of both marches of one instance (plan 1): forward into the q history,
+// conjugate into the qd history, each with the factor of its next step for the fused z
+// passes (none at the instance's last step).
+void fill_pair(const pft_ctx* c, int s, pft::BatchStep* f, pft::BatchStep* b) {
+  const pft::CtxData& d = c->d;
+  const size_t we = (d.prec == PFT_FP64 ? 8 : 4) * (d.kind == PFT_SCFT_REAL ? 1 : 2);
+  const size_t slice = (size_t)d.M * we;
+  const char* hist = (const char*)d.hist;
+  char* qdh = (char*)d.qdh;
+  memset(f, 0, sizeof(*f));
+  memset(b, 0, sizeof(*b));
+  const int nb = d.Ns + 1 - s;
+  f->in = hist + (size_t)(s - 1) * slice;
+  f->B = (s <= d.NsA) ? d.BA : d.BB;
+  f->out = (void*)(hist + (size_t)s * slice);
+  f->spec = d.spec;
+  b->in = (s == 1) ? d.qd0 : (const void*)(qdh + (size_t)(s - 1) * slice);
+  b->B = (nb <= d.NsA) ? d.BA : d.BB;
+  b->out = qdh + (size_t)s * slice;
+  b->spec = d.spec2;
+  if (s < d.Ns) {
+    f->Bnext = (s + 1 <= d.NsA) ? d.BA : d.BB;
+    b->Bnext = (nb - 1 <= d.NsA) ? d.BA : d.BB;
+  }
+  const char* t = (const char*)d.tables;
+  for (int a = 0; a < 4; a++) f->tw[a] = b->tw[a] = t + d.tw_off[a];
+  for (int a = 0; a < 3; a++) f->d[a] = b->d[a] = t + d.d_off[a];
+}
+
+// qd histories and the pair-step table of a class (plan 1), once.
+pft_status prepare_pairs(pft_batch* b, BatchClass& c) {
+  if (c.d_conc) return PFT_OK;
+  for (int i : c.members) {
+    pft::CtxData& d = b->inst[i]->d;
+    if (d.qdh) continue;
+    const size_t we = (d.prec == PFT_FP64 ? 8 : 4) * (d.kind == PFT_SCFT_REAL ? 1 : 2);
+    const size_t bytes = (size_t)(d.Ns + 1) * d.M * we;
+    cudaError_t e = cudaMalloc(&d.qdh, bytes);
+    if (e != cudaSuccess) return bcuda(e, "batch qd history");
+    d.bytes += bytes;
+  }
+  const int K = (int)c.members.size();
+  std::vector<pft::BatchStep> h((size_t)c.maxNs * 2 * K);
+  for (int s = 1; s <= c.maxNs; s++)
+    for (int k = 0; k < c.active[s - 1]; k++)
+      fill_pair(b->inst[c.members[k]], s, &h[((size_t)(s - 1) * K + k) * 2], &h[((size_t)(s - 1) * K + k) * 2 + 1]);
+  const size_t bytes = h.size() * sizeof(pft::BatchStep);
+  cudaError_t e = cudaMalloc(&c.d_conc, bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(c.d_conc, h.data(), bytes, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? PFT_OK : bcuda(e, "batch pair-step table");
+}
+
+// Both marches and the densities of one class under its plan, on b->stream.
+pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches) {
+  const int K = (int)c.members.size();
+  pft::Engine* eng = b->inst[c.members[0]]->eng;
+  if (c.plan == 1) {
+    for (int s = 1; s <= c.maxNs; s++) {
+      const pft::BatchStep* st = c.d_conc + (size_t)(s - 1) * 2 * K;
+      cudaError_t e = eng->batch_pair_step(c.g, st, 2 * c.active[s - 1], s == 1, b->stream);
+      if (e != cudaSuccess) return bcuda(e, "batched pair step");
+      *launches += (s == 1) ? 5 : 4;
     }
-    for (pft_ctx* x : b->inst) {
+    for (int i : c.members) {
+      pft_ctx* x = b->inst[i];
+      cudaError_t e = x->eng->solve_mid(x->d);
+      if (e == cudaSuccess) e = x->eng->quadrature(x->d);
+      if (e == cudaSuccess) e = x->eng->solve_tail(x->d);
+      if (e != cudaSuccess) return bcuda(e, "batched quadrature");
+      *launches += 6;
+    }
+    return PFT_OK;
+  }
+  for (int march = 0; march < 2; march++) {
+    for (int s = 1; s <= c.maxNs; s++) {
+      const pft::BatchStep* st = (march ? c.d_bwd : c.d_fwd) + (size_t)(s - 1) * K;
+      cudaError_t e = eng->batch_contour_step(c.g, st, c.active[s - 1], march, b->stream);
+      if (e != cudaSuccess) return bcuda(e, "batched contour step");
+      *launches += 5;
+    }
+    for (int i : c.members) {
+      pft_ctx* x = b->inst[i];
       cudaError_t e = march ? x->eng->solve_tail(x->d) : x->eng->solve_mid(x->d);
       if (e != cudaSuccess) return bcuda(e, "batched reductions");
-      launches += march ? 2 : 3;
+      *launches += march ? 2 : 3;
     }
+  }
+  return PFT_OK;
+}
+
+// One field update of every instance, on b->stream.
+pft_status record_update(pft_batch* b, double lam, double dt) {
+  long long launches = 0;
+  for (auto& c : b->classes) {  // plan-1 tables are prepared before any capture
+    pft_status s = record_class_solve(b, c, &launches);
+    if (s != PFT_OK) return s;
   }
   for (pft_ctx* x : b->inst) {
     const bool scft = (x->d.kind == PFT_SCFT_REAL);
@@ -286,6 +367,11 @@ pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_b
     return bfail(PFT_ERR_ARG, "lam and dt must be positive");
   for (pft_ctx* x : b->inst)
     if (!x->d.fields_set) return bfail(PFT_ERR_STATE, "every batch instance needs pft_batch_set_fields first");
+  for (auto& c : b->classes) {  // allocations and table uploads happen outside any capture
+    if (c.plan != 1) continue;
+    pft_status s = prepare_pairs(b, c);
+    if (s != PFT_OK) return s;
+  }
   if (mode == PFT_BATCH_GRAPHED) {
     if (!b->graph || lam != b->g_lam || dt != b->g_dt) {
       if (b->graph) {
@@ -334,6 +420,79 @@ pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_b
     x->d.step += updates;
     x->d.solved = false;
     if (updates > 0) x->have_obs = true;
+  }
+  return PFT_OK;
+}
+
+pft_status pft_batch_autotune(pft_batch* b) {
+  if (!b) return bfail(PFT_ERR_ARG, "NULL batch");
+  for (pft_ctx* x : b->inst)
+    if (!x->d.fields_set) return bfail(PFT_ERR_STATE, "every batch instance needs pft_batch_set_fields first");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) return bcuda(e, "autotune events");
+  pft_status st = PFT_OK;
+  for (auto& c : b->classes) {
+    float best = -1.f;
+    int bplan = c.plan;
+    for (int plan = 0; plan < 2 && st == PFT_OK; plan++) {
+      c.plan = plan;
+      if (plan == 1 && (st = prepare_pairs(b, c)) != PFT_OK) break;
+      long long n = 0;
+      if ((st = record_class_solve(b, c, &n)) != PFT_OK) break;  // warm-up
+      cudaEventRecord(e0, b->stream);
+      if ((st = record_class_solve(b, c, &n)) != PFT_OK) break;
+      cudaEventRecord(e1, b->stream);
+      e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = bcuda(e, "autotune timing");
+        break;
+      }
+      c.tuned_ms[plan] = ms;
+      if (best < 0.f || ms < best) {
+        best = ms;
+        bplan = plan;
+      }
+    }
+    c.plan = bplan;
+    if (st != PFT_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (b->graph) {  // the next graphed run captures the chosen plans
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return st;
+}
+
+pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
+  if (!b || cls < -1 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
+  if (plan != 0 && plan != 1) return bfail(PFT_ERR_ARG, "plan must be 0 or 1");
+  for (int k = 0; k < (int)b->classes.size(); k++)
+    if (cls < 0 || k == cls) b->classes[k].plan = plan;
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return PFT_OK;
+}
+
+pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind, int* members, int* plan,
+                                float tuned_ms[2]) {
+  if (!b || cls < 0 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
+  const BatchClass& c = b->classes[cls];
+  if (n)
+    for (int a = 0; a < 3; a++) n[a] = c.g.n[a];
+  if (kind) *kind = (int)c.kind;
+  if (members) *members = (int)c.members.size();
+  if (plan) *plan = c.plan;
+  if (tuned_ms) {
+    tuned_ms[0] = c.tuned_ms[0];
+    tuned_ms[1] = c.tuned_ms[1];
   }
   return PFT_OK;
 }

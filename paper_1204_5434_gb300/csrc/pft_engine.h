@@ -177,6 +177,12 @@ class Engine {
   // One contour step of every active instance of a batch class (epi 0: forward, 1: conjugate).
   virtual cudaError_t batch_contour_step(const BatchGeom& g, const BatchStep* d_steps, int nactive, int epi,
                                          cudaStream_t st) = 0;
+  // one step of both marches for `nactive` entries (pairs of forward / conjugate members):
+  // z forward when `first`, then y, x (D), y inverse, and the fused z inverse / forward
+  virtual cudaError_t batch_pair_step(const BatchGeom& g, const BatchStep* d_steps, int nactive, bool first,
+                                      cudaStream_t stream) = 0;
+  // contour quadrature of Eq. 8 over the stored q and qd histories (after solve_mid)
+  virtual cudaError_t quadrature(CtxData& c) = 0;
   virtual cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p,
                                  const double* eta_m) = 0;
   virtual cudaError_t fft3d(CtxData& c, void* data, int inverse) = 0;   // complex, in place

@@ -756,13 +756,18 @@ class EngineT : public Engine {
     return cudaSuccess;
   }
 
-  // Q, the quadrature over both histories, densities and H
-  cudaError_t finish_concurrent(CtxData& c) {
+  cudaError_t batch_pair_step(const BatchGeom& g, const BatchStep* st, int nact, bool first,
+                              cudaStream_t stream) override {
+    if (nact <= 0) return cudaSuccess;
     cudaError_t e;
-    if ((e = solve_mid(c)) != cudaSuccess) return e;
+    if (first && (e = batch_zf(g, st, nact, stream)) != cudaSuccess) return e;
+    if ((e = batch_mid(g, st, nact, stream)) != cudaSuccess) return e;
+    return batch_zz(g, st, nact, stream);
+  }
+
+  cudaError_t quadrature(CtxData& c) override {
     mark(c, KK_QUADRATURE);
     const int blocks = c.sms * 8;
-    // qd = q for the reversible Edwards chain (its q_0 is the qd_0 of the pairing)
     const void* qdh = c.edw ? c.hist : c.qdh;
     const void* qd0 = c.edw ? c.hist : c.qd0;
     if (c.kind == PFT_SCFT_REAL) {
@@ -772,7 +777,14 @@ class EngineT : public Engine {
       k_quadrature_cplx<T><<<blocks, PW_THREADS, 0, c.stream>>>((const Z*)c.hist, (const Z*)qdh, (const Z*)qd0, c.M,
                                                                c.Ns, c.NsA, (double2*)c.accA, (double2*)c.accB);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+
+  // Q, the quadrature over both histories, densities and H
+  cudaError_t finish_concurrent(CtxData& c) {
+    cudaError_t e;
+    if ((e = solve_mid(c)) != cudaSuccess) return e;
+    if ((e = quadrature(c)) != cudaSuccess) return e;
     return solve_tail(c);
   }
 

@@ -134,6 +134,10 @@ _SIGS = {
     "pft_launch_counts": (ct.c_int, [_P, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     "pft_get_checkpoint": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_get_plan": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "pft_batch_autotune": (ct.c_int, [_P]),
+    "pft_batch_set_plan": (ct.c_int, [_P, ct.c_int, ct.c_int]),
+    "pft_batch_class_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                        ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_float)]),
     "pft_philox_normals": (ct.c_int, [ct.c_ulonglong, ct.c_ulonglong, ct.c_ulonglong, ct.c_int, ct.c_longlong,
                                       _P, _P]),
     "pft_philox_raw": (ct.c_int, [ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint), ct.c_longlong, _P, _P]),
@@ -321,6 +325,26 @@ def pft_batch_get_densities(b, i, phiA, phiB):
     w = _where(phiA, phiB)
     _check(_lib().pft_batch_get_densities(b, int(i), _ptr(phiA, True)[0], _ptr(phiB, True)[0], w),
            "pft_batch_get_densities")
+
+
+def pft_batch_autotune(b):
+    _check(_lib().pft_batch_autotune(b), "pft_batch_autotune")
+
+
+def pft_batch_set_plan(b, cls, plan):
+    _check(_lib().pft_batch_set_plan(b, int(cls), int(plan)), "pft_batch_set_plan")
+
+
+def pft_batch_class_info(b, cls):
+    n = (ct.c_int * 3)()
+    kind = ct.c_int()
+    members = ct.c_int()
+    plan = ct.c_int()
+    ms = (ct.c_float * 2)()
+    _check(_lib().pft_batch_class_info(b, int(cls), n, ct.byref(kind), ct.byref(members), ct.byref(plan), ms),
+           "pft_batch_class_info")
+    return {"n": tuple(n), "kind": kind.value, "members": members.value, "plan": plan.value,
+            "tuned_ms": (ms[0], ms[1])}
 
 
 def pft_batch_synchronize(b):

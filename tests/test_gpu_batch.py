@@ -90,11 +90,14 @@ def test_batch_graphed_matches_oracle_fp64():
 
 
 @pytest.mark.parametrize("prec", [pft.PFT_FP64, pft.PFT_FP32_MIXED])
-def test_batch_graphed_equals_per_instance(prec):
+def test_batch_graphed_plan0_equals_per_instance(prec):
+    """Plan 0 (one march after the other, fused quadrature) is the per-instance arithmetic
+    exactly, so the graphed batch reproduces the per-instance mode bit for bit."""
     res = []
     for mode in (pft.PFT_BATCH_GRAPHED, pft.PFT_BATCH_PER_INSTANCE):
         b, _ = _make(prec)
         try:
+            pft.pft_batch_set_plan(b, -1, 0)
             pft.pft_batch_run(b, 3, LAM, DT, mode)
             out = []
             for i, d in enumerate(DESCS):
@@ -121,3 +124,40 @@ def test_batch_rejects_bad_members():
         assert e.value.status == pft.PFT_ERR_STATE
     finally:
         pft.pft_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [pft.PFT_FP64, pft.PFT_FP32_MIXED])
+def test_batch_plans_agree_and_autotune_picks_one(prec):
+    """Plan 1 (both marches per launch, post-march quadrature) against plan 0 after three
+    updates: the propagators are the same arithmetic, the FP64 quadrature sums run in
+    another order (FP64: 1e-12 on fields; FP32: 1e-5, the FP32 Boltzmann factors of
+    fields differing in the last FP64 bits may round apart).  The autotuner then picks a
+    plan per class and the run continues from the same state."""
+    out = {}
+    for plan in (0, 1):
+        b, _ = _make(prec)
+        try:
+            pft.pft_batch_set_plan(b, -1, plan)
+            pft.pft_batch_run(b, 3, LAM, DT, pft.PFT_BATCH_GRAPHED)
+            res = []
+            for i, d in enumerate(DESCS):
+                dt = np.float64 if d["kind"] == SCFT else np.complex128
+                gp = np.empty(d["n"], dt)
+                gm = np.empty(d["n"], dt)
+                pft.pft_batch_get_fields(b, i, gp, gm)
+                res.append((gp, gm))
+            out[plan] = res
+            if plan == 1:
+                pft.pft_batch_autotune(b)
+                info = pft.pft_batch_info(b)
+                for k in range(info["classes"]):
+                    ci = pft.pft_batch_class_info(b, k)
+                    assert ci["plan"] in (0, 1) and min(ci["tuned_ms"]) > 0
+                    assert ci["tuned_ms"][ci["plan"]] == min(ci["tuned_ms"])
+                pft.pft_batch_run(b, 1, LAM, DT, pft.PFT_BATCH_GRAPHED)
+                pft.pft_batch_synchronize(b)
+        finally:
+            pft.pft_batch_destroy(b)
+    tol = 1e-12 if prec == pft.PFT_FP64 else 1e-5
+    for (a0, b0), (a1, b1) in zip(out[0], out[1]):
+        assert np.max(np.abs(a0 - a1)) <= tol and np.max(np.abs(b0 - b1)) <= tol
