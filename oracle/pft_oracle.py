@@ -49,7 +49,7 @@ __all__ = [
     "dense_propagator_matrix", "forward_march_dense", "continuum_Q", "debye_g",
     "variable_cell_step", "rqm4_step", "simpson_weights", "SPLIT2", "RQM4",
     "debye_chain", "scft_sis_step", "cl_sis_step", "EdwardsSolution", "edwards_field", "edwards_solve",
-    "edwards_hamiltonian", "edwards_scft_step", "edwards_cl_step",
+    "edwards_hamiltonian", "edwards_scft_step", "edwards_cl_step", "adjoint_field_gradient",
 ]
 
 SPLIT2 = "split2"   # 2nd-order operator splitting, the A(ds) block of Eq. 13
@@ -424,6 +424,64 @@ def dH_dfields(wp, wm, sol: Solution, chiN: float, C: float, n, L, kind: str):
     dV = float(np.prod(L)) / M
     fp, fm = mean_field_forces(wp, wm, sol.phiA, sol.phiB, chiN, kind)
     return C * dV * fp, C * dV * fm
+
+
+def adjoint_field_gradient(wp, wm, n, L, Ns: int, fA: float, GA, GB):
+    """Gradient of a loss L(phiA, phiB) with respect to the real SCFT fields W+ and W-,
+    through the discrete march (2nd-order steps, trapezoid quadrature), given
+    GA = dL/dphiA and GB = dL/dphiB on the grid.
+
+    Derivation (step by step, the order used below): with T_n = B_n K B_n, K the
+    diffusion operator (real symmetric for real fields) and g_n = (ds/Q)(cA_n GA + cB_n GB),
+      L_acc = sum_n <g_n, q_n qd_{Ns-n}>: the sources a_n = g_n qd_{Ns-n} of the q march
+      are propagated backwards by lambda_Ns = a_Ns, lambda_{n-1} = T_n lambda_n + a_{n-1},
+      and each step contributes -(ds/2) [lambda_n q_n + B_n q_{n-1} K(B_n lambda_n)] to
+      dL/dw of its block; likewise the qd march with sources b_m = g_{Ns-m} q_{Ns-m};
+      the normalisation by Q adds gamma phi / M with gamma = sum_x (GA phiA + GB phiB)
+      (d lnQ / dw = -phi / M); then dL/dW+ = dL/dwA + dL/dwB, dL/dW- = dL/dwB - dL/dwA."""
+    sol = solve(wp, wm, n, L, Ns, fA, SCFT_REAL)
+    ds = 1.0 / Ns
+    NsA = sol.NsA
+    M = int(np.prod(n))
+    q, qd, Q = sol.q, sol.qd, sol.Q
+    cA, cB = quadrature_weights(Ns, NsA)
+    D = sol.D
+
+    def K(v):
+        return np.fft.ifftn(D * np.fft.fftn(v)).real
+
+    def g(k):
+        return (ds / Q) * (cA[k] * GA + cB[k] * GB)
+
+    dwA = np.zeros(q.shape[1:])
+    dwB = np.zeros(q.shape[1:])
+    # adjoint of the forward march
+    lam = g(Ns) * qd[0]
+    for k in range(Ns, 0, -1):
+        Bk = sol.BA if k <= NsA else sol.BB
+        z = K(Bk * lam)
+        term = -0.5 * ds * (lam * q[k] + Bk * q[k - 1] * z)
+        if k <= NsA:
+            dwA += term
+        else:
+            dwB += term
+        lam = Bk * z + g(k - 1) * qd[Ns - k + 1]
+    # adjoint of the conjugate march (step m uses the factor of split step Ns + 1 - m)
+    mu = g(0) * q[0]
+    for m in range(Ns, 0, -1):
+        nb = Ns + 1 - m
+        Bm = sol.BA if nb <= NsA else sol.BB
+        z = K(Bm * mu)
+        term = -0.5 * ds * (mu * qd[m] + Bm * qd[m - 1] * z)
+        if nb <= NsA:
+            dwA += term
+        else:
+            dwB += term
+        mu = Bm * z + g(Ns - m + 1) * q[Ns - m + 1]
+    gamma = float(np.sum(GA * sol.phiA + GB * sol.phiB))
+    dwA += gamma * sol.phiA / M
+    dwB += gamma * sol.phiB / M
+    return dwA + dwB, dwB - dwA
 
 
 def dlnQ_dL(sol: Solution, n, L):

@@ -616,3 +616,61 @@ def test_edwards_debye_response_and_saddle():
     W0 = np.full((4, 4, 4), C / B)
     s = o.edwards_solve(W0, (4, 4, 4), (2.0, 2.0, 2.0), 10, o.SCFT_REAL)
     assert np.max(np.abs(o.edwards_scft_step(W0, s.phi, B, C, 0.5) - W0)) < 1e-13
+
+
+# ------------------------------------------------------- reverse-mode adjoint (f3)
+def _adj_setup(seed=5):
+    n, L, Ns, fA = (6, 4, 4), (3.0, 2.0, 2.0), 12, 0.4
+    rng = np.random.default_rng(seed)
+    return n, L, Ns, fA, rng.normal(0, 0.3, n), rng.normal(0, 0.8, n), rng
+
+
+def test_adjoint_gradient_of_a_linear_loss_matches_finite_differences():
+    """L = sum_x (UA phiA + UB phiB) with random UA, UB: the adjoint gradients with respect
+    to W+ and W- equal 5-point finite differences of L through the full solve (1e-9)."""
+    n, L, Ns, fA, wp, wm, rng = _adj_setup()
+    UA, UB = rng.normal(size=n), rng.normal(size=n)
+
+    def loss(a, b):
+        s = o.solve(a, b, n, L, Ns, fA, o.SCFT_REAL)
+        return float(np.sum(UA * s.phiA + UB * s.phiB))
+    gp, gm = o.adjoint_field_gradient(wp, wm, n, L, Ns, fA, UA, UB)
+    for idx in [(1, 2, 3), (4, 0, 1), (0, 3, 2)]:
+        for which, g in ((0, gp), (1, gm)):
+            def f(h, idx=idx, which=which):
+                a, b = wp.copy(), wm.copy()
+                (a if which == 0 else b)[idx] += h
+                return loss(a, b)
+            fd = fd5(f, 1e-4)
+            assert abs(fd - g[idx]) <= 1e-9 * max(1.0, abs(g[idx])), (idx, which, fd, g[idx])
+
+
+def test_adjoint_gradient_of_a_quadratic_loss_matches_finite_differences():
+    """L = (1/2) sum_x (phiA - t)^2, so dL/dphiA = phiA - t and dL/dphiB = 0."""
+    n, L, Ns, fA, wp, wm, rng = _adj_setup(6)
+    t = rng.uniform(0.2, 0.6, n)
+
+    def loss(a, b):
+        s = o.solve(a, b, n, L, Ns, fA, o.SCFT_REAL)
+        return 0.5 * float(np.sum((s.phiA - t) ** 2))
+    s0 = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    gp, gm = o.adjoint_field_gradient(wp, wm, n, L, Ns, fA, s0.phiA - t, np.zeros(n))
+    for idx in [(2, 1, 0), (5, 3, 3)]:
+        for which, g in ((0, gp), (1, gm)):
+            def f(h, idx=idx, which=which):
+                a, b = wp.copy(), wm.copy()
+                (a if which == 0 else b)[idx] += h
+                return loss(a, b)
+            fd = fd5(f, 1e-4)
+            assert abs(fd - g[idx]) <= 1e-9 * max(1.0, abs(g[idx])), (idx, which, fd, g[idx])
+
+
+@pytest.mark.parametrize("GA,GB", [(1.0, 1.0), (1.0, 0.0), (0.0, 1.0)])
+def test_adjoint_gradient_of_the_sum_rules_vanishes(GA, GB):
+    """sum_x phiA = M fA_eff and sum_x phiB = M (1 - fA_eff) hold exactly for every field
+    (trapezoid rule), so the adjoint gradient of these losses is zero to round-off: a
+    dropped term or a wrong sign in the Q normalisation or in either adjoint march breaks
+    the cancellation."""
+    n, L, Ns, fA, wp, wm, rng = _adj_setup(7)
+    gp, gm = o.adjoint_field_gradient(wp, wm, n, L, Ns, fA, np.full(n, GA), np.full(n, GB))
+    assert np.max(np.abs(gp)) < 1e-13 and np.max(np.abs(gm)) < 1e-13
