@@ -303,6 +303,40 @@ def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, ste
     return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
 
 
+def _adjoint_time(pft, torch, w, prec, reps=5):
+    """Reverse-mode adjoint of a density loss after one solve (device arrays): ms per call
+    and, for scale, ms per solve of the same context."""
+    s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, pft.PFT_SCFT_REAL, prec, checkpoint=1)
+    h = s.h
+    wp, wm = wl.fields(w)
+    pft.pft_set_fields(h, wp, wm)
+    pft.pft_solve(h)
+    ga = torch.randn(w.n, dtype=torch.float64, device="cuda")
+    gb = torch.randn(w.n, dtype=torch.float64, device="cuda")
+    op = torch.empty_like(ga)
+    om = torch.empty_like(gb)
+    pft.pft_adjoint(h, ga, gb, op, om)
+    pft.pft_synchronize(h)
+    st = torch.cuda.ExternalStream(pft.pft_get_stream(h))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        pft.pft_adjoint(h, ga, gb, op, om)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    e0.record(st)
+    for _ in range(reps):
+        pft.pft_solve(h)
+    e1.record(st)
+    e1.synchronize()
+    ms_solve = e0.elapsed_time(e1) / reps
+    s.close()
+    return {"workload": w.name, "ms_per_adjoint": ms, "ms_per_solve": ms_solve,
+            "note": "gradient of a loss on (phiA, phiB) w.r.t. (W+, W-) through the discrete march"}
+
+
 def _library_fft_step(torch, wpa, wma, steps=3, warmup=1):
     """Comparison arm (not the product path): the same field update written with
     torch.fft (cuFFT) R2C/C2R transforms and separate elementwise kernels, eager launches,
@@ -530,6 +564,7 @@ def run(args):
         # Edwards homopolymer model: one reversible chain (q-dagger = q), one march per solve
         "edwards_scft128_fp32": _variant(pft, torch, wl.EDW128, pft.PFT_FP32_MIXED, 10),
         "edwards_cl128_fp32": _variant(pft, torch, wl.EDWCL128, pft.PFT_FP32_MIXED, 10),
+        "adjoint_fp32": _adjoint_time(pft, torch, WORK, pft.PFT_FP32_MIXED),
     }
     torch.cuda.empty_cache()
     lib_fft = _library_fft_step(torch, wpa, wma)

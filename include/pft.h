@@ -224,6 +224,18 @@ pft_status pft_get_densities(pft_ctx* ctx, void* phiA, void* phiB, pft_mem where
 pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt,
                           const void* eta_p, const void* eta_m, pft_mem where);
 
+/* Reverse-mode adjoint of the last solve for a loss L(phiA, phiB) given on the grid as
+ * dL_dphiA and dL_dphiB (M float64 each): writes dL/dW+ and dL/dW- (M float64 each), the
+ * exact gradient of L through the discrete march (2nd-order steps, trapezoid quadrature,
+ * the normalisation by Q).  Method: the q and qd marches are adjoined backwards with the
+ * source terms of the quadrature (Eq. 8), both adjoint chains sharing each batched
+ * transform; every step adds -(ds/2) [lambda_k q_k + B_k q_{k-1} F^-1 D F (B_k lambda_k)]
+ * to the gradient of its block.  Arrays on host or device per `where`.
+ * Errors: PFT_ERR_UNSUPPORTED unless real SCFT diblock fields, SPLIT2, the pass march and
+ * both histories kept (checkpoint 1); PFT_ERR_STATE without a solve at the current fields. */
+pft_status pft_adjoint(pft_ctx* ctx, const void* dL_dphiA, const void* dL_dphiB, void* dL_dwp, void* dL_dwm,
+                       pft_mem where);
+
 /* Exact gradients of the discrete H of the last solve:
  *   dH_dwp, dH_dwm (M float64 each, host or device per `where`, either may be NULL):
  *     C dV (phiA+phiB-1) and C dV (2 W-/chiN + phiB - phiA)          (Eq. 7 x C dV)

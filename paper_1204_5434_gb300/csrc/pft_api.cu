@@ -121,7 +121,7 @@ void free_all(pft_ctx* c) {
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
                   d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync, d.qdh, d.steps2, d.stepsg,
-                  d.BAh, d.BBh, d.rq, d.qw, d.sis};
+                  d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
@@ -540,6 +540,45 @@ pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[
     if (dlnQ_dL) dlnQ_dL[a] = g;
     if (dH_dL) dH_dL[a] = H / d.L[a] - d.C * V * g;
   }
+  return PFT_OK;
+}
+
+pft_status pft_adjoint(pft_ctx* ctx, const void* dL_dphiA, const void* dL_dphiB, void* dL_dwp, void* dL_dwm,
+                       pft_mem where) {
+  if (!ctx || !dL_dphiA || !dL_dphiB || !dL_dwp || !dL_dwm) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (d.kind != PFT_SCFT_REAL || d.edw || d.scheme != 0)
+    return fail(PFT_ERR_UNSUPPORTED, "the adjoint is implemented for real SCFT diblock fields and SPLIT2");
+  if (!(d.march == 1 && d.concurrent && d.ckK == 1))
+    return fail(PFT_ERR_UNSUPPORTED, "the adjoint needs the pass march with both histories kept");
+  if (!d.solved || !d.qdh) return fail(PFT_ERR_STATE, "pft_adjoint needs a solve at the current fields");
+  const size_t b = (size_t)d.M * 8;
+  double* io = (double*)ctx->io;  // 2 M doubles of staging: the two loss gradients
+  const double *GA, *GB;
+  double *gp, *gm;
+  double* out_stage = nullptr;
+  if (where == PFT_HOST) {
+    PFT_CK(cudaMemcpyAsync(io, dL_dphiA, b, cudaMemcpyHostToDevice, d.stream));
+    PFT_CK(cudaMemcpyAsync(io + d.M, dL_dphiB, b, cudaMemcpyHostToDevice, d.stream));
+    GA = io;
+    GB = io + d.M;
+    PFT_CK(cudaMalloc(&out_stage, 2 * b));
+    gp = out_stage;
+    gm = out_stage + d.M;
+  } else {
+    GA = (const double*)dL_dphiA;
+    GB = (const double*)dL_dphiB;
+    gp = (double*)dL_dwp;
+    gm = (double*)dL_dwm;
+  }
+  cudaError_t e = ctx->eng->adjoint(d, GA, GB, gp, gm);
+  if (e == cudaSuccess && where == PFT_HOST) {
+    e = cudaMemcpyAsync(dL_dwp, gp, b, cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dL_dwm, gm, b, cudaMemcpyDeviceToHost, d.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(d.stream);
+  }
+  if (out_stage) cudaFree(out_stage);
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
   return PFT_OK;
 }
 

@@ -24,6 +24,7 @@ enum ScalarSlot {
   S_STRESS = 16,    // sum over steps/modes of the box-derivative contraction (3)
   S_DLNQ = 20,      // dlnQ/dL_a (3)
   S_VOL = 24,       // box volume V (written by the host)
+  S_GAMMA = 26,     // adjoint: sum_x (GA phiA + GB phiB) (2 slots of the reduction)
   S_COUNT = 32
 };
 
@@ -77,6 +78,8 @@ struct CtxData {
   size_t g_off[3] = {0, 0, 0};      // k_a^2 per axis (FP64): box derivative, SIS Debye factor
   size_t t64_off[3] = {0, 0, 0};    // FP64 twiddles x, y, z (full nz) for the SIS transforms
   void* sis = nullptr;              // [M] complex FP64 scratch of the semi-implicit step
+  void* adj = nullptr;              // adjoint scratch: 6 working-precision slices + 2 M FP64
+  void* stepsa = nullptr;           // [2 Ns] BatchStep of the adjoint transforms
   size_t tables_bytes = 0;
   int npart = 0;
   size_t bytes = 0;
@@ -183,6 +186,9 @@ class Engine {
                                       cudaStream_t stream) = 0;
   // contour quadrature of Eq. 8 over the stored q and qd histories (after solve_mid)
   virtual cudaError_t quadrature(CtxData& c) = 0;
+  // reverse-mode adjoint of the last solve for a loss with dL/dphiA = GA, dL/dphiB = GB
+  // (device FP64 arrays), into dL/dW+ and dL/dW- (device FP64 arrays)
+  virtual cudaError_t adjoint(CtxData& c, const double* GA, const double* GB, double* dwp, double* dwm) = 0;
   virtual cudaError_t field_step(CtxData& c, int step_kind, double lam, const double* eta_p,
                                  const double* eta_m) = 0;
   virtual cudaError_t fft3d(CtxData& c, void* data, int inverse) = 0;   // complex, in place

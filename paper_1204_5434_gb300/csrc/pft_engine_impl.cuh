@@ -552,6 +552,100 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_cl(double2* __restrict__ wp
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
+// --------------------------------------------- reverse-mode adjoint of the march
+// One step of both adjoint marches (real fields): with z = K(B lambda) from the batched
+// transforms, each chain adds -(ds/2)(lambda q_k + B q_{k-1} z) to the gradient of the
+// block of its split step and moves to lambda_{k-1} = B z + g (ds/Q)(cA GA + cB GB) src,
+// src the partner history slice of the source term.  Chain 0 adjoins the q march, chain 1
+// the qd march.
+struct AdjChain {
+  const void* lam;   // lambda_k
+  void* lam_next;    // lambda_{k-1}
+  const void* z;     // K(B_k lambda_k)
+  const void* qk;    // q_k (or qd_k)
+  const void* qk1;   // q_{k-1}
+  const void* B;     // factor of the split step
+  const void* src;   // partner slice of the source at k-1
+  double cA, cB;     // quadrature weights of that source
+  int blockA;        // the split step lies in the A block
+};
+
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_adjoint_update(AdjChain c0, AdjChain c1,
+                                                               const double* __restrict__ GA,
+                                                               const double* __restrict__ GB,
+                                                               const double* __restrict__ s, double ds,
+                                                               double* __restrict__ dwA, double* __restrict__ dwB,
+                                                               long long M) {
+  const double f = ds / s[S_Q];
+  const double h = -0.5 * ds;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double ga = GA[i], gb = GB[i];
+    double a = dwA[i], b = dwB[i];
+    for (int ch = 0; ch < 2; ch++) {
+      const AdjChain& c = ch ? c1 : c0;
+      const T lam = ((const T*)c.lam)[i];
+      const T z = ((const T*)c.z)[i];
+      const T B = ((const T*)c.B)[i];
+      const double term = h * (widen(lam * ((const T*)c.qk)[i]) + widen(B * ((const T*)c.qk1)[i] * z));
+      if (c.blockA) a += term; else b += term;
+      const double g = f * (c.cA * ga + c.cB * gb);
+      ((T*)c.lam_next)[i] = (T)((double)(B * z) + g * (double)((const T*)c.src)[i]);
+    }
+    dwA[i] = a;
+    dwB[i] = b;
+  }
+}
+
+// lambda_Ns = g_Ns qd_0 and mu_Ns = g_0 q_0 (both starting slices are the initial
+// conditions), and the gradient accumulators cleared.
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_adjoint_init(T* __restrict__ lam, T* __restrict__ mu,
+                                                             const T* __restrict__ qd0, const T* __restrict__ q0,
+                                                             const double* __restrict__ GA,
+                                                             const double* __restrict__ GB,
+                                                             const double* __restrict__ s, double ds, double cAl,
+                                                             double cBl, double cAm, double cBm,
+                                                             double* __restrict__ dwA, double* __restrict__ dwB,
+                                                             long long M) {
+  const double f = ds / s[S_Q];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double ga = GA[i], gb = GB[i];
+    lam[i] = (T)(f * (cAl * ga + cBl * gb) * (double)qd0[i]);
+    mu[i] = (T)(f * (cAm * ga + cBm * gb) * (double)q0[i]);
+    dwA[i] = 0.0;
+    dwB[i] = 0.0;
+  }
+}
+
+// gamma = sum_x (GA phiA + GB phiB), partial sums per block.
+static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_gamma(const double* __restrict__ GA,
+                                                                     const double* __restrict__ GB,
+                                                                     const double* __restrict__ phiA,
+                                                                     const double* __restrict__ phiB, long long M,
+                                                                     double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x)
+    acc[0] += GA[i] * phiA[i] + GB[i] * phiB[i];
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
+// dL/dW+ = dwA + dwB + gamma (phiA + phiB)/M, dL/dW- = dwB - dwA + gamma (phiB - phiA)/M.
+static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_finish(const double* __restrict__ dwA,
+                                                                      const double* __restrict__ dwB,
+                                                                      const double* __restrict__ phiA,
+                                                                      const double* __restrict__ phiB,
+                                                                      const double* __restrict__ gamma, double invM,
+                                                                      double* __restrict__ dwp,
+                                                                      double* __restrict__ dwm, long long M) {
+  const double gm = gamma[0] * invM;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const double a = dwA[i] + gm * phiA[i], b = dwB[i] + gm * phiB[i];
+    dwp[i] = a + b;
+    dwm[i] = b - a;
+  }
+}
+
 // ------------------------------------------------ Edwards homopolymer model (Eq. 2)
 // Boltzmann factor of the one field (W = i omega stored in SCFT mode, omega in CL mode)
 // and the field term of H per C: -(b/2) W^2 (SCFT) or (b/2) omega^2 (CL), b = B/C.

@@ -780,6 +780,103 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
+  // ------------------------------------------- reverse-mode adjoint (f3)
+  // Adjoint marches of q (chain 0) and qd (chain 1) for a loss on the densities, both in
+  // the same batched transforms: per step k = Ns .. 1, z = K(B lambda_k) by the z forward,
+  // y, x (D), y inverse and z inverse passes (no final factor), then k_adjoint_update.
+  cudaError_t adjoint(CtxData& c, const double* GA, const double* GB, double* dwp, double* dwm) override {
+    if (c.kind != PFT_SCFT_REAL || !c.qdh) return cudaErrorNotSupported;
+    const size_t slice = (size_t)c.M * sizeof(T);
+    cudaError_t e;
+    if (!c.adj) {
+      const size_t bytes = 6 * slice + 2 * (size_t)c.M * sizeof(double);
+      if ((e = cudaMalloc(&c.adj, bytes)) != cudaSuccess) return e;
+      c.bytes += bytes;
+    }
+    char* a = (char*)c.adj;
+    T* lam[2] = {(T*)a, (T*)(a + slice)};
+    T* mu[2] = {(T*)(a + 2 * slice), (T*)(a + 3 * slice)};
+    T* z0 = (T*)(a + 4 * slice);
+    T* z1 = (T*)(a + 5 * slice);
+    double* dwA = (double*)(a + 6 * slice);
+    double* dwB = dwA + c.M;
+    const char* hist = (const char*)c.hist;
+    const char* qdh = (const char*)c.qdh;
+    auto qs = [&](int j) { return (const T*)(hist + (size_t)j * slice); };
+    auto qds = [&](int j) { return j == 0 ? (const T*)c.qd0 : (const T*)(qdh + (size_t)j * slice); };
+    auto Bof = [&](int split) { return (const T*)((split <= c.NsA) ? c.BA : c.BB); };
+    if (!c.stepsa) {  // entries 2(k-1) and 2(k-1)+1: the transforms of step k of both chains
+      std::vector<BatchStep> h((size_t)2 * c.Ns);
+      const char* t = (const char*)c.tables;
+      for (int k = 1; k <= c.Ns; k++) {
+        BatchStep& f = h[(size_t)2 * (k - 1)];
+        BatchStep& b = h[(size_t)2 * (k - 1) + 1];
+        memset(&f, 0, sizeof(f));
+        memset(&b, 0, sizeof(b));
+        f.in = lam[(c.Ns - k) & 1];
+        f.B = Bof(k);
+        f.out = z0;
+        f.spec = c.spec;
+        b.in = mu[(c.Ns - k) & 1];
+        b.B = Bof(c.Ns + 1 - k);
+        b.out = z1;
+        b.spec = c.spec2;
+        for (int x = 0; x < 4; x++) f.tw[x] = b.tw[x] = t + c.tw_off[x];
+        for (int x = 0; x < 3; x++) f.d[x] = b.d[x] = t + c.d_off[x];
+      }
+      if ((e = cudaMalloc(&c.stepsa, h.size() * sizeof(BatchStep))) != cudaSuccess) return e;
+      c.bytes += h.size() * sizeof(BatchStep);
+      e = cudaMemcpy(c.stepsa, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return e;
+    }
+    BatchGeom g;
+    for (int x = 0; x < 3; x++) g.n[x] = c.n[x];
+    g.kind = c.kind;
+    g.nzh = c.nzh;
+    double cA, cB, cAm, cBm;
+    trapezoid_weight(c.Ns, c.Ns, c.NsA, &cA, &cB);
+    trapezoid_weight(0, c.Ns, c.NsA, &cAm, &cBm);
+    k_adjoint_init<T><<<c.npart, PW_THREADS, 0, c.stream>>>(lam[0], mu[0], qds(0), qs(0), GA, GB, c.scal, c.ds, cA, cB,
+                                                            cAm, cBm, dwA, dwB, c.M);
+    const BatchStep* st = (const BatchStep*)c.stepsa;
+    for (int k = c.Ns; k >= 1; k--) {
+      const BatchStep* ss = st + (size_t)2 * (k - 1);
+      if ((e = batch_zf(g, ss, 2, c.stream)) != cudaSuccess) return e;
+      if ((e = batch_mid(g, ss, 2, c.stream)) != cudaSuccess) return e;
+      const long long npen = (long long)c.n[0] * c.n[1];
+      PFT_BATCH_HALF(c.n[2] / 2, e = (bzi_c2r<N, 2>(ss, npen, 2, c.stream)));
+      if (e != cudaSuccess) return e;
+      const int cur = (c.Ns - k) & 1;
+      AdjChain c0, c1;
+      c0.lam = lam[cur];
+      c0.lam_next = lam[cur ^ 1];
+      c0.z = z0;
+      c0.qk = qs(k);
+      c0.qk1 = qs(k - 1);
+      c0.B = Bof(k);
+      c0.src = qds(c.Ns - k + 1);
+      trapezoid_weight(k - 1, c.Ns, c.NsA, &c0.cA, &c0.cB);
+      c0.blockA = (k <= c.NsA) ? 1 : 0;
+      c1.lam = mu[cur];
+      c1.lam_next = mu[cur ^ 1];
+      c1.z = z1;
+      c1.qk = qds(k);
+      c1.qk1 = qds(k - 1);
+      c1.B = Bof(c.Ns + 1 - k);
+      c1.src = qs(c.Ns - k + 1);
+      trapezoid_weight(c.Ns - k + 1, c.Ns, c.NsA, &c1.cA, &c1.cB);
+      c1.blockA = (c.Ns + 1 - k <= c.NsA) ? 1 : 0;
+      k_adjoint_update<T><<<c.npart, PW_THREADS, 0, c.stream>>>(c0, c1, GA, GB, c.scal, c.ds, dwA, dwB, c.M);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_adjoint_gamma<<<c.npart, PW_THREADS, 0, c.stream>>>(GA, GB, (const double*)c.accA, (const double*)c.accB, c.M,
+                                                         c.partials);
+    k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_GAMMA);
+    k_adjoint_finish<<<c.npart, PW_THREADS, 0, c.stream>>>(dwA, dwB, (const double*)c.accA, (const double*)c.accB,
+                                                          c.scal + S_GAMMA, 1.0 / (double)c.M, dwp, dwm, c.M);
+    return cudaGetLastError();
+  }
+
   // Q, the quadrature over both histories, densities and H
   cudaError_t finish_concurrent(CtxData& c) {
     cudaError_t e;

@@ -134,6 +134,7 @@ _SIGS = {
     "pft_launch_counts": (ct.c_int, [_P, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     "pft_get_checkpoint": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_get_plan": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "pft_adjoint": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
     "pft_batch_autotune": (ct.c_int, [_P]),
     "pft_batch_set_plan": (ct.c_int, [_P, ct.c_int, ct.c_int]),
     "pft_batch_class_info": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
@@ -273,6 +274,13 @@ def pft_field_step(h, kind, lam_or_dt, eta_p=None, eta_m=None):
     w = _where(eta_p, eta_m)
     _check(_lib().pft_field_step(h, int(kind), float(lam_or_dt), _ptr(eta_p)[0], _ptr(eta_m)[0], w),
            "pft_field_step")
+
+
+def pft_adjoint(h, dL_dphiA, dL_dphiB, dL_dwp, dL_dwm):
+    """Reverse-mode adjoint of the last solve: fills dL_dwp, dL_dwm from dL/dphiA, dL/dphiB."""
+    w = _where(dL_dphiA, dL_dphiB, dL_dwp, dL_dwm)
+    _check(_lib().pft_adjoint(h, _ptr(dL_dphiA)[0], _ptr(dL_dphiB)[0], _ptr(dL_dwp, True)[0], _ptr(dL_dwm, True)[0],
+                              w), "pft_adjoint")
 
 
 def pft_gradients(h, dH_dwp=None, dH_dwm=None):
@@ -516,6 +524,14 @@ class System:
             eta_p = np.ascontiguousarray(eta_p, dtype=np.float64)
             eta_m = np.ascontiguousarray(eta_m, dtype=np.float64)
         pft_field_step(self.h, kind, lam_or_dt, eta_p, eta_m)
+
+    def adjoint(self, dL_dphiA, dL_dphiB):
+        """dL/dW+, dL/dW- of a loss on the densities of the last solve (host arrays)."""
+        gp = np.empty(self.n)
+        gm = np.empty(self.n)
+        pft_adjoint(self.h, np.ascontiguousarray(dL_dphiA, dtype=np.float64),
+                    np.ascontiguousarray(dL_dphiB, dtype=np.float64), gp, gm)
+        return gp, gm
 
     def propagator(self, which, s):
         out = np.empty(self.n, self.dtype)
