@@ -92,7 +92,7 @@ kb_zz_r2c(const BatchStep* __restrict__ st, long long npen) {
 #pragma unroll
   for (int i = 0; i < E; i++) x.put(t + TPC * i, valid ? sp[t + TPC * i] : mk<T>(T(0), T(0)));
   if (t == 0) x.put(N2, valid ? sp[N2] : mk<T>(T(0), T(0)));
-  __syncthreads();
+  __syncwarp();
   Z v[E];
 #pragma unroll
   for (int i = 0; i < E; i++) {
@@ -102,7 +102,7 @@ kb_zz_r2c(const BatchStep* __restrict__ st, long long npen) {
     const Z d = rot90<true>(cmulc(csub(xk, xc), twf[k]));
     v[i] = cadd(cadd(xk, xc), d);
   }
-  __syncthreads();
+  __syncwarp();
   fft<T, true, N2>(v, t, twh, x);
   const Z* b2 = reinterpret_cast<const Z*>(s.B) + o;
   Z* q2 = reinterpret_cast<Z*>(s.out) + o;
@@ -125,7 +125,7 @@ kb_zz_r2c(const BatchStep* __restrict__ st, long long npen) {
   fft<T, false, N2>(v, t, twh, x);  // the inverse ended with a barrier after its last reads
 #pragma unroll
   for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
-  __syncthreads();
+  __syncwarp();
   const T h = T(0.5);
 #pragma unroll
   for (int i = 0; i < E; i++) {
@@ -173,7 +173,7 @@ kb_zz_c2c(const BatchStep* __restrict__ st, long long npen) {
   const Z* Bn = (const Z*)s.Bnext;
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = cmul(v[i], Bn[o + t + TPC * i]);
-  if (n_stages<Plan<N>>() > 1) __syncthreads();
+  if (n_stages<Plan<N>>() > 1) __syncwarp();
   fft<T, false, N>(v, t, tw, x);
   if (valid) {
 #pragma unroll

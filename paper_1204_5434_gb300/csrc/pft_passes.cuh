@@ -33,7 +33,8 @@ template <typename T> struct XchPencil {
   __device__ __forceinline__ static int idx(int pos) { return pos + (pos >> SH); }
   __device__ __forceinline__ void put(int pos, cpx<T> z) { s[idx(pos)] = z; }
   __device__ __forceinline__ cpx<T> get(int pos) const { return s[idx(pos)]; }
-  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  // a pencil's threads lie in one warp and pencil kernels launch whole warps
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 template <typename T> __host__ __device__ constexpr int pencil_ld(int n) {
   return n + (n >> ((sizeof(cpx<T>) == 8) ? 4 : 3)) + 2;
@@ -43,10 +44,15 @@ template <typename T> __host__ __device__ constexpr int pencil_ld(int n) {
 template <typename T> struct Tile { static constexpr int C = (sizeof(T) == 4) ? 16 : 8; };
 // Pencils per CTA: about 256 threads, with the pencil tile inside the 48 KB of
 // dynamic shared memory a launch gets without an opt-in attribute.
+// Whole warps per CTA (a multiple of 32 / TPC pencils), so that the pencil exchanges
+// synchronise only their warp.
 template <typename T, int N> struct PencilsPerCta {
-  static constexpr int by_threads = (Plan<N>::TPC >= 256) ? 1 : 256 / Plan<N>::TPC;
+  static_assert(Plan<N>::TPC <= 32 && 32 % Plan<N>::TPC == 0, "a pencil's threads lie in one warp");
+  static constexpr int unit = 32 / Plan<N>::TPC;  // pencils per warp
+  static constexpr int by_threads = 256 / Plan<N>::TPC;
   static constexpr int by_smem = (48 * 1024) / (pencil_ld<T>(N) * (int)sizeof(cpx<T>));
-  static constexpr int v = by_threads < by_smem ? by_threads : (by_smem > 0 ? by_smem : 1);
+  static constexpr int raw = by_threads < by_smem ? by_threads : by_smem;
+  static constexpr int v = raw >= unit ? raw - raw % unit : unit;
 };
 
 // ---------------------------------------------------------------- strided pass
@@ -135,7 +141,7 @@ __device__ __forceinline__ void zf_r2c_body(const T* __restrict__ q, const T* __
   fft<T, false, N2>(v, t, twh, x);  // ends with a barrier after its last reads
 #pragma unroll
   for (int i = 0; i < E; i++) x.put(t + TPC * i, v[i]);
-  __syncthreads();
+  __syncwarp();
   const T h = T(0.5);
   cpx<T>* out = spec + pc * (N2 + 1);
 #pragma unroll
@@ -188,7 +194,7 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
     x.put(k, valid ? in[k] : mk<T>(T(0), T(0)));
   }
   if (t == 0) x.put(N2, valid ? in[N2] : mk<T>(T(0), T(0)));
-  __syncthreads();
+  __syncwarp();
   cpx<T> v[E];
 #pragma unroll
   for (int i = 0; i < E; i++) {
@@ -199,7 +205,7 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
     const cpx<T> d = rot90<true>(cmulc(csub(xk, xc), twf[k]));
     v[i] = cadd(cadd(xk, xc), d);
   }
-  __syncthreads();
+  __syncwarp();
   fft<T, true, N2>(v, t, twh, x);
   if (!valid) return;
   const long long o = pc * N2;

@@ -36,6 +36,9 @@ template <int NY, int NZ, int YC_ = (NZ / 2 < 64 ? NZ / 2 : 64), class YPL_ = Pl
   static_assert(N2 % YC == 0 && YC % 32 == 0, "column rounds");
   static_assert(YT <= 32 && THREADS % ZT == 0 && ROWS % 2 == 0, "thread split");
   static_assert(N2 >= 16, "swizzle blocks of 16");
+  // rows are warp-local and the repeated rows past the last one fill whole warps, which
+  // skip the row phase
+  static_assert(32 % ZT == 0 && ((NY % ROWS) * ZT) % 32 == 0, "warp-local rows");
 };
 
 // One column of the plane for the Stockham exchanges: a regular column (kz < N2) under
@@ -50,12 +53,14 @@ struct PColS {
   __device__ __forceinline__ void sync() const { __syncthreads(); }
 };
 
+// A row and the threads that transform it lie in one warp (ZT threads per row, 32/ZT rows
+// per warp), so the row exchanges need only the warp to synchronise.
 struct PRowS {
   float2* w;  // row base W + y * N2
   int y;
   __device__ __forceinline__ void put(int pos, float2 z) { w[pswz(y, pos)] = z; }
   __device__ __forceinline__ float2 get(int pos) const { return w[pswz(y, pos)]; }
-  __device__ __forceinline__ void sync() const { __syncthreads(); }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
 // Column role of this thread in a round: regular column kz (or -1 for the Nyquist
@@ -118,8 +123,8 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
     const int rr = threadIdx.x / ZT;
 #pragma unroll 1
     for (int r0 = 0; r0 < NY; r0 += R::ROWS) {
-      const bool dup = (r0 + rr >= NY);  // past the last row: repeat it, no global stores
-      const int y = dup ? NY - 1 : r0 + rr;
+      if (r0 + rr >= NY) continue;  // past the last row: whole warps, idle in this round
+      const int y = r0 + rr;
       PRowS x{W + y * N2, y};
       const long long off = (rowbase + y) * N2;  // float2 index of the row's first pair
       float2 v[ZE];
@@ -141,14 +146,14 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
           const float2 d = rot90<true>(cmulc(csub(xk, xc), twz[k]));
           v[i] = cadd(cadd(xk, xc), d);
         }
-        __syncthreads();  // every read of the row precedes the transform's writes
+        __syncwarp();  // every read of the row precedes the transform's writes
         fft<float, true, N2, typename R::ZPL>(v, t, twh, x);
         float2* q2 = reinterpret_cast<float2*>(s.out) + off;
 #pragma unroll
         for (int i = 0; i < ZE; i++) {
           v[i].x *= bc[i].x;
           v[i].y *= bc[i].y;
-          if (!dup) q2[t + ZT * i] = v[i];
+          q2[t + ZT * i] = v[i];
         }
       }
       if (Bfwd) {
@@ -168,11 +173,11 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
             v[i].y *= b.y;
           }
         }
-        __syncthreads();  // the inverse's reads of this row are complete
+        __syncwarp();  // the inverse's reads of this row are complete
         fft<float, false, N2, typename R::ZPL>(v, t, twh, x);
 #pragma unroll
         for (int i = 0; i < ZE; i++) x.put(t + ZT * i, v[i]);
-        __syncthreads();
+        __syncwarp();
         const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);
         const float h = 0.5f;
 #pragma unroll
@@ -183,14 +188,15 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
           const float2 od = cscale(rot90<false>(csub(v[i], zc)), h);
           v[i] = cadd(ev, cmul(twz[k], od));
         }
-        __syncthreads();
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < ZE; i++) x.put(t + ZT * i, v[i]);
-        if (t == 0 && !dup) Wn[y] = nyq;
+        if (t == 0) Wn[y] = nyq;
       }
-      __syncthreads();
+      __syncwarp();  // the row's shared-memory traffic is done before the warp moves on
     }
   }
+  __syncthreads();  // the columns read every row
   if (!Bfwd) return;  // last step: q_Ns stored, nothing to transform forward
 
   // ---- y forward: shared memory -> transform -> HBM
