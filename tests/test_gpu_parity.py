@@ -305,6 +305,35 @@ def test_lamellar_scft_32cubed_50_steps():
     assert _rel(obs["H"].real, Href) <= 1e-11
 
 
+def test_lamellar_scft_32cubed_50_steps_fp32_error_table():
+    """The same 50-step trajectory in FP32-mixed against the FP64 oracle trajectory: the
+    error per quantity after 50 updates (printed; bounds from the one-solve tolerance 2e-5
+    carried through 50 relaxation steps of lambda = 0.1, which contract the field error)."""
+    w = wl.LAM32
+    wp, wm = wl.fields(w)
+    with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, FP32) as s:
+        s.set_fields(wp, wm)
+        for it in range(w.steps):
+            s.solve()
+            ref = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL)
+            s.field_step(w.lam)
+            wp, wm = o.scft_euler_step(wp, wm, ref.phiA, ref.phiB, w.chiN, w.lam)
+        s.solve()
+        obs = s.observables()
+        phiA, phiB = s.densities()
+        gp, gm = s.get_fields()
+    ref = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL)
+    Href = o.hamiltonian(wp, wm, ref.lnQ, w.chiN, w.C, w.n, w.L, o.SCFT_REAL)
+    V = float(np.prod(w.L))
+    err = {"Q rel": _rel(obs["Q"].real, ref.Q), "lnQ abs": abs(obs["lnQ"].real - ref.lnQ),
+           "h abs": abs(obs["H"].real - Href) / (w.C * V),
+           "phi abs": max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB))),
+           "W+ abs": np.max(np.abs(gp - wp)), "W- abs": np.max(np.abs(gm - wm))}
+    print("\nFP32-mixed after 50 SCFT steps: " + ", ".join(f"{k} {v:.2e}" for k, v in err.items()))
+    assert err["Q rel"] <= 1e-4 and err["lnQ abs"] <= 1e-4 and err["h abs"] <= 1e-4
+    assert err["phi abs"] <= 1e-4 and err["W+ abs"] <= 1e-4 and err["W- abs"] <= 1e-4
+
+
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_gyroid_128cubed_full_size(prec):
     """The 128^3 gyroid-seeded SCFT workload (Ns=100, fA=0.35, chiN=18) at full size:
