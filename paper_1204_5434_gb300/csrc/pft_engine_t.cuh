@@ -886,12 +886,14 @@ class EngineT : public Engine {
   }
 
   // ------------------------------------------------------ 4th-order scheme
-  // One contour step of Eq. 13 for both propagators, six members per step:
-  //   0, 1  A(ds) q_{s-1} and A(ds) qd_{s-1}                  -> rq[0], rq[1]
-  //   2, 3  first A(ds/2) of each (z inverse fused with the z forward of the second)
-  //   4, 5  second A(ds/2), stored as (4 A(ds/2)A(ds/2) q - A(ds) q) / 3 -> q_s, qd_s
-  // Launches per step: z forward, y, x (D), y inverse of members 0-3; z inverse of 0-1;
-  // fused z inverse / z forward of 2-3; y, x (D/2), y inverse and z inverse of 4-5.
+  // One contour step of Eq. 13 for both propagators, three members per propagator
+  // (entries 3p .. 3p+2 of a step, p = 0 for q and 1 for qd):
+  //   3p      A(ds) of the previous slice                          -> rq[p]
+  //   3p + 1  first A(ds/2) (z inverse fused with the z forward of the second)
+  //   3p + 2  second A(ds/2), stored as (4 A(ds/2)A(ds/2) q - A(ds) q) / 3 -> q_s, qd_s
+  // Per step and propagator (one chain per stream): z forward, y, x (D), y inverse of the
+  // first two members; z inverse of the full step; fused z inverse / z forward of the
+  // first half step; y, x (D/2), y inverse and combining z inverse of the second.
   cudaError_t prepare_rqm4(CtxData& c) {
     const size_t we = (c.kind == PFT_SCFT_REAL ? sizeof(T) : sizeof(Z));
     const size_t slice = (size_t)c.M * we;
@@ -937,9 +939,9 @@ class EngineT : public Engine {
         for (int p = 0; p < 2; p++) {
           const void* Bf = inA[p] ? c.BA : c.BB;
           const void* Bh = inA[p] ? c.BAh : c.BBh;
-          BatchStep& f = e6[p];
-          BatchStep& h1 = e6[2 + p];
-          BatchStep& h2 = e6[4 + p];
+          BatchStep& f = e6[3 * p];       // entries of one propagator are contiguous:
+          BatchStep& h1 = e6[3 * p + 1];  // full step, first and second half step
+          BatchStep& h2 = e6[3 * p + 2];
           f.in = in[p];
           f.B = Bf;
           f.out = rqs[p];
@@ -976,16 +978,25 @@ class EngineT : public Engine {
     g.nzh = c.nzh;
     const BatchStep* st = (const BatchStep*)c.steps2;
     cudaError_t e;
+    // one chain per propagator on two streams, three members per step (full step, first
+    // and second half step)
+    if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream2, c.fork_ev, 0)) != cudaSuccess) return e;
     for (int s = 1; s <= c.Ns; s++) {
       mark(c, KK_PAIR_STEP);
-      const BatchStep* e6 = st + (size_t)6 * (s - 1);
-      if ((e = batch_zf(g, e6, 4, c.stream)) != cudaSuccess) return e;
-      if ((e = batch_mid(g, e6, 4, c.stream)) != cudaSuccess) return e;
-      if ((e = batch_zi(g, e6, 2, 0, c.stream)) != cudaSuccess) return e;
-      if ((e = batch_zz(g, e6 + 2, 2, c.stream)) != cudaSuccess) return e;
-      if ((e = batch_mid(g, e6 + 4, 2, c.stream)) != cudaSuccess) return e;
-      if ((e = batch_zi(g, e6 + 4, 2, 3, c.stream)) != cudaSuccess) return e;
+      for (int p = 0; p < 2; p++) {
+        cudaStream_t sm = p ? c.stream2 : c.stream;
+        const BatchStep* e3 = st + (size_t)6 * (s - 1) + 3 * p;
+        if ((e = batch_zf(g, e3, 2, sm)) != cudaSuccess) return e;
+        if ((e = batch_mid(g, e3, 2, sm)) != cudaSuccess) return e;
+        if ((e = batch_zi(g, e3, 1, 0, sm)) != cudaSuccess) return e;
+        if ((e = batch_zz(g, e3 + 1, 1, sm)) != cudaSuccess) return e;
+        if ((e = batch_mid(g, e3 + 2, 1, sm)) != cudaSuccess) return e;
+        if ((e = batch_zi(g, e3 + 2, 1, 3, sm)) != cudaSuccess) return e;
+      }
     }
+    if ((e = cudaEventRecord(c.join_ev, c.stream2)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
     if ((e = solve_mid(c)) != cudaSuccess) return e;
     mark(c, KK_QUADRATURE);
     const int blocks = c.sms * 8;
