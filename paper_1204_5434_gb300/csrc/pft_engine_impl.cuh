@@ -570,30 +570,27 @@ struct AdjChain {
   int blockA;        // the split step lies in the A block
 };
 
+// One chain per launch (the two chains run on two streams), each with its own gradient
+// accumulators dwA, dwB.
 template <typename T>
-__global__ void __launch_bounds__(PW_THREADS) k_adjoint_update(AdjChain c0, AdjChain c1,
-                                                               const double* __restrict__ GA,
+__global__ void __launch_bounds__(PW_THREADS) k_adjoint_update(AdjChain c, const double* __restrict__ GA,
                                                                const double* __restrict__ GB,
                                                                const double* __restrict__ s, double ds,
                                                                double* __restrict__ dwA, double* __restrict__ dwB,
                                                                long long M) {
   const double f = ds / s[S_Q];
   const double h = -0.5 * ds;
+  double* __restrict__ dw = c.blockA ? dwA : dwB;
+  const double g0 = f * c.cA, g1 = f * c.cB;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
-    const double ga = GA[i], gb = GB[i];
-    double a = dwA[i], b = dwB[i];
-    for (int ch = 0; ch < 2; ch++) {
-      const AdjChain& c = ch ? c1 : c0;
-      const T lam = ((const T*)c.lam)[i];
-      const T z = ((const T*)c.z)[i];
-      const T B = ((const T*)c.B)[i];
-      const double term = h * (widen(lam * ((const T*)c.qk)[i]) + widen(B * ((const T*)c.qk1)[i] * z));
-      if (c.blockA) a += term; else b += term;
-      const double g = f * (c.cA * ga + c.cB * gb);
-      ((T*)c.lam_next)[i] = (T)((double)(B * z) + g * (double)((const T*)c.src)[i]);
-    }
-    dwA[i] = a;
-    dwB[i] = b;
+    const T lam = ((const T*)c.lam)[i];
+    const T z = ((const T*)c.z)[i];
+    const T B = ((const T*)c.B)[i];
+    dw[i] += h * (widen(lam * ((const T*)c.qk)[i]) + widen(B * ((const T*)c.qk1)[i] * z));
+    double g = 0.0;
+    if (g0 != 0.0) g += g0 * GA[i];
+    if (g1 != 0.0) g += g1 * GB[i];
+    ((T*)c.lam_next)[i] = (T)((double)(B * z) + g * (double)((const T*)c.src)[i]);
   }
 }
 
@@ -606,15 +603,13 @@ __global__ void __launch_bounds__(PW_THREADS) k_adjoint_init(T* __restrict__ lam
                                                              const double* __restrict__ GB,
                                                              const double* __restrict__ s, double ds, double cAl,
                                                              double cBl, double cAm, double cBm,
-                                                             double* __restrict__ dwA, double* __restrict__ dwB,
-                                                             long long M) {
+                                                             double* __restrict__ dw, long long M) {
   const double f = ds / s[S_Q];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
     const double ga = GA[i], gb = GB[i];
     lam[i] = (T)(f * (cAl * ga + cBl * gb) * (double)qd0[i]);
     mu[i] = (T)(f * (cAm * ga + cBm * gb) * (double)q0[i]);
-    dwA[i] = 0.0;
-    dwB[i] = 0.0;
+    for (int j = 0; j < 4; j++) dw[(long long)j * M + i] = 0.0;
   }
 }
 
@@ -630,9 +625,9 @@ static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_gamma(const doubl
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
-// dL/dW+ = dwA + dwB + gamma (phiA + phiB)/M, dL/dW- = dwB - dwA + gamma (phiB - phiA)/M.
-static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_finish(const double* __restrict__ dwA,
-                                                                      const double* __restrict__ dwB,
+// dL/dW+ = dwA + dwB + gamma (phiA + phiB)/M, dL/dW- = dwB - dwA + gamma (phiB - phiA)/M,
+// dwA and dwB the sums of the two chains' accumulators (dw[0..1] chain 0, dw[2..3] chain 1).
+static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_finish(const double* __restrict__ dw,
                                                                       const double* __restrict__ phiA,
                                                                       const double* __restrict__ phiB,
                                                                       const double* __restrict__ gamma, double invM,
@@ -640,7 +635,7 @@ static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_finish(const doub
                                                                       double* __restrict__ dwm, long long M) {
   const double gm = gamma[0] * invM;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
-    const double a = dwA[i] + gm * phiA[i], b = dwB[i] + gm * phiB[i];
+    const double a = dw[i] + dw[2 * M + i] + gm * phiA[i], b = dw[M + i] + dw[3 * M + i] + gm * phiB[i];
     dwp[i] = a + b;
     dwm[i] = b - a;
   }

@@ -788,8 +788,8 @@ class EngineT : public Engine {
     if (c.kind != PFT_SCFT_REAL || !c.qdh) return cudaErrorNotSupported;
     const size_t slice = (size_t)c.M * sizeof(T);
     cudaError_t e;
-    if (!c.adj) {
-      const size_t bytes = 6 * slice + 2 * (size_t)c.M * sizeof(double);
+    if (!c.adj) {  // lambda and mu ping-pong, the two z slices, four FP64 accumulators
+      const size_t bytes = 6 * slice + 4 * (size_t)c.M * sizeof(double);
       if ((e = cudaMalloc(&c.adj, bytes)) != cudaSuccess) return e;
       c.bytes += bytes;
     }
@@ -798,8 +798,7 @@ class EngineT : public Engine {
     T* mu[2] = {(T*)(a + 2 * slice), (T*)(a + 3 * slice)};
     T* z0 = (T*)(a + 4 * slice);
     T* z1 = (T*)(a + 5 * slice);
-    double* dwA = (double*)(a + 6 * slice);
-    double* dwB = dwA + c.M;
+    double* dw = (double*)(a + 6 * slice);  // [4][M]: dwA, dwB of chain 0, then of chain 1
     const char* hist = (const char*)c.hist;
     const char* qdh = (const char*)c.qdh;
     auto qs = [&](int j) { return (const T*)(hist + (size_t)j * slice); };
@@ -837,15 +836,13 @@ class EngineT : public Engine {
     trapezoid_weight(c.Ns, c.Ns, c.NsA, &cA, &cB);
     trapezoid_weight(0, c.Ns, c.NsA, &cAm, &cBm);
     k_adjoint_init<T><<<c.npart, PW_THREADS, 0, c.stream>>>(lam[0], mu[0], qds(0), qs(0), GA, GB, c.scal, c.ds, cA, cB,
-                                                            cAm, cBm, dwA, dwB, c.M);
+                                                            cAm, cBm, dw, c.M);
     const BatchStep* st = (const BatchStep*)c.stepsa;
+    // the two adjoint chains on two streams
+    if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream2, c.fork_ev, 0)) != cudaSuccess) return e;
     for (int k = c.Ns; k >= 1; k--) {
       const BatchStep* ss = st + (size_t)2 * (k - 1);
-      if ((e = batch_zf(g, ss, 2, c.stream)) != cudaSuccess) return e;
-      if ((e = batch_mid(g, ss, 2, c.stream)) != cudaSuccess) return e;
-      const long long npen = (long long)c.n[0] * c.n[1];
-      PFT_BATCH_HALF(c.n[2] / 2, e = (bzi_c2r<N, 2>(ss, npen, 2, c.stream)));
-      if (e != cudaSuccess) return e;
       const int cur = (c.Ns - k) & 1;
       AdjChain c0, c1;
       c0.lam = lam[cur];
@@ -866,13 +863,25 @@ class EngineT : public Engine {
       c1.src = qs(c.Ns - k + 1);
       trapezoid_weight(c.Ns - k + 1, c.Ns, c.NsA, &c1.cA, &c1.cB);
       c1.blockA = (c.Ns + 1 - k <= c.NsA) ? 1 : 0;
-      k_adjoint_update<T><<<c.npart, PW_THREADS, 0, c.stream>>>(c0, c1, GA, GB, c.scal, c.ds, dwA, dwB, c.M);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      const long long npen = (long long)c.n[0] * c.n[1];
+      for (int ch = 0; ch < 2; ch++) {
+        cudaStream_t sm = ch ? c.stream2 : c.stream;
+        const BatchStep* sc = ss + ch;
+        if ((e = batch_zf(g, sc, 1, sm)) != cudaSuccess) return e;
+        if ((e = batch_mid(g, sc, 1, sm)) != cudaSuccess) return e;
+        PFT_BATCH_HALF(c.n[2] / 2, e = (bzi_c2r<N, 2>(sc, npen, 1, sm)));
+        if (e != cudaSuccess) return e;
+        k_adjoint_update<T><<<c.npart, PW_THREADS, 0, sm>>>(ch ? c1 : c0, GA, GB, c.scal, c.ds, dw + 2 * ch * c.M,
+                                                           dw + (2 * ch + 1) * c.M, c.M);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
     }
+    if ((e = cudaEventRecord(c.join_ev, c.stream2)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
     k_adjoint_gamma<<<c.npart, PW_THREADS, 0, c.stream>>>(GA, GB, (const double*)c.accA, (const double*)c.accB, c.M,
                                                          c.partials);
     k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_GAMMA);
-    k_adjoint_finish<<<c.npart, PW_THREADS, 0, c.stream>>>(dwA, dwB, (const double*)c.accA, (const double*)c.accB,
+    k_adjoint_finish<<<c.npart, PW_THREADS, 0, c.stream>>>(dw, (const double*)c.accA, (const double*)c.accB,
                                                           c.scal + S_GAMMA, 1.0 / (double)c.M, dwp, dwm, c.M);
     return cudaGetLastError();
   }
