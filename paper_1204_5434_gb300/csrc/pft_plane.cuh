@@ -8,8 +8,13 @@
 //   columns: y forward transform, results stored from registers to HBM.
 // Shared memory holds kz < nz/2 of every ky under an XOR swizzle (conflict-free for the
 // column accesses, a warp on 32 consecutive kz of one ky, and for the two access
-// patterns of the 8-thread row transforms, two rows per half-warp); the Nyquist column
-// kz = nz/2 sits in a separate array.  Real fields (SCFT), FP32 propagators.
+// patterns of the 8-thread row transforms, two rows per half-warp).
+// The kz = 0 and kz = nz/2 columns of a real plane are real in y, so the two ride in one
+// complex column, X0 + i XN: its y inverse gives x0 + i xN (the row's DC and Nyquist
+// inputs, both real), the rows store DC + i Nyquist in slot kz = 0, and the y forward of
+// that column is split by Hermitian symmetry, X0[k] = (Z[k] + conj Z[-k]) / 2 and
+// XN[k] = -i (Z[k] - conj Z[-k]) / 2.  Every thread owns a regular column: 16 warps at
+// 128^3, 8 at 64^3.  Real fields (SCFT), FP32 propagators.
 #pragma once
 #include "pft_batch.cuh"
 
@@ -30,9 +35,10 @@ template <int NY, int NZ, int YC_ = (NZ / 2 < 64 ? NZ / 2 : 64), class YPL_ = Pl
   static constexpr int ZT = ZPL::TPC, ZE = ZPL::E;
   static constexpr int YC = YC_;                    // regular columns per round
   static constexpr int CR = N2 / YC;                // column rounds
-  static constexpr int THREADS = YC * YT + 32;      // plus one warp for the Nyquist column
+  static constexpr int THREADS = YC * YT;
   static constexpr int ROWS = THREADS / ZT;         // rows per round
-  static constexpr size_t SMEM = ((size_t)NY * N2 + 2 * NY) * sizeof(float2);
+  // the plane (kz < N2) and the packed column's forward transform
+  static constexpr size_t SMEM = ((size_t)NY * N2 + NY) * sizeof(float2);
   static_assert(N2 % YC == 0 && YC % 32 == 0, "column rounds");
   static_assert(YT <= 32 && THREADS % ZT == 0 && ROWS % 2 == 0, "thread split");
   static_assert(N2 >= 16, "swizzle blocks of 16");
@@ -41,13 +47,12 @@ template <int NY, int NZ, int YC_ = (NZ / 2 < 64 ? NZ / 2 : 64), class YPL_ = Pl
   static_assert(32 % ZT == 0 && ((NY % ROWS) * ZT) % 32 == 0, "warp-local rows");
 };
 
-// One column of the plane for the Stockham exchanges: a regular column (kz < N2) under
-// the swizzle, or a linear array (the Nyquist column, or scratch for idle threads).
+// One column of the plane (kz < N2, under the swizzle) for the Stockham exchanges.
 struct PColS {
-  float2* w;    // plane base, or the linear array
-  int kz;       // column, or -1 for a linear array
+  float2* w;  // plane base
+  int kz;
   int n2;
-  __device__ __forceinline__ int at(int pos) const { return kz < 0 ? pos : pos * n2 + pswz(pos, kz); }
+  __device__ __forceinline__ int at(int pos) const { return pos * n2 + pswz(pos, kz); }
   __device__ __forceinline__ void put(int pos, float2 z) { w[at(pos)] = z; }
   __device__ __forceinline__ float2 get(int pos) const { return w[at(pos)]; }
   __device__ __forceinline__ void sync() const { __syncthreads(); }
@@ -63,20 +68,6 @@ struct PRowS {
   __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
-// Column role of this thread in a round: regular column kz (or -1 for the Nyquist
-// column, -2 for an idle thread) and its position index t within the column.
-template <class R> __device__ __forceinline__ void col_role(int round, int& kz, int& t) {
-  const int tid = threadIdx.x;
-  if (tid < R::YC * R::YT) {
-    kz = round * R::YC + tid % R::YC;
-    t = tid / R::YC;
-  } else {
-    const int e = tid - R::YC * R::YT;
-    t = e % R::YT;
-    kz = (round == 0 && e < R::YT) ? -1 : -2;
-  }
-}
-
 // MODE 0: first step (rows from q_0 = st.in, x B, z forward, y forward to HBM).
 // MODE 1: a full step (y inverse from HBM, rows: z inverse, x B, store q, then if
 //         st.Bnext: x Bnext, z forward; y forward to HBM).
@@ -89,8 +80,7 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* W = reinterpret_cast<float2*>(smraw);
-  float2* Wn = W + NY * N2;      // Nyquist column
-  float2* Wd = Wn + NY;          // scratch of idle threads
+  float2* Wd = W + NY * N2;  // the packed column's forward transform, for the split
   const int p = blockIdx.x;
   float2* g = reinterpret_cast<float2*>(s.spec) + (long long)p * NY * NZH;
   const float2* twy = (const float2*)s.tw[1];
@@ -98,21 +88,29 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
   const float2* twh = (const float2*)s.tw[3];
   const long long rowbase = (long long)p * NY;
   const float* Bfwd = (MODE == 0) ? (const float*)s.B : (const float*)s.Bnext;
+  const int ct = threadIdx.x / YC;  // position index within a column
+  const int cc = threadIdx.x % YC;  // column within a round
 
   if (MODE == 1) {
-    // ---- y inverse: HBM -> registers -> transform -> shared memory
+    // ---- y inverse.  Column kz = 0 carries X0 + i XN (X0, XN the kz = 0 and kz = N2
+    // columns, each Hermitian in ky): its inverse is x0 + i xN with x0, xN real.
 #pragma unroll 1
     for (int round = 0; round < R::CR; round++) {
-      int kz, t;
-      col_role<R>(round, kz, t);
-      const int gk = kz >= 0 ? kz : (kz == -1 ? N2 : 0);
+      const int kz = round * YC + cc;
       float2 v[YE];
 #pragma unroll
-      for (int i = 0; i < YE; i++) v[i] = g[(long long)(t + YT * i) * NZH + gk];
-      PColS x{kz >= 0 ? W : (kz == -1 ? Wn : Wd), kz >= 0 ? kz : -1, N2};
-      fft<float, true, NY, YPL>(v, t, twy, x);
+      for (int i = 0; i < YE; i++) v[i] = g[(long long)(ct + YT * i) * NZH + kz];
+      if (kz == 0) {
 #pragma unroll
-      for (int i = 0; i < YE; i++) x.put(t + YT * i, v[i]);
+        for (int i = 0; i < YE; i++) {
+          const float2 xn = g[(long long)(ct + YT * i) * NZH + N2];
+          v[i] = make_float2(v[i].x - xn.y, v[i].y + xn.x);
+        }
+      }
+      PColS x{W, kz, N2};
+      fft<float, true, NY, YPL>(v, ct, twy, x);
+#pragma unroll
+      for (int i = 0; i < YE; i++) x.put(ct + YT * i, v[i]);
     }
     __syncthreads();
   }
@@ -141,8 +139,14 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
 #pragma unroll
         for (int i = 0; i < ZE; i++) {
           const int k = t + ZT * i;
-          const float2 xk = x.get(k);
-          const float2 xc = cconj(k == 0 ? Wn[y] : x.get(N2 - k));
+          float2 xk = x.get(k);
+          float2 xc;
+          if (k == 0) {  // packed x0 + i xN of this row: both real
+            xc = make_float2(xk.y, 0.f);
+            xk.y = 0.f;
+          } else {
+            xc = cconj(x.get(N2 - k));
+          }
           const float2 d = rot90<true>(cmulc(csub(xk, xc), twz[k]));
           v[i] = cadd(cadd(xk, xc), d);
         }
@@ -178,7 +182,6 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
 #pragma unroll
         for (int i = 0; i < ZE; i++) x.put(t + ZT * i, v[i]);
         __syncwarp();
-        const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);
         const float h = 0.5f;
 #pragma unroll
         for (int i = 0; i < ZE; i++) {
@@ -186,12 +189,13 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
           const float2 zc = cconj(x.get(k == 0 ? 0 : N2 - k));
           const float2 ev = cscale(cadd(v[i], zc), h);
           const float2 od = cscale(rot90<false>(csub(v[i], zc)), h);
-          v[i] = cadd(ev, cmul(twz[k], od));
+          float2 X = cadd(ev, cmul(twz[k], od));
+          if (k == 0) X.y = v[i].x - v[i].y;  // DC (real) + i Nyquist (real)
+          v[i] = X;
         }
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < ZE; i++) x.put(t + ZT * i, v[i]);
-        if (t == 0) Wn[y] = nyq;
       }
       __syncwarp();  // the row's shared-memory traffic is done before the warp moves on
     }
@@ -199,23 +203,37 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
   __syncthreads();  // the columns read every row
   if (!Bfwd) return;  // last step: q_Ns stored, nothing to transform forward
 
-  // ---- y forward: shared memory -> transform -> HBM
+  // ---- y forward; the packed column's transform Z = X0 + i XN is split after a barrier:
+  // X0[k] = (Z[k] + conj Z[-k]) / 2, XN[k] = -i (Z[k] - conj Z[-k]) / 2
 #pragma unroll 1
   for (int round = 0; round < R::CR; round++) {
-    int kz, t;
-    col_role<R>(round, kz, t);
-    PColS x{kz >= 0 ? W : (kz == -1 ? Wn : Wd), kz >= 0 ? kz : -1, N2};
+    const int kz = round * YC + cc;
+    PColS x{W, kz, N2};
     float2 v[YE];
 #pragma unroll
-    for (int i = 0; i < YE; i++) v[i] = x.get(t + YT * i);
+    for (int i = 0; i < YE; i++) v[i] = x.get(ct + YT * i);
     __syncthreads();
-    fft<float, false, NY, YPL>(v, t, twy, x);
-    if (kz != -2) {
-      const int gk = kz >= 0 ? kz : N2;
+    fft<float, false, NY, YPL>(v, ct, twy, x);
+    if (kz == 0) {
 #pragma unroll
-      for (int i = 0; i < YE; i++) g[(long long)(t + YT * i) * NZH + gk] = v[i];
+      for (int i = 0; i < YE; i++) Wd[ct + YT * i] = v[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < YE; i++) g[(long long)(ct + YT * i) * NZH + kz] = v[i];
+    }
+  }
+  __syncthreads();
+  if (cc == 0) {
+#pragma unroll
+    for (int i = 0; i < YE; i++) {
+      const int k = ct + YT * i;
+      const float2 z = Wd[k];
+      const float2 zm = cconj(Wd[(NY - k) & (NY - 1)]);
+      g[(long long)k * NZH] = cscale(cadd(z, zm), 0.5f);
+      g[(long long)k * NZH + N2] = cscale(rot90<false>(csub(z, zm)), 0.5f);
     }
   }
 }
+
 
 }  // namespace pft
