@@ -14,7 +14,9 @@
 // inputs, both real), the rows store DC + i Nyquist in slot kz = 0, and the y forward of
 // that column is split by Hermitian symmetry, X0[k] = (Z[k] + conj Z[-k]) / 2 and
 // XN[k] = -i (Z[k] - conj Z[-k]) / 2.  Every thread owns a regular column: 16 warps at
-// 128^3, 8 at 64^3.  Real fields (SCFT), FP32 propagators.
+// 128^3, 8 at 64^3.  B_s of the plane is copied to shared memory asynchronously while the
+// y inverse runs; the twiddle tables are copied to shared memory at the start.  Real
+// fields (SCFT), FP32 propagators.
 #pragma once
 #include "pft_batch.cuh"
 
@@ -37,14 +39,22 @@ template <int NY, int NZ, int YC_ = (NZ / 2 < 64 ? NZ / 2 : 64), class YPL_ = Pl
   static constexpr int CR = N2 / YC;                // column rounds
   static constexpr int THREADS = YC * YT;
   static constexpr int ROWS = THREADS / ZT;         // rows per round
-  // the plane (kz < N2) and the packed column's forward transform
-  static constexpr size_t SMEM = ((size_t)NY * N2 + NY) * sizeof(float2);
+  // the plane (kz < N2), the packed column's forward transform, B_s of the plane (fetched
+  // while the y inverse runs) and the y, z, z/2 twiddles
+  static constexpr size_t SMEM = ((size_t)NY * N2 + NY) * sizeof(float2) + (size_t)NY * NZ * sizeof(float) +
+                                 (size_t)(NY + NZ + N2) * sizeof(float2);
+  // B rows in 16-byte chunks: chunk c of row y sits at c ^ bsw(y), so that the warp's rows
+  // (32 / ZT of them, ZT / 2 chunks each per access) spread over the 8 chunk slots of a
+  // 128-byte bank line
+  static constexpr int BROWS = 16 / ZT;
+  __device__ static __forceinline__ int bsw(int y) { return (y % BROWS) * (ZT / 2); }
   static_assert(N2 % YC == 0 && YC % 32 == 0, "column rounds");
   static_assert(YT <= 32 && THREADS % ZT == 0 && ROWS % 2 == 0, "thread split");
   static_assert(N2 >= 16, "swizzle blocks of 16");
   // rows are warp-local and the repeated rows past the last one fill whole warps, which
   // skip the row phase
   static_assert(32 % ZT == 0 && ((NY % ROWS) * ZT) % 32 == 0, "warp-local rows");
+  static_assert(ZT <= 16 && 16 % ZT == 0 && NZ / 4 >= 8, "B chunk swizzle");
 };
 
 // One column of the plane (kz < N2, under the swizzle) for the Stockham exchanges.
@@ -80,16 +90,38 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* W = reinterpret_cast<float2*>(smraw);
-  float2* Wd = W + NY * N2;  // the packed column's forward transform, for the split
+  float2* Wd = W + NY * N2;                       // the packed column's forward transform
+  float* Bs = reinterpret_cast<float*>(Wd + NY);  // B_s of this plane (MODE 1)
+  float2* tws = Wd + NY + NY * NZ / 2;            // twiddles y, z, z/2
   const int p = blockIdx.x;
   float2* g = reinterpret_cast<float2*>(s.spec) + (long long)p * NY * NZH;
-  const float2* twy = (const float2*)s.tw[1];
-  const float2* twz = (const float2*)s.tw[2];
-  const float2* twh = (const float2*)s.tw[3];
   const long long rowbase = (long long)p * NY;
   const float* Bfwd = (MODE == 0) ? (const float*)s.B : (const float*)s.Bnext;
   const int ct = threadIdx.x / YC;  // position index within a column
   const int cc = threadIdx.x % YC;  // column within a round
+  if (MODE == 1) {
+    // B_s of the plane into shared memory by asynchronous 16-byte copies, waited for
+    // after the y inverse
+    constexpr int CPR = NZ / 4;  // chunks per row
+    const float* Bg = (const float*)s.B + rowbase * NZ;
+    const unsigned sb = (unsigned)__cvta_generic_to_shared(Bs);
+#pragma unroll
+    for (int c = threadIdx.x; c < NY * CPR; c += R::THREADS) {
+      const int y = c / CPR;
+      const unsigned dst = sb + (unsigned)((y * CPR + ((c % CPR) ^ R::bsw(y))) * 16);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(Bg + (long long)c * 4) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < NY + NZ + N2; i += R::THREADS) {
+    const float2* src = i < NY ? (const float2*)s.tw[1] + i
+                               : (i < NY + NZ ? (const float2*)s.tw[2] + (i - NY) : (const float2*)s.tw[3] + (i - NY - NZ));
+    tws[i] = *src;
+  }
+  const float2* twy = tws;
+  const float2* twz = tws + NY;
+  const float2* twh = tws + NY + NZ;
+  __syncthreads();
 
   if (MODE == 1) {
     // ---- y inverse.  Column kz = 0 carries X0 + i XN (X0, XN the kz = 0 and kz = N2
@@ -112,6 +144,7 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
 #pragma unroll
       for (int i = 0; i < YE; i++) x.put(ct + YT * i, v[i]);
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
   }
 
@@ -132,10 +165,6 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
 #pragma unroll
         for (int i = 0; i < ZE; i++) v[i] = q2[t + ZT * i];
       } else {
-        // the factors of this row first: their latency overlaps the inverse transform
-        const float2* b2 = reinterpret_cast<const float2*>(s.B) + off;
-#pragma unroll
-        for (int i = 0; i < ZE; i++) bc[i] = b2[t + ZT * i];
 #pragma unroll
         for (int i = 0; i < ZE; i++) {
           const int k = t + ZT * i;
@@ -153,6 +182,12 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
         __syncwarp();  // every read of the row precedes the transform's writes
         fft<float, true, N2, typename R::ZPL>(v, t, twh, x);
         float2* q2 = reinterpret_cast<float2*>(s.out) + off;
+        const float2* b2s = reinterpret_cast<const float2*>(Bs) + y * N2;
+#pragma unroll
+        for (int i = 0; i < ZE; i++) {
+          const int m = t + ZT * i;  // float2 m of the row: chunk m / 2, half m % 2
+          bc[i] = b2s[(((m >> 1) ^ R::bsw(y)) << 1) | (m & 1)];
+        }
 #pragma unroll
         for (int i = 0; i < ZE; i++) {
           v[i].x *= bc[i].x;
