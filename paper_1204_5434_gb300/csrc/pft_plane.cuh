@@ -28,6 +28,10 @@ __device__ __forceinline__ int pswz(int y, int p) {
   return (p & ~15) | ((p & 15) ^ (((p >> 4) << 1) & 15) ^ ((y & 1) ? 9 : 0));
 }
 
+// The two radices of a two-stage plan.
+template <class RR> struct Radix2;
+template <int A, int B> struct Radix2<Radices<A, B>> { static constexpr int r1 = A, r2 = B; };
+
 template <int NY, int NZ, int YC_ = (NZ / 2 < 64 ? NZ / 2 : 64), class YPL_ = Plan<NY>> struct PlaneCfg {
   static constexpr int N2 = NZ / 2;
   static constexpr int NZH = N2 + 1;
@@ -35,6 +39,7 @@ template <int NY, int NZ, int YC_ = (NZ / 2 < 64 ? NZ / 2 : 64), class YPL_ = Pl
   using ZPL = Plan<N2>;
   static constexpr int YT = YPL::TPC, YE = YPL::E;
   static constexpr int ZT = ZPL::TPC, ZE = ZPL::E;
+  static constexpr int ZR1 = Radix2<typename ZPL::R>::r1, ZR2 = Radix2<typename ZPL::R>::r2;  // row radices
   static constexpr int YC = YC_;                    // regular columns per round
   static constexpr int CR = N2 / YC;                // column rounds
   static constexpr int THREADS = YC * YT;
@@ -78,6 +83,57 @@ struct PRowS {
   __device__ __forceinline__ void sync() const { __syncwarp(); }
 };
 
+// Row transforms: two-stage plans (radix R1 then R2, N = R1 R2) whose second-stage
+// twiddles w^(r k) depend only on the thread's position t in the row; they are loaded
+// once per kernel into registers (NB2 (R2 - 1) of them) instead of once per transform.
+template <class PL> struct TwoStage;
+template <int N_, int E_, int R1_, int R2_> struct TwoStage<PlanX<N_, E_, R1_, R2_>> {
+  static constexpr int N = N_, E = E_, R1 = R1_, R2 = R2_, TPC = N_ / E_;
+  static constexpr int NB1 = E / R1, NB2 = E / R2;
+  static constexpr int NW = NB2 * (R2 - 1);
+  static_assert(R1 * R2 == N && E % R1 == 0 && E % R2 == 0, "two-stage plan");
+  // wr[b (R2 - 1) + r - 1] = tw[r k], k = (t + b TPC) mod R1
+  __device__ static __forceinline__ void load(float2 (&wr)[NW], int t, const float2* __restrict__ tw) {
+#pragma unroll
+    for (int b = 0; b < NB2; b++) {
+      const int k = (t + b * TPC) % R1;
+#pragma unroll
+      for (int r = 1; r < R2; r++) wr[b * (R2 - 1) + r - 1] = tw[r * k];
+    }
+  }
+  // the Stockham transform of fft() for this plan, twiddles from wr
+  template <bool INV, class X>
+  __device__ static __forceinline__ void run(float2 (&v)[E], int t, const float2 (&wr)[NW], X& xch) {
+#pragma unroll
+    for (int b = 0; b < NB1; b++) {
+      float2 u[R1];
+#pragma unroll
+      for (int r = 0; r < R1; r++) u[r] = v[b + r * NB1];
+      Dft<R1, INV, float2>::run(u);
+      const int base = (t + b * TPC) * R1;
+#pragma unroll
+      for (int r = 0; r < R1; r++) xch.put(base + r, u[r]);
+    }
+    xch.sync();
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = xch.get(t + TPC * i);
+    xch.sync();
+#pragma unroll
+    for (int b = 0; b < NB2; b++) {
+      float2 u[R2];
+#pragma unroll
+      for (int r = 0; r < R2; r++) u[r] = v[b + r * NB2];
+#pragma unroll
+      for (int r = 1; r < R2; r++) {
+        const float2 w = wr[b * (R2 - 1) + r - 1];
+        u[r] = INV ? cmulc(u[r], w) : cmul(u[r], w);
+      }
+      Dft<R2, INV, float2>::run(u);
+#pragma unroll
+      for (int r = 0; r < R2; r++) v[b + r * NB2] = u[r];
+    }
+  }
+};
 // MODE 0: first step (rows from q_0 = st.in, x B, z forward, y forward to HBM).
 // MODE 1: a full step (y inverse from HBM, rows: z inverse, x B, store q, then if
 //         st.Bnext: x Bnext, z forward; y forward to HBM).
@@ -152,6 +208,13 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
   {
     const int t = threadIdx.x % ZT;
     const int rr = threadIdx.x / ZT;
+    using RT = TwoStage<PlanX<N2, ZE, R::ZR1, R::ZR2>>;
+    // this thread's twiddles of the rows: the real-transform split w_nz^k, k = t + ZT i,
+    // and the second transform stage
+    float2 tz[ZE], wr[RT::NW];
+#pragma unroll
+    for (int i = 0; i < ZE; i++) tz[i] = twz[t + ZT * i];
+    RT::load(wr, t, twh);
 #pragma unroll 1
     for (int r0 = 0; r0 < NY; r0 += R::ROWS) {
       if (r0 + rr >= NY) continue;  // past the last row: whole warps, idle in this round
@@ -176,11 +239,11 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
           } else {
             xc = cconj(x.get(N2 - k));
           }
-          const float2 d = rot90<true>(cmulc(csub(xk, xc), twz[k]));
+          const float2 d = rot90<true>(cmulc(csub(xk, xc), tz[i]));
           v[i] = cadd(cadd(xk, xc), d);
         }
         __syncwarp();  // every read of the row precedes the transform's writes
-        fft<float, true, N2, typename R::ZPL>(v, t, twh, x);
+        RT::template run<true>(v, t, wr, x);
         float2* q2 = reinterpret_cast<float2*>(s.out) + off;
         const float2* b2s = reinterpret_cast<const float2*>(Bs) + y * N2;
 #pragma unroll
@@ -213,7 +276,7 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
           }
         }
         __syncwarp();  // the inverse's reads of this row are complete
-        fft<float, false, N2, typename R::ZPL>(v, t, twh, x);
+        RT::template run<false>(v, t, wr, x);
 #pragma unroll
         for (int i = 0; i < ZE; i++) x.put(t + ZT * i, v[i]);
         __syncwarp();
@@ -224,7 +287,7 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
           const float2 zc = cconj(x.get(k == 0 ? 0 : N2 - k));
           const float2 ev = cscale(cadd(v[i], zc), h);
           const float2 od = cscale(rot90<false>(csub(v[i], zc)), h);
-          float2 X = cadd(ev, cmul(twz[k], od));
+          float2 X = cadd(ev, cmul(tz[i], od));
           if (k == 0) X.y = v[i].x - v[i].y;  // DC (real) + i Nyquist (real)
           v[i] = X;
         }
@@ -258,15 +321,12 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
     }
   }
   __syncthreads();
-  if (cc == 0) {
-#pragma unroll
-    for (int i = 0; i < YE; i++) {
-      const int k = ct + YT * i;
-      const float2 z = Wd[k];
-      const float2 zm = cconj(Wd[(NY - k) & (NY - 1)]);
-      g[(long long)k * NZH] = cscale(cadd(z, zm), 0.5f);
-      g[(long long)k * NZH + N2] = cscale(rot90<false>(csub(z, zm)), 0.5f);
-    }
+  // the split, one ky per thread
+  for (int k = threadIdx.x; k < NY; k += R::THREADS) {
+    const float2 z = Wd[k];
+    const float2 zm = cconj(Wd[(NY - k) & (NY - 1)]);
+    g[(long long)k * NZH] = cscale(cadd(z, zm), 0.5f);
+    g[(long long)k * NZH + N2] = cscale(rot90<false>(csub(z, zm)), 0.5f);
   }
 }
 
