@@ -247,6 +247,26 @@ pft_status pft_adjoint(pft_ctx* ctx, const void* dL_dphiA, const void* dL_dphiB,
 pft_status pft_gradients(pft_ctx* ctx, void* dH_dwp, void* dH_dwm, double dH_dL[3],
                          double dlnQ_dL[3], pft_mem where);
 
+/* Checkpoint and resume of a run (no counterpart in the paper).  pft_save writes the
+ * state a field-update loop needs to continue bit for bit: the box L, the fields W+ and
+ * W- (float64 or complex128 as stored; W- omitted for the Edwards model), the complex
+ * Langevin noise key and counter (seed, instance, steps taken since the fields were
+ * set) and the system's parameters for validation.  File layout (little-endian): the
+ * 8 bytes "PFTCKPT1", uint32 version (1), uint32 header bytes (112), the header (n[3],
+ * Ns, kind, arch, precision as int32, 4 zero bytes; L[3], fA, chiN, C, B as float64;
+ * seed, instance as uint64; step as int64), the fields, then a 64-bit FNV-1a hash of
+ * every byte before it.
+ * The file is written to `path` through a temporary file in the same directory and
+ * renamed, so an interrupted save leaves the previous checkpoint intact.
+ * pft_load reads such a file into a context of the same system (grid, Ns, kind, arch,
+ * fA, chiN, C, B must match; the precision may differ), sets the box, the fields and
+ * the noise key and counter; a solve is needed before observables.
+ * Errors: PFT_ERR_ARG for NULL arguments or a checkpoint of another system;
+ * PFT_ERR_STATE (save) before fields are set; PFT_ERR_IO when the file cannot be
+ * written or read, is not a checkpoint, is truncated or fails its hash. */
+pft_status pft_save(pft_ctx* ctx, const char* path);
+pft_status pft_load(pft_ctx* ctx, const char* path);
+
 /* Batches of independent systems ------------------------------------------ */
 
 /* One member of a batch: its grid, chain and model, and the Philox key of its complex

@@ -1,11 +1,13 @@
 // pft_api.cu -- the extern "C" entry points declared in include/pft.h.
 #include <math.h>
+#include <stdint.h>
 #include <stdio.h>
 #include <string.h>
 
 #include <map>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "pft_engine.h"
 
@@ -410,6 +412,140 @@ pft_status pft_set_box(pft_ctx* ctx, const double L[3]) {
   for (int a = 0; a < 3; a++) d.L[a] = L[a];
   PFT_CK(ctx->eng->upload_tables(d));
   return write_volume(d);
+}
+
+// ------------------------------------------------------------------ checkpoints
+namespace {
+struct CkptHeader {
+  int32_t n[3];
+  int32_t Ns, kind, arch, prec;
+  double L[3];
+  double fA, chiN, C, B;
+  uint64_t seed, instance;
+  int64_t step;
+};
+static_assert(sizeof(CkptHeader) == 7 * 4 + 4 + 7 * 8 + 3 * 8, "checkpoint header layout");
+const char kCkptMagic[8] = {'P', 'F', 'T', 'C', 'K', 'P', 'T', '1'};
+const uint32_t kCkptVersion = 1;
+
+// 64-bit FNV-1a, continued over successive buffers
+uint64_t fnv1a(uint64_t h, const void* p, size_t n) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; i++) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+const uint64_t kFnvBasis = 14695981039346656037ull;
+
+void fill_header(const CtxData& d, CkptHeader* h) {
+  memset(h, 0, sizeof(*h));
+  for (int a = 0; a < 3; a++) {
+    h->n[a] = d.n[a];
+    h->L[a] = d.L[a];
+  }
+  h->Ns = d.Ns;
+  h->kind = (int32_t)d.kind;
+  h->arch = d.edw ? (int32_t)PFT_ARCH_EDWARDS : (int32_t)PFT_ARCH_DIBLOCK;
+  h->prec = (int32_t)d.prec;
+  h->fA = d.fA;
+  h->chiN = d.chiN;
+  h->C = d.C;
+  h->B = d.edw ? d.bC * d.C : 0.0;
+  h->seed = d.seed;
+  h->instance = d.instance;
+  h->step = d.step;
+}
+}  // namespace
+
+pft_status pft_save(pft_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  if (!d.fields_set) return fail(PFT_ERR_STATE, "pft_save before pft_set_fields");
+  const size_t b = (size_t)d.M * felem(d);
+  const int nf = d.edw ? 1 : 2;
+  std::vector<unsigned char> f((size_t)nf * b);
+  PFT_CK(cudaMemcpyAsync(f.data(), d.wp, b, cudaMemcpyDeviceToHost, d.stream));
+  if (nf == 2) PFT_CK(cudaMemcpyAsync(f.data() + b, d.wm, b, cudaMemcpyDeviceToHost, d.stream));
+  PFT_CK(cudaStreamSynchronize(d.stream));
+  CkptHeader h;
+  fill_header(d, &h);
+  const uint32_t ver = kCkptVersion, hb = (uint32_t)sizeof(CkptHeader);
+  uint64_t hash = kFnvBasis;
+  hash = fnv1a(hash, kCkptMagic, 8);
+  hash = fnv1a(hash, &ver, 4);
+  hash = fnv1a(hash, &hb, 4);
+  hash = fnv1a(hash, &h, sizeof(h));
+  hash = fnv1a(hash, f.data(), f.size());
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* fp = fopen(tmp.c_str(), "wb");
+  if (!fp) return fail(PFT_ERR_IO, std::string("cannot write ") + tmp);
+  bool ok = fwrite(kCkptMagic, 1, 8, fp) == 8 && fwrite(&ver, 4, 1, fp) == 1 && fwrite(&hb, 4, 1, fp) == 1 &&
+            fwrite(&h, sizeof(h), 1, fp) == 1 && fwrite(f.data(), 1, f.size(), fp) == f.size() &&
+            fwrite(&hash, 8, 1, fp) == 1;
+  ok = (fclose(fp) == 0) && ok;
+  if (!ok || rename(tmp.c_str(), path) != 0) {
+    remove(tmp.c_str());
+    return fail(PFT_ERR_IO, std::string("cannot write ") + path);
+  }
+  return PFT_OK;
+}
+
+pft_status pft_load(pft_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(PFT_ERR_ARG, "NULL argument");
+  CtxData& d = ctx->d;
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(PFT_ERR_IO, std::string("cannot open ") + path);
+  char magic[8];
+  uint32_t ver = 0, hb = 0;
+  CkptHeader h;
+  bool ok = fread(magic, 1, 8, fp) == 8 && memcmp(magic, kCkptMagic, 8) == 0 && fread(&ver, 4, 1, fp) == 1 &&
+            ver == kCkptVersion && fread(&hb, 4, 1, fp) == 1 && hb == sizeof(CkptHeader) &&
+            fread(&h, sizeof(h), 1, fp) == 1;
+  if (!ok) {
+    fclose(fp);
+    return fail(PFT_ERR_IO, std::string(path) + " is not a checkpoint of this format");
+  }
+  CkptHeader mine;
+  fill_header(d, &mine);
+  const bool same = h.n[0] == mine.n[0] && h.n[1] == mine.n[1] && h.n[2] == mine.n[2] && h.Ns == mine.Ns &&
+                    h.kind == mine.kind && h.arch == mine.arch && h.fA == mine.fA && h.chiN == mine.chiN &&
+                    h.C == mine.C && h.B == mine.B;
+  if (!same) {
+    fclose(fp);
+    return fail(PFT_ERR_ARG, std::string(path) + " holds the state of another system");
+  }
+  for (int a = 0; a < 3; a++) {
+    if (!(h.L[a] > 0.0) || !isfinite(h.L[a])) {
+      fclose(fp);
+      return fail(PFT_ERR_IO, std::string(path) + ": invalid box");
+    }
+  }
+  const size_t b = (size_t)d.M * felem(d);
+  const int nf = d.edw ? 1 : 2;
+  std::vector<unsigned char> f((size_t)nf * b);
+  uint64_t stored = 0;
+  ok = fread(f.data(), 1, f.size(), fp) == f.size() && fread(&stored, 8, 1, fp) == 1;
+  char extra;
+  ok = ok && fread(&extra, 1, 1, fp) == 0;
+  fclose(fp);
+  if (!ok) return fail(PFT_ERR_IO, std::string(path) + " is truncated or too long");
+  uint64_t hash = kFnvBasis;
+  hash = fnv1a(hash, kCkptMagic, 8);
+  hash = fnv1a(hash, &ver, 4);
+  hash = fnv1a(hash, &hb, 4);
+  hash = fnv1a(hash, &h, sizeof(h));
+  hash = fnv1a(hash, f.data(), f.size());
+  if (hash != stored) return fail(PFT_ERR_IO, std::string(path) + " fails its hash");
+  pft_status st = pft_set_box(ctx, h.L);
+  if (st != PFT_OK) return st;
+  st = pft_set_fields(ctx, f.data(), nf == 2 ? f.data() + b : nullptr, PFT_HOST);
+  if (st != PFT_OK) return st;
+  d.seed = h.seed;
+  d.instance = h.instance;
+  d.step = h.step;
+  return PFT_OK;
 }
 
 pft_status pft_get_box(const pft_ctx* ctx, double L[3]) {

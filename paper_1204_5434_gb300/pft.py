@@ -106,6 +106,8 @@ _SIGS = {
     "pft_set_fields": (ct.c_int, [_P, _P, _P, ct.c_int]),
     "pft_get_fields": (ct.c_int, [_P, _P, _P, ct.c_int]),
     "pft_set_box": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
+    "pft_save": (ct.c_int, [_P, ct.c_char_p]),
+    "pft_load": (ct.c_int, [_P, ct.c_char_p]),
     "pft_get_box": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
     "pft_solve": (ct.c_int, [_P]),
     "pft_get_observables": (ct.c_int, [_P, ct.POINTER(pft_obs)]),
@@ -247,6 +249,14 @@ def pft_get_fields(h, wp, wm):
 
 def pft_set_box(h, L):
     _check(_lib().pft_set_box(h, (ct.c_double * 3)(*[float(v) for v in L])), "pft_set_box")
+
+
+def pft_save(h, path):
+    _check(_lib().pft_save(h, os.fsencode(path)), "pft_save")
+
+
+def pft_load(h, path):
+    _check(_lib().pft_load(h, os.fsencode(path)), "pft_load")
 
 
 def pft_get_box(h):
@@ -546,6 +556,12 @@ class System:
 
     def set_box(self, L):
         pft_set_box(self.h, L)
+
+    def save(self, path):
+        pft_save(self.h, path)
+
+    def load(self, path):
+        pft_load(self.h, path)
 
     def gradients(self, want_fields=True):
         if want_fields:
