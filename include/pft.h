@@ -403,7 +403,8 @@ pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles);
 pft_status pft_get_march(const pft_ctx* ctx, int* march);
 
 /* Plan of the pass march in use: *plane = 1 if the y/z plane kernel runs the steps (FP32
- * real 64^3/128^3 grids), *streams = 1 if the two propagators run as two chains on two
+ * real fields with ny = nz = 64 or 128, complex fields with ny = nz = 64), *streams = 1
+ * if the two propagators run as two chains on two
  * streams.  Either pointer may be NULL.  Errors: PFT_ERR_ARG for a NULL ctx. */
 pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams);
 

@@ -1026,7 +1026,8 @@ class EngineT : public Engine {
     if constexpr (!std::is_same<T, float>::value) {
       return false;
     } else {
-      return c.kind == PFT_SCFT_REAL && c.n[1] == c.n[2] && (c.n[1] == 64 || c.n[1] == 128);
+      if (c.kind == PFT_SCFT_REAL) return c.n[1] == c.n[2] && (c.n[1] == 64 || c.n[1] == 128);
+      return c.n[1] == 64 && c.n[2] == 64;  // complex: the 64 x 64 plane kernel
     }
   }
 
@@ -1040,12 +1041,27 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
+  template <int NY, int MODE>
+  static cudaError_t launch_plane_c(const BatchStep* st, int nx, int members, cudaStream_t stream) {
+    using R = PlaneCfgC<NY, NY>;
+    auto kern = kb_plane_c2c<NY, NY, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)nx, (unsigned)members), R::THREADS, R::SMEM, stream>>>(st);
+    return cudaGetLastError();
+  }
+
   // the plane kernel over `members` consecutive entries of st
   cudaError_t batch_plane(CtxData& c, const BatchStep* st, int mode, int members, cudaStream_t sm) {
     if constexpr (!std::is_same<T, float>::value) {
       return cudaErrorNotSupported;
     } else {
       const int nx = c.n[0];
+      if (c.kind != PFT_SCFT_REAL) {
+        if (c.n[1] == 64 && c.n[2] == 64)
+          return mode ? launch_plane_c<64, 1>(st, nx, members, sm) : launch_plane_c<64, 0>(st, nx, members, sm);
+        return cudaErrorNotSupported;
+      }
       if (c.n[1] == 64)
         return mode ? launch_plane<64, 1>(st, nx, members, sm) : launch_plane<64, 0>(st, nx, members, sm);
       if (c.n[1] == 128)

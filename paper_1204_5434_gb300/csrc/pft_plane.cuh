@@ -331,4 +331,140 @@ kb_plane_r2c(const BatchStep* __restrict__ st) {
 }
 
 
+// ----------------------------------------------------------- complex fields (CL)
+// The same step for complex fields: the plane holds NY x NZ complex values (all kz), the
+// rows are complex transforms of length NZ (no real split), B is complex.  One CTA per
+// x-plane, NZ columns on YT threads each, NY rows on ZT threads each, one round of both
+// (64^3: 512 threads).  B_s of the plane is copied to shared memory by cp.async during
+// the y inverse as in the real kernel.
+template <int NY, int NZ> struct PlaneCfgC {
+  using YPL = Plan<NY>;
+  using ZPL = Plan<NZ>;
+  static constexpr int YT = YPL::TPC, YE = YPL::E;
+  static constexpr int ZT = ZPL::TPC, ZE = ZPL::E;
+  static constexpr int ZR1 = Radix2<typename ZPL::R>::r1, ZR2 = Radix2<typename ZPL::R>::r2;
+  static constexpr int THREADS = NZ * YT;
+  static constexpr int ROWS = THREADS / ZT;
+  // plane, B_s of the plane, y and z twiddles
+  static constexpr size_t SMEM = (size_t)NY * NZ * sizeof(float2) * 2 + (size_t)(NY + NZ) * sizeof(float2);
+  static constexpr int BROWS = 16 / ZT;
+  __device__ static __forceinline__ int bsw(int y) { return (y % BROWS) * (ZT / 2); }
+  static_assert(NZ % 32 == 0 && THREADS <= 1024 && ROWS == NY, "one round of columns and rows");
+  static_assert(32 % ZT == 0 && ZT <= 16 && 16 % ZT == 0 && NZ / 2 >= 8, "warp-local rows, B chunk swizzle");
+};
+
+// MODE 0: first step (rows from q_0, x B, z forward; y forward to HBM).
+// MODE 1: a full step (y inverse from HBM; rows: z inverse, x B, store q, then if
+//         st.Bnext: x Bnext, z forward; y forward to HBM).
+template <int NY, int NZ, int MODE>
+__global__ void __launch_bounds__(PlaneCfgC<NY, NZ>::THREADS, 1) kb_plane_c2c(const BatchStep* __restrict__ st) {
+  using R = PlaneCfgC<NY, NZ>;
+  constexpr int YE = R::YE, YT = R::YT, ZE = R::ZE, ZT = R::ZT;
+  const BatchStep& s = st[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* W = reinterpret_cast<float2*>(smraw);  // [NY][NZ] under the swizzle
+  float2* Bs = W + NY * NZ;                       // B_s of this plane (MODE 1)
+  float2* tws = Bs + NY * NZ;                     // twiddles y, z
+  const int p = blockIdx.x;
+  float2* g = reinterpret_cast<float2*>(s.spec) + (long long)p * NY * NZ;
+  const long long rowbase = (long long)p * NY;
+  const float2* Bfwd = (const float2*)((MODE == 0) ? s.B : s.Bnext);
+  const int ct = threadIdx.x / NZ;  // position index within a column
+  const int kz = threadIdx.x % NZ;  // column
+  if (MODE == 1) {
+    constexpr int CPR = NZ / 2;  // 16-byte chunks per row
+    const float2* Bg = (const float2*)s.B + rowbase * NZ;
+    const unsigned sb = (unsigned)__cvta_generic_to_shared(Bs);
+#pragma unroll
+    for (int c = threadIdx.x; c < NY * CPR; c += R::THREADS) {
+      const int y = c / CPR;
+      const unsigned dst = sb + (unsigned)((y * CPR + ((c % CPR) ^ R::bsw(y))) * 16);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(Bg + (long long)c * 2) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < NY + NZ; i += R::THREADS)
+    tws[i] = i < NY ? ((const float2*)s.tw[1])[i] : ((const float2*)s.tw[2])[i - NY];
+  const float2* twy = tws;
+  const float2* twz = tws + NY;
+  __syncthreads();
+
+  if (MODE == 1) {
+    // ---- y inverse: HBM -> registers -> transform -> shared memory
+    float2 v[YE];
+#pragma unroll
+    for (int i = 0; i < YE; i++) v[i] = g[(long long)(ct + YT * i) * NZ + kz];
+    PColS x{W, kz, NZ};
+    fft<float, true, NY, typename R::YPL>(v, ct, twy, x);
+#pragma unroll
+    for (int i = 0; i < YE; i++) x.put(ct + YT * i, v[i]);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+  }
+
+  // ---- rows (one round: every row on ZT threads of one warp)
+  {
+    const int t = threadIdx.x % ZT;
+    const int y = threadIdx.x / ZT;
+    using RT = TwoStage<PlanX<NZ, ZE, R::ZR1, R::ZR2>>;
+    float2 wr[RT::NW];
+    RT::load(wr, t, twz);
+    PRowS x{W + y * NZ, y};
+    const long long off = (rowbase + y) * NZ;
+    float2 v[ZE];
+    if (MODE == 0) {
+      const float2* q2 = reinterpret_cast<const float2*>(s.in) + off;
+#pragma unroll
+      for (int i = 0; i < ZE; i++) v[i] = q2[t + ZT * i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < ZE; i++) v[i] = x.get(t + ZT * i);
+      __syncwarp();  // every read of the row precedes the transform's writes
+      RT::template run<true>(v, t, wr, x);
+      float2* q2 = reinterpret_cast<float2*>(s.out) + off;
+      const float2* b2s = Bs + y * NZ;
+#pragma unroll
+      for (int i = 0; i < ZE; i++) {
+        const int m = t + ZT * i;  // element m of the row: chunk m / 2, half m % 2
+        v[i] = cmul(v[i], b2s[(((m >> 1) ^ R::bsw(y)) << 1) | (m & 1)]);
+        q2[m] = v[i];
+      }
+    }
+    if (Bfwd) {
+      if (MODE == 1 && Bfwd == (const float2*)s.B) {
+        // the next split step lies in the same block: same factor, in shared memory
+        const float2* b2s = Bs + y * NZ;
+#pragma unroll
+        for (int i = 0; i < ZE; i++) {
+          const int m = t + ZT * i;
+          v[i] = cmul(v[i], b2s[(((m >> 1) ^ R::bsw(y)) << 1) | (m & 1)]);
+        }
+      } else {
+        const float2* b2 = Bfwd + off;
+#pragma unroll
+        for (int i = 0; i < ZE; i++) v[i] = cmul(v[i], b2[t + ZT * i]);
+      }
+      __syncwarp();  // the inverse's reads of this row are complete
+      RT::template run<false>(v, t, wr, x);
+#pragma unroll
+      for (int i = 0; i < ZE; i++) x.put(t + ZT * i, v[i]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();  // the columns read every row
+  if (!Bfwd) return;  // last step: q_Ns stored, nothing to transform forward
+
+  // ---- y forward: shared memory -> transform -> HBM
+  {
+    PColS x{W, kz, NZ};
+    float2 v[YE];
+#pragma unroll
+    for (int i = 0; i < YE; i++) v[i] = x.get(ct + YT * i);
+    __syncthreads();
+    fft<float, false, NY, typename R::YPL>(v, ct, twy, x);
+#pragma unroll
+    for (int i = 0; i < YE; i++) g[(long long)(ct + YT * i) * NZ + kz] = v[i];
+  }
+}
+
 }  // namespace pft
