@@ -175,7 +175,7 @@ pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches) 
       const pft::BatchStep* st = c.d_conc + (size_t)(s - 1) * 2 * K;
       cudaError_t e = eng->batch_pair_step(c.g, st, 2 * c.active[s - 1], s == 1, b->stream);
       if (e != cudaSuccess) return bcuda(e, "batched pair step");
-      *launches += (s == 1) ? 5 : 4;
+      *launches += eng->batch_pair_launches(c.g, s == 1);
     }
     for (int i : c.members) {
       pft_ctx* x = b->inst[i];

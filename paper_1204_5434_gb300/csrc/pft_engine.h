@@ -184,6 +184,8 @@ class Engine {
   // z forward when `first`, then y, x (D), y inverse, and the fused z inverse / forward
   virtual cudaError_t batch_pair_step(const BatchGeom& g, const BatchStep* d_steps, int nactive, bool first,
                                       cudaStream_t stream) = 0;
+  // kernels one batch_pair_step launches for this geometry
+  virtual int batch_pair_launches(const BatchGeom& g, bool first) const = 0;
   // contour quadrature of Eq. 8 over the stored q and qd histories (after solve_mid)
   virtual cudaError_t quadrature(CtxData& c) = 0;
   // reverse-mode adjoint of the last solve for a loss with dL/dphiA = GA, dL/dphiB = GB

@@ -760,9 +760,32 @@ class EngineT : public Engine {
                               cudaStream_t stream) override {
     if (nact <= 0) return cudaSuccess;
     cudaError_t e;
+    if (plane_geom(g)) {
+      // plane kernel (z and y of step 1), then per step: x pass, plane kernel
+      CtxData cg;
+      for (int a = 0; a < 3; a++) cg.n[a] = g.n[a];
+      cg.kind = g.kind;
+      if (first && (e = batch_plane(cg, st, 0, nact, stream)) != cudaSuccess) return e;
+      const long long nzc = g.nzh;
+      PFT_BATCH_AXIS(g.n[0], e = (bs<N, 2>(st, g.n[1] * nzc, g.n[1] * nzc, 0, g.n[1] * nzc, (int)nzc, 0, nact, stream)));
+      if (e != cudaSuccess) return e;
+      return batch_plane(cg, st, 1, nact, stream);
+    }
     if (first && (e = batch_zf(g, st, nact, stream)) != cudaSuccess) return e;
     if ((e = batch_mid(g, st, nact, stream)) != cudaSuccess) return e;
     return batch_zz(g, st, nact, stream);
+  }
+
+  int batch_pair_launches(const BatchGeom& g, bool first) const override {
+    return plane_geom(g) ? (first ? 3 : 2) : (first ? 5 : 4);
+  }
+
+  // the plane kernel applies to a batch class of this geometry
+  static bool plane_geom(const BatchGeom& g) {
+    CtxData cg;
+    for (int a = 0; a < 3; a++) cg.n[a] = g.n[a];
+    cg.kind = g.kind;
+    return plane_supported(cg);
   }
 
   cudaError_t quadrature(CtxData& c) override {
