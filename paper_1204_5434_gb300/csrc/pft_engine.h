@@ -76,6 +76,7 @@ struct CtxData {
   size_t tw_off[4] = {0, 0, 0, 0};  // x, y, z (full nz), z half (nz/2): byte offsets
   size_t d_off[3] = {0, 0, 0};      // dx (with 1/M), dy, dz
   size_t g_off[3] = {0, 0, 0};      // k_a^2 per axis (FP64): box derivative, SIS Debye factor
+  size_t e_off[3] = {0, 0, 0};      // exp(-k_a^2 ds) per axis (FP64): box derivative
   size_t t64_off[3] = {0, 0, 0};    // FP64 twiddles x, y, z (full nz) for the SIS transforms
   void* sis = nullptr;              // [M] complex FP64 scratch of the semi-implicit step
   void* adj = nullptr;              // adjoint scratch: 6 working-precision slices + 2 M FP64

@@ -941,8 +941,10 @@ static __global__ void __launch_bounds__(PW_THREADS) k_grad_fields(const double*
 template <typename T>
 __global__ void __launch_bounds__(PW_THREADS) k_stress_real(const cpx<T>* __restrict__ u, const cpx<T>* __restrict__ v,
                                                             const double* __restrict__ k2x, const double* __restrict__ k2y,
-                                                            const double* __restrict__ k2z, int nx, int ny, int nzh, int nz,
-                                                            double ds, double* __restrict__ partials) {
+                                                            const double* __restrict__ k2z, const double* __restrict__ ex,
+                                                            const double* __restrict__ ey, const double* __restrict__ ez,
+                                                            int nx, int ny, int nzh, int nz, double* __restrict__ partials) {
+  // exp(-k^2 ds) = ex[kx] ey[ky] ez[kz]; the float spectra are widened exactly
   double acc[3] = {0.0, 0.0, 0.0};
   const long long Ms = (long long)nx * ny * nzh;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < Ms; i += (long long)gridDim.x * blockDim.x) {
@@ -951,12 +953,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_stress_real(const cpx<T>* __rest
     const int ky = (int)(r % ny), kx = (int)(r / ny);
     const double wz = (kz == 0 || 2 * kz == nz) ? 1.0 : 2.0;
     const cpx<T> a = u[i], b = v[i];
-    const double re = (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-    const double gx = k2x[kx], gy = k2y[ky], gz = k2z[kz];
-    const double w = wz * re * exp(-(gx + gy + gz) * ds);
-    acc[0] += w * gx;
-    acc[1] += w * gy;
-    acc[2] += w * gz;
+    const double re = fma(widen(a.x), widen(b.x), widen(a.y) * widen(b.y));
+    const double w = wz * re * (ex[kx] * ey[ky] * ez[kz]);
+    acc[0] = fma(w, k2x[kx], acc[0]);
+    acc[1] = fma(w, k2y[ky], acc[1]);
+    acc[2] = fma(w, k2z[kz], acc[2]);
   }
   block_reduce_store<3, true>(acc, partials + 3 * blockIdx.x);
 }

@@ -261,6 +261,10 @@ class EngineT : public Engine {
       c.g_off[a] = off;
       off = al(off + sizeof(double) * (size_t)dn[a]);
     }
+    for (int a = 0; a < 3; a++) {
+      c.e_off[a] = off;
+      off = al(off + sizeof(double) * (size_t)dn[a]);
+    }
     // half-step diffusion tables exp(-k^2 ds/2) of the 4th-order scheme
     for (int a = 0; a < 3; a++) {
       c.dh_off[a] = off;
@@ -309,6 +313,7 @@ class EngineT : public Engine {
         d[m] = (T)dval;
         reinterpret_cast<T*>(h.data() + c.dh_off[a])[m] = (T)hval;
         g[m] = k * k;
+        reinterpret_cast<double*>(h.data() + c.e_off[a])[m] = exp(-k * k * c.ds);
       }
     }
     return cudaMemcpyAsync(c.tables, h.data(), off, cudaMemcpyHostToDevice, c.stream);
@@ -1315,7 +1320,9 @@ class EngineT : public Engine {
         PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 0>(c, sp, ny * nzc, ny * nzc, 0, ny * nzc, twx, dx, dy, dz, (int)nzc));
         if (e != cudaSuccess) return e;
       }
-      k_stress_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>(u, v, gx, gy, gz, nx, ny, (int)nzc, nz, c.ds, c.partials);
+      k_stress_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>(u, v, gx, gy, gz, tab<double>(c, c.e_off[0]),
+                                                            tab<double>(c, c.e_off[1]), tab<double>(c, c.e_off[2]), nx,
+                                                            ny, (int)nzc, nz, c.partials);
       PFT_DISPATCH_AXIS(nx, e = launch_strided<N, 3>(c, u, ny * nzc, ny * nzc, 0, ny * nzc, twx, dx, dy, dz, (int)nzc));
       if (e != cudaSuccess) return e;
       PFT_DISPATCH_AXIS(ny, e = launch_strided<N, 1>(c, u, nx * nzc, nzc, ny * nzc, nzc, twy, dx, dy, dz, (int)nzc));
@@ -1330,7 +1337,8 @@ class EngineT : public Engine {
 
   // Box derivative from the two stored histories of the last (concurrent) solve: for each
   // split step n the forward spectra of B_n qd_{Ns-n} and B_n q_{n-1} (two members of
-  // batched z, y and x forward passes), then the contraction.
+  // batched z and y forward passes, or of the plane kernel's first step, then the x
+  // forward pass), then the contraction.
   cudaError_t gradients_from_histories(CtxData& c) {
     const size_t slice = (size_t)c.M * sizeof(T);
     cudaError_t e;
@@ -1369,15 +1377,22 @@ class EngineT : public Engine {
     const double* gy = tab<double>(c, c.g_off[1]);
     const double* gz = tab<double>(c, c.g_off[2]);
     const BatchStep* st = (const BatchStep*)c.stepsg;
+    const bool plane = plane_supported(c) && c.plan_plane;
     for (int n = 1; n <= c.Ns; n++) {
       const BatchStep* ss = st + (size_t)2 * (n - 1);
-      if ((e = batch_zf(g, ss, 2, c.stream)) != cudaSuccess) return e;
-      PFT_BATCH_AXIS(ny, e = (bs<N, 0>(ss, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, 2, c.stream)));
-      if (e != cudaSuccess) return e;
+      if (plane) {  // rows x B, z and y forward in one kernel (the plane kernel's first step)
+        if ((e = batch_plane(c, ss, 0, 2, c.stream)) != cudaSuccess) return e;
+      } else {
+        if ((e = batch_zf(g, ss, 2, c.stream)) != cudaSuccess) return e;
+        PFT_BATCH_AXIS(ny, e = (bs<N, 0>(ss, nx * nzc, nzc, ny * nzc, nzc, (int)nzc, 1, 2, c.stream)));
+        if (e != cudaSuccess) return e;
+      }
       PFT_BATCH_AXIS(nx, e = (bs<N, 0>(ss, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 2, c.stream)));
       if (e != cudaSuccess) return e;
-      k_stress_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)c.spec, (const Z*)c.spec2, gx, gy, gz, nx, ny,
-                                                            (int)nzc, nz, c.ds, c.partials);
+      k_stress_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)c.spec, (const Z*)c.spec2, gx, gy, gz,
+                                                            tab<double>(c, c.e_off[0]), tab<double>(c, c.e_off[1]),
+                                                            tab<double>(c, c.e_off[2]), nx, ny, (int)nzc, nz,
+                                                            c.partials);
     }
     k_reduce_final<3><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_STRESS);
     return cudaGetLastError();
