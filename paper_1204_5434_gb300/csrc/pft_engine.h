@@ -81,6 +81,7 @@ struct CtxData {
   void* sis = nullptr;              // [M] complex FP64 scratch of the semi-implicit step
   void* adj = nullptr;              // adjoint scratch: 6 working-precision slices + 2 M FP64
   void* stepsa = nullptr;           // [2 Ns] BatchStep of the adjoint transforms
+  void* stepsap = nullptr;          // [2 Ns] AdjPlaneStep of the adjoint on the plane kernel
   size_t tables_bytes = 0;
   int npart = 0;
   size_t bytes = 0;

@@ -869,6 +869,53 @@ class EngineT : public Engine {
     // the two adjoint chains on two streams
     if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c.stream2, c.fork_ev, 0)) != cudaSuccess) return e;
+    if constexpr (std::is_same<T, float>::value) {
+      if (plane_supported(c) && c.plan_plane) {
+        if (!c.stepsap) {  // entries 2(k-1) + ch: step k of chain ch
+          std::vector<AdjPlaneStep> h((size_t)2 * c.Ns);
+          const char* t = (const char*)c.tables;
+          for (int k = 1; k <= c.Ns; k++) {
+            const int cur = (c.Ns - k) & 1;
+            for (int ch = 0; ch < 2; ch++) {
+              AdjPlaneStep& a = h[(size_t)2 * (k - 1) + ch];
+              memset(&a, 0, sizeof(a));
+              const int split = ch ? c.Ns + 1 - k : k;         // split step of this chain at k
+              a.lam = (ch ? mu : lam)[cur];
+              a.lam_next = (ch ? mu : lam)[cur ^ 1];
+              a.B = Bof(split);
+              a.Bnext = (k > 1) ? Bof(ch ? split + 1 : split - 1) : nullptr;
+              a.qk = ch ? qds(k) : qs(k);
+              a.qk1 = ch ? qds(k - 1) : qs(k - 1);
+              a.src = ch ? qs(c.Ns - k + 1) : qds(c.Ns - k + 1);
+              trapezoid_weight(ch ? c.Ns - k + 1 : k - 1, c.Ns, c.NsA, &a.cA, &a.cB);
+              a.dw = dw + (size_t)(2 * ch + (split <= c.NsA ? 0 : 1)) * c.M;
+              a.spec = ch ? c.spec2 : c.spec;
+              for (int x = 0; x < 4; x++) a.tw[x] = t + c.tw_off[x];
+            }
+          }
+          if ((e = cudaMalloc(&c.stepsap, h.size() * sizeof(AdjPlaneStep))) != cudaSuccess) return e;
+          c.bytes += h.size() * sizeof(AdjPlaneStep);
+          e = cudaMemcpy(c.stepsap, h.data(), h.size() * sizeof(AdjPlaneStep), cudaMemcpyHostToDevice);
+          if (e != cudaSuccess) return e;
+        }
+        const AdjPlaneStep* ap = (const AdjPlaneStep*)c.stepsap;
+        const int nx = c.n[0], ny = c.n[1];
+        const long long nzc = c.nzh;
+        for (int ch = 0; ch < 2; ch++) {
+          cudaStream_t sm = ch ? c.stream2 : c.stream;
+          // z and y forward of B_Ns lambda_Ns (the plane kernel's first step), then per
+          // step: x pass (D), the fused adjoint step
+          if ((e = batch_plane(c, st + (size_t)2 * (c.Ns - 1) + ch, 0, 1, sm)) != cudaSuccess) return e;
+          for (int k = c.Ns; k >= 1; k--) {
+            const BatchStep* sc = st + (size_t)2 * (k - 1) + ch;
+            PFT_BATCH_AXIS(nx, e = (bs<N, 2>(sc, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 1, sm)));
+            if (e != cudaSuccess) return e;
+            if ((e = launch_plane_adj(c, ap + (size_t)2 * (k - 1) + ch, GA, GB, sm)) != cudaSuccess) return e;
+          }
+        }
+        goto joined;
+      }
+    }
     for (int k = c.Ns; k >= 1; k--) {
       const BatchStep* ss = st + (size_t)2 * (k - 1);
       const int cur = (c.Ns - k) & 1;
@@ -904,6 +951,7 @@ class EngineT : public Engine {
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
       }
     }
+  joined:
     if ((e = cudaEventRecord(c.join_ev, c.stream2)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
     k_adjoint_gamma<<<c.npart, PW_THREADS, 0, c.stream>>>(GA, GB, (const double*)c.accA, (const double*)c.accB, c.M,
@@ -1077,6 +1125,21 @@ class EngineT : public Engine {
     if (e != cudaSuccess) return e;
     kern<<<dim3((unsigned)nx, (unsigned)members), R::THREADS, R::SMEM, stream>>>(st);
     return cudaGetLastError();
+  }
+
+  // one fused adjoint step (real fields, FP32) of one chain
+  static cudaError_t launch_plane_adj(CtxData& c, const AdjPlaneStep* ap, const double* GA, const double* GB,
+                                      cudaStream_t sm) {
+    cudaError_t e = cudaErrorNotSupported;
+    auto go = [&](auto kern, size_t smem, int threads) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return;
+      kern<<<dim3((unsigned)c.n[0], 1), threads, smem, sm>>>(ap, GA, GB, c.scal + S_Q, c.ds);
+      e = cudaGetLastError();
+    };
+    if (c.n[1] == 64) go(kb_plane_adj<64, 64>, PlaneCfg<64, 64>::SMEM, PlaneCfg<64, 64>::THREADS);
+    if (c.n[1] == 128) go(kb_plane_adj<128, 128>, PlaneCfg<128, 128>::SMEM, PlaneCfg<128, 128>::THREADS);
+    return e;
   }
 
   // the plane kernel over `members` consecutive entries of st

@@ -105,3 +105,25 @@ def test_adjoint_refuses_what_it_does_not_cover():
         with pytest.raises(pft.PftError) as ei:
             s.adjoint(np.ones(n), np.ones(n))
         assert ei.value.status == pft.PFT_ERR_UNSUPPORTED
+
+
+def test_adjoint_128cubed_fp32_on_the_plane_kernel_matches_fp64():
+    """128^3 FP32-mixed (the fused adjoint step on the plane kernel) against the FP64 path
+    (pencil passes, pinned to the oracle above) on the gyroid workload, Ns = 20."""
+    from paper_1204_5434_gb300 import workloads as wl
+    w = wl.GYR128.with_(Ns=20)
+    wp, wm = wl.fields(w)
+    rng = np.random.default_rng(12)
+    GA, GB = rng.normal(size=w.n), rng.normal(size=w.n)
+    out = {}
+    for prec in (FP64, FP32):
+        with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec, checkpoint=1) as s:
+            s.set_fields(wp, wm)
+            s.solve()
+            out[prec] = s.adjoint(GA, GB)
+            if prec == FP32:
+                assert pft.pft_get_plan(s.h)[0] == 1
+    scale = max(np.max(np.abs(out[FP64][0])), np.max(np.abs(out[FP64][1])))
+    err = max(np.max(np.abs(out[FP32][0] - out[FP64][0])), np.max(np.abs(out[FP32][1] - out[FP64][1]))) / scale
+    print(f"\nadjoint 128^3 Ns=20 FP32 vs FP64: rel err {err:.2e}")
+    assert err <= 1e-4
