@@ -13,7 +13,7 @@
 #include "pft_engine_impl.cuh"
 #include "pft_batch.cuh"
 #include "pft_persist.cuh"
-#include "pft_plane.cuh"
+#include "pft_plane_ext.cuh"
 #include "pft_resident.cuh"
 
 namespace pft {
