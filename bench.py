@@ -82,6 +82,15 @@ def _dist():
     return ws, rank
 
 
+def _max_over_ranks(torch, x, ws, device):
+    """MAX of a per-rank scalar over every rank of the process group (one rank: x)."""
+    if ws <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -478,11 +487,9 @@ def run(args):
         ms = _time_device(pft, torch, h, stream, steps, args.warmup, units_per_step)
         ck = clocks.stop()
         torch.cuda.synchronize()
+        ms = _max_over_ranks(torch, ms, ws, "cuda")
         if ws > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             torch.distributed.barrier()
-            ms = float(t.item())
         value = ws * units_per_step / (ms * 1e-3)
         # kernels per timed step: the nodes of the solve graph plus the field update
         n_solve, n_field = pft.pft_launch_counts(h)
@@ -510,16 +517,13 @@ def run(args):
             pft.pft_get_fields(h, op, om)
         pft.pft_synchronize(h)
         e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-        if ws > 1:
-            t = torch.tensor([e2e_ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = _max_over_ranks(torch, e2e_ms, ws, "cuda")
         sys_.close()
         del dwp, dwm
         torch.cuda.empty_cache()
         bpu = BYTES_PER_UNIT[prec_name]
-        # the contour step (five pass kernels) over the timed region: units/s from the
-        # event-timed graph replays, which include the ~3% of pointwise kernels
+        # the contour step (plane kernel and x pass) over the timed region: units/s from
+        # the event-timed graph replays, which include the quadrature and pointwise kernels
         step_ms = ms / (2 * WORK.Ns)
         achieved = bpu * WORK.M / (step_ms * 1e-3) / 1e9
         top = max(prof["kinds"].items(), key=lambda kv: kv[1]["ms"])
