@@ -431,6 +431,13 @@ pft_status pft_philox_normals(unsigned long long seed, unsigned long long instan
 pft_status pft_philox_raw(const unsigned int ctr[4], const unsigned int key[2], long long count,
                           unsigned int* out_device, void* stream);
 
+/* The library's double -> float narrowing on the integer pipe (used where an FP64 result
+ * is stored in a float propagator array): y[i] = x[i] rounded to nearest, ties to even,
+ * for results in the normal float range; below the smallest normal float a signed zero,
+ * overflow gives infinity, NaN stays NaN.  x (n float64) and y (n float32) are device
+ * pointers, on `stream` (NULL: the default stream).  Errors: PFT_ERR_ARG, PFT_ERR_CUDA. */
+pft_status pft_debug_narrow_rn(const double* x_device, float* y_device, long long n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -925,4 +925,11 @@ pft_status pft_philox_raw(const unsigned int ctr[4], const unsigned int key[2], 
   return PFT_OK;
 }
 
+pft_status pft_debug_narrow_rn(const double* x_device, float* y_device, long long n, void* stream) {
+  if (!x_device || !y_device || n < 0) return fail(PFT_ERR_ARG, "bad argument");
+  if (n == 0) return PFT_OK;
+  PFT_CK(pft::launch_narrow_rn(x_device, y_device, n, (cudaStream_t)stream));
+  return PFT_OK;
+}
+
 }  // extern "C"

@@ -207,6 +207,7 @@ Engine* make_engine_f64();
 
 cudaError_t launch_philox_normals(unsigned long long seed, unsigned long long instance, unsigned long long step,
                                   int field, long long M, double* out, cudaStream_t st);
+cudaError_t launch_narrow_rn(const double* x, float* y, long long n, cudaStream_t st);
 cudaError_t launch_philox_raw(const unsigned int ctr[4], const unsigned int key[2], long long count,
                               unsigned int* out, cudaStream_t st);
 

@@ -19,4 +19,14 @@ cudaError_t launch_philox_raw(const unsigned int ctr[4], const unsigned int key[
                                                        make_uint2(key[0], key[1]), count, out);
   return cudaGetLastError();
 }
+static __global__ void k_narrow_rn(const double* __restrict__ x, float* __restrict__ y, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = narrow_rn(x[i]);
+}
+
+cudaError_t launch_narrow_rn(const double* x, float* y, long long n, cudaStream_t st) {
+  const int blocks = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_narrow_rn<<<blocks > 0 ? blocks : 1, 256, 0, st>>>(x, y, n);
+  return cudaGetLastError();
+}
 }  // namespace pft

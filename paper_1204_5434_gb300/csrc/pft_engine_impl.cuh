@@ -10,6 +10,7 @@
 
 #include "pft_engine.h"
 #include "pft_passes.cuh"
+#include "pft_narrow.cuh"
 
 namespace pft {
 
@@ -586,11 +587,11 @@ __global__ void __launch_bounds__(PW_THREADS) k_adjoint_update(AdjChain c, const
     const T lam = ((const T*)c.lam)[i];
     const T z = ((const T*)c.z)[i];
     const T B = ((const T*)c.B)[i];
-    dw[i] += h * (widen(lam * ((const T*)c.qk)[i]) + widen(B * ((const T*)c.qk1)[i] * z));
+    dw[i] = fma(h, widen(lam * ((const T*)c.qk)[i]) + widen(B * ((const T*)c.qk1)[i] * z), dw[i]);
     double g = 0.0;
     if (g0 != 0.0) g += g0 * GA[i];
     if (g1 != 0.0) g += g1 * GB[i];
-    ((T*)c.lam_next)[i] = (T)((double)(B * z) + g * (double)((const T*)c.src)[i]);
+    ((T*)c.lam_next)[i] = narrow_rn_as(fma(g, widen(((const T*)c.src)[i]), widen(B * z)), T(0));
   }
 }
 

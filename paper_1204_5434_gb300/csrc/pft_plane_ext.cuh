@@ -3,6 +3,7 @@
 // (real fields) and the plane kernel for complex Langevin fields.
 #pragma once
 #include "pft_plane.cuh"
+#include "pft_narrow.cuh"
 
 namespace pft {
 
@@ -138,8 +139,8 @@ kb_plane_adj(const AdjPlaneStep* __restrict__ st, const double* __restrict__ GA,
         const float2 qk1 = reinterpret_cast<const float2*>(s.qk1)[o];
         const float2 sr = reinterpret_cast<const float2*>(s.src)[o];
         double2 dw = reinterpret_cast<const double2*>(s.dw)[o];
-        dw.x += h * (widen(lam.x * qk.x) + widen(b.x * qk1.x * z.x));
-        dw.y += h * (widen(lam.y * qk.y) + widen(b.y * qk1.y * z.y));
+        dw.x = fma(h, widen(lam.x * qk.x) + widen(b.x * qk1.x * z.x), dw.x);
+        dw.y = fma(h, widen(lam.y * qk.y) + widen(b.y * qk1.y * z.y), dw.y);
         reinterpret_cast<double2*>(s.dw)[o] = dw;
         double gx = 0.0, gy = 0.0;
         if (g0 != 0.0) {
@@ -152,8 +153,8 @@ kb_plane_adj(const AdjPlaneStep* __restrict__ st, const double* __restrict__ GA,
           gx += g1 * a.x;
           gy += g1 * a.y;
         }
-        const float2 ln = make_float2((float)((double)(b.x * z.x) + gx * (double)sr.x),
-                                      (float)((double)(b.y * z.y) + gy * (double)sr.y));
+        const float2 ln = make_float2(narrow_rn(fma(gx, widen(sr.x), widen(b.x * z.x))),
+                                      narrow_rn(fma(gy, widen(sr.y), widen(b.y * z.y))));
         reinterpret_cast<float2*>(s.lam_next)[o] = ln;
         v[i] = ln;
       }

@@ -144,6 +144,7 @@ _SIGS = {
     "pft_philox_normals": (ct.c_int, [ct.c_ulonglong, ct.c_ulonglong, ct.c_ulonglong, ct.c_int, ct.c_longlong,
                                       _P, _P]),
     "pft_philox_raw": (ct.c_int, [ct.POINTER(ct.c_uint), ct.POINTER(ct.c_uint), ct.c_longlong, _P, _P]),
+    "pft_debug_narrow_rn": (ct.c_int, [_P, _P, ct.c_longlong, _P]),
 }
 
 
@@ -571,3 +572,11 @@ class System:
             return a, b, dL, dq
         dL, dq = pft_gradients(self.h)
         return None, None, dL, dq
+
+
+def pft_debug_narrow_rn(x_device, y_device, stream=None):
+    """torch CUDA tensors: x float64, y float32 of the same size."""
+    (px, wx), (py, wy) = _ptr(x_device), _ptr(y_device, True)
+    if wx != PFT_DEVICE or wy != PFT_DEVICE:
+        raise ValueError("pft_debug_narrow_rn takes device arrays")
+    _check(_lib().pft_debug_narrow_rn(px, py, int(x_device.numel()), stream), "pft_debug_narrow_rn")

@@ -2,7 +2,7 @@
 the fields resident on the device, then one line of observables.
 
     python -m paper_1204_5434_gb300.run --workload gyr128 --precision fp32 \
-        --steps 1 --warmup 3 [--scheme split2|rqm4] [--march passes|resident|persistent]
+        --steps 1 --warmup 3 [--scheme split2|rqm4] [--march passes|resident|persistent] [--adjoint]
 
 Each update is one pft_solve (both propagators, Q, densities, H) and one explicit field
 step (SCFT Euler for SCFT workloads, Euler-Maruyama with device Philox noise for complex
@@ -37,6 +37,9 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--no-graph", action="store_true", help="launch each solve eagerly")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="after the updates, one reverse-mode adjoint of a seeded linear loss on the "
+                         "densities (real SCFT diblock workloads)")
     a = ap.parse_args(argv)
     w = wl.ALL[a.workload]
     if a.Ns > 0:
@@ -74,11 +77,23 @@ def main(argv=None) -> int:
         pft.pft_solve(h)
         obs = s.observables()
         n_solve, n_field = pft.pft_launch_counts(h)
+        adj_ms = None
+        if a.adjoint:
+            import time
+
+            import numpy as np
+            rng = np.random.default_rng(w.seed)
+            GA, GB = rng.normal(size=w.n), rng.normal(size=w.n)
+            t0 = time.perf_counter()
+            s.adjoint(GA, GB)
+            adj_ms = (time.perf_counter() - t0) * 1e3
     units = (1 if arch == pft.PFT_ARCH_EDWARDS else 2) * w.M * w.Ns  # propagators marched
     out = {"workload": w.name, "precision": a.precision, "scheme": a.scheme, "Ns": w.Ns, "steps": a.steps,
            "ms_per_update": ms, "units_per_s": (units / (ms * 1e-3)) if ms else None,
            "kernels_per_solve": n_solve, "kernels_per_field_step": n_field,
            "Q": [obs["Q"].real, obs["Q"].imag], "H": [obs["H"].real, obs["H"].imag]}
+    if a.adjoint:
+        out["adjoint_ms_host_wall"] = adj_ms
     print(json.dumps(out), flush=True)
     return 0
 
