@@ -228,9 +228,10 @@ pft_status pft_field_step(pft_ctx* ctx, pft_step_kind kind, double lam_or_dt,
  * dL_dphiA and dL_dphiB (M float64 each): writes dL/dW+ and dL/dW- (M float64 each), the
  * exact gradient of L through the discrete march (2nd-order steps, trapezoid quadrature,
  * the normalisation by Q).  Method: the q and qd marches are adjoined backwards with the
- * source terms of the quadrature (Eq. 8), both adjoint chains sharing each batched
- * transform; every step adds -(ds/2) [lambda_k q_k + B_k q_{k-1} F^-1 D F (B_k lambda_k)]
- * to the gradient of its block.  Arrays on host or device per `where`.
+ * source terms of the quadrature (Eq. 8), the two adjoint chains on two streams; every
+ * step adds -(ds/2) [lambda_k q_k + B_k q_{k-1} F^-1 D F (B_k lambda_k)] to the gradient
+ * of its block (FP64 accumulation in both precisions).  Arrays on host or device per
+ * `where`.
  * Errors: PFT_ERR_UNSUPPORTED unless real SCFT diblock fields, SPLIT2, the pass march and
  * both histories kept (checkpoint 1); PFT_ERR_STATE without a solve at the current fields. */
 pft_status pft_adjoint(pft_ctx* ctx, const void* dL_dphiA, const void* dL_dphiB, void* dL_dwp, void* dL_dwm,

@@ -121,3 +121,34 @@ def test_variable_cell_relaxation_lowers_h():
             s.set_box(tuple(L))
         gp, gm = s.get_fields()
     assert np.max(np.abs(gm - wm)) <= 1e-10
+
+
+def test_box_derivative_on_the_plane_kernel_64cubed_fp32():
+    """64^3 FP32-mixed: the forward spectra of the box derivative come from the plane
+    kernel's first step (z and y forward in one kernel) -- against the oracle."""
+    w = wl.GYR64.with_(Ns=12)
+    wp, wm = wl.fields(w)
+    ref = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL)
+    gq = o.dlnQ_dL(ref, w.n, w.L)
+    with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, FP32) as s:
+        s.set_fields(wp, wm)
+        s.solve()
+        assert pft.pft_get_plan(s.h)[0] == 1
+        _, _, _, dq = s.gradients(want_fields=False)
+    err = max(abs(dq[i] - gq[i]) / abs(gq[i]) for i in range(3))
+    print(f"\nbox derivative 64^3 FP32 (plane path) rel err {err:.2e}")
+    assert err <= 2e-4
+
+
+def test_box_derivative_128cubed_fp32_matches_fp64():
+    w = wl.GYR128.with_(Ns=10)
+    wp, wm = wl.fields(w)
+    out = {}
+    for prec in (FP64, FP32):
+        with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec) as s:
+            s.set_fields(wp, wm)
+            s.solve()
+            out[prec] = s.gradients(want_fields=False)[3]
+    err = max(abs(out[FP32][i] - out[FP64][i]) / abs(out[FP64][i]) for i in range(3))
+    print(f"\nbox derivative 128^3 FP32 vs FP64 rel err {err:.2e}")
+    assert err <= 2e-4
