@@ -89,6 +89,15 @@ kb_zz_r2c(const BatchStep* __restrict__ st, long long npen) {
   const Z* twh = (const Z*)s.tw[3];
   const Z* twf = (const Z*)s.tw[2];
   const long long o = pc * N2;
+  // FP32: B_s of the pencil first (its latency overlaps the inverse transform) and kept
+  // for step s+1 inside a block; FP64 (FP64-pipe bound, registers short) loads it after
+  constexpr bool kPre = sizeof(T) == 4;
+  const Z* b2 = reinterpret_cast<const Z*>(s.B) + o;
+  Z bb[E];
+  if (kPre) {
+#pragma unroll
+    for (int i = 0; i < E; i++) bb[i] = b2[t + TPC * i];
+  }
 #pragma unroll
   for (int i = 0; i < E; i++) x.put(t + TPC * i, valid ? sp[t + TPC * i] : mk<T>(T(0), T(0)));
   if (t == 0) x.put(N2, valid ? sp[N2] : mk<T>(T(0), T(0)));
@@ -104,23 +113,34 @@ kb_zz_r2c(const BatchStep* __restrict__ st, long long npen) {
   }
   __syncwarp();
   fft<T, true, N2>(v, t, twh, x);
-  const Z* b2 = reinterpret_cast<const Z*>(s.B) + o;
   Z* q2 = reinterpret_cast<Z*>(s.out) + o;
 #pragma unroll
   for (int i = 0; i < E; i++) {
     const int m = t + TPC * i;
-    const Z b = b2[m];
+    const Z b = kPre ? bb[i] : b2[m];
     v[i].x *= b.x;
     v[i].y *= b.y;
     if (valid) q2[m] = v[i];
   }
   if (!s.Bnext) return;  // uniform per launch member
   const Z* bn = reinterpret_cast<const Z*>(s.Bnext) + o;
+  if constexpr (kPre) {
+    if (s.Bnext != s.B) {  // the block junction; inside a block the same factors apply again
 #pragma unroll
-  for (int i = 0; i < E; i++) {
-    const Z b = bn[t + TPC * i];
-    v[i].x *= b.x;
-    v[i].y *= b.y;
+      for (int i = 0; i < E; i++) bb[i] = bn[t + TPC * i];
+    }
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      v[i].x *= bb[i].x;
+      v[i].y *= bb[i].y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      const Z b = bn[t + TPC * i];
+      v[i].x *= b.x;
+      v[i].y *= b.y;
+    }
   }
   fft<T, false, N2>(v, t, twh, x);  // the inverse ended with a barrier after its last reads
 #pragma unroll
@@ -157,22 +177,38 @@ kb_zz_c2c(const BatchStep* __restrict__ st, long long npen) {
   XchPencil<T> x{reinterpret_cast<Z*>(smraw) + p * LD};
   Z* sp = (Z*)s.spec;
   const Z* tw = (const Z*)s.tw[2];
-  Z v[E];
+  // FP32: B_s first (its latency overlaps the inverse transform) and kept for step s+1
+  // inside a block; FP64 (FP64-pipe bound, registers short) loads it after
+  constexpr bool kPre = sizeof(T) == 4;
+  Z v[E], bb[E];
+  const Z* B = (const Z*)s.B;
+  if (kPre) {
+#pragma unroll
+    for (int i = 0; i < E; i++) bb[i] = B[o + t + TPC * i];
+  }
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = valid ? sp[o + t + TPC * i] : mk<T>(T(0), T(0));
   fft<T, true, N>(v, t, tw, x);
-  const Z* B = (const Z*)s.B;
   Z* q = (Z*)s.out;
 #pragma unroll
   for (int i = 0; i < E; i++) {
     const long long m = o + t + TPC * i;
-    v[i] = cmul(v[i], B[m]);
+    v[i] = cmul(v[i], kPre ? bb[i] : B[m]);
     if (valid) q[m] = v[i];
   }
   if (!s.Bnext) return;
   const Z* Bn = (const Z*)s.Bnext;
+  if constexpr (kPre) {
+    if (s.Bnext != s.B) {  // the block junction; inside a block the same factors apply again
 #pragma unroll
-  for (int i = 0; i < E; i++) v[i] = cmul(v[i], Bn[o + t + TPC * i]);
+      for (int i = 0; i < E; i++) bb[i] = Bn[o + t + TPC * i];
+    }
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cmul(v[i], bb[i]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cmul(v[i], Bn[o + t + TPC * i]);
+  }
   if (n_stages<Plan<N>>() > 1) __syncwarp();
   fft<T, false, N>(v, t, tw, x);
   if (valid) {
