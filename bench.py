@@ -48,10 +48,10 @@ FP64_PEAK_TFLOPS = 1.25
 # + x pass, steady state inside a block), dram__bytes_read.sum + dram__bytes_write.sum from
 # one ncu capture (profiles/plane_kernel_and_x_pass_fp32_128cubed_ncu.md).  Valid only for
 # the kernel sources it was taken on: reported as null once any of them changes.
-TRAFFIC_FP32 = {"bytes_per_contour_step": 16.943104e6 + 0.0 + 8.543744e6,
+TRAFFIC_FP32 = {"bytes_per_contour_step": 16.943360e6 + 0.0 + 8.543488e6,
                 "sources": ("paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
                             "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_fft.cuh"),
-                "sha256": "46438aeea38c02bc25b554284188a00fe70efd957d9535e64ff879cb5aec459d"}
+                "sha256": "5bf2efea65550e9b9e41ae536b150f5cb45c210cc445190db20227d64b33e068"}
 
 
 def _traffic_fp32():

@@ -188,6 +188,20 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
   const long long pc = valid ? pen : 0;
   XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
   const cpx<T>* in = spec + pc * (N2 + 1);
+  // FP32: the epilogue's factor and partner first, so that their latency overlaps the
+  // transform (FP64 is FP64-pipe bound and short of registers: it loads them after)
+  constexpr bool kPre = sizeof(T) == 4;
+  const long long o = pc * N2;
+  const cpx<T>* b2 = reinterpret_cast<const cpx<T>*>(B);
+  const cpx<T>* f2 = reinterpret_cast<const cpx<T>*>(partner);
+  cpx<T> bb[E], ff[E];
+  if (kPre) {
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      if (EPI != 2) bb[i] = b2[o + t + TPC * i];
+      if (EPI == 3) ff[i] = f2[o + t + TPC * i];
+    }
+  }
 #pragma unroll
   for (int i = 0; i < E; i++) {
     const int k = t + TPC * i;
@@ -208,20 +222,18 @@ __device__ __forceinline__ void zi_c2r_body(const cpx<T>* __restrict__ spec, con
   __syncwarp();
   fft<T, true, N2>(v, t, twh, x);
   if (!valid) return;
-  const long long o = pc * N2;
-  const cpx<T>* b2 = reinterpret_cast<const cpx<T>*>(B);
   cpx<T>* q2 = reinterpret_cast<cpx<T>*>(qout);
 #pragma unroll
   for (int i = 0; i < E; i++) {
     const long long m = o + t + TPC * i;
     cpx<T> y = v[i];
     if (EPI != 2) {
-      const cpx<T> b = b2[m];
+      const cpx<T> b = kPre ? bb[i] : b2[m];
       y.x *= b.x;
       y.y *= b.y;
     }
     if (EPI == 3) {
-      const cpx<T> f = reinterpret_cast<const cpx<T>*>(partner)[m];
+      const cpx<T> f = kPre ? ff[i] : f2[m];
       y.x = (T(4) * y.x - f.x) / T(3);
       y.y = (T(4) * y.y - f.y) / T(3);
     }
@@ -311,6 +323,16 @@ __device__ __forceinline__ void zi_c2c_body(const cpx<T>* __restrict__ spec, con
   const bool valid = pen < npen;
   const long long o = (valid ? pen : 0) * N;
   XchPencil<T> x{reinterpret_cast<cpx<T>*>(smraw) + p * LD};
+  // FP32: the epilogue's factor and partner first (latency overlaps the transform)
+  constexpr bool kPre = sizeof(T) == 4;
+  cpx<T> bb[E], ff[E];
+  if (kPre) {
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      if (EPI != 2) bb[i] = B[o + t + TPC * i];
+      if (EPI == 3) ff[i] = partner[o + t + TPC * i];
+    }
+  }
   cpx<T> v[E];
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = valid ? spec[o + t + TPC * i] : mk<T>(T(0), T(0));
@@ -320,9 +342,9 @@ __device__ __forceinline__ void zi_c2c_body(const cpx<T>* __restrict__ spec, con
   for (int i = 0; i < E; i++) {
     const long long m = o + t + TPC * i;
     cpx<T> y = v[i];
-    if (EPI != 2) y = cmul(y, B[m]);
+    if (EPI != 2) y = cmul(y, kPre ? bb[i] : B[m]);
     if (EPI == 3) {
-      const cpx<T> f = partner[m];
+      const cpx<T> f = kPre ? ff[i] : partner[m];
       y.x = (T(4) * y.x - f.x) / T(3);
       y.y = (T(4) * y.y - f.y) / T(3);
     }
