@@ -112,6 +112,7 @@ struct CtxData {
   // q history: ckK = 1 keeps every slice in hist; ckK = K >= 2 keeps q_{cK} in slots
   // 0..nck-1 (nck = Ns/K + 1), q_Ns in slot nck when K does not divide Ns, and the
   // segment q_{cK+j} (j = 1..K-1) being recomputed in slots nck+j
+  bool rq_plane = false;  // RQM4 steps on the plane kernels (decided when the step table is built)
   int ckK = 1;
   int nck = 0;
   void* BAh = nullptr;

@@ -166,6 +166,15 @@ template <> __device__ __forceinline__ double one_val<double>() { return 1.0; }
 template <> __device__ __forceinline__ float2 one_val<float2>() { return make_float2(1.f, 0.f); }
 template <> __device__ __forceinline__ double2 one_val<double2>() { return make_double2(1.0, 0.0); }
 
+// The Richardson combination of Eq. 13, q = (4 A(ds/2)A(ds/2) q - A(ds) q) / 3, over n
+// working-precision values (the same expression as the combining z-inverse epilogue).
+template <typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_rqm4_combine(const T* __restrict__ half2, const T* __restrict__ full,
+                                                              T* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T(4) * half2[i] - full[i]) / T(3);
+}
+
 template <typename W> __global__ void k_fill_one(W* __restrict__ dst, long long M) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x)
     dst[i] = one_val<W>();

@@ -1003,6 +1003,9 @@ class EngineT : public Engine {
       if ((e = cudaMemcpy(c.qw, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
     }
     if (!c.steps2) {
+      // on the plane kernels the second half step stores B y into the scratch slice of the
+      // first (free by then) and a separate kernel forms the combination
+      c.rq_plane = plane_supported(c) && c.plan_plane;
       char* rq = (char*)c.rq;
       void* rqs[4] = {rq, rq + slice, rq + 2 * slice, rq + 3 * slice};
       void* spec3 = rq + 4 * slice;
@@ -1037,7 +1040,7 @@ class EngineT : public Engine {
           h1.spec = half_spec[p];
           h1.Bnext = Bh;
           h2.B = Bh;
-          h2.out = out[p];
+          h2.out = c.rq_plane ? rqs[2 + p] : out[p];
           h2.partner = rqs[p];
           h2.spec = half_spec[p];
           for (BatchStep* b : {&f, &h1, &h2})
@@ -1072,6 +1075,29 @@ class EngineT : public Engine {
       for (int p = 0; p < 2; p++) {
         cudaStream_t sm = p ? c.stream2 : c.stream;
         const BatchStep* e3 = st + (size_t)6 * (s - 1) + 3 * p;
+        if (c.rq_plane) {
+          // full and first half step: rows x B, z and y forward; x pass (D, D/2); y^-1,
+          // z^-1, x B, store (the half step then x B_h, z and y forward of the second);
+          // second half: x pass (D/2), y^-1, z^-1, x B_h; the combination
+          const int nx = c.n[0], ny = c.n[1];
+          const long long nzc = c.nzh;
+          if ((e = batch_plane(c, e3, 0, 2, sm)) != cudaSuccess) return e;
+          PFT_BATCH_AXIS(nx, e = (bs<N, 2>(e3, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 2, sm)));
+          if (e != cudaSuccess) return e;
+          if ((e = batch_plane(c, e3, 1, 2, sm)) != cudaSuccess) return e;
+          PFT_BATCH_AXIS(nx, e = (bs<N, 2>(e3 + 2, ny * nzc, ny * nzc, 0, ny * nzc, (int)nzc, 0, 1, sm)));
+          if (e != cudaSuccess) return e;
+          if ((e = batch_plane(c, e3 + 2, 1, 1, sm)) != cudaSuccess) return e;
+          const size_t slice = (size_t)c.M * sizeof(T);  // real working-precision slice
+          const char* rq = (const char*)c.rq;
+          const size_t sl = (c.kind == PFT_SCFT_REAL) ? slice : 2 * slice;
+          T* outp = (T*)((char*)(p ? c.qdh : c.hist) + (size_t)s * sl);
+          const long long nval = (c.kind == PFT_SCFT_REAL) ? c.M : 2 * c.M;
+          k_rqm4_combine<T><<<c.npart, PW_THREADS, 0, sm>>>((const T*)(rq + (size_t)(2 + p) * sl),
+                                                            (const T*)(rq + (size_t)p * sl), outp, nval);
+          if ((e = cudaGetLastError()) != cudaSuccess) return e;
+          continue;
+        }
         if ((e = batch_zf(g, e3, 2, sm)) != cudaSuccess) return e;
         if ((e = batch_mid(g, e3, 2, sm)) != cudaSuccess) return e;
         if ((e = batch_zi(g, e3, 1, 0, sm)) != cudaSuccess) return e;

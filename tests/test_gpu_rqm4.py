@@ -239,3 +239,21 @@ def test_rqm4_gyroid_128cubed(prec):
         assert _rel(obs["H"].real, Href) <= t["H"]
     else:
         assert abs(obs["H"].real - Href) / (w.C * float(np.prod(w.L))) <= t["h"]
+
+
+@pytest.mark.parametrize("kind,Ns,fA", [(SCFT, 9, 0.35), (CL, 6, 0.5)])
+def test_rqm4_on_the_plane_kernels_64cubed(kind, Ns, fA):
+    """FP32 64^3 (real and complex): the three split steps of each contour step run on the
+    plane kernels with a separate combination kernel -- against the oracle."""
+    n, L = (64, 64, 64), (8.0, 8.0, 8.0)
+    wp, wm = _fields(n, kind, 70 + Ns)
+    ref = o.solve(wp, wm, n, L, Ns, fA, OKIND[kind], scheme=o.RQM4)
+    with pft.System(n, L, Ns, fA, 15.0, 1.0, kind, FP32, scheme=RQM4) as s:
+        s.set_fields(wp, wm)
+        s.solve()
+        assert pft.pft_get_plan(s.h)[0] == 1
+        obs = s.observables()
+        phiA, phiB = s.densities()
+    t = TOL[FP32]
+    assert _rel(obs["Q"], ref.Q) <= t["Q"]
+    assert max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB))) <= t["phi"]
