@@ -328,16 +328,134 @@ def test_homogeneous_saddle_is_fixed_point():
     assert np.max(np.abs(a - cp)) < 1e-14 and np.max(np.abs(b - cm)) < 1e-13
 
 
-def test_scft_step_signs():
-    """Wick-rotated relaxation: W+ follows +(phiA+phiB-1) (ascent on the pressure
-    field) and W- follows -(2W-/chiN + phiB - phiA) (descent on the exchange field)."""
-    n = (2, 2, 2)
+def _h_cl(wp, wm, n, L, Ns, fA, chiN, C, kind):
+    s = o.solve(wp, wm, n, L, Ns, fA, kind)
+    return o.hamiltonian(wp, wm, s.lnQ, chiN, C, n, L, kind), s
+
+
+def test_scft_step_is_ascent_on_W_plus_and_descent_on_W_minus():
+    """Direction and scale of the relaxation of Eq. 9 (Wick-rotated, force per C), pinned
+    through H alone: a step along +lam dH/dW+/(C dV) changes H by +(C dV/lam)|dW+|^2 to
+    first order, one along -lam dH/dW-/(C dV) by -(C dV/lam)|dW-|^2.  A flipped sign,
+    a dropped 1/C or a missing dV in the step fails the ratio; H is pinned elsewhere by
+    closed forms and by finite differences."""
+    n, L, Ns, fA, chiN, C, lam = (6, 4, 8), (3.0, 2.0, 4.0), 12, 0.35, 16.0, 2.5, 1e-5
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 61)
+    dV = float(np.prod(L)) / int(np.prod(n))
+    H0, s = _h_cl(wp, wm, n, L, Ns, fA, chiN, C, o.SCFT_REAL)
+    wpn, wmn = o.scft_euler_step(wp, wm, s.phiA, s.phiB, chiN, lam)
+    dp, dm = wpn - wp, wmn - wm
+    Hp = _h_cl(wpn, wm, n, L, Ns, fA, chiN, C, o.SCFT_REAL)[0]
+    Hm = _h_cl(wp, wmn, n, L, Ns, fA, chiN, C, o.SCFT_REAL)[0]
+    pred_p = C * dV / lam * np.sum(dp * dp)
+    pred_m = -C * dV / lam * np.sum(dm * dm)
+    assert Hp - H0 > 0 and Hm - H0 < 0
+    assert abs((Hp - H0) / pred_p - 1) < 1e-3 and abs((Hm - H0) / pred_m - 1) < 1e-3
+
+
+def test_cl_drift_is_minus_the_holomorphic_gradient():
+    """Direction and scale of the noise-free complex Langevin step of Eq. 9 (lam = 1,
+    force per C): H is holomorphic in the complex fields, so a drift d omega =
+    -dt dH/domega/(C dV) changes H by -(C dV/dt) sum(d omega^2) (the complex square, not the
+    modulus) to first order, separately for omega+ and omega-."""
+    n, L, Ns, fA, chiN, C, dt = (4, 6, 4), (2.0, 3.0, 2.5), 10, 0.3, 20.0, 50.0, 1e-6
+    wp, wm = _rand_fields(n, o.CL_COMPLEX, 62)
+    dV = float(np.prod(L)) / int(np.prod(n))
+    H0, s = _h_cl(wp, wm, n, L, Ns, fA, chiN, C, o.CL_COMPLEX)
+    z = np.zeros(n)
+    wpn, wmn = o.cl_euler_maruyama_step(wp, wm, s.phiA, s.phiB, chiN, dt, z, z)
+    dp, dm = wpn - wp, wmn - wm
+    Hp = _h_cl(wpn, wm, n, L, Ns, fA, chiN, C, o.CL_COMPLEX)[0]
+    Hm = _h_cl(wp, wmn, n, L, Ns, fA, chiN, C, o.CL_COMPLEX)[0]
+    for dH, d in ((Hp - H0, dp), (Hm - H0, dm)):
+        pred = -C * dV / dt * np.sum(d * d)
+        assert abs(dH / pred - 1) < 1e-3, (dH, pred)
+
+
+def test_cl_step_without_noise_is_the_wick_rotated_scft_step():
+    """omega+ = -i W+ (purely imaginary), real omega- = W- and no noise: the CL drift with
+    dt = lam is the SCFT relaxation rotated back (W+ = i omega+), i.e. ascent on W+ comes
+    out of the same equation of motion as descent on omega+."""
+    n, L, Ns, fA, chiN, lam = (6, 4, 8), (3.0, 2.0, 4.0), 12, 0.4, 14.0, 0.3
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 63)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
+    wpn, wmn = o.scft_euler_step(wp, wm, s.phiA, s.phiB, chiN, lam)
+    sc = o.solve(-1j * wp, wm.astype(complex), n, L, Ns, fA, o.CL_COMPLEX)
+    assert np.max(np.abs(sc.phiA - s.phiA)) < 1e-13
+    z = np.zeros(n)
+    cpn, cmn = o.cl_euler_maruyama_step(-1j * wp, wm.astype(complex), sc.phiA, sc.phiB, chiN, lam, z, z)
+    assert np.max(np.abs(1j * cpn - wpn)) < 1e-13 and np.max(np.abs(cmn - wmn)) < 1e-13
+
+
+def test_dH_dfields_matches_finite_difference_complex():
+    """The CL forces times C dV are the holomorphic derivatives of H: a real increment h
+    of one grid value of omega+- changes H by h dH/domega (finite differences of Eq. 3)."""
+    n, L, Ns, fA, chiN, C = (4, 4, 6), (2.0, 2.0, 3.0), 10, 0.3, 20.0, 50.0
+    wp, wm = _rand_fields(n, o.CL_COMPLEX, 64)
+    s = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    gp, gm = o.dH_dfields(wp, wm, s, chiN, C, n, L, o.CL_COMPLEX)
+
+    def H(a, b):
+        return _h_cl(a, b, n, L, Ns, fA, chiN, C, o.CL_COMPLEX)[0]
+    for j in (5, 50, 90):
+        idx = np.unravel_index(j, n)
+        fdp = fd5(lambda h: H(_perturbed(wp, idx, h), wm))
+        fdm = fd5(lambda h: H(wp, _perturbed(wm, idx, h)))
+        assert abs(fdp - gp[idx]) < 1e-8 * abs(gp[idx]) + 1e-9
+        assert abs(fdm - gm[idx]) < 1e-8 * abs(gm[idx]) + 1e-9
+
+
+def test_scft_relaxation_converges_to_a_lamellar_saddle():
+    """From the perturbed lamellar seed (W- = 5 cos(2 pi x/L) + noise, W+ = 0), repeated
+    explicit Euler steps of Eq. 9 drive both forces of Eq. 7 to zero (a saddle point of H),
+    with the lamellar order kept (the fundamental of W- stays large).  A step with either
+    sign flipped runs away instead."""
+    n, L, Ns, fA, chiN, lam = (16, 2, 2), (4.0, 1.0, 1.0), 32, 0.5, 15.0, 1.0
+    x = np.arange(n[0]) * L[0] / n[0]
+    rng = np.random.default_rng(65)
+    wm = 5.0 * np.cos(2 * np.pi * x / L[0])[:, None, None] + rng.normal(0, 0.1, n)
     wp = np.zeros(n)
-    wm = np.zeros(n)
-    phiA = np.full(n, 0.7)
-    phiB = np.full(n, 0.5)
-    a, b = o.scft_euler_step(wp, wm, phiA, phiB, 10.0, 0.1)
-    assert np.allclose(a, 0.1 * 0.2) and np.allclose(b, -0.1 * (0.5 - 0.7))
+
+    def run(sgn_p, sgn_m, steps):
+        a, b = wp.copy(), wm.copy()
+        norms = []
+        for _ in range(steps):
+            with np.errstate(all="ignore"):
+                s = o.solve(a, b, n, L, Ns, fA, o.SCFT_REAL)
+            fp, fm = o.mean_field_forces(a, b, s.phiA, s.phiB, chiN, o.SCFT_REAL)
+            norms.append(math.sqrt(np.mean(fp * fp) + np.mean(fm * fm)))
+            an, bn = o.scft_euler_step(a, b, s.phiA, s.phiB, chiN, lam)
+            a, b = a + sgn_p * (an - a), b + sgn_m * (bn - b)
+            if not np.all(np.isfinite(b)) or np.max(np.abs(b)) > 1e3:
+                norms.append(float("inf"))
+                break
+        return norms, b
+    norms, b = run(1, 1, 300)
+    assert norms[-1] < 1e-4 * norms[0]
+    fund = abs(np.fft.fft(b.mean(axis=(1, 2)))[1]) / n[0]
+    assert fund > 1.0
+    for sp, sm in ((1, -1), (-1, 1)):
+        bad, _ = run(sp, sm, 300)
+        assert not bad[-1] < 1e-2 * norms[0]
+
+
+def test_variable_cell_step_lowers_h():
+    """The cell step of the variable-cell relaxation, L_a <- L_a - lam_L dh/dL_a with
+    h = H/(C V) = <field term> - lnQ, lowers h by lam_L |dh/dL|^2 to first order (fields
+    held on the grid; dlnQ/dL pinned by finite differences above)."""
+    n, Ns, fA, chiN, lam_L = (6, 4, 8), 12, 0.35, 16.0, 1e-5
+    L = np.array([3.0, 2.0, 4.0])
+    wp, wm = _rand_fields(n, o.SCFT_REAL, 66)
+
+    def h(Lx):
+        s = o.solve(wp, wm, n, Lx, Ns, fA, o.SCFT_REAL)
+        return o.hamiltonian(wp, wm, s.lnQ, chiN, 1.0, n, Lx, o.SCFT_REAL) / float(np.prod(Lx)), s
+    h0, s = h(L)
+    Ln = o.variable_cell_step(L, s, n, lam_L)
+    h1, _ = h(Ln)
+    g = -np.real(o.dlnQ_dL(s, n, L))
+    pred = -lam_L * float(np.sum(g * g))
+    assert h1 - h0 < 0 and abs((h1 - h0) / pred - 1) < 1e-3
 
 
 # ---------------------------------------------------------------- generator
