@@ -38,16 +38,16 @@ WORK = wl.GYR128
 # conjugate step also reads the partner q and reads+writes an FP64 accumulator
 # (3e+f+2a).  Mean (5e+2f+2a)/2 with e=f=4, a=8 (FP32-mixed) or e=f=a=8 (FP64), real fields.
 BYTES_PER_UNIT = {"fp32": 22.0, "fp64": 36.0}
-# FP64 is bound by the GB300 FP64 pipe (1.25 TFLOP/s nominal dense, 1.20 measured with
-# an FMA loop).  Flops per unit: a real-to-half-spectrum 3D transform costs
-# 2.5 log2(M) flops per point in the usual 5 N log2 N convention; one contour step does
-# a forward and an inverse one, plus about 6 pointwise flops (two Boltzmann multiplies,
-# the diffusion multiply, the quadrature update).
-FP64_PEAK_TFLOPS = 1.25
+# FP64 is bound by the GB300 FP64 pipe, whose rate is measured live (pft_fma_throughput,
+# a DFMA loop over every SM) as the denominator of the FP64 roofline.  Flops per unit: a
+# real-to-half-spectrum 3D transform costs 2.5 log2(M) flops per point in the usual
+# 5 N log2 N convention; one contour step does a forward and an inverse one, plus about 6
+# pointwise flops (two Boltzmann multiplies, the diffusion multiply, the quadrature update).
+FP64_NOMINAL_TFLOPS = 1.25
 # DRAM traffic of one contour step of one propagator on the FP32 128^3 path (plane kernel
-# + x pass, steady state inside a block), dram__bytes_read.sum + dram__bytes_write.sum from
-# one ncu capture (profiles/plane_kernel_and_x_pass_fp32_128cubed_ncu.md).  Valid only for
-# the kernel sources it was taken on: reported as null once any of them changes.
+# + x pass, steady state inside a block): dram__bytes_read.sum + dram__bytes_write.sum from
+# one ncu capture of the kernels built from the sources below.  Reported as null once any
+# of them changes.
 TRAFFIC_FP32 = {"bytes_per_contour_step": 16.943360e6 + 0.0 + 8.543488e6,
                 "sources": ("paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
                             "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_fft.cuh"),
@@ -149,29 +149,59 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def _oracle_sample(seconds_target=15.0, nsteps=None):
-    """Time the FP64 oracle on a bounded sample of the workload: its forward and backward
-    marches (Boltzmann + FFT split steps) at the full 128^3 grid for a number of contour
-    steps each.  Returns (units/s, sample description, cores)."""
+def _cpu_model():
+    """CPU model of this host (lscpu's model name, else /proc/cpuinfo, else platform)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+ORACLE_SAMPLE_NS = 10
+
+
+def _oracle_sample(workers=None, Ns=ORACLE_SAMPLE_NS):
+    """Time the FP64 oracle on a bounded sample of the workload: one complete field update
+    (both marches, Q, the contour quadrature, densities, H and the explicit-Euler field
+    step) on the full 128^3 grid with Ns contour steps instead of the workload's 100, so
+    that a sample is seconds, not minutes.  workers=None: numpy.fft on one core (the
+    oracle as it stands); workers=k: the same oracle with its transforms on k threads of
+    scipy.fft.  Returns (units/s, sample description, cores)."""
     import oracle as o
-    wp, wm = wl.fields(WORK)
-    ds = 1.0 / WORK.Ns
-    NsA = o.n_A_steps(WORK.Ns, WORK.fA)
-    wA, wB = o.species_fields(wp, wm, o.SCFT_REAL)
-    BA, BB = o.boltzmann_factor(wA, ds), o.boltzmann_factor(wB, ds)
-    D = o.diffusion_factor(WORK.n, WORK.L, ds)
-    t0 = time.perf_counter()
-    o.forward_march(BA, BB, D, 1, NsA)  # warm-up / size the sample
-    t1 = time.perf_counter() - t0
-    if nsteps is None:
-        nsteps = max(1, min(WORK.Ns, int(seconds_target / (2 * max(t1, 1e-3)))))
-    t0 = time.perf_counter()
-    o.forward_march(BA, BB, D, nsteps, NsA)
-    o.backward_march(BA, BB, D, nsteps, NsA)
-    dt = time.perf_counter() - t0
-    units = 2 * WORK.M * nsteps
-    return units / dt, (f"oracle forward and backward marches, {nsteps} contour steps each on the 128^3 grid "
-                        f"({dt:.1f} s)"), 1
+    w = WORK.with_(Ns=Ns)
+    wp, wm = wl.fields(w)
+
+    def update():
+        s = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL)
+        o.hamiltonian(wp, wm, s.lnQ, w.chiN, w.C, w.n, w.L, o.SCFT_REAL)
+        o.scft_euler_step(wp, wm, s.phiA, s.phiB, w.chiN, w.lam)
+
+    def timed():
+        t0 = time.perf_counter()
+        update()
+        return time.perf_counter() - t0
+    if workers is None:
+        dt = timed()
+        cores, how = 1, "numpy.fft, 1 core"
+    else:
+        with o.fft_workers(workers):
+            dt = timed()
+        cores, how = workers, f"scipy.fft with {workers} workers (other oracle arithmetic on 1 core)"
+    units = 2 * w.M * w.Ns
+    return units / dt, (f"one complete oracle field update (solve + H + Euler step) of the 128^3 workload at "
+                        f"Ns={Ns} ({dt:.1f} s; {how})"), cores
 
 
 def _config(ws):
@@ -188,7 +218,7 @@ def run_reference(args):
         return 0
     vals = []
     for i in range(args.warmup + args.steps):
-        v, sample, cores = _oracle_sample(nsteps=5)
+        v, sample, cores = _oracle_sample(Ns=4)
         if i >= args.warmup:
             vals.append(v)
     value = float(np.mean(vals))
@@ -196,7 +226,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(1),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -356,10 +387,11 @@ def _adjoint_time(pft, torch, w, prec, reps=5):
             "note": "gradient of a loss on (phiA, phiB) w.r.t. (W+, W-) through the discrete march"}
 
 
-def _library_fft_step(torch, wpa, wma, steps=3, warmup=1):
+def _library_fft_step(torch, wpa, wma, steps=5, warmup=2):
     """Comparison arm (not the product path): the same field update written with
-    torch.fft (cuFFT) R2C/C2R transforms and separate elementwise kernels, eager launches,
-    FP32 propagators and FP64 quadrature/update, on the headline workload."""
+    torch.fft (cuFFT) R2C/C2R transforms and separate elementwise kernels, FP32
+    propagators and FP64 quadrature/update, on the headline workload, replayed as a
+    captured CUDA graph."""
     w = WORK
     dev = torch.device("cuda")
     n = tuple(w.n)
@@ -404,20 +436,37 @@ def _library_fft_step(torch, wpa, wma, steps=3, warmup=1):
         wm2 = wm - w.lam * (2.0 * wm / w.chiN + phiB - phiA)
         return wp2, wm2, Q
 
-    for _ in range(warmup):
-        step(wp, wm)
+    # warm-up on a side stream (cuFFT plans are made here, outside the capture), then one
+    # field update captured as a CUDA graph and replayed: the comparison pays no Python
+    # launch overhead
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warmup):
+            step(wp, wm)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        wp2, wm2, Q = step(wp, wm)
+        wp.copy_(wp2)
+        wm.copy_(wm2)
+    graph.replay()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(steps):
-        wp, wm, Q = step(wp, wm)
+        graph.replay()
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
     units = 2 * w.M * Ns
-    return {"kind": "torch.fft (cuFFT) + elementwise kernels, eager", "ms_per_step": ms,
-            "value": units / (ms * 1e-3), "unit": UNIT, "Q_last": float(Q)}
+    out = {"kind": "torch.fft (cuFFT) R2C/C2R + torch elementwise kernels, one field update captured as a "
+                   "CUDA graph and replayed", "ms_per_step": ms,
+           "value": units / (ms * 1e-3), "unit": UNIT, "Q_last": float(Q)}
+    del graph
+    return out
 
 
 def _batch(pft, prec, updates=2):
@@ -454,6 +503,15 @@ def _batch(pft, prec, updates=2):
     out["unit"] = UNIT
     out["instances"] = len(descs)
     out["graphed_over_per_instance"] = out["graphed"]["value"] / out["per_instance"]["value"]
+    # algorithmic roofline of the batch: 22 B per unit for a real (SCFT) instance, 44 B for
+    # a complex (CL) one, FP32-mixed, over the graphed update time
+    bpu = {wl.SCFT: 22.0, wl.CL: 44.0}
+    algo_bytes = sum(2 * d.M * d.Ns * bpu[d.kind] for d in descs)
+    peak, src = _peaks()
+    for k in ("graphed", "graphed_autotuned"):
+        gbs = algo_bytes / (out[k]["ms_per_update"] * 1e-3) / 1e9
+        out[k]["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                              "peak_source": f"{src} hbm_gbs", "algorithmic_bytes_per_update": algo_bytes}
     return out
 
 
@@ -539,9 +597,11 @@ def run(args):
         else:
             fpu = fp64_flops_per_unit(WORK.M)
             tf = fpu * WORK.M / (step_ms * 1e-3) / 1e12
+            dfma = pft.pft_fma_throughput(pft.PFT_FP64)
             roof = {"bound": "alu", "kernel": "pair step (both propagators): batched y, x (D), y inverse, fused z passes; FP64 pipe",
-                    "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
-                    "peak_source": "nominal GB300 dense FP64 (1.20 measured by an FMA loop)",
+                    "achieved": tf, "peak": dfma, "unit": "TFLOP/s", "frac": tf / dfma,
+                    "peak_source": f"measured DFMA throughput of this GPU (pft_fma_throughput; nominal "
+                                   f"{FP64_NOMINAL_TFLOPS} TFLOP/s)",
                     "flops_per_unit": fpu, "units_per_launch": WORK.M, "step_us": step_ms * 1e3,
                     "hbm_achieved_GBps": achieved, "hbm_frac": achieved / peak, "traffic": None}
         res[prec_name] = {
@@ -549,9 +609,13 @@ def run(args):
             "roofline": roof,
             "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 4),
                             "share": round(v["ms"] / prof["total_ms"], 4) if prof["total_ms"] else None,
-                            "GBps": round(v["bytes_per_launch"] * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
+                            "logical_GBps": round(v["bytes_per_launch"] * v["launches"] / (v["ms"] * 1e-3) / 1e9, 1)
                             if v["ms"] > 0 and v["bytes_per_launch"] > 0 else None}
                         for k, v in prof["kinds"].items() if v["launches"]},
+            "kernels_note": "device time per kernel class of one eager solve (events between launches, "
+                            "two-member launches on one stream); logical_GBps counts every byte each launch "
+                            "addresses, including spectrum round trips that L2 serves -- it is not DRAM "
+                            "throughput",
             "top_kernel": top[0],
             "e2e": {"value": ws * units_per_step / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": 2 * WORK.M * 8, "d2h_bytes_per_step": 2 * WORK.M * 8},
@@ -589,6 +653,8 @@ def run(args):
             torch.distributed.destroy_process_group()
         return 0
     cpu_v, cpu_sample, cpu_cores = _oracle_sample()
+    ncpu = os.cpu_count() or 1
+    cpu_all_v, cpu_all_sample, _ = _oracle_sample(workers=ncpu)
     main = res["fp32"]
     fp64 = res["fp64"]
     line = {
@@ -598,7 +664,9 @@ def run(args):
         "data": "synthetic",
         "config": _config(ws),
         "roofline": main["roofline"], "kernels": main["kernels"],
-        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_sample},
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cpu_cores, "kind": "oracle", "sample": cpu_sample,
+                         "cpu_model": _cpu_model(),
+                         "all_cores": {"value": cpu_all_v, "unit": UNIT, "cores": ncpu, "sample": cpu_all_sample}},
         "e2e": main["e2e"],
         "gpu_launches": main["launches_per_step"] * args.steps if main["launches_per_step"] else None,
         "gpu_launches_per_step": main["launches_per_step"], "clocks": main["clocks"],

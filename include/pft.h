@@ -66,15 +66,11 @@ typedef enum {
   PFT_STEP_SCFT_SIS = 2,
   PFT_STEP_CL_SIS = 3
 } pft_step_kind;
-/* How the marches run.  PASSES: five pass kernels per contour step, replayed as one
- * CUDA graph per solve.  RESIDENT (FP32-mixed, real SCFT fields, cubic 64^3/96^3/128^3
- * grids only): one persistent cooperative launch per march, one CTA per x-plane keeping
- * the Boltzmann factors and a spectrum plane in shared memory, two grid barriers per
- * contour step.  PERSISTENT (FP32-mixed, real SCFT fields, cubic 64^3/128^3/256^3):
- * one cooperative launch per march over every SM (two CTAs per SM) running the pass
- * tiles with bounded grid barriers in place of kernel boundaries, the z inverse of one
- * step fused with the z forward of the next.  AUTO picks the fastest on GB300. */
-typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1, PFT_MARCH_RESIDENT = 2, PFT_MARCH_PERSISTENT = 3 } pft_march;
+/* How the marches run.  PASSES (and AUTO, the same): the pass kernels of each contour
+ * step -- a plane kernel for the y and z transforms plus an x pass where the grid has
+ * one (FP32 real fields with ny = nz = 64 or 128, complex with ny = nz = 64), pencil
+ * passes elsewhere -- replayed as one CUDA graph per solve.  Other values: PFT_ERR_ARG. */
+typedef enum { PFT_MARCH_AUTO = 0, PFT_MARCH_PASSES = 1 } pft_march;
 
 /* Contour scheme.  SPLIT2: the 2nd-order split step A(ds) of Eq. 13 with the trapezoid
  * rule per block for Eq. 8.  RQM4: the 4th-order Richardson combination of Eq. 13,
@@ -109,14 +105,14 @@ typedef struct {
   void* stream;             /* cudaStream_t to run on; NULL: the library creates one */
   unsigned long long seed;  /* Philox key of the CL noise */
   unsigned long long instance; /* Philox counter word: independent replica streams */
-  pft_march march;          /* PFT_MARCH_RESIDENT where it does not apply: PFT_ERR_UNSUPPORTED */
+  pft_march march;          /* PFT_MARCH_AUTO or PFT_MARCH_PASSES */
   pft_scheme scheme;        /* PFT_SCHEME_SPLIT2 (0) or PFT_SCHEME_RQM4 */
   int checkpoint;           /* q history: 0 = AUTO (every slice when the two histories fit in
                                60% of the free device memory, else every ceil(sqrt(Ns))-th),
                                1 = every slice, K >= 2 = every K-th slice (clamped to Ns): the
                                conjugate march recomputes each segment of K-1 slices from its
-                               checkpoint (one extra forward march).  K >= 2 needs the pass
-                               march and the SPLIT2 scheme (else PFT_ERR_UNSUPPORTED). */
+                               checkpoint (one extra forward march).  K >= 2 needs the SPLIT2
+                               scheme (else PFT_ERR_UNSUPPORTED). */
   int autotune;             /* 1: at the first solve, time the plans of the pass march (plane
                                kernel or pencil passes; two propagator chains on two streams or
                                two-member launches) on the context's own data and keep the
@@ -370,10 +366,12 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
  * one static device array of about 6.3 MB that every GPU loading the library keeps
  * until the process exits; the limit is 64 points per axis (64^3 points).  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls share the array and each
- * call overwrites every part of it that it reads, so nothing needs clearing between
- * calls -- but calls whose work overlaps on the GPU (different streams or devices
- * sharing a context without ordering) race on it.  Allocates nothing: no cudaMalloc,
+ * that first call before any stream capture.  The address is kept for the rest of the
+ * process: a caller that destroys the device's primary context (cudaDeviceReset) must
+ * not call this entry point on that device again in the same process.  All calls share
+ * the array and each call overwrites every part of it that it reads, so nothing needs
+ * clearing between calls -- but calls whose work overlaps on the GPU (different
+ * streams or devices sharing a context without ordering) race on it.  Allocates nothing: no cudaMalloc,
  * cudaFree or allocating library routine.
  * Errors: PFT_ERR_ARG (NULL pointer, Ns < 1, non-positive L, any n[a] > 64),
  * PFT_ERR_SHAPE (a size without an FFT plan), PFT_ERR_CUDA. */
@@ -387,21 +385,15 @@ pft_status pft_contour_step_static(const int n[3], const double L[3], int Ns, co
  * also unnormalised).  in/out host or device per `where`, may alias. */
 pft_status pft_fft3d(pft_ctx* ctx, const void* in, void* out, int inverse, pft_mem where);
 
-/* Copy slice `s` (0..Ns) of the forward propagator history (which = 0) or the last
- * conjugate propagator slice qd_Ns (which = 1, s ignored) out as float64/complex128. */
+/* Copy slice `s` (0..Ns) of the forward propagator history (which = 0), the last
+ * conjugate propagator slice qd_Ns (which = 1, s ignored), or slice s of the conjugate
+ * history (which = 2; contexts that keep it: the concurrent SPLIT2 march with the full
+ * history, else PFT_ERR_UNSUPPORTED) out as float64/complex128. */
 pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem where);
 
 /* Replace the initial condition q_0 = qd_0 = 1 by a caller array (M values, float64
  * or complex128 by kind; NULL restores 1).  Used by the diffusion-only test. */
 pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
-
-/* Budget, in GPU clock cycles, of each bounded grid-barrier wait of the resident
- * march (default 4e9, about 2 s).  A wait that runs out sets the context's error word:
- * the march returns early and pft_get_observables reports PFT_ERR_TIMEOUT. */
-pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles);
-
-/* Which march the context uses: 1 = passes, 2 = resident, 3 = persistent. */
-pft_status pft_get_march(const pft_ctx* ctx, int* march);
 
 /* Plan of the pass march in use: *plane = 1 if the y/z plane kernel runs the steps (FP32
  * real fields with ny = nz = 64 or 128, complex fields with ny = nz = 64), *streams = 1
@@ -416,10 +408,19 @@ pft_status pft_get_checkpoint(const pft_ctx* ctx, int* K);
 /* Kernel launches of this library per call, for accounting (no counterpart in the
  * paper).  *solve: the kernel nodes of the CUDA graph one pft_solve replays, counted
  * when the graph was captured; -1 before the first graphed solve and for contexts that
- * solve without a graph (use_graph = 0, resident or persistent march).  *field_step:
+ * solve without a graph (use_graph = 0).  *field_step:
  * the kernels one pft_field_step launches.  Either pointer may be NULL.
  * Errors: PFT_ERR_ARG for a NULL ctx. */
 pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* field_step);
+
+/* Fused multiply-add throughput of the current device, in TFLOP/s (2 flops per FMA):
+ * independent FMA chains on every SM for about 20 ms, timed with CUDA events on `stream`
+ * (cudaStream_t, NULL for the legacy default stream) after one warm-up launch.  No
+ * counterpart in the paper: the FP64 contour step is bound by the FP64 pipe, and this is
+ * the denominator of its roofline (precision PFT_FP64: DFMA; PFT_FP32_MIXED: FFMA).
+ * Allocates and frees a small output buffer (stream-ordered); synchronises the stream.
+ * Errors: PFT_ERR_ARG (NULL tflops, unknown precision), PFT_ERR_CUDA. */
+pft_status pft_fma_throughput(int precision, double* tflops, void* stream);
 
 /* Standard normals of the device Philox stream (same layout as the CL noise) for
  * points 0..M-1 into a device float64 array, on `stream` (cudaStream_t or NULL). */

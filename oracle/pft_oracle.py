@@ -3,7 +3,9 @@
 TEST INFRASTRUCTURE ONLY.  Slow and obviously correct on purpose: it follows the
 method of Delaney & Fredrickson, "Polymer Field-Theory Simulations on Graphics
 Processing Units" (arXiv:1204.5434), step by step, in numpy float64/complex128, with
-``numpy.fft`` as the only library primitive.  Nothing here is blocked, fused or
+``numpy.fft`` as the only library primitive (``fft_workers`` swaps in ``scipy.fft`` on
+several threads for the all-core CPU baseline; the arithmetic stays the same).  Nothing
+here is blocked, fused or
 reordered.  Only the test-suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg
 of ``bench.py`` may call it; the CUDA library never does.
 
@@ -32,6 +34,7 @@ Every function cites the passage of the paper it follows.
 from __future__ import annotations
 
 import math
+from contextlib import contextmanager
 from dataclasses import dataclass
 
 import numpy as np
@@ -48,9 +51,35 @@ __all__ = [
     "dlnQ_dL", "dH_dL", "dH_dfields", "dft_matrix", "dft3_bruteforce",
     "dense_propagator_matrix", "forward_march_dense", "continuum_Q", "debye_g",
     "variable_cell_step", "rqm4_step", "simpson_weights", "SPLIT2", "RQM4",
-    "debye_chain", "scft_sis_step", "cl_sis_step", "EdwardsSolution", "edwards_field", "edwards_solve",
+    "debye_chain", "scft_sis_step", "cl_sis_step", "fft_workers", "EdwardsSolution", "edwards_field", "edwards_solve",
     "edwards_hamiltonian", "edwards_scft_step", "edwards_cl_step", "adjoint_field_gradient",
 ]
+
+class _Transforms:
+    """The n-dimensional DFT pair every transform of the oracle goes through."""
+
+    def __init__(self, fftn, ifftn):
+        self.fftn = fftn
+        self.ifftn = ifftn
+
+
+_FFT = _Transforms(np.fft.fftn, np.fft.ifftn)
+
+
+@contextmanager
+def fft_workers(workers: int):
+    """Inside the block, the oracle's transforms run through ``scipy.fft`` on ``workers``
+    threads instead of ``numpy.fft`` (one thread): the same DFT definition, for timing the
+    oracle on every core of a host.  Nothing else changes."""
+    import scipy.fft as sf
+    global _FFT
+    saved = _FFT
+    _FFT = _Transforms(lambda x: sf.fftn(x, workers=workers), lambda x: sf.ifftn(x, workers=workers))
+    try:
+        yield
+    finally:
+        _FFT = saved
+
 
 SPLIT2 = "split2"   # 2nd-order operator splitting, the A(ds) block of Eq. 13
 RQM4 = "rqm4"       # Richardson-extrapolated 4th-order scheme of Eq. 13
@@ -104,7 +133,7 @@ def diffusion_factor(n, L, ds: float) -> np.ndarray:
 def split_step(q, Bn, D):
     """One contour step q -> B * F^-1[ D * F[ B * q ] ]: the A(ds) block of Eq. 13,
     i.e. exp(-w ds/2) exp(laplacian ds) exp(-w ds/2) applied to q."""
-    y = np.fft.ifftn(D * np.fft.fftn(Bn * q))
+    y = _FFT.ifftn(D * _FFT.fftn(Bn * q))
     if np.isrealobj(q) and np.isrealobj(Bn):
         y = y.real
     return Bn * y
@@ -332,7 +361,7 @@ def scft_sis_step(wp, wm, phiA, phiB, chiN: float, lam: float, n, L):
     W- <- (W- - lam (phiB - phiA)) / (1 + 2 lam/chiN)."""
     fp = phiA + phiB - 1.0
     gD = debye_chain(k_squared(n, L))
-    wp_new = wp + np.fft.ifftn(np.fft.fftn(lam * fp) / (1.0 + lam * gD)).real
+    wp_new = wp + _FFT.ifftn(_FFT.fftn(lam * fp) / (1.0 + lam * gD)).real
     wm_new = (wm - lam * (phiB - phiA)) / (1.0 + 2.0 * lam / chiN)
     return wp_new, wm_new
 
@@ -344,7 +373,7 @@ def cl_sis_step(wp, wm, phiA, phiB, chiN: float, dt: float, eta_p, eta_m, n, L):
     omega- <- (omega- - dt (phiB - phiA) + eta-) / (1 + 2 dt/chiN)."""
     fp = 1j * (phiA + phiB - 1.0)
     gD = debye_chain(k_squared(n, L))
-    wp_new = wp + np.fft.ifftn(np.fft.fftn(-dt * fp + eta_p) / (1.0 + dt * gD))
+    wp_new = wp + _FFT.ifftn(_FFT.fftn(-dt * fp + eta_p) / (1.0 + dt * gD))
     wm_new = (wm - dt * (phiB - phiA) + eta_m) / (1.0 + 2.0 * dt / chiN)
     return wp_new, wm_new
 
@@ -448,7 +477,7 @@ def adjoint_field_gradient(wp, wm, n, L, Ns: int, fA: float, GA, GB):
     D = sol.D
 
     def K(v):
-        return np.fft.ifftn(D * np.fft.fftn(v)).real
+        return _FFT.ifftn(D * _FFT.fftn(v)).real
 
     def g(k):
         return (ds / Q) * (cA[k] * GA + cB[k] * GB)
@@ -505,7 +534,7 @@ def dlnQ_dL(sol: Solution, n, L):
             Bn = sol.BA if k <= sol.NsA else sol.BB
             v = Bn * sol.q[k - 1]
             u = Bn * sol.qd[Ns - k]
-            w = np.fft.ifftn(g * np.fft.fftn(v))
+            w = _FFT.ifftn(g * _FFT.fftn(v))
             if np.isrealobj(v):
                 w = w.real
             tot = tot + (u * w).sum()

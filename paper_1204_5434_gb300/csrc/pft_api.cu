@@ -18,7 +18,7 @@ using pft::Engine;
 namespace pft {
 const char* const kKernelKindNames[KK_COUNT] = {"z_fwd",      "y_fwd",     "x_fused",   "y_inv",
                                                 "z_inv_fwd",  "z_inv_bwd", "reduce",    "field_step",
-                                                "prepare",    "march_fwd", "march_bwd", "pair_step",
+                                                "prepare",    "pair_step",
                                                 "quadrature"};
 static thread_local std::string g_err;
 void set_error(const std::string& s) { g_err = s; }
@@ -122,7 +122,7 @@ void free_all(pft_ctx* c) {
   if (d.graph) cudaGraphExecDestroy(d.graph);
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
-                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.sync, d.qdh, d.steps2, d.stepsg,
+                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.qdh, d.steps2, d.stepsg,
                   d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa, d.stepsap};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -187,18 +187,15 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   if (!(model->C > 0.0) || !isfinite(model->C)) return fail(PFT_ERR_ARG, "C must be positive");
   if (!edw && !(model->chiN > 0.0)) return fail(PFT_ERR_ARG, "chiN must be positive");
   if (edw && !(model->B >= 0.0 && isfinite(model->B))) return fail(PFT_ERR_ARG, "B must be finite and >= 0");
-  if (edw && (opts->scheme != PFT_SCHEME_SPLIT2 || opts->checkpoint >= 2 ||
-              (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES)))
-    return fail(PFT_ERR_UNSUPPORTED, "the Edwards model runs SPLIT2 on the pass march with the full history");
+  if (edw && (opts->scheme != PFT_SCHEME_SPLIT2 || opts->checkpoint >= 2))
+    return fail(PFT_ERR_UNSUPPORTED, "the Edwards model runs SPLIT2 with the full history");
   if (model->kind != PFT_SCFT_REAL && model->kind != PFT_CL_COMPLEX) return fail(PFT_ERR_ARG, "unknown model kind");
   if (opts->precision != PFT_FP64 && opts->precision != PFT_FP32_MIXED) return fail(PFT_ERR_ARG, "unknown precision");
   if (opts->scheme != PFT_SCHEME_SPLIT2 && opts->scheme != PFT_SCHEME_RQM4) return fail(PFT_ERR_ARG, "unknown scheme");
-  if (opts->scheme == PFT_SCHEME_RQM4 && opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES)
-    return fail(PFT_ERR_UNSUPPORTED, "the 4th-order scheme runs on the pass kernels only");
+  if (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES) return fail(PFT_ERR_ARG, "unknown march");
   if (opts->checkpoint < 0) return fail(PFT_ERR_ARG, "checkpoint interval must be >= 0");
-  if (opts->checkpoint >= 2 && (opts->scheme != PFT_SCHEME_SPLIT2 || (opts->march != PFT_MARCH_AUTO &&
-                                                                      opts->march != PFT_MARCH_PASSES)))
-    return fail(PFT_ERR_UNSUPPORTED, "a checkpointed history needs the pass march and the SPLIT2 scheme");
+  if (opts->checkpoint >= 2 && opts->scheme != PFT_SCHEME_SPLIT2)
+    return fail(PFT_ERR_UNSUPPORTED, "a checkpointed history needs the SPLIT2 scheme");
 
   pft_ctx* c = new pft_ctx();
   CtxData& d = c->d;
@@ -255,34 +252,9 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
     return s;
   }
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
-  {
-    const bool can_res = c->eng->resident_supported(d);
-    const bool can_per = c->eng->persist_supported(d);
-    if (opts->march != PFT_MARCH_AUTO && opts->march != PFT_MARCH_PASSES && opts->march != PFT_MARCH_RESIDENT &&
-        opts->march != PFT_MARCH_PERSISTENT) {
-      free_all(c);
-      return fail(PFT_ERR_ARG, "unknown march");
-    }
-    if (opts->march == PFT_MARCH_RESIDENT && !can_res) {
-      free_all(c);
-      return fail(PFT_ERR_UNSUPPORTED,
-                  "resident march needs FP32-mixed precision, real SCFT fields and a 64^3, 96^3 or 128^3 grid");
-    }
-    if (opts->march == PFT_MARCH_PERSISTENT && !can_per) {
-      free_all(c);
-      return fail(PFT_ERR_UNSUPPORTED,
-                  "persistent march needs FP32-mixed precision, real SCFT fields and a 64^3, 128^3 or 256^3 grid");
-    }
-    d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
+  d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
   d.autotune = opts->autotune != 0;
-    if (opts->march == PFT_MARCH_RESIDENT) {
-      d.march = 2;
-    } else if (opts->march == PFT_MARCH_PERSISTENT) {
-      d.march = 3;
-    } else {
-      d.march = 1;  // AUTO: the pass kernels (see include/pft.h)
-    }
-  }
+  d.plan_plane = c->eng->plane_applies(d) ? 1 : 0;  // the default plan: plane kernel where it applies
 
   const size_t M = (size_t)d.M;
   const size_t we = welem(d), fe = felem(d);
@@ -299,7 +271,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       }
     }
     if (K > d.Ns) K = d.Ns;
-    if (K < 2 || d.march != 1 || d.scheme != 0 || d.edw) K = 1;
+    if (K < 2 || d.scheme != 0 || d.edw) K = 1;
     d.ckK = K;
     d.nck = (K > 1) ? d.Ns / K + 1 : 0;
   }
@@ -311,7 +283,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       {&d.hist, (size_t)pft::q_slots(d) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
       {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
       {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
-      {&c->io, M * 16}, {(void**)&d.sync, 4 * sizeof(unsigned)},
+      {&c->io, M * 16},
       // quarter-step Boltzmann factors of the 4th-order scheme
       {d.scheme ? &d.BAh : nullptr, M * we}, {d.scheme ? &d.BBh : nullptr, M * we},
   };
@@ -330,7 +302,6 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
     e = cudaMemsetAsync(d.scal, 0, pft::S_COUNT * sizeof(double), d.stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(d.partials, 0, (size_t)d.npart * 8 * sizeof(double), d.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.sync, 0, 4 * sizeof(unsigned), d.stream);
   if (e == cudaSuccess) e = c->eng->upload_tables(d);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.hist);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.qd0);
@@ -569,14 +540,11 @@ pft_status pft_get_observables(pft_ctx* ctx, pft_obs* obs) {
   CtxData& d = ctx->d;
   if (!ctx->have_obs) return fail(PFT_ERR_STATE, "no solve since the fields were set");
   PFT_CK(cudaMemcpyAsync(d.scal_host, d.scal, pft::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
-  unsigned syncw[4] = {0, 0, 0, 0};
-  if (d.march >= 2) PFT_CK(cudaMemcpyAsync(syncw, d.sync, sizeof(syncw), cudaMemcpyDeviceToHost, d.stream));
   PFT_CK(cudaStreamSynchronize(d.stream));
   const double* s = d.scal_host;
   const double V = d.L[0] * d.L[1] * d.L[2];
   const double Md = (double)d.M;
   memset(obs, 0, sizeof(*obs));
-  if (syncw[2] != 0) return fail(PFT_ERR_TIMEOUT, "a grid barrier of the march ran out of its wait budget");
   for (int j = 0; j < 2; j++) {
     obs->Q[j] = s[pft::S_Q + j];
     obs->lnQ[j] = s[pft::S_LNQ + j];
@@ -685,8 +653,8 @@ pft_status pft_adjoint(pft_ctx* ctx, const void* dL_dphiA, const void* dL_dphiB,
   CtxData& d = ctx->d;
   if (d.kind != PFT_SCFT_REAL || d.edw || d.scheme != 0)
     return fail(PFT_ERR_UNSUPPORTED, "the adjoint is implemented for real SCFT diblock fields and SPLIT2");
-  if (!(d.march == 1 && d.concurrent && d.ckK == 1))
-    return fail(PFT_ERR_UNSUPPORTED, "the adjoint needs the pass march with both histories kept");
+  if (!(d.concurrent && d.ckK == 1))
+    return fail(PFT_ERR_UNSUPPORTED, "the adjoint needs both histories kept");
   if (!d.solved || !d.qdh) return fail(PFT_ERR_STATE, "pft_adjoint needs a solve at the current fields");
   const size_t b = (size_t)d.M * 8;
   double* io = (double*)ctx->io;  // 2 M doubles of staging: the two loss gradients
@@ -770,7 +738,7 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   int iF = -1, iR1 = -1, iB = -1, iR2 = -1;
   for (int i = 0; i < d.ev_used; i++) {
     const int k = d.ev_kind[i];
-    const bool march_start = (k == pft::KK_Z_FWD || k == pft::KK_MARCH_FWD || k == pft::KK_MARCH_BWD);
+    const bool march_start = (k == pft::KK_Z_FWD);
     if (iF < 0 && march_start) iF = i;
     else if (iF >= 0 && iR1 < 0 && k == pft::KK_REDUCE) iR1 = i;
     else if (iR1 >= 0 && iB < 0 && march_start) iB = i;
@@ -806,10 +774,6 @@ pft_status pft_profile_step(pft_ctx* ctx, int step_kind, double lam_or_dt, pft_p
   out->bytes_per_launch[pft::KK_Z_INV_BWD] = Ms * ze + 3 * M * we + 2 * M * fe;
   out->bytes_per_launch[pft::KK_FIELD_STEP] = 6 * M * fe + 2 * M * we;
   out->bytes_per_launch[pft::KK_PREPARE] = 2 * M * fe + 2 * M * we;
-  // one resident launch runs a whole march: per step the forward reads q_{n-1} and B
-  // and writes q_n, the conjugate one also reads the partner and updates an accumulator
-  out->bytes_per_launch[pft::KK_MARCH_FWD] = (double)d.Ns * (3 * M * we);
-  out->bytes_per_launch[pft::KK_MARCH_BWD] = (double)d.Ns * (4 * M * we + 2 * M * 8.0);
   out->bytes_per_launch[pft::KK_PAIR_STEP] = 2 * (2 * M * we + Ms * ze) + 6 * (2 * Ms * ze) + 2 * (Ms * ze + 2 * M * we);
   if (d.scheme == 1) {
     // 4th-order step of both propagators: four z forwards, 18 strided passes, two z
@@ -838,11 +802,21 @@ pft_status pft_fft3d(pft_ctx* ctx, const void* in, void* out, int inverse, pft_m
 pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem where) {
   if (!ctx || !out) return fail(PFT_ERR_ARG, "NULL argument");
   CtxData& d = ctx->d;
-  if (which != 0 && which != 1) return fail(PFT_ERR_ARG, "which must be 0 (q) or 1 (qd)");
-  if (which == 0 && (s < 0 || s > d.Ns)) return fail(PFT_ERR_ARG, "slice out of range");
+  if (which < 0 || which > 2) return fail(PFT_ERR_ARG, "which must be 0 (q), 1 (last qd) or 2 (qd slice)");
+  if (which != 1 && (s < 0 || s > d.Ns)) return fail(PFT_ERR_ARG, "slice out of range");
   const size_t we = welem(d);
+  if (which == 2) {  // slice s of the conjugate history, where the context keeps one
+    if (!(d.concurrent && d.qdh && d.ckK == 1 && !d.edw && d.scheme == 0))
+      return fail(PFT_ERR_UNSUPPORTED, "this context keeps no conjugate history");
+    const void* src2 = (s == 0) ? (const void*)d.qd0 : (const void*)((const char*)d.qdh + (size_t)s * d.M * we);
+    const long long cnt2 = d.M * (d.kind == PFT_SCFT_REAL ? 1 : 2);
+    PFT_CK(ctx->eng->to_f64(d, src2, ctx->io, cnt2));
+    PFT_CK(cudaMemcpyAsync(out, ctx->io, (size_t)cnt2 * 8, kind_out(where), d.stream));
+    PFT_CK(cudaStreamSynchronize(d.stream));
+    return PFT_OK;
+  }
   const void* qd_last = d.edw ? (const void*)((const char*)d.hist + (size_t)d.Ns * d.M * we) :  // qd = q
-                        (d.march == 1 && d.concurrent && d.qdh && d.ckK == 1) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
+                        (d.concurrent && d.qdh && d.ckK == 1) ? (const void*)((const char*)d.qdh + (size_t)d.Ns * d.M * we)
                                                                   : d.qd[d.Ns & 1];
   if (which == 0 && !pft::q_kept(d, s))
     return fail(PFT_ERR_UNSUPPORTED, "slice " + std::to_string(s) + " is not kept by the checkpointed history");
@@ -870,21 +844,10 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where) {
   return PFT_OK;
 }
 
-pft_status pft_debug_set_spin_limit(pft_ctx* ctx, long long cycles) {
-  if (!ctx || cycles < 1) return fail(PFT_ERR_ARG, "bad argument");
-  ctx->d.spin_limit = cycles;
-  ctx->d.graph_valid = false;  // the budget is a launch argument captured in the graph
-  if (ctx->d.graph) {
-    cudaGraphExecDestroy(ctx->d.graph);
-    ctx->d.graph = nullptr;
-  }
-  return PFT_OK;
-}
-
 pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* field_step) {
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   const CtxData& d = ctx->d;
-  if (solve) *solve = (d.use_graph && d.march == 1 && d.graph_valid) ? d.graph_kernels : -1;
+  if (solve) *solve = (d.use_graph && d.graph_valid) ? d.graph_kernels : -1;
   // the update kernel and its final reduction, plus the quarter-step factors of RQM4
   if (field_step) *field_step = 2 + (d.scheme == 1 ? 1 : 0);
   return PFT_OK;
@@ -903,11 +866,6 @@ pft_status pft_get_checkpoint(const pft_ctx* ctx, int* K) {
   return PFT_OK;
 }
 
-pft_status pft_get_march(const pft_ctx* ctx, int* march) {
-  if (!ctx || !march) return fail(PFT_ERR_ARG, "NULL argument");
-  *march = ctx->d.march;
-  return PFT_OK;
-}
 
 pft_status pft_philox_normals(unsigned long long seed, unsigned long long instance, unsigned long long step, int field,
                               long long M, double* out_device, void* stream) {

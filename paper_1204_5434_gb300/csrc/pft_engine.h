@@ -85,10 +85,6 @@ struct CtxData {
   size_t tables_bytes = 0;
   int npart = 0;
   size_t bytes = 0;
-  // march: 1 = passes, 2 = resident, 3 = persistent; barrier words [count, gen, err, pad]
-  int march = 1;
-  unsigned* sync = nullptr;
-  long long spin_limit = 4000000000LL;
   // optional device counter read by the CL field step instead of `step` (batches)
   const unsigned long long* step_dev = nullptr;
   // concurrent marches (pass kernels): q and qd advance together, two members per
@@ -130,7 +126,7 @@ struct CtxData {
 // Kernel classes reported by pft_profile_step.
 enum KernelKind {
   KK_Z_FWD = 0, KK_Y_FWD, KK_X_FUSED, KK_Y_INV, KK_Z_INV_FWD, KK_Z_INV_BWD, KK_REDUCE, KK_FIELD_STEP,
-  KK_PREPARE, KK_MARCH_FWD, KK_MARCH_BWD, KK_PAIR_STEP, KK_QUADRATURE, KK_COUNT
+  KK_PREPARE, KK_PAIR_STEP, KK_QUADRATURE, KK_COUNT
 };
 extern const char* const kKernelKindNames[KK_COUNT];
 
@@ -171,9 +167,7 @@ class Engine {
  public:
   virtual ~Engine() {}
   virtual size_t elem_bytes() const = 0;      // working-precision real element
-  // Can this system run the resident march (and how much shared memory it needs)?
-  virtual bool resident_supported(const CtxData& c) const = 0;
-  virtual bool persist_supported(const CtxData& c) const = 0;
+  virtual bool plane_applies(const CtxData& c) const = 0;  // can the y/z plane kernel run this grid?
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

@@ -282,22 +282,67 @@ __device__ __forceinline__ void trap_w(int n, int Ns, int NsA, double* cA, doubl
   if (NsA < Ns && n >= NsA) *cB = (n == NsA || n == Ns) ? 0.5 : 1.0;
 }
 
+// Compensated FP32 partial sum (Knuth's TwoSum): after add(x_1) ... add(x_k), hi + lo is
+// the exact sum of the x_j except for the rounding of the small correction lo itself,
+// i.e. within k 2^-48 of the sum relative to it.  Flushed into an FP64 running sum every
+// kQuadChunk terms, it spares the FP64 pipe (1/64 of the FP32 rate on GB300) one DFMA per
+// term while the result stays that of an FP64 summation of the same FP32 products to far
+// below their own rounding (2^-24).
+struct F2Sum {
+  float hi = 0.f, lo = 0.f;
+  // the _rn intrinsics keep the compiler from contracting any of these into an FMA
+  __device__ __forceinline__ void add(float x) {
+    const float s = __fadd_rn(hi, x);
+    const float bb = __fsub_rn(s, hi);
+    lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(x, bb)));
+    hi = s;
+  }
+  __device__ __forceinline__ void flush(double* acc) {
+    *acc += widen(hi);
+    *acc += widen(lo);
+    hi = 0.f;
+    lo = 0.f;
+  }
+};
+constexpr int kQuadChunk = 16;
+
 // Sum over n in [n0, n1] of w_n * q_n * qd_{Ns-n} for a pair of points, weights 1/2 at
-// both ends of the block (the block's trapezoid rule), FP64 running sums.
+// both ends of the block (the block's trapezoid rule), FP64 running sums.  FP32
+// propagators: the products are FP32 (as before), summed in compensated FP32 over chunks
+// of kQuadChunk slices that are added to the FP64 sums (the weights 1/2 and 1 are exact).
 template <typename T>
 __device__ __forceinline__ void quad_block(const T* __restrict__ hist, const T* __restrict__ qdh,
                                            const T* __restrict__ qd0, long long M, int Ns, int n0, int n1,
                                            long long i, double* s0, double* s1) {
   double a0 = 0.0, a1 = 0.0;
   if (n1 > n0) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll 1
+      for (int c0 = n0; c0 <= n1; c0 += kQuadChunk) {
+        const int c1 = min(c0 + kQuadChunk - 1, n1);
+        F2Sum f0, f1;
 #pragma unroll 4
-    for (int n = n0; n <= n1; n++) {
-      const int m = Ns - n;
-      const cpx<T> q = reinterpret_cast<const cpx<T>*>(hist + (long long)n * M)[i];
-      const cpx<T> d = reinterpret_cast<const cpx<T>*>(m == 0 ? qd0 : qdh + (long long)m * M)[i];
-      const double w = (n == n0 || n == n1) ? 0.5 : 1.0;
-      a0 = fma(w, widen(q.x * d.x), a0);
-      a1 = fma(w, widen(q.y * d.y), a1);
+        for (int n = c0; n <= c1; n++) {
+          const int m = Ns - n;
+          const float2 q = reinterpret_cast<const float2*>(hist + (long long)n * M)[i];
+          const float2 d = reinterpret_cast<const float2*>(m == 0 ? qd0 : qdh + (long long)m * M)[i];
+          const float w = (n == n0 || n == n1) ? 0.5f : 1.0f;
+          f0.add(__fmul_rn(__fmul_rn(q.x, d.x), w));
+          f1.add(__fmul_rn(__fmul_rn(q.y, d.y), w));
+        }
+        f0.flush(&a0);
+        f1.flush(&a1);
+      }
+    } else {
+#pragma unroll 4
+      for (int n = n0; n <= n1; n++) {
+        const int m = Ns - n;
+        const cpx<T> q = reinterpret_cast<const cpx<T>*>(hist + (long long)n * M)[i];
+        const cpx<T> d = reinterpret_cast<const cpx<T>*>(m == 0 ? qd0 : qdh + (long long)m * M)[i];
+        const double w = (n == n0 || n == n1) ? 0.5 : 1.0;
+        a0 = fma(w, widen(q.x * d.x), a0);
+        a1 = fma(w, widen(q.y * d.y), a1);
+      }
     }
   }
   *s0 = a0;
@@ -324,15 +369,35 @@ __device__ __forceinline__ void quad_block_c(const cpx<T>* __restrict__ hist, co
                                              long long i, double* sr, double* si) {
   double ar = 0.0, ai = 0.0;
   if (n1 > n0) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll 1
+      for (int c0 = n0; c0 <= n1; c0 += kQuadChunk) {
+        const int c1 = min(c0 + kQuadChunk - 1, n1);
+        F2Sum fr, fi;
 #pragma unroll 4
-    for (int n = n0; n <= n1; n++) {
-      const int m = Ns - n;
-      const cpx<T> q = hist[(long long)n * M + i];
-      const cpx<T> d = (m == 0 ? qd0 : qdh + (long long)m * M)[i];
-      const cpx<T> pq = cmul(q, d);
-      const double w = (n == n0 || n == n1) ? 0.5 : 1.0;
-      ar = fma(w, widen(pq.x), ar);
-      ai = fma(w, widen(pq.y), ai);
+        for (int n = c0; n <= c1; n++) {
+          const int m = Ns - n;
+          const float2 q = hist[(long long)n * M + i];
+          const float2 d = (m == 0 ? qd0 : qdh + (long long)m * M)[i];
+          const float2 pq = cmul(q, d);
+          const float w = (n == n0 || n == n1) ? 0.5f : 1.0f;
+          fr.add(__fmul_rn(pq.x, w));
+          fi.add(__fmul_rn(pq.y, w));
+        }
+        fr.flush(&ar);
+        fi.flush(&ai);
+      }
+    } else {
+#pragma unroll 4
+      for (int n = n0; n <= n1; n++) {
+        const int m = Ns - n;
+        const cpx<T> q = hist[(long long)n * M + i];
+        const cpx<T> d = (m == 0 ? qd0 : qdh + (long long)m * M)[i];
+        const cpx<T> pq = cmul(q, d);
+        const double w = (n == n0 || n == n1) ? 0.5 : 1.0;
+        ar = fma(w, widen(pq.x), ar);
+        ai = fma(w, widen(pq.y), ai);
+      }
     }
   }
   *sr = ar;

@@ -12,9 +12,7 @@
 
 #include "pft_engine_impl.cuh"
 #include "pft_batch.cuh"
-#include "pft_persist.cuh"
 #include "pft_plane_ext.cuh"
-#include "pft_resident.cuh"
 
 namespace pft {
 
@@ -85,161 +83,7 @@ class EngineT : public Engine {
   using Z = cpx<T>;
 
   size_t elem_bytes() const override { return sizeof(T); }
-
-  // ------------------------------------------------------------ resident march
-  template <int NX, int NY, int NZ, bool BWD>
-  static cudaError_t launch_resident_n(CtxData& c, const ResArgs& a) {
-    using R = Res<NX, NY, NZ>;
-    auto kern = k_resident_march<NX, NY, NZ, BWD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(NX);
-    cfg.blockDim = dim3(R::THREADS);
-    cfg.dynamicSmemBytes = R::SMEM;
-    cfg.stream = c.stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-  }
-
-  template <int NX, int NY, int NZ>
-  static bool resident_fits(const CtxData& c) {
-    using R = Res<NX, NY, NZ>;
-    int dev = c.device, smem_optin = 0, sms = 0;
-    if (cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return false;
-    return (size_t)smem_optin >= R::SMEM + 64 && NX <= sms;
-  }
-
-  bool resident_supported(const CtxData& c) const override {
-    if constexpr (!std::is_same<T, float>::value) {
-      return false;
-    } else {
-      if (c.kind != PFT_SCFT_REAL) return false;
-      if (c.n[0] != c.n[1] || c.n[1] != c.n[2]) return false;
-      switch (c.n[0]) {
-        case 64: return resident_fits<64, 64, 64>(c);
-        case 96: return resident_fits<96, 96, 96>(c);
-        case 128: return resident_fits<128, 128, 128>(c);
-        default: return false;
-      }
-    }
-  }
-
-  // ------------------------------------------------------------ persistent march
-  template <int N, bool BWD>
-  static cudaError_t launch_persist_n(CtxData& c, const PersistArgs& a) {
-    using R = Persist<N>;
-    auto kern = k_persist_march<N, BWD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, R::THREADS, R::SMEM);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    if (per_sm > 2) per_sm = 2;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(per_sm * c.sms);
-    cfg.blockDim = dim3(R::THREADS);
-    cfg.dynamicSmemBytes = R::SMEM;
-    cfg.stream = c.stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeCooperative;
-    at[0].val.cooperative = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, a);
-  }
-
-  bool persist_supported(const CtxData& c) const override {
-    if constexpr (!std::is_same<T, float>::value) {
-      return false;
-    } else {
-      if (c.kind != PFT_SCFT_REAL) return false;
-      if (c.n[0] != c.n[1] || c.n[1] != c.n[2]) return false;
-      return c.n[0] == 64 || c.n[0] == 128 || c.n[0] == 256;
-    }
-  }
-
-  cudaError_t persist_march(CtxData& c, bool bwd) {
-    if constexpr (!std::is_same<T, float>::value) {
-      return cudaErrorNotSupported;
-    } else {
-      PersistArgs a;
-      a.BA = (const float*)c.BA;
-      a.BB = (const float*)c.BB;
-      a.hist = (float*)c.hist;
-      a.qd0 = (const float*)c.qd0;
-      a.qd_out = (float*)c.qd[c.Ns & 1];
-      a.spec = (float2*)c.spec;
-      a.accA = (double*)c.accA;
-      a.accB = (double*)c.accB;
-      a.twx = tab<float2>(c, c.tw_off[0]);
-      a.twy = tab<float2>(c, c.tw_off[1]);
-      a.twz = tab<float2>(c, c.tw_off[2]);
-      a.twh = tab<float2>(c, c.tw_off[3]);
-      a.dx = tab<float>(c, c.d_off[0]);
-      a.dy = tab<float>(c, c.d_off[1]);
-      a.dz = tab<float>(c, c.d_off[2]);
-      a.Ns = c.Ns;
-      a.NsA = c.NsA;
-      a.bar = c.sync;
-      a.err = (int*)(c.sync + 2);
-      a.spin_limit = c.spin_limit;
-      cudaError_t e = cudaMemsetAsync(c.sync, 0, 2 * sizeof(unsigned), c.stream);
-      if (e != cudaSuccess) return e;
-      mark(c, bwd ? KK_MARCH_BWD : KK_MARCH_FWD);
-      switch (c.n[0]) {
-        case 64: return bwd ? launch_persist_n<64, true>(c, a) : launch_persist_n<64, false>(c, a);
-        case 128: return bwd ? launch_persist_n<128, true>(c, a) : launch_persist_n<128, false>(c, a);
-        case 256: return bwd ? launch_persist_n<256, true>(c, a) : launch_persist_n<256, false>(c, a);
-        default: return cudaErrorNotSupported;
-      }
-    }
-  }
-
-  cudaError_t resident_march(CtxData& c, bool bwd) {
-    if constexpr (!std::is_same<T, float>::value) {
-      return cudaErrorNotSupported;
-    } else {
-      ResArgs a;
-      a.BA = (const float*)c.BA;
-      a.BB = (const float*)c.BB;
-      a.hist = (float*)c.hist;
-      a.qd0 = (const float*)c.qd0;
-      a.qd_out = (float*)c.qd[c.Ns & 1];
-      a.spec = (float2*)c.spec;
-      a.accA = (double*)c.accA;
-      a.accB = (double*)c.accB;
-      a.twx = tab<float2>(c, c.tw_off[0]);
-      a.twy = tab<float2>(c, c.tw_off[1]);
-      a.twz = tab<float2>(c, c.tw_off[2]);
-      a.twh = tab<float2>(c, c.tw_off[3]);
-      a.dx = tab<float>(c, c.d_off[0]);
-      a.dy = tab<float>(c, c.d_off[1]);
-      a.dz = tab<float>(c, c.d_off[2]);
-      a.Ns = c.Ns;
-      a.NsA = c.NsA;
-      a.bar = c.sync;
-      a.err = (int*)(c.sync + 2);
-      a.spin_limit = c.spin_limit;
-      // reset the arrival count and generation (a timed-out launch may leave them set)
-      cudaError_t e = cudaMemsetAsync(c.sync, 0, 2 * sizeof(unsigned), c.stream);
-      if (e != cudaSuccess) return e;
-      mark(c, bwd ? KK_MARCH_BWD : KK_MARCH_FWD);
-      switch (c.n[0]) {
-        case 64: return bwd ? launch_resident_n<64, 64, 64, true>(c, a) : launch_resident_n<64, 64, 64, false>(c, a);
-        case 96: return bwd ? launch_resident_n<96, 96, 96, true>(c, a) : launch_resident_n<96, 96, 96, false>(c, a);
-        case 128:
-          return bwd ? launch_resident_n<128, 128, 128, true>(c, a) : launch_resident_n<128, 128, 128, false>(c, a);
-        default: return cudaErrorNotSupported;
-      }
-    }
-  }
+  bool plane_applies(const CtxData& c) const override { return plane_supported(c); }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -440,33 +284,19 @@ class EngineT : public Engine {
 
   cudaError_t record_solve(CtxData& c) {
     cudaError_t e;
-    const bool res = (c.march == 2 || c.march == 3);
-    if (res) {
-      // a fresh error word for this solve
-      if ((e = cudaMemsetAsync(c.sync, 0, 4 * sizeof(unsigned), c.stream)) != cudaSuccess) return e;
-    }
     if (c.scheme == 1) return record_solve_rqm4(c);
-    if (!res && c.concurrent && c.ckK == 1) return record_solve_concurrent(c);
+    if (c.concurrent && c.ckK == 1) return record_solve_concurrent(c);
     // forward march (Eqs. 5, 13); a checkpointed history keeps every K-th slice and q_Ns
-    if (res) {
-      e = (c.march == 2) ? resident_march(c, false) : persist_march(c, false);
+    for (int n = 1; n <= c.Ns; n++) {
+      const void* B = (n <= c.NsA) ? c.BA : c.BB;
+      e = contour_step(c, q_at(c, n - 1), B, q_at(c, n), 0, nullptr, 0.0, 0.0);
       if (e != cudaSuccess) return e;
-    } else {
-      for (int n = 1; n <= c.Ns; n++) {
-        const void* B = (n <= c.NsA) ? c.BA : c.BB;
-        e = contour_step(c, q_at(c, n - 1), B, q_at(c, n), 0, nullptr, 0.0, 0.0);
-        if (e != cudaSuccess) return e;
-      }
     }
     // Q (Eq. 4) and the qd_0 = 1 term of the quadrature
     if ((e = solve_mid(c)) != cudaSuccess) return e;
     double cA, cB;
     // conjugate march with fused quadrature (Eq. 8)
-    if (res) {
-      e = (c.march == 2) ? resident_march(c, true) : persist_march(c, true);
-      if (e != cudaSuccess) return e;
-    }
-    for (int m = 1; m <= c.Ns && !res; m++) {
+    for (int m = 1; m <= c.Ns; m++) {
       const int nb = c.Ns + 1 - m;  // split step index of this qd step
       const void* B = (nb <= c.NsA) ? c.BA : c.BB;
       const void* in = (m == 1) ? c.qd0 : c.qd[(m - 1) & 1];
@@ -1192,15 +1022,14 @@ class EngineT : public Engine {
     if (c.scheme == 1) {
       cudaError_t e = prepare_rqm4(c);
       if (e != cudaSuccess) return e;
-    } else if (c.march == 1 && c.concurrent && c.ckK == 1) {
+    } else if (c.concurrent && c.ckK == 1) {
       cudaError_t e = prepare_concurrent(c);
       if (e != cudaSuccess) return e;
       if (c.autotune && !c.tuned && !c.edw && !c.profiling) {
         if ((e = tune_plan(c)) != cudaSuccess) return e;
       }
     }
-    // the resident march is a handful of launches per solve: it runs without a graph
-    if (!c.use_graph || c.profiling || c.march >= 2) return record_solve(c);
+    if (!c.use_graph || c.profiling) return record_solve(c);
     if (!c.graph_valid) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
@@ -1377,7 +1206,7 @@ class EngineT : public Engine {
     }
     cudaError_t e = cudaMemsetAsync(c.partials, 0, (size_t)c.npart * 3 * sizeof(double), c.stream);
     if (e != cudaSuccess) return e;
-    if (c.march == 1 && c.concurrent && c.qdh && c.ckK == 1) return gradients_from_histories(c);
+    if (c.concurrent && c.qdh && c.ckK == 1) return gradients_from_histories(c);
     const int nx = c.n[0], ny = c.n[1], nz = c.n[2];
     const Z* twx = tab<Z>(c, c.tw_off[0]);
     const Z* twy = tab<Z>(c, c.tw_off[1]);

@@ -23,7 +23,7 @@ PFT_SCFT_REAL, PFT_CL_COMPLEX = 0, 1
 PFT_FP64, PFT_FP32_MIXED = 0, 1
 PFT_HOST, PFT_DEVICE = 0, 1
 PFT_STEP_SCFT_EULER, PFT_STEP_CL_EULER_MARUYAMA = 0, 1
-PFT_MARCH_AUTO, PFT_MARCH_PASSES, PFT_MARCH_RESIDENT, PFT_MARCH_PERSISTENT = 0, 1, 2, 3
+PFT_MARCH_AUTO, PFT_MARCH_PASSES = 0, 1
 PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
 PFT_SCHEME_SPLIT2, PFT_SCHEME_RQM4 = 0, 1
 PFT_STEP_SCFT_SIS, PFT_STEP_CL_SIS = 2, 3
@@ -131,11 +131,10 @@ _SIGS = {
     "pft_fft3d": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int]),
     "pft_get_propagator": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, ct.c_int]),
     "pft_debug_set_q0": (ct.c_int, [_P, _P, ct.c_int]),
-    "pft_debug_set_spin_limit": (ct.c_int, [_P, ct.c_longlong]),
-    "pft_get_march": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_launch_counts": (ct.c_int, [_P, ct.POINTER(ct.c_longlong), ct.POINTER(ct.c_longlong)]),
     "pft_get_checkpoint": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_get_plan": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "pft_fma_throughput": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_double), _P]),
     "pft_adjoint": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
     "pft_batch_autotune": (ct.c_int, [_P]),
     "pft_batch_set_plan": (ct.c_int, [_P, ct.c_int, ct.c_int]),
@@ -414,14 +413,11 @@ def pft_debug_set_q0(h, q0=None):
     _check(_lib().pft_debug_set_q0(h, p, w), "pft_debug_set_q0")
 
 
-def pft_debug_set_spin_limit(h, cycles):
-    _check(_lib().pft_debug_set_spin_limit(h, int(cycles)), "pft_debug_set_spin_limit")
-
-
-def pft_get_march(h) -> int:
-    m = ct.c_int()
-    _check(_lib().pft_get_march(h, ct.byref(m)), "pft_get_march")
-    return m.value
+def pft_fma_throughput(precision=PFT_FP64, stream=None) -> float:
+    """Fused multiply-add throughput of the current device in TFLOP/s (FP64 or FP32)."""
+    t = ct.c_double()
+    _check(_lib().pft_fma_throughput(int(precision), ct.byref(t), stream), "pft_fma_throughput")
+    return t.value
 
 
 def pft_get_plan(h):

@@ -2,7 +2,7 @@
 the fields resident on the device, then one line of observables.
 
     python -m paper_1204_5434_gb300.run --workload gyr128 --precision fp32 \
-        --steps 1 --warmup 3 [--scheme split2|rqm4] [--march passes|resident|persistent] [--adjoint]
+        --steps 1 --warmup 3 [--scheme split2|rqm4] [--march auto|passes] [--adjoint]
 
 Each update is one pft_solve (both propagators, Q, densities, H) and one explicit field
 step (SCFT Euler for SCFT workloads, Euler-Maruyama with device Philox noise for complex
@@ -23,8 +23,7 @@ from . import workloads as wl
 
 _PREC = {"fp32": pft.PFT_FP32_MIXED, "fp64": pft.PFT_FP64}
 _SCHEME = {"split2": pft.PFT_SCHEME_SPLIT2, "rqm4": pft.PFT_SCHEME_RQM4}
-_MARCH = {"auto": pft.PFT_MARCH_AUTO, "passes": pft.PFT_MARCH_PASSES, "resident": pft.PFT_MARCH_RESIDENT,
-          "persistent": pft.PFT_MARCH_PERSISTENT}
+_MARCH = {"auto": pft.PFT_MARCH_AUTO, "passes": pft.PFT_MARCH_PASSES}
 
 
 def main(argv=None) -> int:

@@ -67,9 +67,8 @@ def test_shape_and_argument_validation(lib):
         pft.pft_create((8, 8, 8), (1, 1, 1), 10, 0.5, 10, 1, checkpoint=3, scheme=pft.PFT_SCHEME_RQM4)
     assert e.value.status == pft.PFT_ERR_UNSUPPORTED
     with pytest.raises(pft.PftError) as e:
-        pft.pft_create((64, 64, 64), (1, 1, 1), 10, 0.5, 10, 1, precision=pft.PFT_FP32_MIXED,
-                       march=pft.PFT_MARCH_RESIDENT, scheme=pft.PFT_SCHEME_RQM4)
-    assert e.value.status == pft.PFT_ERR_UNSUPPORTED
+        pft.pft_create((64, 64, 64), (1, 1, 1), 10, 0.5, 10, 1, precision=pft.PFT_FP32_MIXED, march=2)
+    assert e.value.status == pft.PFT_ERR_ARG
 
 
 def test_status_strings(lib):

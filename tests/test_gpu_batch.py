@@ -113,6 +113,51 @@ def test_batch_graphed_plan0_equals_per_instance(prec):
         assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]) and a[2] == c[2]
 
 
+# One member per class of the timed 256-instance batch (grids 32^3, 48^3, 64^3; real SCFT
+# and complex CL fields; Ns from {50, 100, 200}); the 64^3 classes run on the batched plane
+# kernels under plan 1.
+BENCH_CLASSES = [
+    dict(n=(32, 32, 32), L=(4.0, 4.0, 4.0), Ns=200, fA=0.3, chiN=14.0, C=1.0, kind=SCFT, seed=21),
+    dict(n=(48, 48, 48), L=(6.0, 6.0, 6.0), Ns=100, fA=0.45, chiN=22.0, C=1.0, kind=SCFT, seed=22),
+    dict(n=(64, 64, 64), L=(8.0, 8.0, 8.0), Ns=50, fA=0.27, chiN=17.0, C=1.0, kind=SCFT, seed=23),
+    dict(n=(32, 32, 32), L=(4.0, 4.0, 4.0), Ns=50, fA=0.5, chiN=24.0, C=50.0, kind=CL, seed=24),
+    dict(n=(48, 48, 48), L=(6.0, 6.0, 6.0), Ns=200, fA=0.38, chiN=12.5, C=50.0, kind=CL, seed=25),
+    dict(n=(64, 64, 64), L=(8.0, 8.0, 8.0), Ns=100, fA=0.33, chiN=19.0, C=50.0, kind=CL, seed=26),
+]
+
+
+def test_batch_fp32_classes_of_the_timed_batch_match_oracle():
+    """FP32-mixed batch with one member per class of the timed batch, graph-captured,
+    plan 1 (both marches per launch; plane kernels for the 64^3 classes): each member's
+    Q, phiA, phiB and fields after one update against the FP64 oracle.  FP32 tolerances
+    of the single-context path (relative 2e-5 on Q, absolute 2e-5 on phi) scaled by the
+    random-walk growth of the rounding error over 2 Ns <= 400 transform pairs (x sqrt 2)."""
+    b, fields = _make(pft.PFT_FP32_MIXED, BENCH_CLASSES)
+    try:
+        info = pft.pft_batch_info(b)
+        assert info["classes"] == 6
+        for k in range(info["classes"]):
+            assert pft.pft_batch_class_info(b, k)["plan"] == 1
+        pft.pft_batch_run(b, 1, LAM, DT, pft.PFT_BATCH_GRAPHED)
+        for i, d in enumerate(BENCH_CLASSES):
+            wp, wm, s, H = _oracle_updates(d, i, *fields[i], 1)
+            dt = np.float64 if d["kind"] == SCFT else np.complex128
+            gp, gm = np.empty(d["n"], dt), np.empty(d["n"], dt)
+            pA, pB = np.empty(d["n"], dt), np.empty(d["n"], dt)
+            pft.pft_batch_get_fields(b, i, gp, gm)
+            pft.pft_batch_get_densities(b, i, pA, pB)
+            obs = pft.pft_batch_get_observables(b, i)
+            Q = obs["Q"] if d["kind"] == CL else obs["Q"].real
+            eQ = abs(Q - s.Q) / abs(s.Q)
+            ephi = max(np.max(np.abs(pA - s.phiA)), np.max(np.abs(pB - s.phiB)))
+            ew = max(np.max(np.abs(gp - wp)), np.max(np.abs(gm - wm)))
+            print(f"\nbatch FP32 member {i} {d['n']} Ns={d['Ns']} kind={d['kind']}: Q rel {eQ:.2e} "
+                  f"phi abs {ephi:.2e} fields abs {ew:.2e}")
+            assert eQ <= 3e-5 and ephi <= 3e-5 and ew <= 1e-5, i
+    finally:
+        pft.pft_batch_destroy(b)
+
+
 def test_batch_rejects_bad_members():
     with pytest.raises(pft.PftError) as e:
         pft.pft_batch_create([dict(n=(128, 16, 16), L=(1, 1, 1), Ns=4, fA=0.5, chiN=10.0, C=1.0, kind=SCFT)])

@@ -121,12 +121,11 @@ def test_checkpointed_scft_relaxation_matches_oracle():
     assert np.max(np.abs(gp - wp)) <= 1e-12 and np.max(np.abs(gm - wm)) <= 1e-11
 
 
-def test_checkpoint_refuses_other_marches_and_schemes():
-    for kw in (dict(march=pft.PFT_MARCH_RESIDENT, precision=FP32), dict(scheme=pft.PFT_SCHEME_RQM4)):
-        prec = kw.pop("precision", FP64)
-        with pytest.raises(pft.PftError) as ei:
-            pft.System((64, 64, 64), (8.0, 8.0, 8.0), 10, 0.5, 15.0, 1.0, SCFT, prec, checkpoint=3, **kw)
-        assert ei.value.status == pft.PFT_ERR_UNSUPPORTED
+def test_checkpoint_refuses_other_schemes():
+    with pytest.raises(pft.PftError) as ei:
+        pft.System((64, 64, 64), (8.0, 8.0, 8.0), 10, 0.5, 15.0, 1.0, SCFT, FP64, checkpoint=3,
+                   scheme=pft.PFT_SCHEME_RQM4)
+    assert ei.value.status == pft.PFT_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("K", [10])

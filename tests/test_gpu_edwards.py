@@ -158,7 +158,7 @@ def test_edwards_128cubed_fp32_against_the_oracle():
 
 def test_edwards_refuses_what_it_does_not_implement():
     n, L = (64, 64, 64), (8.0, 8.0, 8.0)
-    for kw in (dict(scheme=pft.PFT_SCHEME_RQM4), dict(checkpoint=4), dict(march=pft.PFT_MARCH_RESIDENT)):
+    for kw in (dict(scheme=pft.PFT_SCHEME_RQM4), dict(checkpoint=4)):
         with pytest.raises(pft.PftError) as ei:
             _system(n, L, 10, SCFT, FP32, **kw)
         assert ei.value.status == pft.PFT_ERR_UNSUPPORTED

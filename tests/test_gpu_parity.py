@@ -336,139 +336,69 @@ def test_lamellar_scft_32cubed_50_steps_fp32_error_table():
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_gyroid_128cubed_full_size(prec):
-    """The 128^3 gyroid-seeded SCFT workload (Ns=100, fA=0.35, chiN=18) at full size:
-    Q, H and phi sampled at 4096 random points against the oracle."""
+    """The 128^3 gyroid-seeded SCFT workload (Ns=100, fA=0.35, chiN=18) at full size, in
+    the plan the bench times (FP32: plane kernel, two chains): Q and H, phiA and phiB over
+    every one of the 2,097,152 points, and the propagator slices q_1, q_NsA, q_Ns and
+    qd_1, qd_(Ns-NsA), qd_Ns element by element against the oracle (a fault confined to one
+    kz column or one x-plane of a transform touches every slice after it).
+    FP32 slices: the maximum over all 2,097,152 points of the error relative to the slice
+    maximum, bounded by 1e-4 -- the per-point random-walk estimate of the derivation above
+    (1.8e-5 after 2 Ns = 200 transforms of log2(M) = 21 stages) times the tail factor
+    sqrt(2 ln M) = 5.4 of the largest of M such errors."""
     w = wl.GYR128
     wp, wm = wl.fields(w)
     ref = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL)
     Href = o.hamiltonian(wp, wm, ref.lnQ, w.chiN, w.C, w.n, w.L, o.SCFT_REAL)
+    NsA, Ns = ref.NsA, w.Ns
+    t = TOL[prec]
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec) as s:
+        if prec == FP32:
+            assert pft.pft_get_plan(s.h) == (1, 1)
+        assert pft.pft_get_checkpoint(s.h) == 1
         s.set_fields(wp, wm)
         s.solve()
         obs = s.observables()
         phiA, phiB = s.densities()
-    idx = np.random.default_rng(0).choice(phiA.size, 4096, replace=False)
-    t = TOL[prec]
+        eq = 0.0
+        for which, hist in ((0, ref.q), (2, ref.qd)):
+            for k in sorted({1, NsA if which == 0 else Ns - NsA, Ns}):
+                g = s.propagator(which, k)
+                e = np.max(np.abs(g - hist[k])) / np.max(np.abs(hist[k]))
+                eq = max(eq, e)
+                assert e <= (t["q"] if prec == FP64 else 1e-4), (which, k, e)
     eQ, eH = _rel(obs["Q"].real, ref.Q), _rel(obs["H"].real, Href)
-    ephi = max(np.max(np.abs(phiA.ravel()[idx] - ref.phiA.ravel()[idx])),
-               np.max(np.abs(phiB.ravel()[idx] - ref.phiB.ravel()[idx])))
-    print(f"\n128^3 prec={prec}: Q rel {eQ:.2e} H rel {eH:.2e} phi abs {ephi:.2e}")
+    ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+    print(f"\n128^3 prec={prec}: Q rel {eQ:.2e} H rel {eH:.2e} phi abs {ephi:.2e} (all points) "
+          f"slices rel {eq:.2e}")
     assert eQ <= t["Q"] and _check_H(obs["H"].real, Href, w.C, w.L, prec) and ephi <= t["phi"]
     assert abs(phiA.mean() - ref.NsA / w.Ns) <= (1e-12 if prec == FP64 else 1e-6)
 
 
-# ------------------------------------------------------------ resident march
-def _gyroid_like(n, L, seed):
-    x = [np.arange(n[a]) * L[a] / n[a] for a in range(3)]
-    X = (2 * np.pi * x[0] / L[0])[:, None, None]
-    Y = (2 * np.pi * x[1] / L[1])[None, :, None]
-    Z = (2 * np.pi * x[2] / L[2])[None, None, :]
-    G = np.sin(X) * np.cos(Y) + np.sin(Y) * np.cos(Z) + np.sin(Z) * np.cos(X)
-    rng = np.random.default_rng(seed)
-    return rng.normal(0, 0.1, n), 4.0 * G + rng.normal(0, 0.1, n)
-
-
-@pytest.mark.parametrize("nn", [64, 96, 128])
-def test_resident_march_matches_oracle_and_passes(nn):
-    """The persistent resident march (FP32) against the oracle and the pass-kernel path."""
-    n, L, Ns, fA, chiN = (nn, nn, nn), (8.0, 8.0, 8.0), 20, 0.35, 18.0
-    wp, wm = _gyroid_like(n, L, nn)
-    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
-    Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, 1.0, n, L, o.SCFT_REAL)
-    out = {}
-    for march in (pft.PFT_MARCH_RESIDENT, pft.PFT_MARCH_PASSES):
-        with pft.System(n, L, Ns, fA, chiN, 1.0, SCFT, FP32, march=march) as s:
-            assert pft.pft_get_march(s.h) == (2 if march == pft.PFT_MARCH_RESIDENT else 1)
-            s.set_fields(wp, wm)
-            s.solve()
-            s.solve()
-            obs = s.observables()
-            phiA, phiB = s.densities()
-            q = s.propagator(0, Ns)
-            qd = s.propagator(1, 0)
-        eQ = _rel(obs["Q"].real, ref.Q)
-        ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
-        print(f"\nresident={march} {nn}^3: Q rel {eQ:.2e} phi abs {ephi:.2e}")
-        assert eQ <= TOL[FP32]["Q"] and ephi <= TOL[FP32]["phi"]
-        assert _check_H(obs["H"].real, Href, 1.0, L, FP32)
-        assert np.max(np.abs(q - ref.q[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.q[Ns]))
-        assert np.max(np.abs(qd - ref.qd[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.qd[Ns]))
-        out[march] = (phiA, obs["Q"].real)
-    a, b = out[pft.PFT_MARCH_RESIDENT], out[pft.PFT_MARCH_PASSES]
-    assert abs(a[1] - b[1]) <= 1e-5 * abs(b[1]) and np.max(np.abs(a[0] - b[0])) <= 1e-5
-
-
-def test_resident_march_refuses_unsupported_configs():
-    with pytest.raises(pft.PftError) as e:
-        pft.System((32, 32, 32), (4, 4, 4), 10, 0.5, 15.0, 1.0, SCFT, FP32, march=pft.PFT_MARCH_RESIDENT)
-    assert e.value.status == pft.PFT_ERR_UNSUPPORTED
-    with pytest.raises(pft.PftError) as e:
-        pft.System((64, 64, 64), (4, 4, 4), 10, 0.5, 15.0, 1.0, SCFT, FP64, march=pft.PFT_MARCH_RESIDENT)
-    assert e.value.status == pft.PFT_ERR_UNSUPPORTED
-
-
-def test_resident_barrier_timeout_is_reported_and_recoverable():
-    """A barrier wait budget of one cycle makes the grid barriers give up: the march
-    returns early, the host sees PFT_ERR_TIMEOUT, and the context still works."""
-    n, L, Ns, fA = (64, 64, 64), (8.0, 8.0, 8.0), 8, 0.35
-    wp, wm = _gyroid_like(n, L, 5)
-    with pft.System(n, L, Ns, fA, 18.0, 1.0, SCFT, FP32, march=pft.PFT_MARCH_RESIDENT) as s:
+@pytest.mark.parametrize("n,Ns,fA", [((32, 32, 32), 40, 0.35), ((128, 128, 128), 100, 0.35)])
+def test_fp32_quadrature_is_an_fp64_sum_of_the_fp32_products(n, Ns, fA):
+    """FP32-mixed: the contour quadrature of Eq. 8 sums the FP32 products q_n qd_(Ns-n)
+    in FP64 (compensated FP32 partial sums over chunks of slices, flushed into FP64 sums).
+    Recomputed here from the GPU's own stored histories with a plain float64 sum of the
+    same float32 products: the densities must agree to FP64 rounding, far below the FP32
+    rounding of the products (6e-8)."""
+    L = (8.0, 8.0, 8.0) if n[0] == 128 else (4.0, 4.0, 4.0)
+    wp, wm = _fields(n, SCFT, 91)
+    with pft.System(n, L, Ns, fA, 18.0, 1.0, SCFT, FP32) as s:
         s.set_fields(wp, wm)
-        pft.pft_debug_set_spin_limit(s.h, 1)
         s.solve()
-        with pytest.raises(pft.PftError) as e:
-            s.observables()
-        assert e.value.status == pft.PFT_ERR_TIMEOUT
-        pft.pft_debug_set_spin_limit(s.h, 4_000_000_000)
-        s.solve()
-        obs = s.observables()
-    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
-    assert _rel(obs["Q"].real, ref.Q) <= TOL[FP32]["Q"]
-
-
-# ---------------------------------------------------------- persistent march
-@pytest.mark.parametrize("nn,Ns", [(64, 20), (128, 20), (256, 4)])
-def test_persistent_march_matches_oracle(nn, Ns):
-    """The persistent multi-pass march (FP32, one cooperative launch per march) against
-    the oracle and against the pass-kernel path."""
-    n, L, fA, chiN = (nn, nn, nn), (8.0, 8.0, 8.0), 0.35, 18.0
-    wp, wm = _gyroid_like(n, L, nn + 1)
-    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
-    Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, 1.0, n, L, o.SCFT_REAL)
-    out = {}
-    for march in (pft.PFT_MARCH_PERSISTENT, pft.PFT_MARCH_PASSES):
-        with pft.System(n, L, Ns, fA, chiN, 1.0, SCFT, FP32, march=march) as s:
-            s.set_fields(wp, wm)
-            s.solve()
-            s.solve()
-            obs = s.observables()
-            phiA, phiB = s.densities()
-            q = s.propagator(0, Ns)
-            qd = s.propagator(1, 0)
-        eQ = _rel(obs["Q"].real, ref.Q)
-        ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
-        print(f"\npersistent={march} {nn}^3: Q rel {eQ:.2e} phi abs {ephi:.2e}")
-        assert eQ <= TOL[FP32]["Q"] and ephi <= TOL[FP32]["phi"]
-        assert _check_H(obs["H"].real, Href, 1.0, L, FP32)
-        assert np.max(np.abs(q - ref.q[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.q[Ns]))
-        assert np.max(np.abs(qd - ref.qd[Ns])) <= TOL[FP32]["q"] * np.max(np.abs(ref.qd[Ns]))
-        out[march] = (phiA, obs["Q"].real)
-    a, b = out[pft.PFT_MARCH_PERSISTENT], out[pft.PFT_MARCH_PASSES]
-    assert abs(a[1] - b[1]) <= 1e-5 * abs(b[1]) and np.max(np.abs(a[0] - b[0])) <= 1e-5
-
-
-def test_persistent_barrier_timeout_is_reported_and_recoverable():
-    n, L, Ns, fA = (64, 64, 64), (8.0, 8.0, 8.0), 8, 0.35
-    wp, wm = _gyroid_like(n, L, 6)
-    with pft.System(n, L, Ns, fA, 18.0, 1.0, SCFT, FP32, march=pft.PFT_MARCH_PERSISTENT) as s:
-        s.set_fields(wp, wm)
-        pft.pft_debug_set_spin_limit(s.h, 1)
-        s.solve()
-        with pytest.raises(pft.PftError) as e:
-            s.observables()
-        assert e.value.status == pft.PFT_ERR_TIMEOUT
-        pft.pft_debug_set_spin_limit(s.h, 4_000_000_000)
-        s.solve()
-        obs = s.observables()
-    ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
-    assert _rel(obs["Q"].real, ref.Q) <= TOL[FP32]["Q"]
+        phiA, phiB = s.densities()
+        NsA = o.n_A_steps(Ns, fA)
+        cA, cB = o.quadrature_weights(Ns, NsA)
+        accA = np.zeros(n)
+        accB = np.zeros(n)
+        for k in range(Ns + 1):
+            prod = (s.propagator(0, k).astype(np.float32) * s.propagator(2, Ns - k).astype(np.float32))
+            prod = prod.astype(np.float64)
+            accA += cA[k] * prod
+            accB += cB[k] * prod
+        Q = s.propagator(0, Ns).mean()
+    ds = 1.0 / Ns
+    eA = np.max(np.abs(phiA - ds * accA / Q))
+    eB = np.max(np.abs(phiB - ds * accB / Q))
+    print(f"\nFP32 quadrature {n} Ns={Ns} vs FP64 sum of the same products: {eA:.2e} {eB:.2e}")
+    assert eA <= 1e-12 and eB <= 1e-12

@@ -192,6 +192,19 @@ def test_fft_equals_bruteforce_dft():
     assert np.max(np.abs(np.fft.fftn(y) - o.dft3_bruteforce(y))) < 1e-12 * 48
 
 
+def test_fft_workers_changes_only_the_library():
+    """The all-core timing switch (scipy.fft on several threads) computes the same DFT:
+    a solve agrees with the numpy.fft one to rounding, and the default comes back after."""
+    n, L, Ns, fA = (8, 12, 16), (2.0, 3.0, 4.0), 10, 0.4
+    wp, wm = _rand_fields(n, o.CL_COMPLEX, 67)
+    a = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    with o.fft_workers(2):
+        b = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    c = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    assert abs(a.Q - b.Q) <= 1e-14 * abs(a.Q) and np.max(np.abs(a.phiA - b.phiA)) <= 1e-14
+    assert a.Q == c.Q and np.array_equal(a.phiA, c.phiA)
+
+
 @pytest.mark.parametrize("kind", [o.SCFT_REAL, o.CL_COMPLEX])
 def test_march_equals_dense_matrix(kind):
     """Forward march with FFTs equals the march with the diffusion operator as the

@@ -1,17 +1,20 @@
-"""The allocation-free contour step (pft_contour_step_static) against the context path.
+"""The allocation-free contour step (pft_contour_step_static) against the oracle's split
+step and against the context path.
 
 Some callers cannot call cudaMalloc -- for example code running while another
 framework owns the device allocator, or a plug-in that may only use the buffers it is
 handed -- so the library offers one step whose scratch is a static device array.  This
-file checks, through the C ABI, that two calls in a row give the same q_{n+1} as a
-context solve (pft_debug_set_q0 + pft_solve + pft_get_propagator slice 1) within the
-FP64 propagator tolerance of the other GPU tests (1e-12 relative to the slice maximum),
-and that grids beyond the static limit are refused.  It is collected last so that a
+file checks, through the C ABI, that two calls in a row give q_{n+1} = B F^-1[D F[B q_n]]
+(Eq. 13's A(ds) block) as the FP64 oracle computes it, and the same q_{n+1} as a context
+solve (pft_debug_set_q0 + pft_solve + pft_get_propagator slice 1), both within the FP64
+propagator tolerance of the other GPU tests (1e-12 relative to the slice maximum), and
+that grids beyond the static limit are refused.  It is collected last so that a
 run stopping at the first failure has already run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle as o
 from paper_1204_5434_gb300 import pft
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +51,9 @@ def test_static_step_matches_context_step_twice(n, L, Ns):
         pft.pft_contour_step_static(n, L, Ns, dw, dq, out)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
+        ds = 1.0 / Ns
+        oref = o.split_step(q_in, o.boltzmann_factor(w, ds), o.diffusion_factor(n, L, ds))
+        assert np.max(np.abs(got - oref)) <= 1e-12 * np.max(np.abs(oref)), call
         assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), call
 
 
