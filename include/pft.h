@@ -395,11 +395,23 @@ pft_status pft_get_propagator(pft_ctx* ctx, int which, int s, void* out, pft_mem
  * or complex128 by kind; NULL restores 1).  Used by the diffusion-only test. */
 pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
 
-/* Plan of the pass march in use: *plane = 1 if the y/z plane kernel runs the steps (FP32
- * real fields with ny = nz = 64 or 128, complex fields with ny = nz = 64), *streams = 1
- * if the two propagators run as two chains on two
- * streams.  Either pointer may be NULL.  Errors: PFT_ERR_ARG for a NULL ctx. */
+/* Plan of the pass march in use.  *plane: 0 = pencil passes (a 3D transform pair per
+ * contour step); 1 = the y/z plane kernel plus an x pass per step (FP32 real fields with
+ * ny = nz = 64 or 128, complex fields with ny = nz = 64); 2 = the separable march (FP32 real
+ * fields, ny = nz and nx in {64, 128}): the diffusion factor exp(-k^2 ds) of Eq. 13 is the
+ * product of three per-axis factors, so F^-1 D F is the product of three 1D periodic
+ * Gaussian convolutions, applied in alternating axis order so that one launch -- a y/z
+ * plane kernel or an x kernel in turn -- advances one contour step.  *streams = 1 if the
+ * two propagators run as two chains on two streams.  Either pointer may be NULL.
+ * Errors: PFT_ERR_ARG for a NULL ctx. */
 pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams);
+
+/* Fix the plan of the pass march (values as pft_get_plan reports them); the context
+ * keeps it (no autotuning) and recaptures its solve graph at the next pft_solve.  The RQM4
+ * scheme, the adjoint and the box derivative run the plane kernel wherever plane >= 1.
+ * Errors: PFT_ERR_ARG (NULL ctx, values out of range), PFT_ERR_UNSUPPORTED (a plan the
+ * context's grid, field kind or precision does not allow). */
+pft_status pft_set_plan(pft_ctx* ctx, int plane, int streams);
 
 /* History interval in use: 1 = every slice of q is kept, K >= 2 = every K-th slice (see
  * pft_opts.checkpoint).  Errors: PFT_ERR_ARG for NULL arguments. */

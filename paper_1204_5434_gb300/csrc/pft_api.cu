@@ -122,7 +122,7 @@ void free_all(pft_ctx* c) {
   if (d.graph) cudaGraphExecDestroy(d.graph);
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
-                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.qdh, d.steps2, d.stepsg,
+                  d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.kerr, d.qdh, d.steps2, d.stepsS, d.stepsg,
                   d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa, d.stepsap};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -254,7 +254,8 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
   d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
   d.autotune = opts->autotune != 0;
-  d.plan_plane = c->eng->plane_applies(d) ? 1 : 0;  // the default plan: plane kernel where it applies
+  // the default plan: the separable march where it applies, else the plane kernel
+  d.plan_plane = c->eng->sep_applies(d) ? 2 : (c->eng->plane_applies(d) ? 1 : 0);
 
   const size_t M = (size_t)d.M;
   const size_t we = welem(d), fe = felem(d);
@@ -283,7 +284,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       {&d.hist, (size_t)pft::q_slots(d) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
       {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
       {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
-      {&c->io, M * 16},
+      {&c->io, M * 16}, {(void**)&d.kerr, 16},
       // quarter-step Boltzmann factors of the 4th-order scheme
       {d.scheme ? &d.BAh : nullptr, M * we}, {d.scheme ? &d.BBh : nullptr, M * we},
   };
@@ -302,6 +303,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
     e = cudaMemsetAsync(d.scal, 0, pft::S_COUNT * sizeof(double), d.stream);
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(d.partials, 0, (size_t)d.npart * 8 * sizeof(double), d.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.kerr, 0, 16, d.stream);
   if (e == cudaSuccess) e = c->eng->upload_tables(d);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.hist);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.qd0);
@@ -540,7 +542,14 @@ pft_status pft_get_observables(pft_ctx* ctx, pft_obs* obs) {
   CtxData& d = ctx->d;
   if (!ctx->have_obs) return fail(PFT_ERR_STATE, "no solve since the fields were set");
   PFT_CK(cudaMemcpyAsync(d.scal_host, d.scal, pft::S_COUNT * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+  int kerr = 0;
+  PFT_CK(cudaMemcpyAsync(&kerr, d.kerr, sizeof(int), cudaMemcpyDeviceToHost, d.stream));
   PFT_CK(cudaStreamSynchronize(d.stream));
+  if (kerr != 0) {
+    PFT_CK(cudaMemsetAsync(d.kerr, 0, sizeof(int), d.stream));
+    PFT_CK(cudaStreamSynchronize(d.stream));
+    return fail(PFT_ERR_TIMEOUT, "a bounded wait in a kernel of the last solve ran out (its results are invalid)");
+  }
   const double* s = d.scal_host;
   const double V = d.L[0] * d.L[1] * d.L[2];
   const double Md = (double)d.M;
@@ -850,6 +859,25 @@ pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* fi
   if (solve) *solve = (d.use_graph && d.graph_valid) ? d.graph_kernels : -1;
   // the update kernel and its final reduction, plus the quarter-step factors of RQM4
   if (field_step) *field_step = 2 + (d.scheme == 1 ? 1 : 0);
+  return PFT_OK;
+}
+
+pft_status pft_set_plan(pft_ctx* ctx, int plane, int streams) {
+  if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
+  CtxData& d = ctx->d;
+  if (plane < 0 || plane > 2 || streams < 0 || streams > 1) return fail(PFT_ERR_ARG, "plane in {0,1,2}, streams in {0,1}");
+  if (plane == 1 && !ctx->eng->plane_applies(d))
+    return fail(PFT_ERR_UNSUPPORTED, "the plane kernel needs FP32 with ny = nz = 64 or 128 (real) or 64 (complex)");
+  if (plane == 2 && !ctx->eng->sep_applies(d))
+    return fail(PFT_ERR_UNSUPPORTED, "the separable march needs FP32 real fields, ny = nz and nx in {64, 128}");
+  d.plan_plane = plane;
+  d.plan_streams = streams;
+  d.tuned = true;  // an explicit plan is not re-tuned
+  d.graph_valid = false;
+  if (d.graph) {
+    cudaGraphExecDestroy(d.graph);
+    d.graph = nullptr;
+  }
   return PFT_OK;
 }
 

@@ -33,6 +33,11 @@ struct BatchClass {
   int plan = 1;
   pft::BatchStep* d_conc = nullptr;  // [maxNs][2K]
   float tuned_ms[2] = {-1.f, -1.f};   // autotuner timings of the two plans
+  // the class's branch of the captured update: its marches, reductions and field steps
+  // run on their own stream, forked from and joined back into the batch stream, so that
+  // the classes overlap on the GPU
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 __global__ void k_batch_increment(unsigned long long* __restrict__ c, int n) {
@@ -59,6 +64,7 @@ struct pft_batch {
   bool own_stream = false;
   std::vector<BatchClass> classes;
   unsigned long long* d_steps = nullptr;
+  cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph = nullptr;
   double g_lam = -1.0, g_dt = -1.0;
   long long launches = 0;
@@ -74,7 +80,10 @@ void batch_free(pft_batch* b) {
     if (c.d_fwd) cudaFree(c.d_fwd);
     if (c.d_bwd) cudaFree(c.d_bwd);
     if (c.d_conc) cudaFree(c.d_conc);
+    if (c.stream) cudaStreamDestroy(c.stream);
+    if (c.done) cudaEventDestroy(c.done);
   }
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_steps) cudaFree(b->d_steps);
   for (pft_ctx* c : b->inst)
     if (c) pft_destroy(c);
@@ -166,14 +175,15 @@ pft_status prepare_pairs(pft_batch* b, BatchClass& c) {
   return e == cudaSuccess ? PFT_OK : bcuda(e, "batch pair-step table");
 }
 
-// Both marches and the densities of one class under its plan, on b->stream.
-pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches) {
+// Both marches and the densities of one class under its plan, on `sm` (the members'
+// context streams must be `sm` too).
+pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches, cudaStream_t sm) {
   const int K = (int)c.members.size();
   pft::Engine* eng = b->inst[c.members[0]]->eng;
   if (c.plan == 1) {
     for (int s = 1; s <= c.maxNs; s++) {
       const pft::BatchStep* st = c.d_conc + (size_t)(s - 1) * 2 * K;
-      cudaError_t e = eng->batch_pair_step(c.g, st, 2 * c.active[s - 1], s == 1, b->stream);
+      cudaError_t e = eng->batch_pair_step(c.g, st, 2 * c.active[s - 1], s == 1, sm);
       if (e != cudaSuccess) return bcuda(e, "batched pair step");
       *launches += eng->batch_pair_launches(c.g, s == 1);
     }
@@ -190,7 +200,7 @@ pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches) 
   for (int march = 0; march < 2; march++) {
     for (int s = 1; s <= c.maxNs; s++) {
       const pft::BatchStep* st = (march ? c.d_bwd : c.d_fwd) + (size_t)(s - 1) * K;
-      cudaError_t e = eng->batch_contour_step(c.g, st, c.active[s - 1], march, b->stream);
+      cudaError_t e = eng->batch_contour_step(c.g, st, c.active[s - 1], march, sm);
       if (e != cudaSuccess) return bcuda(e, "batched contour step");
       *launches += 5;
     }
@@ -204,24 +214,34 @@ pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches) 
   return PFT_OK;
 }
 
-// One field update of every instance, on b->stream.
+// One field update of every instance: each class on its own stream (forked from and
+// joined back into b->stream), then the step counters on b->stream.
 pft_status record_update(pft_batch* b, double lam, double dt) {
   long long launches = 0;
+  cudaError_t e = cudaEventRecord(b->fork, b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch fork");
   for (auto& c : b->classes) {  // plan-1 tables are prepared before any capture
-    pft_status s = record_class_solve(b, c, &launches);
+    if ((e = cudaStreamWaitEvent(c.stream, b->fork, 0)) != cudaSuccess) return bcuda(e, "class fork");
+    for (int i : c.members) b->inst[i]->d.stream = c.stream;
+    pft_status s = record_class_solve(b, c, &launches, c.stream);
+    for (int i : c.members) {
+      if (s != PFT_OK) break;
+      pft_ctx* x = b->inst[i];
+      const bool scft = (x->d.kind == PFT_SCFT_REAL);
+      e = x->eng->field_step(x->d, scft ? PFT_STEP_SCFT_EULER : PFT_STEP_CL_EULER_MARUYAMA, scft ? lam : dt, nullptr,
+                             nullptr);
+      if (e != cudaSuccess) s = bcuda(e, "batched field step");
+      launches += 2;
+    }
+    for (int i : c.members) b->inst[i]->d.stream = b->stream;
     if (s != PFT_OK) return s;
-  }
-  for (pft_ctx* x : b->inst) {
-    const bool scft = (x->d.kind == PFT_SCFT_REAL);
-    cudaError_t e = x->eng->field_step(x->d, scft ? PFT_STEP_SCFT_EULER : PFT_STEP_CL_EULER_MARUYAMA, scft ? lam : dt,
-                                       nullptr, nullptr);
-    if (e != cudaSuccess) return bcuda(e, "batched field step");
-    launches += 2;
+    if ((e = cudaEventRecord(c.done, c.stream)) != cudaSuccess) return bcuda(e, "class join");
+    if ((e = cudaStreamWaitEvent(b->stream, c.done, 0)) != cudaSuccess) return bcuda(e, "class join");
   }
   const int n = (int)b->inst.size();
   k_batch_increment<<<(n + 255) / 256, 256, 0, b->stream>>>(b->d_steps, n);
   launches += 1;
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return bcuda(e, "batched step counter");
   b->launches = launches;
   return PFT_OK;
@@ -277,7 +297,12 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
     // march (the batched launches already fill the GPU), in both batch modes
     b->inst[i]->d.concurrent = false;
   }
-  cudaError_t e = cudaMalloc(&b->d_steps, sizeof(unsigned long long) * count);
+  cudaError_t e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return bcuda(e, "batch fork event");
+  }
+  e = cudaMalloc(&b->d_steps, sizeof(unsigned long long) * count);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long) * count, b->stream);
   if (e != cudaSuccess) {
     batch_free(b);
@@ -318,7 +343,9 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
         fill_steps(b->inst[c.members[k]], s, true, &hb[(size_t)(s - 1) * K + k]);
       }
     const size_t bytes = hf.size() * sizeof(pft::BatchStep);
-    e = cudaMalloc(&c.d_fwd, bytes);
+    e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMalloc(&c.d_fwd, bytes);
     if (e == cudaSuccess) e = cudaMalloc(&c.d_bwd, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(c.d_fwd, hf.data(), bytes, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(c.d_bwd, hb.data(), bytes, cudaMemcpyHostToDevice);
@@ -440,9 +467,9 @@ pft_status pft_batch_autotune(pft_batch* b) {
       c.plan = plan;
       if (plan == 1 && (st = prepare_pairs(b, c)) != PFT_OK) break;
       long long n = 0;
-      if ((st = record_class_solve(b, c, &n)) != PFT_OK) break;  // warm-up
+      if ((st = record_class_solve(b, c, &n, b->stream)) != PFT_OK) break;  // warm-up
       cudaEventRecord(e0, b->stream);
-      if ((st = record_class_solve(b, c, &n)) != PFT_OK) break;
+      if ((st = record_class_solve(b, c, &n, b->stream)) != PFT_OK) break;
       cudaEventRecord(e1, b->stream);
       e = cudaEventSynchronize(e1);
       float ms = 0.f;

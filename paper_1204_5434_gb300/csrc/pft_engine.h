@@ -75,6 +75,7 @@ struct CtxData {
   void* tables = nullptr;      // twiddles + diffusion factors
   size_t tw_off[4] = {0, 0, 0, 0};  // x, y, z (full nz), z half (nz/2): byte offsets
   size_t d_off[3] = {0, 0, 0};      // dx (with 1/M), dy, dz
+  size_t sd_off[3] = {0, 0, 0};     // per-axis factors exp(-k_a^2 ds)/n_a over the full axis (separable march)
   size_t g_off[3] = {0, 0, 0};      // k_a^2 per axis (FP64): box derivative, SIS Debye factor
   size_t e_off[3] = {0, 0, 0};      // exp(-k_a^2 ds) per axis (FP64): box derivative
   size_t t64_off[3] = {0, 0, 0};    // FP64 twiddles x, y, z (full nz) for the SIS transforms
@@ -84,6 +85,7 @@ struct CtxData {
   void* stepsap = nullptr;          // [2 Ns] AdjPlaneStep of the adjoint on the plane kernel
   size_t tables_bytes = 0;
   int npart = 0;
+  int* kerr = nullptr;  // kernel error word: a bounded wait that ran out (read by pft_get_observables)
   size_t bytes = 0;
   // optional device counter read by the CL field step instead of `step` (batches)
   const unsigned long long* step_dev = nullptr;
@@ -92,6 +94,7 @@ struct CtxData {
   bool concurrent = true;
   void* qdh = nullptr;      // [(Ns+1) * M] qd_0..qd_Ns (slice 0 unused: qd0 holds it)
   void* steps2 = nullptr;   // [2 * Ns] BatchStep: forward and conjugate step s
+  void* stepsS = nullptr;   // [2 * Ns] the same steps with the separable march's tables
   void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
   // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
   // scratch slices for the full and the two half steps, quadrature weight tables
@@ -168,6 +171,7 @@ class Engine {
   virtual ~Engine() {}
   virtual size_t elem_bytes() const = 0;      // working-precision real element
   virtual bool plane_applies(const CtxData& c) const = 0;  // can the y/z plane kernel run this grid?
+  virtual bool sep_applies(const CtxData& c) const = 0;    // can the separable march run it?
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

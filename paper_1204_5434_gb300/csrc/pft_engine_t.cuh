@@ -13,6 +13,7 @@
 #include "pft_engine_impl.cuh"
 #include "pft_batch.cuh"
 #include "pft_plane_ext.cuh"
+#include "pft_sep.cuh"
 
 namespace pft {
 
@@ -84,6 +85,7 @@ class EngineT : public Engine {
 
   size_t elem_bytes() const override { return sizeof(T); }
   bool plane_applies(const CtxData& c) const override { return plane_supported(c); }
+  bool sep_applies(const CtxData& c) const override { return sep_supported(c); }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -113,6 +115,11 @@ class EngineT : public Engine {
     for (int a = 0; a < 3; a++) {
       c.dh_off[a] = off;
       off = al(off + sizeof(T) * (size_t)dn[a]);
+    }
+    // per-axis Gaussian factors of the separable march, full axis, 1/n_a folded in
+    for (int a = 0; a < 3; a++) {
+      c.sd_off[a] = off;
+      off = al(off + sizeof(T) * (size_t)c.n[a]);
     }
     // FP64 twiddles of the full x, y, z lengths (the transforms of the semi-implicit step)
     for (int a = 0; a < 3; a++) {
@@ -158,6 +165,12 @@ class EngineT : public Engine {
         reinterpret_cast<T*>(h.data() + c.dh_off[a])[m] = (T)hval;
         g[m] = k * k;
         reinterpret_cast<double*>(h.data() + c.e_off[a])[m] = exp(-k * k * c.ds);
+      }
+      T* sd = reinterpret_cast<T*>(h.data() + c.sd_off[a]);
+      for (int m = 0; m < na; m++) {
+        const int mm = (m <= na / 2) ? m : m - na;
+        const double k = 2.0 * M_PI * (double)mm / c.L[a];
+        sd[m] = (T)(exp(-k * k * c.ds) / (double)na);
       }
     }
     return cudaMemcpyAsync(c.tables, h.data(), off, cudaMemcpyHostToDevice, c.stream);
@@ -462,6 +475,84 @@ class EngineT : public Engine {
       c.bytes += h.size() * sizeof(BatchStep);
       e = cudaMemcpy(c.steps2, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return e;
+      if (sep_supported(c)) {
+        // the separable march: the same steps with the full-axis factors and twiddles
+        for (auto& b : h)
+          for (int a = 0; a < 3; a++) b.d[a] = t + c.sd_off[a];
+        e = cudaMalloc(&c.stepsS, h.size() * sizeof(BatchStep));
+        if (e != cudaSuccess) return e;
+        c.bytes += h.size() * sizeof(BatchStep);
+        e = cudaMemcpy(c.stepsS, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return e;
+      }
+    }
+    return cudaSuccess;
+  }
+
+  // ---------------------------------------------------------------- separable march
+  // FP32 real fields with ny = nz = N in {64, 128} and nx in {64, 128}.
+  static bool sep_supported(const CtxData& c) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return false;
+    } else {
+      if (c.kind != PFT_SCFT_REAL || c.n[1] != c.n[2]) return false;
+      return (c.n[1] == 64 || c.n[1] == 128) && (c.n[0] == 64 || c.n[0] == 128);
+    }
+  }
+
+  template <int N, int MODE>
+  static cudaError_t launch_sep_plane(const BatchStep* st, int nx, int members, int* err, cudaStream_t sm) {
+    using R = SepCfg<N>;
+    auto kern = kb_sep_plane<N, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)nx, (unsigned)members), R::THREADS, R::SMEM, sm>>>(st, err);
+    return cudaGetLastError();
+  }
+
+  template <int NX, int MODE>
+  static cudaError_t launch_sep_x(const BatchStep* st, long long P, int members, cudaStream_t sm) {
+    constexpr int C = 16;
+    auto kern = kb_sep_x<NX, MODE, C>;
+    const unsigned grid = (unsigned)((P + C - 1) / C);
+    kern<<<dim3(grid, (unsigned)members), C * Plan<NX>::TPC, sep_x_smem<NX, C>(), sm>>>(st, P);
+    return cudaGetLastError();
+  }
+
+  // launch j of a separable march (j = 0: the first plane launch; j >= 1 stores q_j)
+  cudaError_t sep_launch(CtxData& c, const BatchStep* ss, int j, int members, cudaStream_t sm) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      const int nx = c.n[0], N = c.n[1];
+      const int mode = (j == 0) ? 0 : (j == c.Ns ? 2 : 1);
+      if (j >= 1 && (j & 1)) {  // x kernel
+        const long long P = (long long)c.n[1] * c.n[2] / 2;
+        if (nx == 128) return mode == 2 ? launch_sep_x<128, 2>(ss, P, members, sm) : launch_sep_x<128, 1>(ss, P, members, sm);
+        if (nx == 64) return mode == 2 ? launch_sep_x<64, 2>(ss, P, members, sm) : launch_sep_x<64, 1>(ss, P, members, sm);
+        return cudaErrorNotSupported;
+      }
+      int* err = c.kerr;
+      if (N == 128) {
+        if (mode == 0) return launch_sep_plane<128, 0>(ss, nx, members, err, sm);
+        return mode == 2 ? launch_sep_plane<128, 2>(ss, nx, members, err, sm)
+                         : launch_sep_plane<128, 1>(ss, nx, members, err, sm);
+      }
+      if (N == 64) {
+        if (mode == 0) return launch_sep_plane<64, 0>(ss, nx, members, err, sm);
+        return mode == 2 ? launch_sep_plane<64, 2>(ss, nx, members, err, sm) : launch_sep_plane<64, 1>(ss, nx, members, err, sm);
+      }
+      return cudaErrorNotSupported;
+    }
+  }
+
+  // A whole separable march of `members` chains whose step-1 entry is st (entries of
+  // consecutive steps two apart).
+  cudaError_t sep_march(CtxData& c, const BatchStep* st, int members, cudaStream_t sm) {
+    for (int j = 0; j <= c.Ns; j++) {
+      const BatchStep* ss = st + (size_t)2 * (j == 0 ? 0 : j - 1);
+      cudaError_t e = sep_launch(c, ss, j, members, sm);
+      if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
   }
@@ -488,6 +579,14 @@ class EngineT : public Engine {
       }
       if ((e = cudaEventRecord(c.join_ev, c.stream2)) != cudaSuccess) return e;
       if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
+      return finish_concurrent(c);
+    }
+    if (c.plan_plane == 2 && c.stepsS) {  // separable march, both propagators per launch
+      for (int j = 0; j <= c.Ns; j++) {
+        mark(c, KK_PAIR_STEP);
+        const BatchStep* ss = (const BatchStep*)c.stepsS + (size_t)2 * (j == 0 ? 0 : j - 1);
+        if ((e = sep_launch(c, ss, j, 2, c.stream)) != cudaSuccess) return e;
+      }
       return finish_concurrent(c);
     }
     if (plane_supported(c) && c.plan_plane) {
@@ -523,6 +622,10 @@ class EngineT : public Engine {
   // (entries of consecutive steps are two apart).
   cudaError_t march_chain(CtxData& c, const BatchGeom& g, const BatchStep* st, cudaStream_t sm) {
     cudaError_t e;
+    if (c.plan_plane == 2 && c.stepsS) {  // separable march: one launch per contour step
+      const BatchStep* ss = (const BatchStep*)c.stepsS + (st - (const BatchStep*)c.steps2);
+      return sep_march(c, ss, 1, sm);
+    }
     if (plane_supported(c) && c.plan_plane) {
       if ((e = batch_plane(c, st, 0, 1, sm)) != cudaSuccess) return e;
       const int nx = c.n[0], ny = c.n[1];
@@ -555,7 +658,7 @@ class EngineT : public Engine {
              c.kind == PFT_SCFT_REAL ? "real" : "complex", sizeof(T) == 4 ? "fp32" : "fp64", c.Ns);
     int pl = 0, sm = 0;
     if (plan_cache_lookup(key, &pl, &sm)) {
-      c.plan_plane = (pl && plane_supported(c)) ? 1 : 0;
+      c.plan_plane = (pl == 2 && sep_supported(c) && c.stepsS) ? 2 : ((pl && plane_supported(c)) ? 1 : 0);
       c.plan_streams = sm ? 1 : 0;
       return cudaSuccess;
     }
@@ -564,9 +667,11 @@ class EngineT : public Engine {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = -1.f;
     int bpl = c.plan_plane, bsm = c.plan_streams;
-    for (int cand = 0; cand < 4 && e == cudaSuccess; cand++) {
-      const int cpl = (cand >> 1) & 1 ? 0 : 1, csm = (cand & 1) ? 0 : 1;
-      if (cpl && !plane_supported(c)) continue;
+    // candidates: separable march, plane kernel, pencil passes; two chains or two-member launches
+    for (int cand = 0; cand < 6 && e == cudaSuccess; cand++) {
+      const int cpl = 2 - cand / 2, csm = (cand & 1) ? 0 : 1;
+      if (cpl == 2 && !(sep_supported(c) && c.stepsS)) continue;
+      if (cpl == 1 && !plane_supported(c)) continue;
       c.plan_plane = cpl;
       c.plan_streams = csm;
       if ((e = record_solve(c)) != cudaSuccess) break;  // warm-up

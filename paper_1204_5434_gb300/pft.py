@@ -135,6 +135,7 @@ _SIGS = {
     "pft_get_checkpoint": (ct.c_int, [_P, ct.POINTER(ct.c_int)]),
     "pft_get_plan": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "pft_fma_throughput": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_double), _P]),
+    "pft_set_plan": (ct.c_int, [_P, ct.c_int, ct.c_int]),
     "pft_adjoint": (ct.c_int, [_P, _P, _P, _P, _P, ct.c_int]),
     "pft_batch_autotune": (ct.c_int, [_P]),
     "pft_batch_set_plan": (ct.c_int, [_P, ct.c_int, ct.c_int]),
@@ -418,6 +419,11 @@ def pft_fma_throughput(precision=PFT_FP64, stream=None) -> float:
     t = ct.c_double()
     _check(_lib().pft_fma_throughput(int(precision), ct.byref(t), stream), "pft_fma_throughput")
     return t.value
+
+
+def pft_set_plan(h, plane, streams=1):
+    """Fix the march plan: plane 0 pencils, 1 plane kernel + x pass, 2 separable march."""
+    _check(_lib().pft_set_plan(h, int(plane), int(streams)), "pft_set_plan")
 
 
 def pft_get_plan(h):

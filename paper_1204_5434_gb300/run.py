@@ -36,6 +36,7 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--no-graph", action="store_true", help="launch each solve eagerly")
+    ap.add_argument("--plan", default="", help="fix the march plan as PLANE,STREAMS (pft_set_plan), e.g. 2,1")
     ap.add_argument("--adjoint", action="store_true",
                     help="after the updates, one reverse-mode adjoint of a seeded linear loss on the "
                          "densities (real SCFT diblock workloads)")
@@ -52,6 +53,9 @@ def main(argv=None) -> int:
                     seed=w.seed, march=_MARCH[a.march], scheme=_SCHEME[a.scheme], arch=arch, B=w.B) as s:
         s.set_fields(wp, wm)
         h = s.h
+        if a.plan:
+            pl, st = (int(v) for v in a.plan.split(","))
+            pft.pft_set_plan(h, pl, st)
         for _ in range(a.warmup):
             pft.pft_solve(h)
             pft.pft_field_step(h, step_kind, step_size)
@@ -76,6 +80,7 @@ def main(argv=None) -> int:
         pft.pft_solve(h)
         obs = s.observables()
         n_solve, n_field = pft.pft_launch_counts(h)
+        plan_used = list(pft.pft_get_plan(h))
         adj_ms = None
         if a.adjoint:
             import time
@@ -89,7 +94,7 @@ def main(argv=None) -> int:
     units = (1 if arch == pft.PFT_ARCH_EDWARDS else 2) * w.M * w.Ns  # propagators marched
     out = {"workload": w.name, "precision": a.precision, "scheme": a.scheme, "Ns": w.Ns, "steps": a.steps,
            "ms_per_update": ms, "units_per_s": (units / (ms * 1e-3)) if ms else None,
-           "kernels_per_solve": n_solve, "kernels_per_field_step": n_field,
+           "kernels_per_solve": n_solve, "kernels_per_field_step": n_field, "plan": plan_used,
            "Q": [obs["Q"].real, obs["Q"].imag], "H": [obs["H"].real, obs["H"].imag]}
     if a.adjoint:
         out["adjoint_ms_host_wall"] = adj_ms

@@ -122,7 +122,7 @@ def test_adjoint_128cubed_matches_oracle(prec):
         s.solve()
         gp, gm = s.adjoint(GA, GB)
         if prec == FP32:
-            assert pft.pft_get_plan(s.h)[0] == 1
+            assert pft.pft_get_plan(s.h)[0] >= 1
     ep, em = o.adjoint_field_gradient(wp, wm, w.n, w.L, w.Ns, w.fA, GA, GB)
     scale = max(np.max(np.abs(ep)), np.max(np.abs(em)))
     err = max(np.max(np.abs(gp - ep)), np.max(np.abs(gm - em))) / scale

@@ -133,7 +133,7 @@ def test_box_derivative_on_the_plane_kernel_64cubed_fp32():
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, FP32) as s:
         s.set_fields(wp, wm)
         s.solve()
-        assert pft.pft_get_plan(s.h)[0] == 1
+        assert pft.pft_get_plan(s.h)[0] >= 1
         _, _, _, dq = s.gradients(want_fields=False)
     err = max(abs(dq[i] - gq[i]) / abs(gq[i]) for i in range(3))
     print(f"\nbox derivative 64^3 FP32 (plane path) rel err {err:.2e}")
@@ -152,7 +152,7 @@ def test_box_derivative_128cubed_matches_oracle(prec):
         s.set_fields(wp, wm)
         s.solve()
         if prec == FP32:
-            assert pft.pft_get_plan(s.h)[0] == 1
+            assert pft.pft_get_plan(s.h)[0] >= 1
         dq = s.gradients(want_fields=False)[3]
     err = max(abs(dq[i] - gq[i]) / abs(gq[i]) for i in range(3))
     print(f"\nbox derivative 128^3 prec={prec} vs oracle: rel err {err:.2e}")

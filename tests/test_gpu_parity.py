@@ -337,10 +337,11 @@ def test_lamellar_scft_32cubed_50_steps_fp32_error_table():
 @pytest.mark.parametrize("prec", [FP64, FP32])
 def test_gyroid_128cubed_full_size(prec):
     """The 128^3 gyroid-seeded SCFT workload (Ns=100, fA=0.35, chiN=18) at full size, in
-    the plan the bench times (FP32: plane kernel, two chains): Q and H, phiA and phiB over
-    every one of the 2,097,152 points, and the propagator slices q_1, q_NsA, q_Ns and
-    qd_1, qd_(Ns-NsA), qd_Ns element by element against the oracle (a fault confined to one
-    kz column or one x-plane of a transform touches every slice after it).
+    the plan the bench times (FP32: the separable march, two chains) and, in FP32, also in
+    the plane-kernel plan: Q and H, phiA and phiB over every one of the 2,097,152 points,
+    and the propagator slices q_1, q_NsA, q_Ns and qd_1, qd_(Ns-NsA), qd_Ns element by
+    element against the oracle (a fault confined to one kz column or one x-plane of a
+    transform touches every slice after it).
     FP32 slices: the maximum over all 2,097,152 points of the error relative to the slice
     maximum, bounded by 1e-4 -- the per-point random-walk estimate of the derivation above
     (1.8e-5 after 2 Ns = 200 transforms of log2(M) = 21 stages) times the tail factor
@@ -351,27 +352,30 @@ def test_gyroid_128cubed_full_size(prec):
     Href = o.hamiltonian(wp, wm, ref.lnQ, w.chiN, w.C, w.n, w.L, o.SCFT_REAL)
     NsA, Ns = ref.NsA, w.Ns
     t = TOL[prec]
-    with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec) as s:
-        if prec == FP32:
-            assert pft.pft_get_plan(s.h) == (1, 1)
-        assert pft.pft_get_checkpoint(s.h) == 1
-        s.set_fields(wp, wm)
-        s.solve()
-        obs = s.observables()
-        phiA, phiB = s.densities()
-        eq = 0.0
-        for which, hist in ((0, ref.q), (2, ref.qd)):
-            for k in sorted({1, NsA if which == 0 else Ns - NsA, Ns}):
-                g = s.propagator(which, k)
-                e = np.max(np.abs(g - hist[k])) / np.max(np.abs(hist[k]))
-                eq = max(eq, e)
-                assert e <= (t["q"] if prec == FP64 else 1e-4), (which, k, e)
-    eQ, eH = _rel(obs["Q"].real, ref.Q), _rel(obs["H"].real, Href)
-    ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
-    print(f"\n128^3 prec={prec}: Q rel {eQ:.2e} H rel {eH:.2e} phi abs {ephi:.2e} (all points) "
-          f"slices rel {eq:.2e}")
-    assert eQ <= t["Q"] and _check_H(obs["H"].real, Href, w.C, w.L, prec) and ephi <= t["phi"]
-    assert abs(phiA.mean() - ref.NsA / w.Ns) <= (1e-12 if prec == FP64 else 1e-6)
+    for plan in ((None,) if prec == FP64 else (None, (1, 1))):
+        with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec) as s:
+            if plan is not None:
+                pft.pft_set_plan(s.h, *plan)
+            elif prec == FP32:
+                assert pft.pft_get_plan(s.h) == (2, 1)
+            assert pft.pft_get_checkpoint(s.h) == 1
+            s.set_fields(wp, wm)
+            s.solve()
+            obs = s.observables()
+            phiA, phiB = s.densities()
+            eq = 0.0
+            for which, hist in ((0, ref.q), (2, ref.qd)):
+                for k in sorted({1, NsA if which == 0 else Ns - NsA, Ns}):
+                    g = s.propagator(which, k)
+                    e = np.max(np.abs(g - hist[k])) / np.max(np.abs(hist[k]))
+                    eq = max(eq, e)
+                    assert e <= (t["q"] if prec == FP64 else 1e-4), (plan, which, k, e)
+        eQ, eH = _rel(obs["Q"].real, ref.Q), _rel(obs["H"].real, Href)
+        ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+        print(f"\n128^3 prec={prec} plan={plan}: Q rel {eQ:.2e} H rel {eH:.2e} phi abs {ephi:.2e} (all points) "
+              f"slices rel {eq:.2e}")
+        assert eQ <= t["Q"] and _check_H(obs["H"].real, Href, w.C, w.L, prec) and ephi <= t["phi"]
+        assert abs(phiA.mean() - ref.NsA / w.Ns) <= (1e-12 if prec == FP64 else 1e-6)
 
 
 @pytest.mark.parametrize("n,Ns,fA", [((32, 32, 32), 40, 0.35), ((128, 128, 128), 100, 0.35)])

@@ -247,7 +247,7 @@ def test_rqm4_on_the_plane_kernels_64cubed(kind, Ns, fA):
     with pft.System(n, L, Ns, fA, 15.0, 1.0, kind, FP32, scheme=RQM4) as s:
         s.set_fields(wp, wm)
         s.solve()
-        assert pft.pft_get_plan(s.h)[0] == 1
+        assert pft.pft_get_plan(s.h)[0] >= 1
         obs = s.observables()
         phiA, phiB = s.densities()
     t = TOL[FP32]
