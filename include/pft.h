@@ -401,7 +401,10 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
  * fields, ny = nz and nx in {64, 128}): the diffusion factor exp(-k^2 ds) of Eq. 13 is the
  * product of three per-axis factors, so F^-1 D F is the product of three 1D periodic
  * Gaussian convolutions, applied in alternating axis order so that one launch -- a y/z
- * plane kernel or an x kernel in turn -- advances one contour step.  *streams = 1 if the
+ * plane kernel or an x kernel in turn -- advances one contour step; 3 = the separable
+ * march on pencils (complex fields, real fields with ny and nz even; either precision):
+ * per contour step one launch of the y convolution and one of the x or z kernel, which
+ * carries the two convolutions of consecutive steps along its axis.  *streams = 1 if the
  * two propagators run as two chains on two streams.  Either pointer may be NULL.
  * Errors: PFT_ERR_ARG for a NULL ctx. */
 pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams);

@@ -254,8 +254,13 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
   d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
   d.autotune = opts->autotune != 0;
-  // the default plan: the separable march where it applies, else the plane kernel
-  d.plan_plane = c->eng->sep_applies(d) ? 2 : (c->eng->plane_applies(d) ? 1 : 0);
+  // the default plan (measured on GB300): FP32 -- the separable march on the plane kernel
+  // where it applies, else the plane kernel, else the pencil passes; FP64 -- the separable
+  // march on pencils (fewer passes of the FP64-pipe-bound transforms)
+  if (c->eng->sep_applies(d)) d.plan_plane = 2;
+  else if (c->eng->plane_applies(d)) d.plan_plane = 1;
+  else if (d.prec == PFT_FP64 && c->eng->sepp_applies(d)) d.plan_plane = 3;
+  else d.plan_plane = 0;
 
   const size_t M = (size_t)d.M;
   const size_t we = welem(d), fe = felem(d);
@@ -865,11 +870,13 @@ pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* fi
 pft_status pft_set_plan(pft_ctx* ctx, int plane, int streams) {
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
-  if (plane < 0 || plane > 2 || streams < 0 || streams > 1) return fail(PFT_ERR_ARG, "plane in {0,1,2}, streams in {0,1}");
+  if (plane < 0 || plane > 3 || streams < 0 || streams > 1) return fail(PFT_ERR_ARG, "plane in {0,1,2,3}, streams in {0,1}");
   if (plane == 1 && !ctx->eng->plane_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the plane kernel needs FP32 with ny = nz = 64 or 128 (real) or 64 (complex)");
   if (plane == 2 && !ctx->eng->sep_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the separable march needs FP32 real fields, ny = nz and nx in {64, 128}");
+  if (plane == 3 && !ctx->eng->sepp_applies(d))
+    return fail(PFT_ERR_UNSUPPORTED, "the separable pencil march needs ny and nz even for real fields");
   d.plan_plane = plane;
   d.plan_streams = streams;
   d.tuned = true;  // an explicit plan is not re-tuned

@@ -166,12 +166,24 @@ struct BatchGeom {
   int nzh;
 };
 
+// The separable pencil march (pft_sepp.cuh): grid and field kind (0 real, 1 complex).
+struct SeppGeom {
+  int n[3];
+  int kind;
+};
+// Launch j (0..Ns) of a separable pencil march for `members` entries starting at ss (for
+// j >= 1 the entries of contour step j; j = 0 uses those of step 1).  Real fields need
+// ny and nz even.  Returns cudaErrorInvalidValue for a length without an FFT plan.
+cudaError_t sepp_launch_f32(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm);
+cudaError_t sepp_launch_f64(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm);
+
 class Engine {
  public:
   virtual ~Engine() {}
   virtual size_t elem_bytes() const = 0;      // working-precision real element
   virtual bool plane_applies(const CtxData& c) const = 0;  // can the y/z plane kernel run this grid?
   virtual bool sep_applies(const CtxData& c) const = 0;    // can the separable march run it?
+  virtual bool sepp_applies(const CtxData& c) const = 0;   // can the separable pencil march run it?
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

@@ -86,6 +86,7 @@ class EngineT : public Engine {
   size_t elem_bytes() const override { return sizeof(T); }
   bool plane_applies(const CtxData& c) const override { return plane_supported(c); }
   bool sep_applies(const CtxData& c) const override { return sep_supported(c); }
+  bool sepp_applies(const CtxData& c) const override { return sepp_supported(c); }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -475,8 +476,8 @@ class EngineT : public Engine {
       c.bytes += h.size() * sizeof(BatchStep);
       e = cudaMemcpy(c.steps2, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) return e;
-      if (sep_supported(c)) {
-        // the separable march: the same steps with the full-axis factors and twiddles
+      if (sep_supported(c) || sepp_supported(c)) {
+        // the separable marches: the same steps with the full-axis factors and twiddles
         for (auto& b : h)
           for (int a = 0; a < 3; a++) b.d[a] = t + c.sd_off[a];
         e = cudaMalloc(&c.stepsS, h.size() * sizeof(BatchStep));
@@ -490,7 +491,27 @@ class EngineT : public Engine {
   }
 
   // ---------------------------------------------------------------- separable march
-  // FP32 real fields with ny = nz = N in {64, 128} and nx in {64, 128}.
+  // On pencils (plan 3): complex fields of any supported size, real fields with ny and nz
+  // even (rows and z pairs carried two at a time).
+  static bool sepp_supported(const CtxData& c) {
+    return c.kind != PFT_SCFT_REAL || (c.n[1] % 2 == 0 && c.n[2] % 2 == 0);
+  }
+  cudaError_t sepp_march(CtxData& c, const BatchStep* st, int members, cudaStream_t sm) {
+    SeppGeom g;
+    for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
+    g.kind = (c.kind == PFT_SCFT_REAL) ? 0 : 1;
+    for (int j = 0; j <= c.Ns; j++) {
+      if (members == 2) mark(c, KK_PAIR_STEP);
+      const BatchStep* ss = st + (size_t)2 * (j == 0 ? 0 : j - 1);
+      cudaError_t e = std::is_same<T, float>::value ? sepp_launch_f32(g, ss, j, members, sm)
+                                                     : sepp_launch_f64(g, ss, j, members, sm);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  // On the plane kernel (plane 2): FP32 real fields with ny = nz = N in {64, 128} and nx
+  // in {64, 128}.
   static bool sep_supported(const CtxData& c) {
     if constexpr (!std::is_same<T, float>::value) {
       return false;
@@ -510,13 +531,20 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
-  template <int NX, int MODE>
-  static cudaError_t launch_sep_x(const BatchStep* st, long long P, int members, cudaStream_t sm) {
+  template <int NX, int NYZ, int MODE>
+  static cudaError_t launch_sep_x(const BatchStep* st, int members, cudaStream_t sm) {
     constexpr int C = 16;
-    auto kern = kb_sep_x<NX, MODE, C>;
-    const unsigned grid = (unsigned)((P + C - 1) / C);
-    kern<<<dim3(grid, (unsigned)members), C * Plan<NX>::TPC, sep_x_smem<NX, C>(), sm>>>(st, P);
+    constexpr long long P = (long long)NYZ * NYZ / 2;
+    auto kern = kb_sep_x<NX, NYZ, MODE, C>;
+    const unsigned grid = (unsigned)(P / C);
+    kern<<<dim3(grid, (unsigned)members), C * Plan<NX>::TPC, sep_x_smem<NX, C>(), sm>>>(st);
     return cudaGetLastError();
+  }
+  template <int NX, int MODE>
+  static cudaError_t launch_sep_x_n(const BatchStep* st, int nyz, int members, cudaStream_t sm) {
+    if (nyz == 128) return launch_sep_x<NX, 128, MODE>(st, members, sm);
+    if (nyz == 64) return launch_sep_x<NX, 64, MODE>(st, members, sm);
+    return cudaErrorNotSupported;
   }
 
   // launch j of a separable march (j = 0: the first plane launch; j >= 1 stores q_j)
@@ -527,9 +555,8 @@ class EngineT : public Engine {
       const int nx = c.n[0], N = c.n[1];
       const int mode = (j == 0) ? 0 : (j == c.Ns ? 2 : 1);
       if (j >= 1 && (j & 1)) {  // x kernel
-        const long long P = (long long)c.n[1] * c.n[2] / 2;
-        if (nx == 128) return mode == 2 ? launch_sep_x<128, 2>(ss, P, members, sm) : launch_sep_x<128, 1>(ss, P, members, sm);
-        if (nx == 64) return mode == 2 ? launch_sep_x<64, 2>(ss, P, members, sm) : launch_sep_x<64, 1>(ss, P, members, sm);
+        if (nx == 128) return mode == 2 ? launch_sep_x_n<128, 2>(ss, N, members, sm) : launch_sep_x_n<128, 1>(ss, N, members, sm);
+        if (nx == 64) return mode == 2 ? launch_sep_x_n<64, 2>(ss, N, members, sm) : launch_sep_x_n<64, 1>(ss, N, members, sm);
         return cudaErrorNotSupported;
       }
       int* err = c.kerr;
@@ -581,6 +608,10 @@ class EngineT : public Engine {
       if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
       return finish_concurrent(c);
     }
+    if (c.plan_plane == 3 && c.stepsS) {  // separable pencil march, both propagators per launch
+      if ((e = sepp_march(c, (const BatchStep*)c.stepsS, 2, c.stream)) != cudaSuccess) return e;
+      return finish_concurrent(c);
+    }
     if (c.plan_plane == 2 && c.stepsS) {  // separable march, both propagators per launch
       for (int j = 0; j <= c.Ns; j++) {
         mark(c, KK_PAIR_STEP);
@@ -626,6 +657,10 @@ class EngineT : public Engine {
       const BatchStep* ss = (const BatchStep*)c.stepsS + (st - (const BatchStep*)c.steps2);
       return sep_march(c, ss, 1, sm);
     }
+    if (c.plan_plane == 3 && c.stepsS) {  // separable pencil march: two launches per step
+      const BatchStep* ss = (const BatchStep*)c.stepsS + (st - (const BatchStep*)c.steps2);
+      return sepp_march(c, ss, 1, sm);
+    }
     if (plane_supported(c) && c.plan_plane) {
       if ((e = batch_plane(c, st, 0, 1, sm)) != cudaSuccess) return e;
       const int nx = c.n[0], ny = c.n[1];
@@ -658,7 +693,8 @@ class EngineT : public Engine {
              c.kind == PFT_SCFT_REAL ? "real" : "complex", sizeof(T) == 4 ? "fp32" : "fp64", c.Ns);
     int pl = 0, sm = 0;
     if (plan_cache_lookup(key, &pl, &sm)) {
-      c.plan_plane = (pl == 2 && sep_supported(c) && c.stepsS) ? 2 : ((pl && plane_supported(c)) ? 1 : 0);
+      if (pl == 3 && sepp_supported(c) && c.stepsS) c.plan_plane = 3;
+      else c.plan_plane = (pl == 2 && sep_supported(c) && c.stepsS) ? 2 : ((pl == 1 && plane_supported(c)) ? 1 : 0);
       c.plan_streams = sm ? 1 : 0;
       return cudaSuccess;
     }
@@ -667,9 +703,11 @@ class EngineT : public Engine {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = -1.f;
     int bpl = c.plan_plane, bsm = c.plan_streams;
-    // candidates: separable march, plane kernel, pencil passes; two chains or two-member launches
-    for (int cand = 0; cand < 6 && e == cudaSuccess; cand++) {
-      const int cpl = 2 - cand / 2, csm = (cand & 1) ? 0 : 1;
+    // candidates: separable pencil march, separable plane march, plane kernel, pencil
+    // passes; two chains or two-member launches
+    for (int cand = 0; cand < 8 && e == cudaSuccess; cand++) {
+      const int cpl = 3 - cand / 2, csm = (cand & 1) ? 0 : 1;
+      if (cpl == 3 && !(sepp_supported(c) && c.stepsS)) continue;
       if (cpl == 2 && !(sep_supported(c) && c.stepsS)) continue;
       if (cpl == 1 && !plane_supported(c)) continue;
       c.plan_plane = cpl;
@@ -1123,7 +1161,8 @@ class EngineT : public Engine {
   }
 
   cudaError_t enqueue_solve(CtxData& c) override {
-    if (!plane_supported(c)) c.plan_plane = 0;
+    if ((c.plan_plane == 1 || c.plan_plane == 2) && !plane_supported(c)) c.plan_plane = sepp_supported(c) ? 3 : 0;
+    if (c.plan_plane == 3 && !sepp_supported(c)) c.plan_plane = 0;
     if (c.scheme == 1) {
       cudaError_t e = prepare_rqm4(c);
       if (e != cudaSuccess) return e;

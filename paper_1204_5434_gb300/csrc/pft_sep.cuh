@@ -212,48 +212,65 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
 // The x kernel: C pencils along x per CTA (consecutive column pairs (y, z/2) of every
 // x-plane), each a complex line a + i b of two real lines.
 // MODE 1: Kx, x B_s, store q_s, x B_{s+1}, Kx.  MODE 2: Kx, x B_Ns, store q_Ns.
-// P = ny nz / 2 column pairs per x-plane; st.d[0] = dx (full length, 1/nx folded in);
-// twiddles st.tw[0].
-template <int NX, int MODE, int C = 16>
-__global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep* __restrict__ st, long long P) {
+// P = NYZ^2 / 2 column pairs per x-plane (ny = nz = NYZ); st.d[0] = dx (full length,
+// 1/nx folded in); twiddles st.tw[0].  B_s of the tile is copied to shared memory by
+// 16-byte cp.async chunks at the start, so its latency hides behind the first Kx.
+template <int NX, int NYZ, int MODE, int C = 16>
+__global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep* __restrict__ st) {
+  constexpr long long P = (long long)NYZ * NYZ / 2;  // column pairs per x-plane (ny = nz = NYZ)
+  static_assert(P % C == 0, "whole tiles");
   using PL = Plan<NX>;
   constexpr int E = PL::E, TPC = PL::TPC;
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
-  float2* tws = sm + NX * C;
+  float2* Bt = sm + NX * C;            // B_s of the tile, [x][C]
+  float2* tws = Bt + NX * C;
   float* dxs = reinterpret_cast<float*>(tws + NX);
   const int c = threadIdx.x % C;
   const int t = threadIdx.x / C;
-  for (int i = threadIdx.x; i < NX; i += C * TPC) {
-    tws[i] = reinterpret_cast<const float2*>(s.tw[0])[i];
-    dxs[i] = reinterpret_cast<const float*>(s.d[0])[i];
-  }
-  const long long col = (long long)blockIdx.x * C + c;
-  const bool valid = col < P;
-  const long long colc = valid ? col : 0;
+  const long long col0 = (long long)blockIdx.x * C;
+  const long long col = col0 + c;
+  const long long colc = col;
   float2* F2 = reinterpret_cast<float2*>(s.spec);
   float2 v[E];
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = F2[(long long)(t + TPC * i) * P + colc];
+  {
+    constexpr int CH = C / 2;  // 16-byte chunks per row of the tile
+    const unsigned sb = (unsigned)__cvta_generic_to_shared(Bt);
+    const float2* Bg = reinterpret_cast<const float2*>(s.B) + col0;
+    for (int k = threadIdx.x; k < NX * CH; k += C * TPC) {
+      const int xr = k / CH, ch = k % CH;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + (unsigned)((xr * C + 2 * ch) * 8)),
+                   "l"(Bg + (long long)xr * P + 2 * ch)
+                   : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < NX; i += C * TPC) {
+    tws[i] = reinterpret_cast<const float2*>(s.tw[0])[i];
+    dxs[i] = reinterpret_cast<const float*>(s.d[0])[i];
+  }
   __syncthreads();  // twiddles and factors in shared memory
   XchCols<float> x{sm, C, c};
   fft<float, false, NX, PL>(v, t, tws, x);
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = cscale(v[i], dxs[t + TPC * i]);
   fft<float, true, NX, PL>(v, t, tws, x);
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncthreads();  // every thread's chunks of B_s have landed
   {
     const bool same = (s.Bnext == s.B);
-    const float2* B2 = reinterpret_cast<const float2*>(s.B);
     const float2* Bn2 = reinterpret_cast<const float2*>(s.Bnext);
     float2* q2 = reinterpret_cast<float2*>(s.out);
 #pragma unroll
     for (int i = 0; i < E; i++) {
       const long long o = (long long)(t + TPC * i) * P + colc;
-      const float2 b = B2[o];
+      const float2 b = Bt[(t + TPC * i) * C + c];
       v[i].x *= b.x;
       v[i].y *= b.y;
-      if (valid) q2[o] = v[i];
+      q2[o] = v[i];
       if (MODE == 1) {
         const float2 bn = same ? b : Bn2[o];
         v[i].x *= bn.x;
@@ -266,14 +283,12 @@ __global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = cscale(v[i], dxs[t + TPC * i]);
   fft<float, true, NX, PL>(v, t, tws, x);
-  if (valid) {
 #pragma unroll
-    for (int i = 0; i < E; i++) F2[(long long)(t + TPC * i) * P + col] = v[i];
-  }
+  for (int i = 0; i < E; i++) F2[(long long)(t + TPC * i) * P + col] = v[i];
 }
 
 template <int NX, int C = 16> constexpr size_t sep_x_smem() {
-  return (size_t)NX * C * sizeof(float2) + (size_t)NX * sizeof(float2) + (size_t)NX * sizeof(float);
+  return 2 * (size_t)NX * C * sizeof(float2) + (size_t)NX * sizeof(float2) + (size_t)NX * sizeof(float);
 }
 
 }  // namespace pft

@@ -1,0 +1,241 @@
+// pft_sepp.cuh -- the separable march on pencils: any grid, real or complex fields,
+// either precision, two launches per contour step.
+//
+// As in pft_sep.cuh the diffusion operator of Eq. 13 is applied as Kx Ky Kz, three 1D
+// periodic Gaussian convolutions (d_a real and even, 1/n_a folded in), in alternating
+// order so that consecutive steps' convolutions along x (and along z) meet in one kernel:
+//   z kernel:  Kz, x B_s, store q_s, x B_{s+1}, Kz     (lines along z, contiguous)
+//   y kernel:  Ky                                      (lines along y, strided)
+//   x kernel:  Kx, x B_s, store q_s, x B_{s+1}, Kx     (lines along x, strided)
+// The march is a first z launch (x B_1, Kz) and then, for s = 1..Ns, a y launch and the x
+// (s odd) or z (s even) launch that stores q_s; an entry without Bnext stops after its store
+// (so members of a batch with different Ns share the launches).
+// Lines: complex fields (KIND 1) transform each line; real fields (KIND 0) carry two real
+// lines as one complex line a + i b -- along x and y the pair (z, z+1) (a complex element
+// of the field viewed as pairs), along z the rows (y, y+1) of one x-plane.
+#pragma once
+#include "pft_batch.cuh"
+
+namespace pft {
+
+// x B for one element: componentwise for real pairs, complex product for complex fields.
+template <int KIND, typename Z>
+__device__ __forceinline__ Z sepp_mul(Z v, Z b) {
+  if constexpr (KIND == 0) {
+    v.x *= b.x;
+    v.y *= b.y;
+    return v;
+  } else {
+    return cmul(v, b);
+  }
+}
+
+// Strided lines (x or y): line `col` (0 <= col < nlines) starts at (col / cin) s_outer +
+// col % cin and its element pos sits s_k further per step (units: complex elements of the
+// field, which for real fields are the (z, z+1) pairs).  PW 0: the convolution only; PW 2:
+// conv, x B_s, store q_s, then (if st.Bnext) x B_{s+1}, conv.  AX: the axis (0 x, 1 y)
+// whose twiddles st.tw[AX] and factors st.d[AX] apply.
+// Registers: at most 128 a thread (2 CTAs of 256 threads, 4 of 128 per SM).
+template <typename T, int N> struct SeppLineCfg {
+  static constexpr int THREADS = Tile<T>::C * Plan<N>::TPC;
+  static constexpr int MINB = (512 / THREADS) > 0 ? 512 / THREADS : 1;
+};
+// Offsets are 32-bit: a field holds fewer than 2^31 complex elements.
+template <typename T, int N, int KIND, int PW, int AX>
+__global__ void __launch_bounds__(SeppLineCfg<T, N>::THREADS, SeppLineCfg<T, N>::MINB)
+kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer, int s_k) {
+  using Z = cpx<T>;
+  using PL = Plan<N>;
+  constexpr int E = PL::E, TPC = PL::TPC, C = Tile<T>::C;
+  const BatchStep& s = st[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  Z* sm = reinterpret_cast<Z*>(smraw);
+  const int c = threadIdx.x % C;
+  const int t = threadIdx.x / C;
+  const int col = blockIdx.x * C + c;
+  const bool valid = col < nlines;
+  const int colc = valid ? col : 0;
+  const int base = (colc / cin) * s_outer + (colc % cin) + t * s_k;  // element t of the line
+  const int step = TPC * s_k;
+  const Z* tw = reinterpret_cast<const Z*>(s.tw[AX]);
+  const T* d = reinterpret_cast<const T*>(s.d[AX]);
+  Z* F = reinterpret_cast<Z*>(s.spec);
+  Z v[E];
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = F[base + i * step];
+  XchCols<T> x{sm, C, c};
+  fft<T, false, N, PL>(v, t, tw, x);
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
+  fft<T, true, N, PL>(v, t, tw, x);
+  if (PW == 2) {
+    const Z* B = reinterpret_cast<const Z*>(s.B);
+    const Z* Bn = reinterpret_cast<const Z*>(s.Bnext);
+    Z* q = reinterpret_cast<Z*>(s.out);
+    const bool more = (Bn != nullptr);
+    const bool same = (Bn == B);
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      const int o = base + i * step;
+      const Z b = B[o];
+      v[i] = sepp_mul<KIND>(v[i], b);
+      if (valid) q[o] = v[i];
+      if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn[o]);
+    }
+    if (!more) return;
+    fft<T, false, N, PL>(v, t, tw, x);
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
+    fft<T, true, N, PL>(v, t, tw, x);
+  }
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < E; i++) F[base + i * step] = v[i];
+  }
+}
+
+// Lines along z (contiguous).  Complex fields: line l is the pencil at l N.  Real fields:
+// line l carries the rows 2l and 2l+1 (floats at 2l N + pos and (2l+1) N + pos).
+// PW 1: the first launch of a march (x B_1 on q_0 = st.in, then Kz); PW 2: Kz, x B_s,
+// store q_s, then (if st.Bnext) x B_{s+1}, Kz.
+template <typename T, int N> struct SeppZCfg {
+  static constexpr int THREADS = PencilsPerCta<T, N>::v * Plan<N>::TPC;
+  static constexpr int MINB = (512 / THREADS) > 0 ? 512 / THREADS : 1;
+};
+template <typename T, int N, int KIND, int PW>
+__global__ void __launch_bounds__(SeppZCfg<T, N>::THREADS, SeppZCfg<T, N>::MINB)
+kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
+  using Z = cpx<T>;
+  using PL = Plan<N>;
+  constexpr int E = PL::E, TPC = PL::TPC, P = PencilsPerCta<T, N>::v, LD = pencil_ld<T>(N);
+  const BatchStep& s = st[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int t = threadIdx.x % TPC;
+  const int p = threadIdx.x / TPC;
+  const long long l = (long long)blockIdx.x * P + p;
+  const bool valid = l < nlines;
+  const long long lc = valid ? l : 0;
+  XchPencil<T> x{reinterpret_cast<Z*>(smraw) + p * LD};
+  const Z* tw = reinterpret_cast<const Z*>(s.tw[2]);
+  const T* d = reinterpret_cast<const T*>(s.d[2]);
+  // element pos of the line: complex index lc N + pos, or the floats ra + pos, rb + pos
+  const long long ra = 2 * lc * N, rb = ra + N;
+  auto ld = [&](const void* a, int pos) -> Z {
+    if constexpr (KIND == 1) {
+      return reinterpret_cast<const Z*>(a)[lc * N + pos];
+    } else {
+      const T* f = reinterpret_cast<const T*>(a);
+      return mk<T>(f[ra + pos], f[rb + pos]);
+    }
+  };
+  auto stz = [&](void* a, int pos, Z z) {
+    if constexpr (KIND == 1) {
+      reinterpret_cast<Z*>(a)[lc * N + pos] = z;
+    } else {
+      T* f = reinterpret_cast<T*>(a);
+      f[ra + pos] = z.x;
+      f[rb + pos] = z.y;
+    }
+  };
+  Z v[E];
+  if (PW == 1) {
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = sepp_mul<KIND>(ld(s.in, t + TPC * i), ld(s.B, t + TPC * i));
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = ld(s.spec, t + TPC * i);
+    fft<T, false, N, PL>(v, t, tw, x);
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
+    fft<T, true, N, PL>(v, t, tw, x);
+    const bool more = (s.Bnext != nullptr);
+    const bool same = (s.Bnext == s.B);
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      const Z b = ld(s.B, t + TPC * i);
+      v[i] = sepp_mul<KIND>(v[i], b);
+      if (valid) stz(s.out, t + TPC * i, v[i]);
+      if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : ld(s.Bnext, t + TPC * i));
+    }
+    if (!more) return;
+    if (n_stages<PL>() > 1) __syncwarp();
+  }
+  fft<T, false, N, PL>(v, t, tw, x);
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
+  fft<T, true, N, PL>(v, t, tw, x);
+  if (valid) {
+#pragma unroll
+    for (int i = 0; i < E; i++) stz(s.spec, t + TPC * i, v[i]);
+  }
+}
+
+}  // namespace pft
+
+namespace pft {
+
+// ------------------------------------------------------------------ launches
+template <typename T, int N, int KIND, int PW, int AX>
+cudaError_t sepp_line_n(const BatchStep* st, long long nlines, long long cin, long long s_outer, long long s_k,
+                        int members, cudaStream_t sm) {
+  constexpr int C = Tile<T>::C;
+  const dim3 grid((unsigned)((nlines + C - 1) / C), (unsigned)members);
+  kb_sepp_line<T, N, KIND, PW, AX><<<grid, C * Plan<N>::TPC, (size_t)N * C * sizeof(cpx<T>), sm>>>(
+      st, (int)nlines, (int)cin, (int)s_outer, (int)s_k);
+  return cudaGetLastError();
+}
+
+template <typename T, int N, int KIND, int PW>
+cudaError_t sepp_z_n(const BatchStep* st, long long nlines, int members, cudaStream_t sm) {
+  constexpr int P = PencilsPerCta<T, N>::v;
+  const dim3 grid((unsigned)((nlines + P - 1) / P), (unsigned)members);
+  kb_sepp_z<T, N, KIND, PW><<<grid, P * Plan<N>::TPC, (size_t)P * pencil_ld<T>(N) * sizeof(cpx<T>), sm>>>(st, nlines);
+  return cudaGetLastError();
+}
+
+#define PFT_SEPP_CASE(NV, ...) \
+  case NV: {                   \
+    constexpr int N = NV;      \
+    __VA_ARGS__;               \
+  } break;
+#define PFT_SEPP_AXIS(n, ...)                                                                                        \
+  switch (n) {                                                                                                       \
+    PFT_SEPP_CASE(4, __VA_ARGS__) PFT_SEPP_CASE(6, __VA_ARGS__) PFT_SEPP_CASE(8, __VA_ARGS__)                        \
+    PFT_SEPP_CASE(12, __VA_ARGS__) PFT_SEPP_CASE(16, __VA_ARGS__) PFT_SEPP_CASE(24, __VA_ARGS__)                     \
+    PFT_SEPP_CASE(32, __VA_ARGS__) PFT_SEPP_CASE(48, __VA_ARGS__) PFT_SEPP_CASE(64, __VA_ARGS__)                     \
+    PFT_SEPP_CASE(96, __VA_ARGS__) PFT_SEPP_CASE(128, __VA_ARGS__) PFT_SEPP_CASE(192, __VA_ARGS__)                   \
+    PFT_SEPP_CASE(256, __VA_ARGS__)                                                                                  \
+    default: return cudaErrorInvalidValue;                                                                           \
+  }
+
+template <typename T, int KIND>
+cudaError_t sepp_launch_k(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm) {
+  const long long nx = g.n[0], ny = g.n[1], nz = g.n[2];
+  const long long nzz = KIND == 0 ? nz / 2 : nz;  // complex elements per row
+  cudaError_t e = cudaSuccess;
+  if (j == 0) {  // x B_1, Kz
+    const long long nl = KIND == 0 ? nx * ny / 2 : nx * ny;
+    PFT_SEPP_AXIS(g.n[2], e = (sepp_z_n<T, N, KIND, 1>(ss, nl, members, sm)));
+    return e;
+  }
+  // Ky on the lines (x, z element) along y
+  PFT_SEPP_AXIS(g.n[1], e = (sepp_line_n<T, N, KIND, 0, 1>(ss, nx * nzz, nzz, ny * nzz, nzz, members, sm)));
+  if (e != cudaSuccess) return e;
+  if (j & 1) {  // Kx, x B_j, store q_j, x B_{j+1}, Kx
+    PFT_SEPP_AXIS(g.n[0], e = (sepp_line_n<T, N, KIND, 2, 0>(ss, ny * nzz, ny * nzz, 0, ny * nzz, members, sm)));
+  } else {      // Kz, x B_j, store q_j, x B_{j+1}, Kz
+    const long long nl = KIND == 0 ? nx * ny / 2 : nx * ny;
+    PFT_SEPP_AXIS(g.n[2], e = (sepp_z_n<T, N, KIND, 2>(ss, nl, members, sm)));
+  }
+  return e;
+}
+
+template <typename T>
+cudaError_t sepp_launch_t(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm) {
+  return g.kind == 0 ? sepp_launch_k<T, 0>(g, ss, j, members, sm) : sepp_launch_k<T, 1>(g, ss, j, members, sm);
+}
+
+#undef PFT_SEPP_AXIS
+#undef PFT_SEPP_CASE
+
+}  // namespace pft

@@ -81,5 +81,73 @@ def test_separable_plan_is_refused_where_it_does_not_apply():
             assert e.value.status == pft.PFT_ERR_UNSUPPORTED
     with pft.System((64, 64, 64), (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, SCFT, FP32) as s:
         with pytest.raises(pft.PftError) as e:
-            pft.pft_set_plan(s.h, 3, 1)
+            pft.pft_set_plan(s.h, 2, 2)
+        assert e.value.status == pft.PFT_ERR_ARG
+
+
+# ------------------------------------------------- separable march on pencils (plan 3)
+PCASES = [
+    # complex Langevin fields: the 64^3 workload's grid, 256-point pencils, ragged sizes
+    ((64, 64, 64), (8.0, 8.0, 8.0), 12, 0.3, CL, FP32, 1),
+    ((256, 16, 256), (16.0, 1.0, 16.0), 4, 0.5, CL, FP32, 1),
+    ((12, 48, 24), (3.0, 6.0, 4.0), 9, 0.4, CL, FP64, 0),
+    ((16, 12, 96), (4.0, 3.0, 9.0), 7, 0.35, CL, FP64, 1),
+    # real fields: batch-class sizes and ragged ones, both precisions, one- and two-step chains
+    ((32, 32, 32), (4.0, 4.0, 4.0), 10, 0.3, SCFT, FP32, 1),
+    ((48, 48, 48), (6.0, 6.0, 6.0), 2, 0.5, SCFT, FP32, 0),
+    ((24, 6, 48), (4.0, 1.5, 6.0), 1, 0.5, SCFT, FP64, 1),
+    ((128, 128, 128), (8.0, 8.0, 8.0), 6, 0.35, SCFT, FP64, 1),
+    ((8, 12, 16), (2.0, 3.0, 4.0), 13, 0.6, SCFT, FP64, 0),
+]
+PTOL = {FP64: dict(Q=1e-12, phi=1e-10, q=1e-12), FP32: dict(Q=2e-5, phi=2e-5, q=2e-5)}
+
+
+def _pfields(n, kind, seed):
+    rng = np.random.default_rng(seed)
+    wp = rng.normal(0, 0.3, n)
+    wm = rng.normal(0, 1.0, n)
+    if kind == CL:
+        wp = wp + 1j * rng.normal(0, 0.3, n)
+        wm = wm + 1j * rng.normal(0, 0.3, n)
+    return wp, wm
+
+
+@pytest.mark.parametrize("case", range(len(PCASES)))
+def test_separable_pencil_march_matches_oracle(case):
+    n, L, Ns, fA, kind, prec, streams = PCASES[case]
+    wp, wm = _pfields(n, kind, 300 + case)
+    okind = o.SCFT_REAL if kind == SCFT else o.CL_COMPLEX
+    ref = o.solve(wp, wm, n, L, Ns, fA, okind)
+    t = PTOL[prec]
+    with pft.System(n, L, Ns, fA, 17.0, 2.0, kind, prec) as s:
+        pft.pft_set_plan(s.h, 3, streams)
+        s.set_fields(wp, wm)
+        s.solve()
+        s.solve()
+        assert pft.pft_get_plan(s.h) == (3, streams)
+        obs = s.observables()
+        phiA, phiB = s.densities()
+        eq = 0.0
+        for which, k in ((0, 1), (0, Ns), (2, 1), (2, Ns)):
+            g = s.propagator(which, k)
+            hist = ref.q if which == 0 else ref.qd
+            eq = max(eq, np.max(np.abs(g - hist[k])) / np.max(np.abs(hist[k])))
+    Q = obs["Q"] if kind == CL else obs["Q"].real
+    eQ = abs(Q - ref.Q) / abs(ref.Q)
+    ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+    print(f"\nseparable pencils {n} Ns={Ns} kind={kind} prec={prec}: Q rel {eQ:.2e} phi abs {ephi:.2e} "
+          f"slices {eq:.2e}")
+    assert eQ <= t["Q"] and ephi <= t["phi"] and eq <= t["q"]
+
+
+def test_default_plans():
+    for n, kind, prec, plan in (((64, 64, 64), CL, FP32, 1), ((32, 32, 32), SCFT, FP32, 0),
+                                ((64, 64, 64), SCFT, FP64, 3), ((256, 16, 256), CL, FP64, 3),
+                                ((256, 16, 256), CL, FP32, 0), ((128, 128, 128), SCFT, FP32, 2)):
+        with pft.System(n, (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, kind, prec) as s:
+            assert pft.pft_get_plan(s.h) == (plan, 1), (n, kind, prec)
+    with pft.System((64, 64, 64), (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, SCFT, FP32) as s:
+        assert pft.pft_get_plan(s.h) == (2, 1)
+        with pytest.raises(pft.PftError) as e:
+            pft.pft_set_plan(s.h, 4, 1)
         assert e.value.status == pft.PFT_ERR_ARG
