@@ -81,8 +81,10 @@ template <typename T> __device__ __forceinline__ void store_w(cpx<T>* p, long lo
 template <typename T> __device__ __forceinline__ T boltz(double w, double ds) {
   return (T)exp(-w * ds * 0.5);
 }
+// FP32 factors: the FP64 argument narrowed by the integer-pipe round-to-nearest (the same
+// float as a conversion, without GB300's 1/64-rate F2F), then expf
 template <> __device__ __forceinline__ float boltz<float>(double w, double ds) {
-  return expf((float)(-w * ds * 0.5));
+  return expf(narrow_rn(-w * ds * 0.5));
 }
 template <typename T> __device__ __forceinline__ cpx<T> boltz_c(double2 w, double ds) {
   const double2 z = cexp_d(make_double2(-w.x * ds * 0.5, -w.y * ds * 0.5));
@@ -248,10 +250,12 @@ __global__ void __launch_bounds__(PW_THREADS) k_qsum_real(const T* __restrict__ 
                                                           double* __restrict__ partials) {
   double acc[2] = {0.0, 0.0};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
-    const double v = (double)q[i];
+    const double v = widen(q[i]);
     acc[0] += v;
-    accA[i] = cA * v;
-    accB[i] = cB * v;
+    if (accA) {  // the qd_0 = 1 term of the quadrature (none when a later kernel forms it)
+      accA[i] = cA * v;
+      accB[i] = cB * v;
+    }
   }
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
@@ -347,6 +351,92 @@ __device__ __forceinline__ void quad_block(const T* __restrict__ hist, const T* 
   }
   *s0 = a0;
   *s1 = a1;
+}
+
+// FP32 real fields, four points a thread (16-byte loads of both histories): the
+// trapezoid sums of one block over n in [n0, n1], compensated FP32 over chunks of
+// kQuadChunk slices flushed into FP64 (as quad_block).
+__device__ __forceinline__ void quad_block4(const float* __restrict__ hist, const float* __restrict__ qdh,
+                                            const float* __restrict__ qd0, long long M, int Ns, int n0, int n1,
+                                            long long i4, double (&a)[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; k++) a[k] = 0.0;
+  if (n1 <= n0) return;
+#pragma unroll 1
+  for (int c0 = n0; c0 <= n1; c0 += kQuadChunk) {
+    const int c1 = min(c0 + kQuadChunk - 1, n1);
+    F2Sum f[4];
+#pragma unroll 4
+    for (int n = c0; n <= c1; n++) {
+      const int m = Ns - n;
+      const float4 q = reinterpret_cast<const float4*>(hist + (long long)n * M)[i4];
+      const float4 d = reinterpret_cast<const float4*>(m == 0 ? qd0 : qdh + (long long)m * M)[i4];
+      const float w = (n == n0 || n == n1) ? 0.5f : 1.0f;
+      f[0].add(__fmul_rn(__fmul_rn(q.x, d.x), w));
+      f[1].add(__fmul_rn(__fmul_rn(q.y, d.y), w));
+      f[2].add(__fmul_rn(__fmul_rn(q.z, d.z), w));
+      f[3].add(__fmul_rn(__fmul_rn(q.w, d.w), w));
+    }
+#pragma unroll
+    for (int k = 0; k < 4; k++) f[k].flush(&a[k]);
+  }
+}
+
+static __global__ void __launch_bounds__(PW_THREADS) k_quadrature_real4(const float* __restrict__ hist,
+                                                                 const float* __restrict__ qdh,
+                                                                 const float* __restrict__ qd0, long long M, int Ns,
+                                                                 int NsA, double* __restrict__ accA,
+                                                                 double* __restrict__ accB) {
+  const long long M4 = M / 4;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M4; i += (long long)gridDim.x * blockDim.x) {
+    double a[4];
+    quad_block4(hist, qdh, qd0, M, Ns, 0, NsA, i, a);
+    reinterpret_cast<double2*>(accA)[2 * i] = make_double2(a[0], a[1]);
+    reinterpret_cast<double2*>(accA)[2 * i + 1] = make_double2(a[2], a[3]);
+    quad_block4(hist, qdh, qd0, M, Ns, NsA, Ns, i, a);
+    reinterpret_cast<double2*>(accB)[2 * i] = make_double2(a[0], a[1]);
+    reinterpret_cast<double2*>(accB)[2 * i + 1] = make_double2(a[2], a[3]);
+  }
+}
+
+// The quadrature above fused with the densities and force sums of the solve's tail:
+// phi = ds acc / Q (Q from s[S_Q]), and per block the sums of phiA, phiB, (phiA + phiB -
+// 1)^2 and (2 W-/chiN + phiB - phiA)^2 into partials (6 a block, as k_finalize_real).
+static __global__ void __launch_bounds__(PW_THREADS) k_quadrature_final_real4(const float* __restrict__ hist,
+                                                                       const float* __restrict__ qdh,
+                                                                       const float* __restrict__ qd0, long long M,
+                                                                       int Ns, int NsA, double* __restrict__ accA,
+                                                                       double* __restrict__ accB,
+                                                                       const double* __restrict__ wm,
+                                                                       const double* __restrict__ s, double ds,
+                                                                       double chiN, double* __restrict__ partials) {
+  const double f = ds / s[S_Q];
+  const double ichiN = 1.0 / chiN;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const long long M4 = M / 4;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M4; i += (long long)gridDim.x * blockDim.x) {
+    double a[4], b[4];
+    quad_block4(hist, qdh, qd0, M, Ns, 0, NsA, i, a);
+    quad_block4(hist, qdh, qd0, M, Ns, NsA, Ns, i, b);
+    const double2 m01 = reinterpret_cast<const double2*>(wm)[2 * i];
+    const double2 m23 = reinterpret_cast<const double2*>(wm)[2 * i + 1];
+    const double m[4] = {m01.x, m01.y, m23.x, m23.y};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      a[k] *= f;
+      b[k] *= f;
+      const double fp = a[k] + b[k] - 1.0, fm = 2.0 * m[k] * ichiN + b[k] - a[k];
+      acc[0] += a[k];
+      acc[2] += b[k];
+      acc[4] += fp * fp;
+      acc[5] += fm * fm;
+    }
+    reinterpret_cast<double2*>(accA)[2 * i] = make_double2(a[0], a[1]);
+    reinterpret_cast<double2*>(accA)[2 * i + 1] = make_double2(a[2], a[3]);
+    reinterpret_cast<double2*>(accB)[2 * i] = make_double2(b[0], b[1]);
+    reinterpret_cast<double2*>(accB)[2 * i + 1] = make_double2(b[2], b[3]);
+  }
+  block_reduce_store<6>(acc, partials + 6 * blockIdx.x);
 }
 
 template <typename T>

@@ -325,12 +325,18 @@ class EngineT : public Engine {
     return solve_tail(c);
   }
 
-  cudaError_t solve_mid(CtxData& c) override {
+  cudaError_t solve_mid(CtxData& c) override { return solve_mid_q(c, true); }
+
+  // Q (Eq. 4) from q_Ns; with_acc: also the qd_0 = 1 terms of the quadrature into the
+  // accumulators (the march-fused quadrature of the sequential path needs them; the
+  // quadrature over both histories forms every term itself).
+  cudaError_t solve_mid_q(CtxData& c, bool with_acc) {
     double cA, cB;
     trapezoid_weight(c.Ns, c.Ns, c.NsA, &cA, &cB);
     mark(c, KK_REDUCE);
     if (c.kind == PFT_SCFT_REAL) {
-      k_qsum_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const T*)q_at(c, c.Ns), (double*)c.accA,
+      k_qsum_real<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const T*)q_at(c, c.Ns),
+                                                          with_acc ? (double*)c.accA : nullptr,
                                                           (double*)c.accB, cA, cB, c.M, c.partials);
     } else {
       k_qsum_cplx<T><<<c.npart, PW_THREADS, 0, c.stream>>>((const Z*)q_at(c, c.Ns), (double2*)c.accA,
@@ -772,8 +778,14 @@ class EngineT : public Engine {
     const void* qdh = c.edw ? c.hist : c.qdh;
     const void* qd0 = c.edw ? c.hist : c.qd0;
     if (c.kind == PFT_SCFT_REAL) {
-      k_quadrature_real<T><<<blocks, PW_THREADS, 0, c.stream>>>((const T*)c.hist, (const T*)qdh, (const T*)qd0, c.M,
-                                                               c.Ns, c.NsA, (double*)c.accA, (double*)c.accB);
+      if (std::is_same<T, float>::value && c.M % 4 == 0) {  // 16-byte loads, four points a thread
+        k_quadrature_real4<<<blocks, PW_THREADS, 0, c.stream>>>((const float*)c.hist, (const float*)qdh,
+                                                                (const float*)qd0, c.M, c.Ns, c.NsA,
+                                                                (double*)c.accA, (double*)c.accB);
+      } else {
+        k_quadrature_real<T><<<blocks, PW_THREADS, 0, c.stream>>>((const T*)c.hist, (const T*)qdh, (const T*)qd0,
+                                                                 c.M, c.Ns, c.NsA, (double*)c.accA, (double*)c.accB);
+      }
     } else {
       k_quadrature_cplx<T><<<blocks, PW_THREADS, 0, c.stream>>>((const Z*)c.hist, (const Z*)qdh, (const Z*)qd0, c.M,
                                                                c.Ns, c.NsA, (double2*)c.accA, (double2*)c.accB);
@@ -938,7 +950,18 @@ class EngineT : public Engine {
   // Q, the quadrature over both histories, densities and H
   cudaError_t finish_concurrent(CtxData& c) {
     cudaError_t e;
-    if ((e = solve_mid(c)) != cudaSuccess) return e;
+    const bool real = (c.kind == PFT_SCFT_REAL);
+    if ((e = solve_mid_q(c, !real)) != cudaSuccess) return e;
+    if (std::is_same<T, float>::value && real && !c.edw && c.M % 4 == 0) {
+      // the quadrature with the densities and force sums of the tail in one pass
+      mark(c, KK_QUADRATURE);
+      k_quadrature_final_real4<<<c.npart, PW_THREADS, 0, c.stream>>>(
+          (const float*)c.hist, (const float*)c.qdh, (const float*)c.qd0, c.M, c.Ns, c.NsA, (double*)c.accA,
+          (double*)c.accB, (const double*)c.wm, c.scal, c.ds, c.chiN, c.partials);
+      mark(c, KK_REDUCE);
+      k_reduce_final<6><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_PHIA);
+      return cudaGetLastError();
+    }
     if ((e = quadrature(c)) != cudaSuccess) return e;
     return solve_tail(c);
   }
