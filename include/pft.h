@@ -305,27 +305,36 @@ pft_status pft_batch_get_fields(pft_batch* b, int i, void* wp, void* wm, pft_mem
 pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_batch_mode mode);
 
 /* Per-class plan autotuner of a batch (uses the instances' current fields): for every class
- * of equal field kind and grid, time the class's two marches and densities under plan 0
- * (one march after the other, the quadrature fused into the conjugate march) and plan 1
- * (both marches in the same launches, fused z passes of consecutive steps, the quadrature
- * after the marches over both histories; one extra q-dagger history per instance) and keep
- * the faster; the next graphed run captures the chosen plans.  Plan 1 is the default.
+ * of equal field kind and grid, time the class's two marches and densities under each plan
+ * that applies to it and keep the fastest; the next graphed run captures the chosen plans.
+ * Plans: 0 -- one march after the other, the quadrature fused into the conjugate march;
+ * 1 -- both marches in the same launches (the 3D transform pair of each step: plane kernel
+ * and x pass for FP32 classes with ny = nz = 64 or 128, else the pencil passes with the z
+ * passes of consecutive steps fused), the quadrature after the marches over both
+ * histories (one extra q-dagger history per instance); 2 -- the separable march of
+ * pft_get_plan's plan 2 (FP32 real classes with nx = ny = nz in {64, 128}); 3 -- the
+ * separable march on pencils (plan 3 of pft_get_plan).  Plans 2 and 3 run both marches in
+ * the same launches and the quadrature after them, as plan 1.  The default is plan 2 where
+ * it applies, else plan 3.
  * Errors: PFT_ERR_STATE if an instance has no fields; PFT_ERR_OOM. */
 pft_status pft_batch_autotune(pft_batch* batch);
 
-/* Set the plan (0 or 1, as for pft_batch_autotune) of class `cls`, or of every class for
- * cls = -1.  Errors: PFT_ERR_ARG for a bad index or plan. */
+/* Set the plan (0..3, as for pft_batch_autotune) of class `cls`, or of every class it
+ * applies to for cls = -1.  Errors: PFT_ERR_ARG for a bad index or plan,
+ * PFT_ERR_UNSUPPORTED for a plan that does not apply to class `cls`. */
 pft_status pft_batch_set_plan(pft_batch* batch, int cls, int plan);
 
 /* Class `cls` (0 .. classes-1 of pft_batch_info): grid n[3], field kind, member count, plan
- * in use and the autotuner's timings of plans 0 and 1 in ms (-1 if not tuned).  Any output
- * pointer may be NULL.  Errors: PFT_ERR_ARG for a bad index. */
+ * in use and the autotuner's timings of plans 0..3 in ms (-1 if not tuned or not
+ * applicable).  Any output pointer may be NULL.  Errors: PFT_ERR_ARG for a bad index. */
 pft_status pft_batch_class_info(const pft_batch* batch, int cls, int n[3], int* kind, int* members, int* plan,
-                                float tuned_ms[2]);
+                                float tuned_ms[4]);
 
 /* Observables and densities of member i's last solve (synchronises). */
 pft_status pft_batch_get_observables(pft_batch* b, int i, pft_obs* obs);
 pft_status pft_batch_get_densities(pft_batch* b, int i, void* phiA, void* phiB, pft_mem where);
+/* Wait for the batch stream.  Errors: PFT_ERR_TIMEOUT if a bounded wait in a kernel of
+ * the updates since the last call ran out (their results are invalid), PFT_ERR_CUDA. */
 pft_status pft_batch_synchronize(pft_batch* b);
 
 /* Grid-point contour steps per field update (sum of 2 M Ns), number of classes, and

@@ -29,10 +29,14 @@ struct BatchClass {
   pft::BatchStep* d_bwd = nullptr;
   // plan 0: one march after the other, the quadrature fused into the conjugate march;
   // plan 1: both marches in the same launches (entries 2k / 2k+1 of a step), the z passes
-  // of consecutive steps fused, the quadrature after the marches over both histories
-  int plan = 1;
+  // of consecutive steps fused, the quadrature after the marches over both histories;
+  // plan 2: the separable march on the plane and x kernels (FP32 real, ny = nz = nx in
+  // {64, 128}); plan 3: the separable march on pencils -- both marches per launch, the
+  // quadrature after them, as plan 1
+  int plan = 3;
   pft::BatchStep* d_conc = nullptr;  // [maxNs][2K]
-  float tuned_ms[2] = {-1.f, -1.f};   // autotuner timings of the two plans
+  pft::BatchStep* d_sep = nullptr;   // the same entries with the per-axis factors of plans 2, 3
+  float tuned_ms[4] = {-1.f, -1.f, -1.f, -1.f};  // autotuner timings of the plans
   // the class's branch of the captured update: its marches, reductions and field steps
   // run on their own stream, forked from and joined back into the batch stream, so that
   // the classes overlap on the GPU
@@ -64,6 +68,7 @@ struct pft_batch {
   bool own_stream = false;
   std::vector<BatchClass> classes;
   unsigned long long* d_steps = nullptr;
+  int* d_err = nullptr;  // error word of the bounded waits in the separable plane kernel
   cudaEvent_t fork = nullptr;
   cudaGraphExec_t graph = nullptr;
   double g_lam = -1.0, g_dt = -1.0;
@@ -80,11 +85,13 @@ void batch_free(pft_batch* b) {
     if (c.d_fwd) cudaFree(c.d_fwd);
     if (c.d_bwd) cudaFree(c.d_bwd);
     if (c.d_conc) cudaFree(c.d_conc);
+    if (c.d_sep) cudaFree(c.d_sep);
     if (c.stream) cudaStreamDestroy(c.stream);
     if (c.done) cudaEventDestroy(c.done);
   }
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->d_steps) cudaFree(b->d_steps);
+  if (b->d_err) cudaFree(b->d_err);
   for (pft_ctx* c : b->inst)
     if (c) pft_destroy(c);
   if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -172,7 +179,20 @@ pft_status prepare_pairs(pft_batch* b, BatchClass& c) {
   const size_t bytes = h.size() * sizeof(pft::BatchStep);
   cudaError_t e = cudaMalloc(&c.d_conc, bytes);
   if (e == cudaSuccess) e = cudaMemcpy(c.d_conc, h.data(), bytes, cudaMemcpyHostToDevice);
-  return e == cudaSuccess ? PFT_OK : bcuda(e, "batch pair-step table");
+  if (e != cudaSuccess) return bcuda(e, "batch pair-step table");
+  // the separable plans: the same entries with each member's full-axis factors
+  for (int s = 1; s <= c.maxNs; s++)
+    for (int k = 0; k < c.active[s - 1]; k++) {
+      const pft::CtxData& d = b->inst[c.members[k]]->d;
+      const char* t = (const char*)d.tables;
+      for (int m = 0; m < 2; m++) {
+        pft::BatchStep& x = h[((size_t)(s - 1) * K + k) * 2 + m];
+        for (int a = 0; a < 3; a++) x.d[a] = t + d.sd_off[a];
+      }
+    }
+  e = cudaMalloc(&c.d_sep, bytes);
+  if (e == cudaSuccess) e = cudaMemcpy(c.d_sep, h.data(), bytes, cudaMemcpyHostToDevice);
+  return e == cudaSuccess ? PFT_OK : bcuda(e, "batch separable step table");
 }
 
 // Both marches and the densities of one class under its plan, on `sm` (the members'
@@ -180,6 +200,22 @@ pft_status prepare_pairs(pft_batch* b, BatchClass& c) {
 pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches, cudaStream_t sm) {
   const int K = (int)c.members.size();
   pft::Engine* eng = b->inst[c.members[0]]->eng;
+  if (c.plan == 2 || c.plan == 3) {
+    for (int j = 0; j <= c.maxNs; j++) {
+      const pft::BatchStep* st = c.d_sep + (size_t)(j == 0 ? 0 : j - 1) * 2 * K;
+      const int nact = 2 * c.active[j == 0 ? 0 : j - 1];
+      cudaError_t e = eng->batch_sep_launch(c.g, st, j, nact, c.plan, b->d_err, sm);
+      if (e != cudaSuccess) return bcuda(e, "batched separable step");
+      *launches += (c.plan == 3 && j > 0) ? 2 : 1;
+    }
+    for (int i : c.members) {
+      pft_ctx* x = b->inst[i];
+      cudaError_t e = x->eng->finish_both(x->d);
+      if (e != cudaSuccess) return bcuda(e, "batched quadrature");
+      *launches += 4;
+    }
+    return PFT_OK;
+  }
   if (c.plan == 1) {
     for (int s = 1; s <= c.maxNs; s++) {
       const pft::BatchStep* st = c.d_conc + (size_t)(s - 1) * 2 * K;
@@ -302,6 +338,12 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
     batch_free(b);
     return bcuda(e, "batch fork event");
   }
+  e = cudaMalloc(&b->d_err, 4 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 4 * sizeof(int), b->stream);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return bcuda(e, "batch error word");
+  }
   e = cudaMalloc(&b->d_steps, sizeof(unsigned long long) * count);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->d_steps, 0, sizeof(unsigned long long) * count, b->stream);
   if (e != cudaSuccess) {
@@ -321,6 +363,10 @@ pft_status pft_batch_create(pft_batch** out, int count, const pft_instance_desc*
       c.g.kind = d.kind;
       c.g.nzh = d.nzh;
       c.kind = d.kind;
+      // the default plan (measured on GB300 with the 256-instance batch): the separable
+      // march on the plane kernel where it applies, else on pencils
+      pft::Engine* eng = b->inst[i]->eng;
+      c.plan = eng->batch_plan_ok(c.g, 2) ? 2 : (eng->batch_plan_ok(c.g, 3) ? 3 : 1);
       index[key] = (int)b->classes.size();
       b->classes.push_back(c);
       it = index.find(key);
@@ -395,7 +441,7 @@ pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_b
   for (pft_ctx* x : b->inst)
     if (!x->d.fields_set) return bfail(PFT_ERR_STATE, "every batch instance needs pft_batch_set_fields first");
   for (auto& c : b->classes) {  // allocations and table uploads happen outside any capture
-    if (c.plan != 1) continue;
+    if (c.plan == 0) continue;
     pft_status s = prepare_pairs(b, c);
     if (s != PFT_OK) return s;
   }
@@ -463,9 +509,11 @@ pft_status pft_batch_autotune(pft_batch* b) {
   for (auto& c : b->classes) {
     float best = -1.f;
     int bplan = c.plan;
-    for (int plan = 0; plan < 2 && st == PFT_OK; plan++) {
+    pft::Engine* eng = b->inst[c.members[0]]->eng;
+    for (int plan = 0; plan < 4 && st == PFT_OK; plan++) {
+      if (!eng->batch_plan_ok(c.g, plan)) continue;
       c.plan = plan;
-      if (plan == 1 && (st = prepare_pairs(b, c)) != PFT_OK) break;
+      if (plan >= 1 && (st = prepare_pairs(b, c)) != PFT_OK) break;
       long long n = 0;
       if ((st = record_class_solve(b, c, &n, b->stream)) != PFT_OK) break;  // warm-up
       cudaEventRecord(e0, b->stream);
@@ -498,9 +546,14 @@ pft_status pft_batch_autotune(pft_batch* b) {
 
 pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
   if (!b || cls < -1 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
-  if (plan != 0 && plan != 1) return bfail(PFT_ERR_ARG, "plan must be 0 or 1");
-  for (int k = 0; k < (int)b->classes.size(); k++)
-    if (cls < 0 || k == cls) b->classes[k].plan = plan;
+  if (plan < 0 || plan > 3) return bfail(PFT_ERR_ARG, "plan must be 0, 1, 2 or 3");
+  if (cls >= 0 && !b->inst[b->classes[cls].members[0]]->eng->batch_plan_ok(b->classes[cls].g, plan))
+    return bfail(PFT_ERR_UNSUPPORTED, "plan " + std::to_string(plan) + " does not apply to class " + std::to_string(cls));
+  for (int k = 0; k < (int)b->classes.size(); k++) {
+    BatchClass& c = b->classes[k];
+    // all classes (cls = -1): the classes the plan applies to
+    if ((cls < 0 || k == cls) && b->inst[c.members[0]]->eng->batch_plan_ok(c.g, plan)) c.plan = plan;
+  }
   if (b->graph) {
     cudaGraphExecDestroy(b->graph);
     b->graph = nullptr;
@@ -509,7 +562,7 @@ pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
 }
 
 pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind, int* members, int* plan,
-                                float tuned_ms[2]) {
+                                float tuned_ms[4]) {
   if (!b || cls < 0 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
   const BatchClass& c = b->classes[cls];
   if (n)
@@ -517,17 +570,23 @@ pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind
   if (kind) *kind = (int)c.kind;
   if (members) *members = (int)c.members.size();
   if (plan) *plan = c.plan;
-  if (tuned_ms) {
-    tuned_ms[0] = c.tuned_ms[0];
-    tuned_ms[1] = c.tuned_ms[1];
-  }
+  if (tuned_ms)
+    for (int k = 0; k < 4; k++) tuned_ms[k] = c.tuned_ms[k];
   return PFT_OK;
 }
 
 pft_status pft_batch_synchronize(pft_batch* b) {
   if (!b) return bfail(PFT_ERR_ARG, "NULL batch");
-  cudaError_t e = cudaStreamSynchronize(b->stream);
-  return e == cudaSuccess ? PFT_OK : bcuda(e, "batch synchronize");
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bcuda(e, "batch synchronize");
+  if (err != 0) {
+    cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
+    cudaStreamSynchronize(b->stream);
+    return bfail(PFT_ERR_TIMEOUT, "a bounded wait in a separable plane kernel ran out (the last updates are invalid)");
+  }
+  return PFT_OK;
 }
 
 pft_status pft_batch_info(const pft_batch* b, double* units_per_update, int* nclasses, long long* launches) {

@@ -198,6 +198,13 @@ class Engine {
   virtual cudaError_t batch_pair_step(const BatchGeom& g, const BatchStep* d_steps, int nactive, bool first,
                                       cudaStream_t stream) = 0;
   // kernels one batch_pair_step launches for this geometry
+  // plans 0..3 of a batch class: may this class geometry run plan `plan`?
+  virtual bool batch_plan_ok(const BatchGeom& g, int plan) const = 0;
+  // launch j of a separable march (plan 2 or 3) of a batch class over nact entries
+  virtual cudaError_t batch_sep_launch(const BatchGeom& g, const BatchStep* ss, int j, int nact, int plan, int* err,
+                                       cudaStream_t sm) = 0;
+  // Q, the quadrature over both stored histories, densities and sums (after both marches)
+  virtual cudaError_t finish_both(CtxData& c) = 0;
   virtual int batch_pair_launches(const BatchGeom& g, bool first) const = 0;
   // contour quadrature of Eq. 8 over the stored q and qd histories (after solve_mid)
   virtual cudaError_t quadrature(CtxData& c) = 0;

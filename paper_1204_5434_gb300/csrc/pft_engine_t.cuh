@@ -516,15 +516,26 @@ class EngineT : public Engine {
     return cudaSuccess;
   }
 
-  // On the plane kernel (plane 2): FP32 real fields with ny = nz = N in {64, 128} and nx
-  // in {64, 128}.
+  // On the plane kernel (plane 2): FP32, nx in {64, 128}; real fields with ny = nz in
+  // {64, 128}, complex fields with ny = nz = 64.
   static bool sep_supported(const CtxData& c) {
     if constexpr (!std::is_same<T, float>::value) {
       return false;
     } else {
-      if (c.kind != PFT_SCFT_REAL || c.n[1] != c.n[2]) return false;
-      return (c.n[1] == 64 || c.n[1] == 128) && (c.n[0] == 64 || c.n[0] == 128);
+      if (c.n[1] != c.n[2] || !(c.n[0] == 64 || c.n[0] == 128)) return false;
+      if (c.kind != PFT_SCFT_REAL) return c.n[1] == 64;
+      return c.n[1] == 64 || c.n[1] == 128;
     }
+  }
+
+  template <int N, int MODE>
+  static cudaError_t launch_sep_plane_c(const BatchStep* st, int nx, int members, int* err, cudaStream_t sm) {
+    using R = SepCfgC<N>;
+    auto kern = kb_sep_plane_c<N, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3((unsigned)nx, (unsigned)members), R::THREADS, R::SMEM, sm>>>(st, err);
+    return cudaGetLastError();
   }
 
   template <int N, int MODE>
@@ -537,17 +548,18 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
-  template <int NX, int NYZ, int MODE>
+  template <int NX, int NYZ, int MODE, int KIND = 0>
   static cudaError_t launch_sep_x(const BatchStep* st, int members, cudaStream_t sm) {
     constexpr int C = 16;
-    constexpr long long P = (long long)NYZ * NYZ / 2;
-    auto kern = kb_sep_x<NX, NYZ, MODE, C>;
+    constexpr long long P = KIND ? (long long)NYZ * NYZ : (long long)NYZ * NYZ / 2;
+    auto kern = kb_sep_x<NX, NYZ, MODE, C, KIND>;
     const unsigned grid = (unsigned)(P / C);
     kern<<<dim3(grid, (unsigned)members), C * Plan<NX>::TPC, sep_x_smem<NX, C>(), sm>>>(st);
     return cudaGetLastError();
   }
   template <int NX, int MODE>
-  static cudaError_t launch_sep_x_n(const BatchStep* st, int nyz, int members, cudaStream_t sm) {
+  static cudaError_t launch_sep_x_n(const BatchStep* st, int nyz, int kind, int members, cudaStream_t sm) {
+    if (kind != PFT_SCFT_REAL) return nyz == 64 ? launch_sep_x<NX, 64, MODE, 1>(st, members, sm) : cudaErrorNotSupported;
     if (nyz == 128) return launch_sep_x<NX, 128, MODE>(st, members, sm);
     if (nyz == 64) return launch_sep_x<NX, 64, MODE>(st, members, sm);
     return cudaErrorNotSupported;
@@ -555,17 +567,27 @@ class EngineT : public Engine {
 
   // launch j of a separable march (j = 0: the first plane launch; j >= 1 stores q_j)
   cudaError_t sep_launch(CtxData& c, const BatchStep* ss, int j, int members, cudaStream_t sm) {
+    return sep_launch_g(c.n, c.kind, (j == 0) ? 0 : (j == c.Ns ? 2 : 1), j, members, c.kerr, ss, sm);
+  }
+  // mode 0: first launch; 1: a step (entries without Bnext end there); 2: the last step
+  static cudaError_t sep_launch_g(const int n[3], int kind, int mode, int j, int members, int* err,
+                                  const BatchStep* ss, cudaStream_t sm) {
     if constexpr (!std::is_same<T, float>::value) {
       return cudaErrorNotSupported;
     } else {
-      const int nx = c.n[0], N = c.n[1];
-      const int mode = (j == 0) ? 0 : (j == c.Ns ? 2 : 1);
+      const int nx = n[0], N = n[1];
       if (j >= 1 && (j & 1)) {  // x kernel
-        if (nx == 128) return mode == 2 ? launch_sep_x_n<128, 2>(ss, N, members, sm) : launch_sep_x_n<128, 1>(ss, N, members, sm);
-        if (nx == 64) return mode == 2 ? launch_sep_x_n<64, 2>(ss, N, members, sm) : launch_sep_x_n<64, 1>(ss, N, members, sm);
+        if (nx == 128)
+          return mode == 2 ? launch_sep_x_n<128, 2>(ss, N, kind, members, sm) : launch_sep_x_n<128, 1>(ss, N, kind, members, sm);
+        if (nx == 64)
+          return mode == 2 ? launch_sep_x_n<64, 2>(ss, N, kind, members, sm) : launch_sep_x_n<64, 1>(ss, N, kind, members, sm);
         return cudaErrorNotSupported;
       }
-      int* err = c.kerr;
+      if (kind != PFT_SCFT_REAL) {
+        if (N != 64) return cudaErrorNotSupported;
+        if (mode == 0) return launch_sep_plane_c<64, 0>(ss, nx, members, err, sm);
+        return mode == 2 ? launch_sep_plane_c<64, 2>(ss, nx, members, err, sm) : launch_sep_plane_c<64, 1>(ss, nx, members, err, sm);
+      }
       if (N == 128) {
         if (mode == 0) return launch_sep_plane<128, 0>(ss, nx, members, err, sm);
         return mode == 2 ? launch_sep_plane<128, 2>(ss, nx, members, err, sm)
@@ -759,6 +781,30 @@ class EngineT : public Engine {
     if ((e = batch_mid(g, st, nact, stream)) != cudaSuccess) return e;
     return batch_zz(g, st, nact, stream);
   }
+
+  bool batch_plan_ok(const BatchGeom& g, int plan) const override {
+    if (plan == 0 || plan == 1) return true;
+    CtxData cg;
+    for (int a = 0; a < 3; a++) cg.n[a] = g.n[a];
+    cg.kind = g.kind;
+    if (plan == 2) return sep_supported(cg);
+    if (plan == 3) return sepp_supported(cg);
+    return false;
+  }
+
+  // Launch j of a separable march of a batch class (plan 2: plane and x kernels; plan 3:
+  // pencils) over nact entries; an entry without Bnext ends its member's march there.
+  cudaError_t batch_sep_launch(const BatchGeom& g, const BatchStep* ss, int j, int nact, int plan, int* err,
+                               cudaStream_t sm) override {
+    if (nact <= 0) return cudaSuccess;
+    if (plan == 2) return sep_launch_g(g.n, g.kind, j == 0 ? 0 : 1, j, nact, err, ss, sm);
+    SeppGeom sg;
+    for (int a = 0; a < 3; a++) sg.n[a] = g.n[a];
+    sg.kind = (g.kind == PFT_SCFT_REAL) ? 0 : 1;
+    return std::is_same<T, float>::value ? sepp_launch_f32(sg, ss, j, nact, sm) : sepp_launch_f64(sg, ss, j, nact, sm);
+  }
+
+  cudaError_t finish_both(CtxData& c) override { return finish_concurrent(c); }
 
   int batch_pair_launches(const BatchGeom& g, bool first) const override {
     return plane_geom(g) ? (first ? 3 : 2) : (first ? 5 : 4);

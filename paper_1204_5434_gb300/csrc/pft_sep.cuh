@@ -19,6 +19,7 @@
 // stops after its store.  FP32 propagators, ny = nz = N in {64, 128}.
 #pragma once
 #include "pft_plane.cuh"
+#include "pft_sepp.cuh"
 #include "pft_tma.cuh"
 
 namespace pft {
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
   }
   if (!mbar_wait(bar, 0, err, 1)) return;  // B_s has arrived
 
-  // ---- x B_s, store q_s, x B_{s+1}
+  // ---- x B_s, store q_s, x B_{s+1} (an entry without Bnext ends its march here)
+  const bool more = (MODE == 1) && (s.Bnext != nullptr);
   {
     const bool same = (s.Bnext == s.B);
     const float* Bn = reinterpret_cast<const float*>(s.Bnext) + pbase;
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
       if (MODE != 0) {
         q[(long long)L * N + k] = v[i].x;
         q[(long long)(L + H) * N + k] = v[i].y;
-        if (MODE == 1) {
+        if (more) {
           if (same) {
             v[i].x *= ba;
             v[i].y *= bb;
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
       }
     }
   }
-  if (MODE == 2) return;
+  if (MODE == 2 || (MODE == 1 && !more)) return;
 
   // ---- Kz of the next step
   __syncwarp();
@@ -215,9 +217,12 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
 // P = NYZ^2 / 2 column pairs per x-plane (ny = nz = NYZ); st.d[0] = dx (full length,
 // 1/nx folded in); twiddles st.tw[0].  B_s of the tile is copied to shared memory by
 // 16-byte cp.async chunks at the start, so its latency hides behind the first Kx.
-template <int NX, int NYZ, int MODE, int C = 16>
+// KIND 1: complex fields -- each x-line is one complex line (P = NYZ^2 of them) and B
+// multiplies as a complex factor.
+template <int NX, int NYZ, int MODE, int C = 16, int KIND = 0>
 __global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep* __restrict__ st) {
-  constexpr long long P = (long long)NYZ * NYZ / 2;  // column pairs per x-plane (ny = nz = NYZ)
+  // lines per x-plane: column pairs (real) or columns (complex) of the ny = nz = NYZ plane
+  constexpr long long P = KIND ? (long long)NYZ * NYZ : (long long)NYZ * NYZ / 2;
   static_assert(P % C == 0, "whole tiles");
   using PL = Plan<NX>;
   constexpr int E = PL::E, TPC = PL::TPC;
@@ -260,6 +265,7 @@ __global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep
   fft<float, true, NX, PL>(v, t, tws, x);
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   __syncthreads();  // every thread's chunks of B_s have landed
+  const bool more = (MODE == 1) && (s.Bnext != nullptr);  // no Bnext: the entry's last step
   {
     const bool same = (s.Bnext == s.B);
     const float2* Bn2 = reinterpret_cast<const float2*>(s.Bnext);
@@ -268,17 +274,12 @@ __global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep
     for (int i = 0; i < E; i++) {
       const long long o = (long long)(t + TPC * i) * P + colc;
       const float2 b = Bt[(t + TPC * i) * C + c];
-      v[i].x *= b.x;
-      v[i].y *= b.y;
+      v[i] = sepp_mul<KIND>(v[i], b);
       q2[o] = v[i];
-      if (MODE == 1) {
-        const float2 bn = same ? b : Bn2[o];
-        v[i].x *= bn.x;
-        v[i].y *= bn.y;
-      }
+      if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn2[o]);
     }
   }
-  if (MODE == 2) return;
+  if (!more) return;
   fft<float, false, NX, PL>(v, t, tws, x);
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = cscale(v[i], dxs[t + TPC * i]);
@@ -289,6 +290,153 @@ __global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep
 
 template <int NX, int C = 16> constexpr size_t sep_x_smem() {
   return 2 * (size_t)NX * C * sizeof(float2) + (size_t)NX * sizeof(float2) + (size_t)NX * sizeof(float);
+}
+
+}  // namespace pft
+
+namespace pft {
+
+// ----------------------------------------------------------------- complex fields
+// The same march for complex (CL) fields with ny = nz = N = 64: every line is complex (no
+// pairing): N column lines along y and N row lines along z per plane, 8 threads a line.
+template <int N> struct SepCfgC {
+  using PL = Plan<N>;
+  static constexpr int E = PL::E, TPC = PL::TPC;
+  static constexpr int R1 = Radix2<typename PL::R>::r1;
+  static constexpr int LINES = N;
+  static constexpr int THREADS = LINES * TPC;  // 512 at N = 64
+  static constexpr int BPITCH = N + 8;         // complex elements per B row in shared memory
+  static constexpr int RSH = (R1 == 16) ? 4 : 3;
+  static constexpr size_t UCOL = (size_t)N * N * sizeof(float2);
+  static constexpr size_t UROW = (size_t)N * N * sizeof(float2);
+  static constexpr size_t BS = (size_t)N * BPITCH * sizeof(float2);
+  static constexpr size_t SMEM = UCOL + UROW + BS + (size_t)N * sizeof(float2) + 2 * (size_t)N * sizeof(float) + 16;
+  static_assert(TPC == 8 && N % 32 == 0 && N >= 32, "eight threads a line, whole-warp column rounds");
+  // Ucol: element (y, z) at y N + (z ^ 8 (y mod 2)): column accesses (32 consecutive z of
+  // one row) and row accesses (two rows per half-warp, eight consecutive z each) are both
+  // conflict-free
+  __device__ static __forceinline__ int ucol(int y, int z) { return y * N + (z ^ ((y & 1) << 3)); }
+  __device__ static __forceinline__ int urow(int L, int p) { return L * N + (p ^ ((p >> RSH) & 7) ^ ((L & 1) << 3)); }
+};
+
+template <int N> struct XSepColC {
+  float2* u;
+  int z;
+  __device__ __forceinline__ void put(int pos, float2 v) { u[SepCfgC<N>::ucol(pos, z)] = v; }
+  __device__ __forceinline__ float2 get(int pos) const { return u[SepCfgC<N>::ucol(pos, z)]; }
+  __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+template <int N> struct XSepRowC {
+  float2* u;
+  int L;
+  __device__ __forceinline__ void put(int pos, float2 v) { u[SepCfgC<N>::urow(L, pos)] = v; }
+  __device__ __forceinline__ float2 get(int pos) const { return u[SepCfgC<N>::urow(L, pos)]; }
+  __device__ __forceinline__ void sync() const { __syncwarp(); }
+};
+
+// MODE as kb_sep_plane (0 first launch, 1 a step -- an entry without Bnext ends there --,
+// 2 the last step); complex B and q, the products complex.
+template <int N, int MODE>
+__global__ void __launch_bounds__(SepCfgC<N>::THREADS, 1) kb_sep_plane_c(const BatchStep* __restrict__ st, int* err) {
+  using R = SepCfgC<N>;
+  constexpr int E = R::E, TPC = R::TPC, LINES = R::LINES;
+  const BatchStep& s = st[blockIdx.y];
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* Ucol = reinterpret_cast<float2*>(smraw);
+  float2* Urow = reinterpret_cast<float2*>(smraw + R::UCOL);
+  float2* Bs = reinterpret_cast<float2*>(smraw + R::UCOL + R::UROW);
+  float2* tws = reinterpret_cast<float2*>(smraw + R::UCOL + R::UROW + R::BS);
+  float* dys = reinterpret_cast<float*>(tws + N);
+  float* dzs = dys + N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dzs + N);
+  const int tid = threadIdx.x;
+  const long long pbase = (long long)blockIdx.x * N * N;  // complex offset of the plane
+  float2* F = reinterpret_cast<float2*>(s.spec) + pbase;
+  const float2* Bg = reinterpret_cast<const float2*>(s.B) + pbase;
+  const int cz = tid % LINES, ct = tid / LINES;  // column phase: column z, position
+  const int L = tid / TPC, t = tid % TPC;        // row phase: row y = L, position
+  float2 v[E];
+  if (MODE != 0) {
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = F[(long long)(ct + TPC * i) * N + cz];
+  }
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (tid == 0) mbar_arrive_expect_tx(bar, (unsigned)(N * N * sizeof(float2)));
+  if (tid < N) bulk_g2s(Bs + tid * R::BPITCH, Bg + (long long)tid * N, (unsigned)(N * sizeof(float2)), bar);
+  for (int i = tid; i < N; i += R::THREADS) {
+    tws[i] = reinterpret_cast<const float2*>(s.tw[1])[i];
+    dys[i] = reinterpret_cast<const float*>(s.d[1])[i];
+    dzs[i] = reinterpret_cast<const float*>(s.d[2])[i];
+  }
+  __syncthreads();
+  XSepColC<N> xc{Ucol, cz};
+  XSepRowC<N> xr{Urow, L};
+  using RT = TwoStage<PlanX<N, E, R::R1, Radix2<typename Plan<N>::R>::r2>>;
+  float2 wr[RT::NW];
+  RT::load(wr, t, tws);
+
+  if (MODE != 0) {
+    // ---- Ky on the columns, transpose, Kz on the rows
+    fft<float, false, N>(v, ct, tws, xc);
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], dys[ct + TPC * i]);
+    fft<float, true, N>(v, ct, tws, xc);
+#pragma unroll
+    for (int i = 0; i < E; i++) Ucol[R::ucol(ct + TPC * i, cz)] = v[i];
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = Ucol[R::ucol(L, t + TPC * i)];
+    RT::template run<false>(v, t, wr, xr);
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], dzs[t + TPC * i]);
+    RT::template run<true>(v, t, wr, xr);
+  } else {
+    const float2* q0 = reinterpret_cast<const float2*>(s.in) + pbase;
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = q0[(long long)L * N + t + TPC * i];
+  }
+  if (!mbar_wait(bar, 0, err, 1)) return;
+
+  const bool more = (MODE == 1) && (s.Bnext != nullptr);
+  {
+    const bool same = (s.Bnext == s.B);
+    const float2* Bn = reinterpret_cast<const float2*>(s.Bnext) + pbase;
+    float2* q = reinterpret_cast<float2*>(s.out) + pbase;
+#pragma unroll
+    for (int i = 0; i < E; i++) {
+      const int k = t + TPC * i;
+      const float2 b = Bs[L * R::BPITCH + k];
+      v[i] = cmul(v[i], b);
+      if (MODE != 0) {
+        q[(long long)L * N + k] = v[i];
+        if (more) v[i] = cmul(v[i], same ? b : Bn[(long long)L * N + k]);
+      }
+    }
+  }
+  if (MODE == 2 || (MODE == 1 && !more)) return;
+
+  // ---- Kz of the next step, transpose, Ky, the field back to global memory
+  __syncwarp();
+  RT::template run<false>(v, t, wr, xr);
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = cscale(v[i], dzs[t + TPC * i]);
+  RT::template run<true>(v, t, wr, xr);
+#pragma unroll
+  for (int i = 0; i < E; i++) Ucol[R::ucol(L, t + TPC * i)] = v[i];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = Ucol[R::ucol(ct + TPC * i, cz)];
+  __syncthreads();
+  fft<float, false, N>(v, ct, tws, xc);
+#pragma unroll
+  for (int i = 0; i < E; i++) v[i] = cscale(v[i], dys[ct + TPC * i]);
+  fft<float, true, N>(v, ct, tws, xc);
+#pragma unroll
+  for (int i = 0; i < E; i++) F[(long long)(ct + TPC * i) * N + cz] = v[i];
 }
 
 }  // namespace pft

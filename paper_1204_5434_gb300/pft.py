@@ -359,11 +359,11 @@ def pft_batch_class_info(b, cls):
     kind = ct.c_int()
     members = ct.c_int()
     plan = ct.c_int()
-    ms = (ct.c_float * 2)()
+    ms = (ct.c_float * 4)()
     _check(_lib().pft_batch_class_info(b, int(cls), n, ct.byref(kind), ct.byref(members), ct.byref(plan), ms),
            "pft_batch_class_info")
     return {"n": tuple(n), "kind": kind.value, "members": members.value, "plan": plan.value,
-            "tuned_ms": (ms[0], ms[1])}
+            "tuned_ms": tuple(ms[k] for k in range(4))}
 
 
 def pft_batch_synchronize(b):

@@ -126,18 +126,22 @@ BENCH_CLASSES = [
 ]
 
 
-def test_batch_fp32_classes_of_the_timed_batch_match_oracle():
-    """FP32-mixed batch with one member per class of the timed batch, graph-captured,
-    plan 1 (both marches per launch; plane kernels for the 64^3 classes): each member's
-    Q, phiA, phiB and fields after one update against the FP64 oracle.  FP32 tolerances
-    of the single-context path (relative 2e-5 on Q, absolute 2e-5 on phi) scaled by the
+@pytest.mark.parametrize("plan", [1, 2, 3])
+def test_batch_fp32_classes_of_the_timed_batch_match_oracle(plan):
+    """FP32-mixed batch with one member per class of the timed batch, graph-captured, in
+    plan 1 (both marches per launch; plane kernels for the 64^3 classes), plan 2 (the
+    separable march on the plane and x kernels for the 64^3 classes, plan 1 elsewhere)
+    or plan 3 (the separable march on pencils for every class): each member's Q, phiA,
+    phiB and fields after one update against the FP64 oracle.  FP32 tolerances of the
+    single-context path (relative 2e-5 on Q, absolute 2e-5 on phi) scaled by the
     random-walk growth of the rounding error over 2 Ns <= 400 transform pairs (x sqrt 2)."""
     b, fields = _make(pft.PFT_FP32_MIXED, BENCH_CLASSES)
     try:
         info = pft.pft_batch_info(b)
         assert info["classes"] == 6
-        for k in range(info["classes"]):
-            assert pft.pft_batch_class_info(b, k)["plan"] == 1
+        pft.pft_batch_set_plan(b, -1, plan)
+        plans = [pft.pft_batch_class_info(b, k)["plan"] for k in range(info["classes"])]
+        assert plans.count(plan) == (2 if plan == 2 else 6), plans
         pft.pft_batch_run(b, 1, LAM, DT, pft.PFT_BATCH_GRAPHED)
         for i, d in enumerate(BENCH_CLASSES):
             wp, wm, s, H = _oracle_updates(d, i, *fields[i], 1)
@@ -151,9 +155,10 @@ def test_batch_fp32_classes_of_the_timed_batch_match_oracle():
             eQ = abs(Q - s.Q) / abs(s.Q)
             ephi = max(np.max(np.abs(pA - s.phiA)), np.max(np.abs(pB - s.phiB)))
             ew = max(np.max(np.abs(gp - wp)), np.max(np.abs(gm - wm)))
-            print(f"\nbatch FP32 member {i} {d['n']} Ns={d['Ns']} kind={d['kind']}: Q rel {eQ:.2e} "
+            print(f"\nbatch FP32 plan {plan} member {i} {d['n']} Ns={d['Ns']} kind={d['kind']}: Q rel {eQ:.2e} "
                   f"phi abs {ephi:.2e} fields abs {ew:.2e}")
             assert eQ <= 3e-5 and ephi <= 3e-5 and ew <= 1e-5, i
+        pft.pft_batch_synchronize(b)
     finally:
         pft.pft_batch_destroy(b)
 
@@ -179,7 +184,7 @@ def test_batch_plans_agree_and_autotune_picks_one(prec):
     fields differing in the last FP64 bits may round apart).  The autotuner then picks a
     plan per class and the run continues from the same state."""
     out = {}
-    for plan in (0, 1):
+    for plan in (0, 1, 3):
         b, _ = _make(prec)
         try:
             pft.pft_batch_set_plan(b, -1, plan)
@@ -197,12 +202,14 @@ def test_batch_plans_agree_and_autotune_picks_one(prec):
                 info = pft.pft_batch_info(b)
                 for k in range(info["classes"]):
                     ci = pft.pft_batch_class_info(b, k)
-                    assert ci["plan"] in (0, 1) and min(ci["tuned_ms"]) > 0
-                    assert ci["tuned_ms"][ci["plan"]] == min(ci["tuned_ms"])
+                    tuned = [v for v in ci["tuned_ms"] if v > 0]
+                    assert ci["plan"] in (0, 1, 2, 3) and ci["tuned_ms"][0] > 0 and ci["tuned_ms"][1] > 0
+                    assert ci["tuned_ms"][ci["plan"]] == min(tuned)
                 pft.pft_batch_run(b, 1, LAM, DT, pft.PFT_BATCH_GRAPHED)
                 pft.pft_batch_synchronize(b)
         finally:
             pft.pft_batch_destroy(b)
     tol = 1e-12 if prec == pft.PFT_FP64 else 1e-5
-    for (a0, b0), (a1, b1) in zip(out[0], out[1]):
-        assert np.max(np.abs(a0 - a1)) <= tol and np.max(np.abs(b0 - b1)) <= tol
+    for other in (1, 3):
+        for (a0, b0), (a1, b1) in zip(out[0], out[other]):
+            assert np.max(np.abs(a0 - a1)) <= tol and np.max(np.abs(b0 - b1)) <= tol

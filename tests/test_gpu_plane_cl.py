@@ -41,6 +41,7 @@ def test_plane_kernel_solve_matches_oracle(case):
     ref = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
     Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, C, n, L, o.CL_COMPLEX)
     with pft.System(n, L, Ns, fA, chiN, C, CL, FP32) as s:
+        pft.pft_set_plan(s.h, 1, 1)  # the 3D plane kernel (plan 2 where nx allows is the default)
         s.set_fields(wp, wm)
         s.solve()
         assert pft.pft_get_plan(s.h) == (1, 1)
@@ -82,3 +83,29 @@ def test_other_complex_grids_keep_the_pencil_passes():
             s.set_fields(*_fields(n, 3))
             s.solve()
             assert pft.pft_get_plan(s.h)[0] == 0, n
+
+
+@pytest.mark.parametrize("n,Ns,streams", [((64, 64, 64), 16, 1), ((128, 64, 64), 7, 0), ((64, 64, 64), 2, 1)])
+def test_complex_separable_march_matches_oracle(n, Ns, streams):
+    """The separable march for complex fields (the default at CL 64^3): complex column and
+    row lines of the 64 x 64 planes, complex x-lines, against the oracle."""
+    L, fA, chiN, C = (n[0] / 8.0, 8.0, 8.0), 0.3, 20.0, 50.0
+    wp, wm = _fields(n, 70 + Ns)
+    ref = o.solve(wp, wm, n, L, Ns, fA, o.CL_COMPLEX)
+    Href = o.hamiltonian(wp, wm, ref.lnQ, chiN, C, n, L, o.CL_COMPLEX)
+    with pft.System(n, L, Ns, fA, chiN, C, CL, FP32) as s:
+        if streams == 1:
+            assert pft.pft_get_plan(s.h) == (2, 1)
+        pft.pft_set_plan(s.h, 2, streams)
+        s.set_fields(wp, wm)
+        s.solve()
+        s.solve()
+        obs = s.observables()
+        phiA, phiB = s.densities()
+        eq = max(np.max(np.abs(s.propagator(w, k) - (ref.q if w == 0 else ref.qd)[k]))
+                 / np.max(np.abs((ref.q if w == 0 else ref.qd)[k])) for w, k in ((0, 1), (0, Ns), (2, 1), (2, Ns)))
+    eQ = abs(obs["Q"] - ref.Q) / abs(ref.Q)
+    ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+    print(f"\ncomplex separable {n} Ns={Ns}: Q rel {eQ:.2e} phi abs {ephi:.2e} slices {eq:.2e}")
+    assert eQ <= 2e-5 and ephi <= 2e-5 and eq <= 2e-5
+    assert abs(obs["H"] - Href) / (C * float(np.prod(L))) <= 2e-5

@@ -73,8 +73,8 @@ def test_separable_march_agrees_with_the_plane_kernel_plan():
 
 
 def test_separable_plan_is_refused_where_it_does_not_apply():
-    for n, kind, prec in (((64, 64, 64), SCFT, FP64), ((64, 64, 64), CL, FP32), ((32, 32, 32), SCFT, FP32),
-                          ((64, 32, 64), SCFT, FP32)):
+    for n, kind, prec in (((64, 64, 64), SCFT, FP64), ((128, 128, 128), CL, FP32), ((32, 32, 32), SCFT, FP32),
+                          ((64, 32, 64), SCFT, FP32), ((32, 64, 64), CL, FP32)):
         with pft.System(n, (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, kind, prec) as s:
             with pytest.raises(pft.PftError) as e:
                 pft.pft_set_plan(s.h, 2, 1)
@@ -141,7 +141,7 @@ def test_separable_pencil_march_matches_oracle(case):
 
 
 def test_default_plans():
-    for n, kind, prec, plan in (((64, 64, 64), CL, FP32, 1), ((32, 32, 32), SCFT, FP32, 0),
+    for n, kind, prec, plan in (((64, 64, 64), CL, FP32, 2), ((32, 32, 32), SCFT, FP32, 0),
                                 ((64, 64, 64), SCFT, FP64, 3), ((256, 16, 256), CL, FP64, 3),
                                 ((256, 16, 256), CL, FP32, 0), ((128, 128, 128), SCFT, FP32, 2)):
         with pft.System(n, (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, kind, prec) as s:
