@@ -413,12 +413,14 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
  * plane kernel or an x kernel in turn -- advances one contour step; 3 = the separable
  * march on pencils (complex fields, real fields with ny and nz even; either precision):
  * per contour step one launch of the y convolution and one of the x or z kernel, which
- * carries the two convolutions of consecutive steps along its axis.  *streams = 1 if the
+ * carries the two convolutions of consecutive steps along its axis; 18 = plan 2 with the x
+ * kernel on half the elements a thread (twice the threads, one more exchange: at nx = 128
+ * eight elements and radices 8, 4, 4 instead of 16 and 16, 8).  *streams = 1 if the
  * two propagators run as two chains on two streams.  Either pointer may be NULL.
  * Errors: PFT_ERR_ARG for a NULL ctx. */
 pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams);
 
-/* Fix the plan of the pass march (values as pft_get_plan reports them); the context
+/* Fix the plan of the pass march (codes as pft_get_plan reports them); the context
  * keeps it (no autotuning) and recaptures its solve graph at the next pft_solve.  The RQM4
  * scheme, the adjoint and the box derivative run the plane kernel wherever plane >= 1.
  * Errors: PFT_ERR_ARG (NULL ctx, values out of range), PFT_ERR_UNSUPPORTED (a plan the

@@ -288,7 +288,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
       {&d.wp, M * fe},   {&d.wm, M * fe},    {&d.BA, M * we},     {&d.BB, M * we},
       {&d.hist, (size_t)pft::q_slots(d) * M * we}, {&d.qd[0], M * we}, {&d.qd[1], M * we}, {&d.qd0, M * we},
       {&d.spec, M * ze}, {&d.spec2, M * ze}, {&d.accA, M * fe},  {&d.accB, M * fe},
-      {(void**)&d.partials, (size_t)d.npart * 8 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
+      {(void**)&d.partials, (size_t)d.npart * 16 * sizeof(double)}, {(void**)&d.scal, pft::S_COUNT * sizeof(double)},
       {&c->io, M * 16}, {(void**)&d.kerr, 16},
       // quarter-step Boltzmann factors of the 4th-order scheme
       {d.scheme ? &d.BAh : nullptr, M * we}, {d.scheme ? &d.BBh : nullptr, M * we},
@@ -307,7 +307,7 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
     memset(d.scal_host, 0, pft::S_COUNT * sizeof(double));
     e = cudaMemsetAsync(d.scal, 0, pft::S_COUNT * sizeof(double), d.stream);
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(d.partials, 0, (size_t)d.npart * 8 * sizeof(double), d.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.partials, 0, (size_t)d.npart * 16 * sizeof(double), d.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(d.kerr, 0, 16, d.stream);
   if (e == cudaSuccess) e = c->eng->upload_tables(d);
   if (e == cudaSuccess) e = c->eng->fill_ones(d, d.hist);
@@ -867,10 +867,12 @@ pft_status pft_launch_counts(const pft_ctx* ctx, long long* solve, long long* fi
   return PFT_OK;
 }
 
-pft_status pft_set_plan(pft_ctx* ctx, int plane, int streams) {
+pft_status pft_set_plan(pft_ctx* ctx, int code, int streams) {
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
-  if (plane < 0 || plane > 3 || streams < 0 || streams > 1) return fail(PFT_ERR_ARG, "plane in {0,1,2,3}, streams in {0,1}");
+  const int plane = code & 15, xv = code >> 4;
+  if (code < 0 || plane > 3 || xv > 1 || (xv && plane != 2) || streams < 0 || streams > 1)
+    return fail(PFT_ERR_ARG, "plan code in {0, 1, 2, 3, 18}, streams in {0, 1}");
   if (plane == 1 && !ctx->eng->plane_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the plane kernel needs FP32 with ny = nz = 64 or 128 (real) or 64 (complex)");
   if (plane == 2 && !ctx->eng->sep_applies(d))
@@ -878,6 +880,7 @@ pft_status pft_set_plan(pft_ctx* ctx, int plane, int streams) {
   if (plane == 3 && !ctx->eng->sepp_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the separable pencil march needs ny and nz even for real fields");
   d.plan_plane = plane;
+  d.plan_xv = xv;
   d.plan_streams = streams;
   d.tuned = true;  // an explicit plan is not re-tuned
   d.graph_valid = false;
@@ -890,7 +893,7 @@ pft_status pft_set_plan(pft_ctx* ctx, int plane, int streams) {
 
 pft_status pft_get_plan(const pft_ctx* ctx, int* plane, int* streams) {
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
-  if (plane) *plane = ctx->d.plan_plane;
+  if (plane) *plane = ctx->d.plan_plane + 16 * ctx->d.plan_xv;
   if (streams) *streams = ctx->d.plan_streams;
   return PFT_OK;
 }

@@ -69,7 +69,7 @@ struct CtxData {
   void* spec2 = nullptr;  // [M] second spectrum (box derivative)
   void* accA = nullptr;   // [M] f64 or c128: quadrature sums, then phiA
   void* accB = nullptr;
-  double* partials = nullptr;  // [npart * 8]
+  double* partials = nullptr;  // [npart * 16]: per-block partial sums of the reductions
   double* scal = nullptr;      // [S_COUNT]
   double* scal_host = nullptr; // pinned mirror
   void* tables = nullptr;      // twiddles + diffusion factors
@@ -103,6 +103,7 @@ struct CtxData {
   // on one stream (0); chosen by timing at the first solve when `autotune` is set
   int plan_plane = 1;
   int plan_streams = 1;
+  int plan_xv = 0;  // separable march: plan variant of the x kernel (0: Plan<nx>, 1: half the elements a thread)
   bool autotune = false;
   bool tuned = false;
   bool edw = false;   // Edwards homopolymer model: one field, q-dagger = q

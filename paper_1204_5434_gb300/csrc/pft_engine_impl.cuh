@@ -654,6 +654,38 @@ __global__ void __launch_bounds__(PW_THREADS) k_step_scft(double* __restrict__ w
   block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
 }
 
+// The same step for FP32 factors, two grid points a thread (16-byte loads): the field
+// update in FP64, the factors' arguments from the narrowed fields (integer-pipe rounding)
+// times -ds/2 in FP32 -- within one FP32 rounding of the FP64 argument, far below the
+// rounding of the stored factor -- so that the FP64 pipe (1/64 of FP32 on GB300) does
+// only the update and the field-term sum.
+static __global__ void __launch_bounds__(PW_THREADS) k_step_scft2(double* __restrict__ wp, double* __restrict__ wm,
+                                                                  const double* __restrict__ phiA,
+                                                                  const double* __restrict__ phiB,
+                                                                  float* __restrict__ BA, float* __restrict__ BB,
+                                                                  double lam, double ds, double chiN, long long M,
+                                                                  double* __restrict__ partials) {
+  double acc[2] = {0.0, 0.0};
+  const double ichiN = 1.0 / chiN;
+  const double cm = 1.0 - 2.0 * lam * ichiN;  // W- <- cm W- - lam (phiB - phiA)
+  const float hds = (float)(-0.5 * ds);
+  const long long M2 = M / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M2; i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = reinterpret_cast<const double2*>(phiA)[i], b = reinterpret_cast<const double2*>(phiB)[i];
+    double2 p = reinterpret_cast<double2*>(wp)[i], m = reinterpret_cast<double2*>(wm)[i];
+    p.x += lam * (a.x + b.x - 1.0);
+    p.y += lam * (a.y + b.y - 1.0);
+    m.x = cm * m.x - lam * (b.x - a.x);
+    m.y = cm * m.y - lam * (b.y - a.y);
+    reinterpret_cast<double2*>(wp)[i] = p;
+    reinterpret_cast<double2*>(wm)[i] = m;
+    reinterpret_cast<float2*>(BA)[i] = make_float2(expf(narrow_rn(p.x - m.x) * hds), expf(narrow_rn(p.y - m.y) * hds));
+    reinterpret_cast<float2*>(BB)[i] = make_float2(expf(narrow_rn(p.x + m.x) * hds), expf(narrow_rn(p.y + m.y) * hds));
+    acc[0] += (m.x * m.x + m.y * m.y) * ichiN - (p.x + p.y);
+  }
+  block_reduce_store<2>(acc, partials + 2 * blockIdx.x);
+}
+
 // Euler-Maruyama complex Langevin step (Eq. 9 with the Eq. 7 forces per C and real
 // noise of variance 2 dt/(C dV)), four grid points per thread so that one Philox
 // block serves four consecutive points of each field.

@@ -548,39 +548,51 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
-  template <int NX, int NYZ, int MODE, int KIND = 0>
+  // XV 0: the x-lines on Plan<NX> (16 elements a thread at 128); XV 1: on SepXAlt (half
+  // the elements a thread, twice the threads, one more exchange)
+  template <int NX, int NYZ, int MODE, int KIND, int XV>
   static cudaError_t launch_sep_x(const BatchStep* st, int members, cudaStream_t sm) {
     constexpr int C = 16;
     constexpr long long P = KIND ? (long long)NYZ * NYZ : (long long)NYZ * NYZ / 2;
-    auto kern = kb_sep_x<NX, NYZ, MODE, C, KIND>;
+    using XPL = typename std::conditional<XV == 1, typename SepXAlt<NX>::P, Plan<NX>>::type;
+    auto kern = kb_sep_x<NX, NYZ, MODE, C, KIND, XPL>;
     const unsigned grid = (unsigned)(P / C);
-    kern<<<dim3(grid, (unsigned)members), C * Plan<NX>::TPC, sep_x_smem<NX, C>(), sm>>>(st);
+    kern<<<dim3(grid, (unsigned)members), C * XPL::TPC, sep_x_smem<NX, C>(), sm>>>(st);
     return cudaGetLastError();
   }
-  template <int NX, int MODE>
-  static cudaError_t launch_sep_x_n(const BatchStep* st, int nyz, int kind, int members, cudaStream_t sm) {
-    if (kind != PFT_SCFT_REAL) return nyz == 64 ? launch_sep_x<NX, 64, MODE, 1>(st, members, sm) : cudaErrorNotSupported;
-    if (nyz == 128) return launch_sep_x<NX, 128, MODE>(st, members, sm);
-    if (nyz == 64) return launch_sep_x<NX, 64, MODE>(st, members, sm);
+  template <int NX, int MODE, int XV>
+  static cudaError_t launch_sep_x_v(const BatchStep* st, int nyz, int kind, int members, cudaStream_t sm) {
+    if (kind != PFT_SCFT_REAL)
+      return nyz == 64 ? launch_sep_x<NX, 64, MODE, 1, XV>(st, members, sm) : cudaErrorNotSupported;
+    if (nyz == 128) return launch_sep_x<NX, 128, MODE, 0, XV>(st, members, sm);
+    if (nyz == 64) return launch_sep_x<NX, 64, MODE, 0, XV>(st, members, sm);
     return cudaErrorNotSupported;
+  }
+  template <int NX, int MODE>
+  static cudaError_t launch_sep_x_n(const BatchStep* st, int nyz, int kind, int xv, int members, cudaStream_t sm) {
+    return xv ? launch_sep_x_v<NX, MODE, 1>(st, nyz, kind, members, sm)
+              : launch_sep_x_v<NX, MODE, 0>(st, nyz, kind, members, sm);
   }
 
   // launch j of a separable march (j = 0: the first plane launch; j >= 1 stores q_j)
   cudaError_t sep_launch(CtxData& c, const BatchStep* ss, int j, int members, cudaStream_t sm) {
-    return sep_launch_g(c.n, c.kind, (j == 0) ? 0 : (j == c.Ns ? 2 : 1), j, members, c.kerr, ss, sm);
+    return sep_launch_g(c.n, c.kind, (j == 0) ? 0 : (j == c.Ns ? 2 : 1), j, members, c.kerr, ss, sm, c.plan_xv);
   }
-  // mode 0: first launch; 1: a step (entries without Bnext end there); 2: the last step
+  // mode 0: first launch; 1: a step (entries without Bnext end there); 2: the last step;
+  // xv: the x kernel's plan variant
   static cudaError_t sep_launch_g(const int n[3], int kind, int mode, int j, int members, int* err,
-                                  const BatchStep* ss, cudaStream_t sm) {
+                                  const BatchStep* ss, cudaStream_t sm, int xv) {
     if constexpr (!std::is_same<T, float>::value) {
       return cudaErrorNotSupported;
     } else {
       const int nx = n[0], N = n[1];
       if (j >= 1 && (j & 1)) {  // x kernel
         if (nx == 128)
-          return mode == 2 ? launch_sep_x_n<128, 2>(ss, N, kind, members, sm) : launch_sep_x_n<128, 1>(ss, N, kind, members, sm);
+          return mode == 2 ? launch_sep_x_n<128, 2>(ss, N, kind, xv, members, sm)
+                           : launch_sep_x_n<128, 1>(ss, N, kind, xv, members, sm);
         if (nx == 64)
-          return mode == 2 ? launch_sep_x_n<64, 2>(ss, N, kind, members, sm) : launch_sep_x_n<64, 1>(ss, N, kind, members, sm);
+          return mode == 2 ? launch_sep_x_n<64, 2>(ss, N, kind, xv, members, sm)
+                           : launch_sep_x_n<64, 1>(ss, N, kind, xv, members, sm);
         return cudaErrorNotSupported;
       }
       if (kind != PFT_SCFT_REAL) {
@@ -721,8 +733,10 @@ class EngineT : public Engine {
              c.kind == PFT_SCFT_REAL ? "real" : "complex", sizeof(T) == 4 ? "fp32" : "fp64", c.Ns);
     int pl = 0, sm = 0;
     if (plan_cache_lookup(key, &pl, &sm)) {
-      if (pl == 3 && sepp_supported(c) && c.stepsS) c.plan_plane = 3;
-      else c.plan_plane = (pl == 2 && sep_supported(c) && c.stepsS) ? 2 : ((pl == 1 && plane_supported(c)) ? 1 : 0);
+      const int fam = pl & 15;
+      c.plan_xv = (fam == 2) ? (pl >> 4) & 1 : 0;
+      if (fam == 3 && sepp_supported(c) && c.stepsS) c.plan_plane = 3;
+      else c.plan_plane = (fam == 2 && sep_supported(c) && c.stepsS) ? 2 : ((fam == 1 && plane_supported(c)) ? 1 : 0);
       c.plan_streams = sm ? 1 : 0;
       return cudaSuccess;
     }
@@ -730,15 +744,17 @@ class EngineT : public Engine {
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = -1.f;
-    int bpl = c.plan_plane, bsm = c.plan_streams;
-    // candidates: separable pencil march, separable plane march, plane kernel, pencil
-    // passes; two chains or two-member launches
-    for (int cand = 0; cand < 8 && e == cudaSuccess; cand++) {
-      const int cpl = 3 - cand / 2, csm = (cand & 1) ? 0 : 1;
+    int bpl = c.plan_plane, bsm = c.plan_streams, bxv = c.plan_xv;
+    // candidates: separable pencil march, separable plane march (two x-kernel plans),
+    // plane kernel, pencil passes; two chains or two-member launches
+    for (int cand = 0; cand < 10 && e == cudaSuccess; cand++) {
+      static const int fam_of[5] = {3, 2, 2, 1, 0}, xv_of[5] = {0, 0, 1, 0, 0};
+      const int cpl = fam_of[cand / 2], cxv = xv_of[cand / 2], csm = (cand & 1) ? 0 : 1;
       if (cpl == 3 && !(sepp_supported(c) && c.stepsS)) continue;
       if (cpl == 2 && !(sep_supported(c) && c.stepsS)) continue;
       if (cpl == 1 && !plane_supported(c)) continue;
       c.plan_plane = cpl;
+      c.plan_xv = cxv;
       c.plan_streams = csm;
       if ((e = record_solve(c)) != cudaSuccess) break;  // warm-up
       if ((e = cudaEventRecord(e0, c.stream)) != cudaSuccess) break;
@@ -751,14 +767,16 @@ class EngineT : public Engine {
         best = ms;
         bpl = cpl;
         bsm = csm;
+        bxv = cxv;
       }
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     c.plan_plane = bpl;
     c.plan_streams = bsm;
+    c.plan_xv = bxv;
     if (e != cudaSuccess) return e;
-    plan_cache_store(key, bpl, bsm, (double)best);
+    plan_cache_store(key, bpl + 16 * bxv, bsm, (double)best);
     return cudaSuccess;
   }
 
@@ -797,7 +815,7 @@ class EngineT : public Engine {
   cudaError_t batch_sep_launch(const BatchGeom& g, const BatchStep* ss, int j, int nact, int plan, int* err,
                                cudaStream_t sm) override {
     if (nact <= 0) return cudaSuccess;
-    if (plan == 2) return sep_launch_g(g.n, g.kind, j == 0 ? 0 : 1, j, nact, err, ss, sm);
+    if (plan == 2) return sep_launch_g(g.n, g.kind, j == 0 ? 0 : 1, j, nact, err, ss, sm, 0);
     SeppGeom sg;
     for (int a = 0; a < 3; a++) sg.n[a] = g.n[a];
     sg.kind = (g.kind == PFT_SCFT_REAL) ? 0 : 1;
@@ -1001,11 +1019,12 @@ class EngineT : public Engine {
     if (std::is_same<T, float>::value && real && !c.edw && c.M % 4 == 0) {
       // the quadrature with the densities and force sums of the tail in one pass
       mark(c, KK_QUADRATURE);
-      k_quadrature_final_real4<<<c.npart, PW_THREADS, 0, c.stream>>>(
+      const int nb = c.npart;
+      k_quadrature_final_real4<<<nb, PW_THREADS, 0, c.stream>>>(
           (const float*)c.hist, (const float*)c.qdh, (const float*)c.qd0, c.M, c.Ns, c.NsA, (double*)c.accA,
           (double*)c.accB, (const double*)c.wm, c.scal, c.ds, c.chiN, c.partials);
       mark(c, KK_REDUCE);
-      k_reduce_final<6><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_PHIA);
+      k_reduce_final<6><<<1, PW_THREADS, 0, c.stream>>>(c.partials, nb, c.scal + S_PHIA);
       return cudaGetLastError();
     }
     if ((e = quadrature(c)) != cudaSuccess) return e;
@@ -1297,9 +1316,15 @@ class EngineT : public Engine {
       return cudaGetLastError();
     }
     if (step_kind == PFT_STEP_SCFT_EULER) {
-      k_step_scft<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (double*)c.wm, (const double*)c.accA,
-                                                           (const double*)c.accB, (T*)c.BA, (T*)c.BB, lam, c.ds, c.chiN,
-                                                           c.M, c.partials);
+      if (std::is_same<T, float>::value && c.M % 2 == 0) {
+        k_step_scft2<<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (double*)c.wm, (const double*)c.accA,
+                                                           (const double*)c.accB, (float*)c.BA, (float*)c.BB, lam, c.ds,
+                                                           c.chiN, c.M, c.partials);
+      } else {
+        k_step_scft<T><<<c.npart, PW_THREADS, 0, c.stream>>>((double*)c.wp, (double*)c.wm, (const double*)c.accA,
+                                                             (const double*)c.accB, (T*)c.BA, (T*)c.BB, lam, c.ds,
+                                                             c.chiN, c.M, c.partials);
+      }
     } else {
       const double dV = c.L[0] * c.L[1] * c.L[2] / (double)c.M;
       const double std = sqrt(2.0 * lam / (c.C * dV));

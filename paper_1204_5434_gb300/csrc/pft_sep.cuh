@@ -218,13 +218,22 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
 // 1/nx folded in); twiddles st.tw[0].  B_s of the tile is copied to shared memory by
 // 16-byte cp.async chunks at the start, so its latency hides behind the first Kx.
 // KIND 1: complex fields -- each x-line is one complex line (P = NYZ^2 of them) and B
-// multiplies as a complex factor.
-template <int NX, int NYZ, int MODE, int C = 16, int KIND = 0>
-__global__ void __launch_bounds__(C * Plan<NX>::TPC, 4) kb_sep_x(const BatchStep* __restrict__ st) {
+// multiplies as a complex factor.  XPL: the transform plan of the x-lines (elements a
+// thread and radices); the CTA has C * XPL::TPC threads.
+template <int NX> struct SepXAlt;  // the alternative x plan: half the elements a thread
+template <> struct SepXAlt<128> { using P = PlanX<128, 8, 8, 4, 4>; };
+template <> struct SepXAlt<64> { using P = PlanX<64, 4, 4, 4, 4>; };
+template <int NX, class XPL> struct SepXCfg {
+  static constexpr int THREADS = 16 * XPL::TPC;
+  static constexpr int MINB = THREADS <= 128 ? 4 : 3;
+};
+template <int NX, int NYZ, int MODE, int C = 16, int KIND = 0, class XPL = Plan<NX>>
+__global__ void __launch_bounds__(SepXCfg<NX, XPL>::THREADS, SepXCfg<NX, XPL>::MINB) kb_sep_x(const BatchStep* __restrict__ st) {
+  static_assert(C == 16, "sixteen lines a CTA");
   // lines per x-plane: column pairs (real) or columns (complex) of the ny = nz = NYZ plane
   constexpr long long P = KIND ? (long long)NYZ * NYZ : (long long)NYZ * NYZ / 2;
   static_assert(P % C == 0, "whole tiles");
-  using PL = Plan<NX>;
+  using PL = XPL;
   constexpr int E = PL::E, TPC = PL::TPC;
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];

@@ -85,8 +85,9 @@ def test_other_complex_grids_keep_the_pencil_passes():
             assert pft.pft_get_plan(s.h)[0] == 0, n
 
 
-@pytest.mark.parametrize("n,Ns,streams", [((64, 64, 64), 16, 1), ((128, 64, 64), 7, 0), ((64, 64, 64), 2, 1)])
-def test_complex_separable_march_matches_oracle(n, Ns, streams):
+@pytest.mark.parametrize("n,Ns,streams,code", [((64, 64, 64), 16, 1, 2), ((128, 64, 64), 7, 0, 2), ((64, 64, 64), 2, 1, 2),
+                                               ((64, 64, 64), 5, 1, 18)])
+def test_complex_separable_march_matches_oracle(n, Ns, streams, code):
     """The separable march for complex fields (the default at CL 64^3): complex column and
     row lines of the 64 x 64 planes, complex x-lines, against the oracle."""
     L, fA, chiN, C = (n[0] / 8.0, 8.0, 8.0), 0.3, 20.0, 50.0
@@ -96,7 +97,7 @@ def test_complex_separable_march_matches_oracle(n, Ns, streams):
     with pft.System(n, L, Ns, fA, chiN, C, CL, FP32) as s:
         if streams == 1:
             assert pft.pft_get_plan(s.h) == (2, 1)
-        pft.pft_set_plan(s.h, 2, streams)
+        pft.pft_set_plan(s.h, code, streams)
         s.set_fields(wp, wm)
         s.solve()
         s.solve()

@@ -40,6 +40,8 @@ def _solve(w, plan, streams, wp, wm):
 # two steps and a junction inside the march, uneven box lengths
 CASES = [
     (wl.GYR128.with_(Ns=20), 1, 1e-4),
+    (wl.GYR128.with_(Ns=9), 1, 1e-4, 18),  # the x kernel's alternative plan
+    (wl.GYR64.with_(n=(64, 64, 64), Ns=4), 0, 2e-5, 18),
     (wl.GYR128.with_(Ns=7), 0, 1e-4),
     (wl.GYR64.with_(Ns=1, fA=0.5), 1, 2e-5),
     (wl.GYR64.with_(Ns=2, fA=0.5), 0, 2e-5),
@@ -50,15 +52,16 @@ CASES = [
 
 @pytest.mark.parametrize("case", range(len(CASES)))
 def test_separable_march_matches_oracle(case):
-    w, streams, qtol = CASES[case]
+    w, streams, qtol = CASES[case][:3]
+    code = CASES[case][3] if len(CASES[case]) > 3 else 2
     wp, wm = wl.fields(w)
     ref = o.solve(wp, wm, w.n, w.L, w.Ns, w.fA, o.SCFT_REAL)
-    obs, phiA, phiB, q, qd = _solve(w, 2, streams, wp, wm)
+    obs, phiA, phiB, q, qd = _solve(w, code, streams, wp, wm)
     eQ = abs(obs["Q"].real - ref.Q) / ref.Q
     ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
     eq = max(np.max(np.abs(v - ref.q[k])) / np.max(np.abs(ref.q[k])) for k, v in q.items())
     eqd = max(np.max(np.abs(v - ref.qd[k])) / np.max(np.abs(ref.qd[k])) for k, v in qd.items())
-    print(f"\nseparable {w.n} Ns={w.Ns} streams={streams}: Q rel {eQ:.2e} phi abs {ephi:.2e} "
+    print(f"\nseparable {w.n} Ns={w.Ns} plan={code} streams={streams}: Q rel {eQ:.2e} phi abs {ephi:.2e} "
           f"q {eq:.2e} qd {eqd:.2e}")
     assert eQ <= 2e-5 and ephi <= 2e-5 and eq <= qtol and eqd <= qtol
 
