@@ -83,6 +83,8 @@ struct CtxData {
   void* adj = nullptr;              // adjoint scratch: 6 working-precision slices + 2 M FP64
   void* stepsa = nullptr;           // [2 Ns] BatchStep of the adjoint transforms
   void* stepsap = nullptr;          // [2 Ns] AdjPlaneStep of the adjoint on the plane kernel
+  void* adjS = nullptr;             // adjoint on the separable march: lambda and mu histories, gA, gB
+  void* stepsAS = nullptr;          // [2 Ns] its step entries
   size_t tables_bytes = 0;
   int npart = 0;
   int* kerr = nullptr;  // kernel error word: a bounded wait that ran out (read by pft_get_observables)

@@ -810,6 +810,124 @@ __global__ void __launch_bounds__(PW_THREADS) k_adjoint_init(T* __restrict__ lam
   }
 }
 
+// ---- the adjoint on the separable march (FP32 real fields): both adjoint marches store
+// their histories (lambda_k, mu_m) and one pass forms the gradient afterwards.
+// Set-up: gA = (ds/Q) GA and gB = (ds/Q) GB in FP32 (the sources of the marches are
+// (cA_k gA + cB_k gB) times a history slice), lambda_Ns = (cA_Ns gA + cB_Ns gB) qd_0 and
+// mu_Ns = (cA_0 gA + cB_0 gB) q_0.
+static __global__ void __launch_bounds__(PW_THREADS) k_adjsep_init(
+    const double* __restrict__ GA, const double* __restrict__ GB, const double* __restrict__ s, double ds,
+    float* __restrict__ gA, float* __restrict__ gB, float* __restrict__ lamNs, float* __restrict__ muNs,
+    const float* __restrict__ qd0, const float* __restrict__ q0, float cAl, float cBl, float cAm, float cBm,
+    long long M) {
+  const double f = ds / s[S_Q];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    const float a = narrow_rn(f * GA[i]), b = narrow_rn(f * GB[i]);
+    gA[i] = a;
+    gB[i] = b;
+    lamNs[i] = (cAl * a + cBl * b) * qd0[i];
+    muNs[i] = (cAm * a + cBm * b) * q0[i];
+  }
+}
+
+// Trapezoid weights of slice n on each block (as trap_w), in FP32 (exact: 0, 1/2, 1).
+__device__ __forceinline__ void trap_wf(int n, int Ns, int NsA, float* cA, float* cB) {
+  *cA = 0.f;
+  *cB = 0.f;
+  if (NsA > 0 && n <= NsA) *cA = (n == 0 || n == NsA) ? 0.5f : 1.f;
+  if (NsA < Ns && n >= NsA) *cB = (n == NsA || n == Ns) ? 0.5f : 1.f;
+}
+
+// The gradient of the loss from the stored histories, one pass, four points a thread.
+// Step n of the lambda chain (split step n) adds -(ds/2) [lambda_n q_n + q_{n-1}
+// (lambda_{n-1} - a_{n-1})] (B_n z_n = lambda_{n-1} - a_{n-1}, a_k = (cA_k gA + cB_k gB)
+// qd_{Ns-k}); step m = Ns + 1 - n of the mu chain (split step n as well) adds -(ds/2)
+// [mu_m qd_m + qd_{m-1} (mu_{m-1} - b_{m-1})], b_k = (cA_{Ns-k} gA + cB_{Ns-k} gB) q_{Ns-k}.
+// Both go to the block of split step n; the sums are compensated FP32 over chunks of
+// kQuadChunk steps flushed into FP64.  Then dL/dW+ = dwA + dwB + gamma (phiA + phiB)/M and
+// dL/dW- = dwB - dwA + gamma (phiB - phiA)/M.
+static __global__ void __launch_bounds__(PW_THREADS) k_adjsep_grad(
+    const float* __restrict__ lam, const float* __restrict__ mu, const float* __restrict__ hist,
+    const float* __restrict__ qdh, const float* __restrict__ qd0, const float* __restrict__ gA,
+    const float* __restrict__ gB, const double* __restrict__ phiA, const double* __restrict__ phiB,
+    const double* __restrict__ gamma, double invM, double ds, int Ns, int NsA, long long M, double* __restrict__ dwp,
+    double* __restrict__ dwm) {
+  const long long M4 = M / 4;
+  const double gm = gamma[0] * invM;
+  auto qd = [&](int m) { return m == 0 ? qd0 : qdh + (long long)m * M; };
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M4; i += (long long)gridDim.x * blockDim.x) {
+    const float4 ga = reinterpret_cast<const float4*>(gA)[i], gb = reinterpret_cast<const float4*>(gB)[i];
+    const float gaa[4] = {ga.x, ga.y, ga.z, ga.w}, gbb[4] = {gb.x, gb.y, gb.z, gb.w};
+    // values of step n - 1: lambda_{n-1}, q_{n-1}, mu_{Ns+1-n}, qd_{Ns+1-n}
+    float4 lp = reinterpret_cast<const float4*>(lam)[i];
+    float4 qp = reinterpret_cast<const float4*>(hist)[i];
+    float4 mp = reinterpret_cast<const float4*>(mu + (long long)Ns * M)[i];
+    float4 dp = reinterpret_cast<const float4*>(qd(Ns))[i];
+    double dA[4] = {0, 0, 0, 0}, dB[4] = {0, 0, 0, 0};
+    F2Sum fA[4], fB[4];
+    int cnt = 0;
+#pragma unroll 1
+    for (int n = 1; n <= Ns; n++) {
+      const int m = Ns + 1 - n;
+      const float4 ln = reinterpret_cast<const float4*>(lam + (long long)n * M)[i];
+      const float4 qn = reinterpret_cast<const float4*>(hist + (long long)n * M)[i];
+      const float4 mm1 = reinterpret_cast<const float4*>(mu + (long long)(m - 1) * M)[i];
+      const float4 dm1 = reinterpret_cast<const float4*>(qd(m - 1))[i];
+      float cAa, cBa, cAb, cBb;
+      trap_wf(n - 1, Ns, NsA, &cAa, &cBa);  // weights of a_{n-1}
+      trap_wf(Ns - m + 1, Ns, NsA, &cAb, &cBb);  // weights of b_{m-1}: index Ns - (m - 1) = n
+      const float l1[4] = {lp.x, lp.y, lp.z, lp.w}, q1[4] = {qp.x, qp.y, qp.z, qp.w};
+      const float l0[4] = {ln.x, ln.y, ln.z, ln.w}, q0v[4] = {qn.x, qn.y, qn.z, qn.w};
+      const float mu0[4] = {mp.x, mp.y, mp.z, mp.w}, d0[4] = {dp.x, dp.y, dp.z, dp.w};
+      const float mu1[4] = {mm1.x, mm1.y, mm1.z, mm1.w}, d1[4] = {dm1.x, dm1.y, dm1.z, dm1.w};
+      const bool blkA = (n <= NsA);
+#pragma unroll
+      for (int k = 0; k < 4; k++) {
+        // lambda chain: a_{n-1} = (cA gA + cB gB) qd_{Ns-n+1}; qd_{Ns+1-n} = d0
+        const float a = (cAa * gaa[k] + cBa * gbb[k]) * d0[k];
+        const float tl = __fadd_rn(__fmul_rn(l0[k], q0v[k]), __fmul_rn(q1[k], __fsub_rn(l1[k], a)));
+        // mu chain: b_{m-1} = (cA_n gA + cB_n gB) q_n
+        const float b = (cAb * gaa[k] + cBb * gbb[k]) * q0v[k];
+        const float tm = __fadd_rn(__fmul_rn(mu0[k], d0[k]), __fmul_rn(d1[k], __fsub_rn(mu1[k], b)));
+        if (blkA) {
+          fA[k].add(tl);
+          fA[k].add(tm);
+        } else {
+          fB[k].add(tl);
+          fB[k].add(tm);
+        }
+      }
+      lp = ln;
+      qp = qn;
+      mp = mm1;
+      dp = dm1;
+      if (++cnt == kQuadChunk || n == Ns) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+          fA[k].flush(&dA[k]);
+          fB[k].flush(&dB[k]);
+        }
+        cnt = 0;
+      }
+    }
+    const double h = -0.5 * ds;
+    const double2 pA0 = reinterpret_cast<const double2*>(phiA)[2 * i], pA1 = reinterpret_cast<const double2*>(phiA)[2 * i + 1];
+    const double2 pB0 = reinterpret_cast<const double2*>(phiB)[2 * i], pB1 = reinterpret_cast<const double2*>(phiB)[2 * i + 1];
+    const double pa[4] = {pA0.x, pA0.y, pA1.x, pA1.y}, pb[4] = {pB0.x, pB0.y, pB1.x, pB1.y};
+    double op[4], om[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      const double a = h * dA[k] + gm * pa[k], b = h * dB[k] + gm * pb[k];
+      op[k] = a + b;
+      om[k] = b - a;
+    }
+    reinterpret_cast<double2*>(dwp)[2 * i] = make_double2(op[0], op[1]);
+    reinterpret_cast<double2*>(dwp)[2 * i + 1] = make_double2(op[2], op[3]);
+    reinterpret_cast<double2*>(dwm)[2 * i] = make_double2(om[0], om[1]);
+    reinterpret_cast<double2*>(dwm)[2 * i + 1] = make_double2(om[2], om[3]);
+  }
+}
+
 // gamma = sum_x (GA phiA + GB phiB), partial sums per block.
 static __global__ void __launch_bounds__(PW_THREADS) k_adjoint_gamma(const double* __restrict__ GA,
                                                                      const double* __restrict__ GB,

@@ -538,10 +538,10 @@ class EngineT : public Engine {
     return cudaGetLastError();
   }
 
-  template <int N, int MODE>
+  template <int N, int MODE, int ADJ = 0>
   static cudaError_t launch_sep_plane(const BatchStep* st, int nx, int members, int* err, cudaStream_t sm) {
     using R = SepCfg<N>;
-    auto kern = kb_sep_plane<N, MODE>;
+    auto kern = kb_sep_plane<N, MODE, ADJ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R::SMEM);
     if (e != cudaSuccess) return e;
     kern<<<dim3((unsigned)nx, (unsigned)members), R::THREADS, R::SMEM, sm>>>(st, err);
@@ -550,12 +550,12 @@ class EngineT : public Engine {
 
   // XV 0: the x-lines on Plan<NX> (16 elements a thread at 128); XV 1: on SepXAlt (half
   // the elements a thread, twice the threads, one more exchange)
-  template <int NX, int NYZ, int MODE, int KIND, int XV>
+  template <int NX, int NYZ, int MODE, int KIND, int XV, int ADJ = 0>
   static cudaError_t launch_sep_x(const BatchStep* st, int members, cudaStream_t sm) {
     constexpr int C = 16;
     constexpr long long P = KIND ? (long long)NYZ * NYZ : (long long)NYZ * NYZ / 2;
     using XPL = typename std::conditional<XV == 1, typename SepXAlt<NX>::P, Plan<NX>>::type;
-    auto kern = kb_sep_x<NX, NYZ, MODE, C, KIND, XPL>;
+    auto kern = kb_sep_x<NX, NYZ, MODE, C, KIND, XPL, ADJ>;
     const unsigned grid = (unsigned)(P / C);
     kern<<<dim3(grid, (unsigned)members), C * XPL::TPC, sep_x_smem<NX, C>(), sm>>>(st);
     return cudaGetLastError();
@@ -611,6 +611,113 @@ class EngineT : public Engine {
       }
       return cudaErrorNotSupported;
     }
+  }
+
+  // Launch j of an adjoint separable march (real fields, ny = nz = N, the source added
+  // before each store; the march's last entry has no Bnext).
+  template <int N>
+  static cudaError_t sep_adj_launch_n(const BatchStep* ss, int nx, int j, int* err, cudaStream_t sm) {
+    if (j >= 1 && (j & 1)) {
+      if (nx == 128) return launch_sep_x<128, N, 1, 0, 0, 1>(ss, 1, sm);
+      if (nx == 64) return launch_sep_x<64, N, 1, 0, 0, 1>(ss, 1, sm);
+      return cudaErrorNotSupported;
+    }
+    return j == 0 ? launch_sep_plane<N, 0, 1>(ss, nx, 1, err, sm) : launch_sep_plane<N, 1, 1>(ss, nx, 1, err, sm);
+  }
+  cudaError_t sep_adj_launch(CtxData& c, const BatchStep* ss, int j, cudaStream_t sm) {
+    if constexpr (!std::is_same<T, float>::value) {
+      return cudaErrorNotSupported;
+    } else {
+      if (c.n[1] == 128) return sep_adj_launch_n<128>(ss, c.n[0], j, c.kerr, sm);
+      if (c.n[1] == 64) return sep_adj_launch_n<64>(ss, c.n[0], j, c.kerr, sm);
+      return cudaErrorNotSupported;
+    }
+  }
+
+  // Reverse-mode adjoint on the separable march (FP32 real fields where plan 2 applies):
+  // the lambda march (adjoint of the q march) and the mu march (of the qd march) are the
+  // separable march run backwards with a source added at every step -- lambda_{k-1} =
+  // B_k K(B_k lambda_k) + a_{k-1} -- on two streams, each storing its history; one pass
+  // over the four histories then forms the gradient (k_adjsep_grad).
+  cudaError_t adjoint_sep(CtxData& c, const double* GA, const double* GB, double* dwp, double* dwm) {
+    const size_t slice = (size_t)c.M * sizeof(float);
+    const int Ns = c.Ns;
+    cudaError_t e;
+    if (!c.adjS) {  // lambda and mu histories (Ns + 1 slices each), gA, gB
+      const size_t bytes = (size_t)(2 * Ns + 4) * slice;
+      if ((e = cudaMalloc(&c.adjS, bytes)) != cudaSuccess) return e;
+      c.bytes += bytes;
+    }
+    float* lam = (float*)c.adjS;
+    float* mu = lam + (size_t)(Ns + 1) * c.M;
+    float* gA = mu + (size_t)(Ns + 1) * c.M;
+    float* gB = gA + c.M;
+    const float* hist = (const float*)c.hist;
+    auto qd = [&](int m) { return m == 0 ? (const float*)c.qd0 : (const float*)c.qdh + (size_t)m * c.M; };
+    auto Bof = [&](int split) { return (const float*)((split <= c.NsA) ? c.BA : c.BB); };
+    if (!c.stepsAS) {  // entries 2(j-1): lambda step j (k = Ns + 1 - j); 2(j-1) + 1: mu step j
+      std::vector<BatchStep> h((size_t)2 * Ns);
+      const char* t = (const char*)c.tables;
+      for (int j = 1; j <= Ns; j++) {
+        BatchStep& f = h[(size_t)2 * (j - 1)];
+        BatchStep& b = h[(size_t)2 * (j - 1) + 1];
+        memset(&f, 0, sizeof(f));
+        memset(&b, 0, sizeof(b));
+        const int k = Ns + 1 - j, m = Ns + 1 - j;
+        double cA, cB;
+        f.spec = c.spec;
+        f.in = lam + (size_t)Ns * c.M;
+        f.B = Bof(k);
+        f.out = lam + (size_t)(k - 1) * c.M;
+        if (k - 1 >= 1) f.Bnext = Bof(k - 1);
+        f.partner = qd(Ns - k + 1);
+        trapezoid_weight(k - 1, Ns, c.NsA, &cA, &cB);
+        f.cA = cA;
+        f.cB = cB;
+        b.spec = c.spec2;
+        b.in = mu + (size_t)Ns * c.M;
+        b.B = Bof(Ns + 1 - m);
+        b.out = mu + (size_t)(m - 1) * c.M;
+        if (m - 1 >= 1) b.Bnext = Bof(Ns + 2 - m);
+        b.partner = hist + (size_t)(Ns - m + 1) * c.M;
+        trapezoid_weight(Ns - m + 1, Ns, c.NsA, &cA, &cB);
+        b.cA = cA;
+        b.cB = cB;
+        f.accA = b.accA = gA;
+        f.accB = b.accB = gB;
+        for (int x = 0; x < 4; x++) f.tw[x] = b.tw[x] = t + c.tw_off[x];
+        for (int x = 0; x < 3; x++) f.d[x] = b.d[x] = t + c.sd_off[x];
+      }
+      if ((e = cudaMalloc(&c.stepsAS, h.size() * sizeof(BatchStep))) != cudaSuccess) return e;
+      c.bytes += h.size() * sizeof(BatchStep);
+      if ((e = cudaMemcpy(c.stepsAS, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e;
+    }
+    double cAl, cBl, cAm, cBm;
+    trapezoid_weight(Ns, Ns, c.NsA, &cAl, &cBl);
+    trapezoid_weight(0, Ns, c.NsA, &cAm, &cBm);
+    k_adjsep_init<<<c.npart, PW_THREADS, 0, c.stream>>>(GA, GB, c.scal, c.ds, gA, gB, lam + (size_t)Ns * c.M,
+                                                        mu + (size_t)Ns * c.M, qd(0), hist, (float)cAl, (float)cBl,
+                                                        (float)cAm, (float)cBm, c.M);
+    k_adjoint_gamma<<<c.npart, PW_THREADS, 0, c.stream>>>(GA, GB, (const double*)c.accA, (const double*)c.accB, c.M,
+                                                          c.partials);
+    k_reduce_final<2><<<1, PW_THREADS, 0, c.stream>>>(c.partials, c.npart, c.scal + S_GAMMA);
+    if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream2, c.fork_ev, 0)) != cudaSuccess) return e;
+    for (int ch = 0; ch < 2; ch++) {
+      cudaStream_t sm = ch ? c.stream2 : c.stream;
+      for (int j = 0; j <= Ns; j++) {
+        const BatchStep* ss = (const BatchStep*)c.stepsAS + (size_t)2 * (j == 0 ? 0 : j - 1) + ch;
+        if ((e = sep_adj_launch(c, ss, j, sm)) != cudaSuccess) return e;
+      }
+    }
+    if ((e = cudaEventRecord(c.join_ev, c.stream2)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
+    k_adjsep_grad<<<c.npart, PW_THREADS, 0, c.stream>>>(lam, mu, hist, (const float*)c.qdh, (const float*)c.qd0, gA, gB,
+                                                        (const double*)c.accA, (const double*)c.accB,
+                                                        c.scal + S_GAMMA, 1.0 / (double)c.M, c.ds, Ns, c.NsA, c.M,
+                                                        dwp, dwm);
+    return cudaGetLastError();
   }
 
   // A whole separable march of `members` chains whose step-1 entry is st (entries of
@@ -863,6 +970,7 @@ class EngineT : public Engine {
   // y, x (D), y inverse and z inverse passes (no final factor), then k_adjoint_update.
   cudaError_t adjoint(CtxData& c, const double* GA, const double* GB, double* dwp, double* dwm) override {
     if (c.kind != PFT_SCFT_REAL || !c.qdh) return cudaErrorNotSupported;
+    if (c.plan_plane == 2 && sep_supported(c) && c.M % 4 == 0) return adjoint_sep(c, GA, GB, dwp, dwm);
     const size_t slice = (size_t)c.M * sizeof(T);
     cudaError_t e;
     if (!c.adj) {  // lambda and mu ping-pong, the two z slices, four FP64 accumulators

@@ -76,7 +76,10 @@ template <int N> struct XSepRow {
 // MODE 2: last launch (Ky, Kz, x B_Ns, store q_Ns).
 // The field plane st.spec[p] is read and written in place.  Per-axis factors:
 // st.d[1] = dy, st.d[2] = dz (full length, 1/n folded in); twiddles st.tw[1] (length N).
-template <int N, int MODE>
+// ADJ 1: the adjoint march of Eq. 13's steps (reverse mode): after x B_s the source of the
+// step, (cA gA + cB gB) * partner, is added before the store (st.accA, st.accB hold the
+// FP32 arrays gA, gB; st.partner the paired history slice; no source where partner is null).
+template <int N, int MODE, int ADJ = 0>
 __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const BatchStep* __restrict__ st, int* err) {
   using R = SepCfg<N>;
   constexpr int E = R::E, TPC = R::TPC, LINES = R::LINES, H = N / 2;
@@ -162,12 +165,22 @@ __global__ void __launch_bounds__(SepCfg<N>::THREADS, 1) kb_sep_plane(const Batc
     const bool same = (s.Bnext == s.B);
     const float* Bn = reinterpret_cast<const float*>(s.Bnext) + pbase;
     float* q = reinterpret_cast<float*>(s.out) + pbase;
+    const bool src = ADJ && MODE != 0 && s.partner;
+    const float* sp = reinterpret_cast<const float*>(s.partner) + pbase;
+    const float* gA = reinterpret_cast<const float*>(s.accA) + pbase;
+    const float* gB = reinterpret_cast<const float*>(s.accB) + pbase;
+    const float cA = (float)s.cA, cB = (float)s.cB;
 #pragma unroll
     for (int i = 0; i < E; i++) {
       const int k = t + TPC * i;
       const float ba = Bs[L * R::BPITCH + k], bb = Bs[(L + H) * R::BPITCH + k];
       v[i].x *= ba;
       v[i].y *= bb;
+      if (src) {
+        const long long ra = (long long)L * N + k, rb = (long long)(L + H) * N + k;
+        v[i].x += (cA * gA[ra] + cB * gB[ra]) * sp[ra];
+        v[i].y += (cA * gA[rb] + cB * gB[rb]) * sp[rb];
+      }
       if (MODE != 0) {
         q[(long long)L * N + k] = v[i].x;
         q[(long long)(L + H) * N + k] = v[i].y;
@@ -227,7 +240,7 @@ template <int NX, class XPL> struct SepXCfg {
   static constexpr int THREADS = 16 * XPL::TPC;
   static constexpr int MINB = THREADS <= 128 ? 4 : 3;
 };
-template <int NX, int NYZ, int MODE, int C = 16, int KIND = 0, class XPL = Plan<NX>>
+template <int NX, int NYZ, int MODE, int C = 16, int KIND = 0, class XPL = Plan<NX>, int ADJ = 0>
 __global__ void __launch_bounds__(SepXCfg<NX, XPL>::THREADS, SepXCfg<NX, XPL>::MINB) kb_sep_x(const BatchStep* __restrict__ st) {
   static_assert(C == 16, "sixteen lines a CTA");
   // lines per x-plane: column pairs (real) or columns (complex) of the ny = nz = NYZ plane
@@ -279,11 +292,21 @@ __global__ void __launch_bounds__(SepXCfg<NX, XPL>::THREADS, SepXCfg<NX, XPL>::M
     const bool same = (s.Bnext == s.B);
     const float2* Bn2 = reinterpret_cast<const float2*>(s.Bnext);
     float2* q2 = reinterpret_cast<float2*>(s.out);
+    const bool src = ADJ && s.partner;  // the adjoint's source (real fields): (cA gA + cB gB) partner
+    const float2* sp2 = reinterpret_cast<const float2*>(s.partner);
+    const float2* gA2 = reinterpret_cast<const float2*>(s.accA);
+    const float2* gB2 = reinterpret_cast<const float2*>(s.accB);
+    const float cA = (float)s.cA, cB = (float)s.cB;
 #pragma unroll
     for (int i = 0; i < E; i++) {
       const long long o = (long long)(t + TPC * i) * P + colc;
       const float2 b = Bt[(t + TPC * i) * C + c];
       v[i] = sepp_mul<KIND>(v[i], b);
+      if (src) {
+        const float2 ga = gA2[o], gb = gB2[o], pp = sp2[o];
+        v[i].x += (cA * ga.x + cB * gb.x) * pp.x;
+        v[i].y += (cA * ga.y + cB * gb.y) * pp.y;
+      }
       q2[o] = v[i];
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn2[o]);
     }

@@ -107,24 +107,27 @@ def test_adjoint_refuses_what_it_does_not_cover():
         assert ei.value.status == pft.PFT_ERR_UNSUPPORTED
 
 
-@pytest.mark.parametrize("prec", [FP64, FP32])
-def test_adjoint_128cubed_matches_oracle(prec):
-    """128^3 gyroid workload, Ns = 20, a linear loss: the FP32-mixed adjoint runs the
-    fused adjoint step on the plane kernel, FP64 the pencil passes; both against the
-    oracle's adjoint_field_gradient over every grid point."""
+@pytest.mark.parametrize("prec,plan", [(FP64, None), (FP32, None), (FP32, 1)])
+def test_adjoint_128cubed_matches_oracle(prec, plan):
+    """128^3 gyroid workload, Ns = 20, a linear loss: the FP32-mixed adjoint on the
+    separable march (the default: both adjoint marches store their histories, one pass
+    forms the gradient) and on the plane kernel (plan 1: the fused adjoint step), FP64 on
+    the pencil passes; all against the oracle's adjoint_field_gradient over every point."""
     from paper_1204_5434_gb300 import workloads as wl
     w = wl.GYR128.with_(Ns=20)
     wp, wm = wl.fields(w)
     rng = np.random.default_rng(12)
     GA, GB = rng.normal(size=w.n), rng.normal(size=w.n)
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, prec, checkpoint=1) as s:
+        if plan is not None:
+            pft.pft_set_plan(s.h, plan, 1)
         s.set_fields(wp, wm)
         s.solve()
         gp, gm = s.adjoint(GA, GB)
         if prec == FP32:
-            assert pft.pft_get_plan(s.h)[0] >= 1
+            assert pft.pft_get_plan(s.h)[0] == (2 if plan is None else plan)
     ep, em = o.adjoint_field_gradient(wp, wm, w.n, w.L, w.Ns, w.fA, GA, GB)
     scale = max(np.max(np.abs(ep)), np.max(np.abs(em)))
     err = max(np.max(np.abs(gp - ep)), np.max(np.abs(gm - em))) / scale
-    print(f"\nadjoint 128^3 Ns=20 prec={prec} vs oracle: rel err {err:.2e}")
+    print(f"\nadjoint 128^3 Ns=20 prec={prec} plan={plan} vs oracle: rel err {err:.2e}")
     assert err <= (1e-11 if prec == FP64 else 1e-4)
