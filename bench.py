@@ -44,14 +44,19 @@ BYTES_PER_UNIT = {"fp32": 22.0, "fp64": 36.0}
 # 5 N log2 N convention; one contour step does a forward and an inverse one, plus about 6
 # pointwise flops (two Boltzmann multiplies, the diffusion multiply, the quadrature update).
 FP64_NOMINAL_TFLOPS = 1.25
-# DRAM traffic of one contour step of one propagator on the FP32 128^3 path (plane kernel
-# + x pass, steady state inside a block): dram__bytes_read.sum + dram__bytes_write.sum from
-# one ncu capture of the kernels built from the sources below.  Reported as null once any
-# of them changes.
-TRAFFIC_FP32 = {"bytes_per_contour_step": 16.943360e6 + 0.0 + 8.543488e6,
-                "sources": ("paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
-                            "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_fft.cuh"),
-                "sha256": "5bf2efea65550e9b9e41ae536b150f5cb45c210cc445190db20227d64b33e068"}
+# DRAM traffic of one launch of the separable march (one contour step of one
+# propagator: a plane kernel or an x kernel in turn) on the FP32 128^3 path in steady state:
+# dram__bytes_read.sum + dram__bytes_write.sum averaged over 60 consecutive launches of
+# the second warm-up update of the bench workload, captured with caches left as the
+# previous launches left them (so each launch is charged with the write-backs its stores
+# cause).  Reads are nearly nil (the field and both factors stay in L2); the writes are the
+# q slices.  Valid only for the kernel sources it was taken on: null once any changes.
+TRAFFIC_FP32 = {"bytes_per_contour_step": 8601062.4,
+                "sources": ("paper_1204_5434_gb300/csrc/pft_sep.cuh", "paper_1204_5434_gb300/csrc/pft_sepp.cuh",
+                            "paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_tma.cuh",
+                            "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
+                            "paper_1204_5434_gb300/csrc/pft_fft.cuh"),
+                "sha256": "89a65bb531cc632d589d5df072455b9fe17cf834a483cfa331c55e64400bfc20"}
 
 
 def _traffic_fp32():
@@ -588,12 +593,14 @@ def run(args):
         achieved = bpu * WORK.M / (step_ms * 1e-3) / 1e9
         top = max(prof["kinds"].items(), key=lambda kv: kv[1]["ms"])
         if prec_name == "fp32":
-            roof = {"bound": "hbm", "kernel": "pair step (both propagators): plane kernel (y, z in shared memory) + batched x pass",
+            roof = {"bound": "hbm", "kernel": "separable march: y/z plane kernel and x kernel in turn, one launch a "
+                                              "contour step, both propagators on two streams",
                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                     "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)", "bytes_per_unit": bpu,
                     "units_per_launch": WORK.M, "step_us": step_ms * 1e3, "traffic": _traffic_fp32(),
-                    "traffic_note": "ncu dram bytes of one contour step (plane kernel + x pass) of one "
-                                    "propagator, cold cache; q writes leave L2 after the kernel"}
+                    "traffic_note": "ncu dram read + write bytes per launch (one contour step of one "
+                                    "propagator) in steady state, caches not flushed between launches; the "
+                                    "field and both factors stay in L2, the writes are the q slices"}
         else:
             fpu = fp64_flops_per_unit(WORK.M)
             tf = fpu * WORK.M / (step_ms * 1e-3) / 1e12
