@@ -39,10 +39,12 @@ WORK = wl.GYR128
 # (3e+f+2a).  Mean (5e+2f+2a)/2 with e=f=4, a=8 (FP32-mixed) or e=f=a=8 (FP64), real fields.
 BYTES_PER_UNIT = {"fp32": 22.0, "fp64": 36.0}
 # FP64 is bound by the GB300 FP64 pipe, whose rate is measured live (pft_fma_throughput,
-# a DFMA loop over every SM) as the denominator of the FP64 roofline.  Flops per unit: a
-# real-to-half-spectrum 3D transform costs 2.5 log2(M) flops per point in the usual
-# 5 N log2 N convention; one contour step does a forward and an inverse one, plus about 6
-# pointwise flops (two Boltzmann multiplies, the diffusion multiply, the quadrature update).
+# a DFMA loop over every SM) as the denominator of the FP64 roofline.  Flops per unit: in the
+# usual 5 N log2 N convention a length-n complex transform of two paired real lines costs
+# 2.5 log2(n) flops per real point, so the separable march's forward and inverse transform
+# along each of the three axes cost 5 log2(M) per point and contour step -- the same count
+# as a real-to-half-spectrum 3D transform pair -- plus about 6 pointwise flops (two
+# Boltzmann multiplies, the diffusion multiplies, the quadrature update).
 FP64_NOMINAL_TFLOPS = 1.25
 # DRAM traffic of one launch of the separable march (one contour step of one
 # propagator: a plane kernel or an x kernel in turn) on the FP32 128^3 path in steady state:
@@ -605,7 +607,7 @@ def run(args):
             fpu = fp64_flops_per_unit(WORK.M)
             tf = fpu * WORK.M / (step_ms * 1e-3) / 1e12
             dfma = pft.pft_fma_throughput(pft.PFT_FP64)
-            roof = {"bound": "alu", "kernel": "pair step (both propagators): batched y, x (D), y inverse, fused z passes; FP64 pipe",
+            roof = {"bound": "alu", "kernel": "separable march on pencils: a y launch and an x or z launch per contour step; FP64 pipe",
                     "achieved": tf, "peak": dfma, "unit": "TFLOP/s", "frac": tf / dfma,
                     "peak_source": f"measured DFMA throughput of this GPU (pft_fma_throughput; nominal "
                                    f"{FP64_NOMINAL_TFLOPS} TFLOP/s)",
