@@ -289,12 +289,15 @@ def _variable_cell(pft, torch, prec, steps, warmup, wpa, wma, lam_L=0.05):
             "timing": "host wall clock around synchronised steps (the gradient call reads back 3 scalars)"}
 
 
-def _cl(pft, torch, w, prec, steps, warmup=1, checkpoint=0):
+def _cl(pft, torch, w, prec, steps, warmup=1, checkpoint=0, plan=None):
     """Complex Langevin field updates (solve + Euler-Maruyama step with the device Philox
     noise) of a complex-field workload, timed with CUDA events on the context stream.
-    checkpoint K >= 2 keeps every K-th q slice and recomputes segments (one extra march)."""
+    checkpoint K >= 2 keeps every K-th q slice and recomputes segments (one extra march);
+    plan: (code, streams) for pft_set_plan, else the context's default."""
     s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, pft.PFT_CL_COMPLEX, prec, seed=w.seed, checkpoint=checkpoint)
     h = s.h
+    if plan is not None:
+        pft.pft_set_plan(h, *plan)
     wp, wm = wl.fields(w)
     pft.pft_set_fields(h, wp, wm)
 
@@ -316,19 +319,20 @@ def _cl(pft, torch, w, prec, steps, warmup=1, checkpoint=0):
     obs = pft.pft_get_observables(h)
     mem = pft.pft_memory_bytes(h)
     hist_k = pft.pft_get_checkpoint(h)
+    plan_used = list(pft.pft_get_plan(h))
     s.close()
     units = 2 * w.M * w.Ns
     bpu = 44.0 if prec == pft.PFT_FP32_MIXED else 72.0
     peak, _ = _peaks()
     return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT,
             "hbm_roofline_frac": bpu * units / (ms * 1e-3) / 1e9 / peak, "bytes_per_unit": bpu,
-            "device_bytes": mem, "history_interval": hist_k,
+            "device_bytes": mem, "history_interval": hist_k, "plan": plan_used,
             "H_last": [obs["H"].real, obs["H"].imag]}
 
 
-def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, step_size=None):
-    """Field updates of a workload with another contour scheme or field-step kind, timed
-    with CUDA events on the context stream (fields resident on the device)."""
+def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, step_size=None, plan=None):
+    """Field updates of a workload with another contour scheme, field-step kind or march
+    plan, timed with CUDA events on the context stream (fields resident on the device)."""
     kind = pft.PFT_SCFT_REAL if w.kind == wl.SCFT else pft.PFT_CL_COMPLEX
     if step_kind is None:
         step_kind = pft.PFT_STEP_SCFT_EULER if kind == pft.PFT_SCFT_REAL else pft.PFT_STEP_CL_EULER_MARUYAMA
@@ -337,6 +341,8 @@ def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, ste
     arch = pft.PFT_ARCH_EDWARDS if w.arch == "edwards" else pft.PFT_ARCH_DIBLOCK
     s = pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, kind, prec, seed=w.seed, scheme=scheme, arch=arch, B=w.B)
     h = s.h
+    if plan is not None:
+        pft.pft_set_plan(h, *plan)
     wp, wm = wl.fields(w)
     pft.pft_set_fields(h, wp, wm)
 
@@ -355,9 +361,10 @@ def _variant(pft, torch, w, prec, steps, warmup=1, scheme=0, step_kind=None, ste
     e1.record(st)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    plan_used = list(pft.pft_get_plan(h))
     s.close()
     units = (1 if arch == pft.PFT_ARCH_EDWARDS else 2) * w.M * w.Ns  # propagators marched
-    return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT}
+    return {"workload": w.name, "ms_per_step": ms, "value": units / (ms * 1e-3), "unit": UNIT, "plan": plan_used}
 
 
 def _adjoint_time(pft, torch, w, prec, reps=5):
@@ -634,6 +641,10 @@ def run(args):
           "cl64_fp64": _cl(pft, torch, wl.CL64, pft.PFT_FP64, 3),
           "cl256_fp32": _cl(pft, torch, wl.CL256, pft.PFT_FP32_MIXED, 3),
           "cl256_fp64": _cl(pft, torch, wl.CL256, pft.PFT_FP64, 1),
+          # FP64 contexts with the double-float march (plan 4): FP64 history, quadrature and
+          # update, the march's arithmetic as pairs of floats on the FP32 pipe
+          "cl64_fp64_double_float": _cl(pft, torch, wl.CL64, pft.PFT_FP64, 5, plan=(4, 1)),
+          "cl256_fp64_double_float": _cl(pft, torch, wl.CL256, pft.PFT_FP64, 1, plan=(4, 1)),
           "cl256_fp32_checkpoint14": _cl(pft, torch, wl.CL256, pft.PFT_FP32_MIXED, 2, checkpoint=14)}
     torch.cuda.empty_cache()
     variants = {
@@ -652,7 +663,16 @@ def run(args):
         "edwards_scft128_fp32": _variant(pft, torch, wl.EDW128, pft.PFT_FP32_MIXED, 10),
         "edwards_cl128_fp32": _variant(pft, torch, wl.EDWCL128, pft.PFT_FP32_MIXED, 10),
         "adjoint_fp32": _adjoint_time(pft, torch, WORK, pft.PFT_FP32_MIXED),
+        # the FP64 line's workload with the double-float march (plan 4, two-member launches)
+        "fp64_double_float": _variant(pft, torch, WORK, pft.PFT_FP64, max(3, args.steps // 4), warmup=2, plan=(4, 0)),
     }
+    ddv = variants["fp64_double_float"]
+    ddv["fp64_equivalent_TFLOPs"] = fp64_flops_per_unit(WORK.M) * ddv["value"] / 1e12
+    ddv["over_measured_dfma_peak"] = ddv["fp64_equivalent_TFLOPs"] / pft.pft_fma_throughput(pft.PFT_FP64)
+    ddv["speedup_over_ieee_fp64"] = res["fp64"]["ms_per_step"] / ddv["ms_per_step"]
+    ddv["note"] = ("FP64 context, march in double-float arithmetic (value = hi + lo of two floats, about 48 "
+                   "significant bits, FP32 pipe); FP64 history, quadrature, reductions and update; parity "
+                   "against the FP64 oracle at the FP64 tolerances (tests/test_gpu_double_float.py)")
     torch.cuda.empty_cache()
     lib_fft = _library_fft_step(torch, wpa, wma)
     torch.cuda.empty_cache()

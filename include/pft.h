@@ -413,7 +413,10 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
  * plane kernel or an x kernel in turn -- advances one contour step; 3 = the separable
  * march on pencils (complex fields, real fields with ny and nz even; either precision):
  * per contour step one launch of the y convolution and one of the x or z kernel, which
- * carries the two convolutions of consecutive steps along its axis; 18 = plan 2 with the x
+ * carries the two convolutions of consecutive steps along its axis; 4 = plan 3 of an FP64
+ * context in double-float arithmetic (each value an unevaluated sum of two floats, about
+ * 48 significant bits, computed on the FP32 pipe; the history, the quadrature and
+ * everything after the march stay FP64); 18 = plan 2 with the x
  * kernel on half the elements a thread (twice the threads, one more exchange: at nx = 128
  * eight elements and radices 8, 4, 4 instead of 16 and 16, 8).  *streams = 1 if the
  * two propagators run as two chains on two streams.  Either pointer may be NULL.

@@ -123,7 +123,7 @@ void free_all(pft_ctx* c) {
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
                   d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.kerr, d.qdh, d.steps2, d.stepsS, d.stepsg,
-                  d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa, d.stepsap, d.adjS, d.stepsAS};
+                  d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa, d.stepsap, d.adjS, d.stepsAS, d.ddbuf, d.stepsD};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);
@@ -871,14 +871,16 @@ pft_status pft_set_plan(pft_ctx* ctx, int code, int streams) {
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
   const int plane = code & 15, xv = code >> 4;
-  if (code < 0 || plane > 3 || xv > 1 || (xv && plane != 2) || streams < 0 || streams > 1)
-    return fail(PFT_ERR_ARG, "plan code in {0, 1, 2, 3, 18}, streams in {0, 1}");
+  if (code < 0 || plane > 4 || xv > 1 || (xv && plane != 2) || streams < 0 || streams > 1)
+    return fail(PFT_ERR_ARG, "plan code in {0, 1, 2, 3, 4, 18}, streams in {0, 1}");
   if (plane == 1 && !ctx->eng->plane_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the plane kernel needs FP32 with ny = nz = 64 or 128 (real) or 64 (complex)");
   if (plane == 2 && !ctx->eng->sep_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the separable march needs FP32 real fields, ny = nz and nx in {64, 128}");
   if (plane == 3 && !ctx->eng->sepp_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the separable pencil march needs ny and nz even for real fields");
+  if (plane == 4 && !ctx->eng->dd_applies(d))
+    return fail(PFT_ERR_UNSUPPORTED, "the double-float march needs an FP64 context and ny, nz even for real fields");
   d.plan_plane = plane;
   d.plan_xv = xv;
   d.plan_streams = streams;

@@ -97,6 +97,13 @@ struct CtxData {
   void* qdh = nullptr;      // [(Ns+1) * M] qd_0..qd_Ns (slice 0 unused: qd0 holds it)
   void* steps2 = nullptr;   // [2 * Ns] BatchStep: forward and conjugate step s
   void* stepsS = nullptr;   // [2 * Ns] the same steps with the separable march's tables
+  // double-float separable march (plan 4, FP64 contexts): dd twiddles and per-axis factors,
+  // the Boltzmann factors split into dd, and the step entries pointing at them
+  void* ddbuf = nullptr;
+  size_t ddtw_off[3] = {0, 0, 0};
+  size_t ddsd_off[3] = {0, 0, 0};
+  size_t ddB_off[2] = {0, 0};
+  void* stepsD = nullptr;   // [2 * Ns]
   void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
   // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
   // scratch slices for the full and the two half steps, quadrature weight tables
@@ -179,6 +186,8 @@ struct SeppGeom {
 // ny and nz even.  Returns cudaErrorInvalidValue for a length without an FFT plan.
 cudaError_t sepp_launch_f32(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm);
 cudaError_t sepp_launch_f64(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm);
+// the same march in double-float arithmetic (FP64 history, dd tables and factors)
+cudaError_t sepp_launch_dd(const SeppGeom& g, const BatchStep* ss, int j, int members, cudaStream_t sm);
 
 class Engine {
  public:
@@ -186,7 +195,8 @@ class Engine {
   virtual size_t elem_bytes() const = 0;      // working-precision real element
   virtual bool plane_applies(const CtxData& c) const = 0;  // can the y/z plane kernel run this grid?
   virtual bool sep_applies(const CtxData& c) const = 0;    // can the separable march run it?
-  virtual bool sepp_applies(const CtxData& c) const = 0;   // can the separable pencil march run it?
+  virtual bool sepp_applies(const CtxData& c) const = 0;
+  virtual bool dd_applies(const CtxData& c) const = 0;     // the double-float separable march (plan 4)?   // can the separable pencil march run it?
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

@@ -11,6 +11,7 @@
 #include "pft_engine.h"
 #include "pft_passes.cuh"
 #include "pft_narrow.cuh"
+#include "pft_dd.cuh"
 
 namespace pft {
 
@@ -175,6 +176,13 @@ __global__ void __launch_bounds__(PW_THREADS) k_rqm4_combine(const T* __restrict
                                                               T* __restrict__ out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     out[i] = (T(4) * half2[i] - full[i]) / T(3);
+}
+
+// FP64 values split into double-float pairs (the Boltzmann factors of the double-float
+// march, once per solve; n doubles, real and imaginary parts alike).
+static __global__ void k_split_dd(const double* __restrict__ a, dd* __restrict__ out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = dd_from_double(a[i]);
 }
 
 template <typename W> __global__ void k_fill_one(W* __restrict__ dst, long long M) {

@@ -87,6 +87,7 @@ class EngineT : public Engine {
   bool plane_applies(const CtxData& c) const override { return plane_supported(c); }
   bool sep_applies(const CtxData& c) const override { return sep_supported(c); }
   bool sepp_applies(const CtxData& c) const override { return sepp_supported(c); }
+  bool dd_applies(const CtxData& c) const override { return dd_supported(c); }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -491,9 +492,88 @@ class EngineT : public Engine {
         c.bytes += h.size() * sizeof(BatchStep);
         e = cudaMemcpy(c.stepsS, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return e;
+        if (dd_supported(c) && (e = prepare_dd(c, h)) != cudaSuccess) return e;
       }
     }
     return cudaSuccess;
+  }
+
+  // ---------------------------------------------------------------- double-float march
+  // Plan 4 of an FP64 context: the separable pencil march with every transform, diffusion
+  // and Boltzmann product in double-float arithmetic on the FP32 pipe; q_0 and the stored
+  // q_s stay FP64, so everything after the march (quadrature, densities, H, gradients) is
+  // the FP64 path's.
+  static bool dd_supported(const CtxData& c) { return std::is_same<T, double>::value && sepp_supported(c); }
+
+  // Tables (twiddles of the three axes, the per-axis factors exp(-k_a^2 ds)/n_a, split from
+  // their FP64 values), the two split Boltzmann factors, and the step entries (from the
+  // separable march's entries h, with B, twiddles and factors redirected).
+  cudaError_t prepare_dd(CtxData& c, std::vector<BatchStep> h) {
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t be = (c.kind == PFT_SCFT_REAL ? sizeof(dd) : sizeof(dd2)) * (size_t)c.M;
+    size_t off = 0;
+    for (int a = 0; a < 3; a++) {
+      c.ddtw_off[a] = off;
+      off = al(off + sizeof(dd2) * (size_t)c.n[a]);
+    }
+    for (int a = 0; a < 3; a++) {
+      c.ddsd_off[a] = off;
+      off = al(off + sizeof(dd) * (size_t)c.n[a]);
+    }
+    const size_t tab = off;
+    for (int b = 0; b < 2; b++) {
+      c.ddB_off[b] = off;
+      off = al(off + be);
+    }
+    cudaError_t e;
+    if (!c.ddbuf) {
+      if ((e = cudaMalloc(&c.ddbuf, off)) != cudaSuccess) return e;
+      c.bytes += off;
+    }
+    std::vector<unsigned char> t(tab, 0);
+    for (int a = 0; a < 3; a++) {
+      const int na = c.n[a];
+      dd2* tw = reinterpret_cast<dd2*>(t.data() + c.ddtw_off[a]);
+      dd* sd = reinterpret_cast<dd*>(t.data() + c.ddsd_off[a]);
+      for (int m = 0; m < na; m++) {
+        const double ang = -2.0 * M_PI * (double)m / (double)na;
+        tw[m].x = dd_split_host(cos(ang));
+        tw[m].y = dd_split_host(sin(ang));
+        const int mm = (m <= na / 2) ? m : m - na;
+        const double k = 2.0 * M_PI * (double)mm / c.L[a];
+        sd[m] = dd_split_host(exp(-k * k * c.ds) / (double)na);
+      }
+    }
+    if ((e = cudaMemcpy(c.ddbuf, t.data(), tab, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+    char* base = (char*)c.ddbuf;
+    auto mapB = [&](const void* B) -> const void* {
+      if (B == nullptr) return nullptr;
+      return base + (B == c.BA ? c.ddB_off[0] : c.ddB_off[1]);
+    };
+    for (auto& b : h) {
+      b.B = mapB(b.B);
+      b.Bnext = mapB(b.Bnext);
+      for (int a = 0; a < 3; a++) {
+        b.tw[a] = base + c.ddtw_off[a];
+        b.d[a] = base + c.ddsd_off[a];
+      }
+      b.tw[3] = nullptr;
+    }
+    if (!c.stepsD) {
+      if ((e = cudaMalloc(&c.stepsD, h.size() * sizeof(BatchStep))) != cudaSuccess) return e;
+      c.bytes += h.size() * sizeof(BatchStep);
+    }
+    return cudaMemcpy(c.stepsD, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+  }
+
+  // The split Boltzmann factors of this solve (first launches of the solve's graph).
+  cudaError_t split_dd(CtxData& c) {
+    const long long n = (c.kind == PFT_SCFT_REAL ? 1 : 2) * c.M;
+    char* base = (char*)c.ddbuf;
+    k_split_dd<<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.BA, (dd*)(base + c.ddB_off[0]), n);
+    if (c.BB && c.BB != c.BA)
+      k_split_dd<<<c.npart, PW_THREADS, 0, c.stream>>>((const double*)c.BB, (dd*)(base + c.ddB_off[1]), n);
+    return cudaGetLastError();
   }
 
   // ---------------------------------------------------------------- separable march
@@ -509,8 +589,9 @@ class EngineT : public Engine {
     for (int j = 0; j <= c.Ns; j++) {
       if (members == 2) mark(c, KK_PAIR_STEP);
       const BatchStep* ss = st + (size_t)2 * (j == 0 ? 0 : j - 1);
-      cudaError_t e = std::is_same<T, float>::value ? sepp_launch_f32(g, ss, j, members, sm)
-                                                     : sepp_launch_f64(g, ss, j, members, sm);
+      cudaError_t e = c.plan_plane == 4 ? sepp_launch_dd(g, ss, j, members, sm)
+                      : std::is_same<T, float>::value ? sepp_launch_f32(g, ss, j, members, sm)
+                                                      : sepp_launch_f64(g, ss, j, members, sm);
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -738,6 +819,7 @@ class EngineT : public Engine {
     g.nzh = c.nzh;
     const BatchStep* st = (const BatchStep*)c.steps2;
     cudaError_t e;
+    if (c.plan_plane == 4 && c.stepsD && (e = split_dd(c)) != cudaSuccess) return e;
     if (c.edw) {  // one reversible chain: the forward march is the whole solve
       if ((e = march_chain(c, g, st, c.stream)) != cudaSuccess) return e;
       return finish_concurrent(c);
@@ -757,6 +839,10 @@ class EngineT : public Engine {
     }
     if (c.plan_plane == 3 && c.stepsS) {  // separable pencil march, both propagators per launch
       if ((e = sepp_march(c, (const BatchStep*)c.stepsS, 2, c.stream)) != cudaSuccess) return e;
+      return finish_concurrent(c);
+    }
+    if (c.plan_plane == 4 && c.stepsD) {  // the same in double-float arithmetic
+      if ((e = sepp_march(c, (const BatchStep*)c.stepsD, 2, c.stream)) != cudaSuccess) return e;
       return finish_concurrent(c);
     }
     if (c.plan_plane == 2 && c.stepsS) {  // separable march, both propagators per launch
@@ -806,6 +892,10 @@ class EngineT : public Engine {
     }
     if (c.plan_plane == 3 && c.stepsS) {  // separable pencil march: two launches per step
       const BatchStep* ss = (const BatchStep*)c.stepsS + (st - (const BatchStep*)c.steps2);
+      return sepp_march(c, ss, 1, sm);
+    }
+    if (c.plan_plane == 4 && c.stepsD) {  // the same in double-float arithmetic
+      const BatchStep* ss = (const BatchStep*)c.stepsD + (st - (const BatchStep*)c.steps2);
       return sepp_march(c, ss, 1, sm);
     }
     if (plane_supported(c) && c.plan_plane) {
@@ -1359,6 +1449,7 @@ class EngineT : public Engine {
   cudaError_t enqueue_solve(CtxData& c) override {
     if ((c.plan_plane == 1 || c.plan_plane == 2) && !plane_supported(c)) c.plan_plane = sepp_supported(c) ? 3 : 0;
     if (c.plan_plane == 3 && !sepp_supported(c)) c.plan_plane = 0;
+    if (c.plan_plane == 4 && !dd_supported(c)) c.plan_plane = sepp_supported(c) ? 3 : 0;
     if (c.scheme == 1) {
       cudaError_t e = prepare_rqm4(c);
       if (e != cudaSuccess) return e;

@@ -13,10 +13,32 @@
 // Lines: complex fields (KIND 1) transform each line; real fields (KIND 0) carry two real
 // lines as one complex line a + i b -- along x and y the pair (z, z+1) (a complex element
 // of the field viewed as pairs), along z the rows (y, y+1) of one x-plane.
+// Arithmetic: float, double, or double-float (dd, pft_dd.cuh: an FP64 context's march on
+// the FP32 pipe).  The working field between launches, the Boltzmann factors and the
+// tables are in the working type; q_0 and the stored q_s are in the history's type
+// (SeppHist: the working type, or FP64 for double-float).
 #pragma once
+#include <type_traits>
+
 #include "pft_batch.cuh"
+#include "pft_dd.cuh"
 
 namespace pft {
+
+template <typename T> struct SeppHist { using S = T; };
+template <> struct SeppHist<dd> { using S = double; };
+template <typename T> __device__ __forceinline__ T hist_in(typename SeppHist<T>::S x) {
+  if constexpr (std::is_same<T, dd>::value) return dd_from_double(x); else return x;
+}
+template <typename T> __device__ __forceinline__ typename SeppHist<T>::S hist_out(T x) {
+  if constexpr (std::is_same<T, dd>::value) return dd_to_double(x); else return x;
+}
+template <typename T> __device__ __forceinline__ cpx<T> hist_in_c(cpx<typename SeppHist<T>::S> z) {
+  return mk<T>(hist_in<T>(z.x), hist_in<T>(z.y));
+}
+template <typename T> __device__ __forceinline__ cpx<typename SeppHist<T>::S> hist_out_c(cpx<T> z) {
+  return mk<typename SeppHist<T>::S>(hist_out<T>(z.x), hist_out<T>(z.y));
+}
 
 // x B for one element: componentwise for real pairs, complex product for complex fields.
 template <int KIND, typename Z>
@@ -35,17 +57,25 @@ __device__ __forceinline__ Z sepp_mul(Z v, Z b) {
 // field, which for real fields are the (z, z+1) pairs).  PW 0: the convolution only; PW 2:
 // conv, x B_s, store q_s, then (if st.Bnext) x B_{s+1}, conv.  AX: the axis (0 x, 1 y)
 // whose twiddles st.tw[AX] and factors st.d[AX] apply.
-// Registers: at most 128 a thread (2 CTAs of 256 threads, 4 of 128 per SM).
+// Registers: at most 128 a thread (2 CTAs of 256 threads, 4 of 128 per SM); double-float
+// (twice the registers a value in flight) at most 255.
+template <typename T> constexpr int sepp_occ() { return std::is_same<T, dd>::value ? 256 : 512; }
+// Transform plan: Plan<N>, except that double-float lines of 128 and 256 points hold 8
+// elements a thread (radices 8, 4, 4 and 8, 8, 4): half the registers of Plan<N>'s 16, at
+// the cost of one more exchange.
+template <typename T, int N> struct SeppPlan { using type = Plan<N>; };
+template <> struct SeppPlan<dd, 128> { using type = PlanX<128, 8, 8, 4, 4>; };
+template <> struct SeppPlan<dd, 256> { using type = PlanX<256, 8, 8, 8, 4>; };
 template <typename T, int N> struct SeppLineCfg {
-  static constexpr int THREADS = Tile<T>::C * Plan<N>::TPC;
-  static constexpr int MINB = (512 / THREADS) > 0 ? 512 / THREADS : 1;
+  static constexpr int THREADS = Tile<T>::C * SeppPlan<T, N>::type::TPC;
+  static constexpr int MINB = (sepp_occ<T>() / THREADS) > 0 ? sepp_occ<T>() / THREADS : 1;
 };
 // Offsets are 32-bit: a field holds fewer than 2^31 complex elements.
 template <typename T, int N, int KIND, int PW, int AX>
 __global__ void __launch_bounds__(SeppLineCfg<T, N>::THREADS, SeppLineCfg<T, N>::MINB)
 kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer, int s_k) {
   using Z = cpx<T>;
-  using PL = Plan<N>;
+  using PL = typename SeppPlan<T, N>::type;
   constexpr int E = PL::E, TPC = PL::TPC, C = Tile<T>::C;
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -71,7 +101,7 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
   if (PW == 2) {
     const Z* B = reinterpret_cast<const Z*>(s.B);
     const Z* Bn = reinterpret_cast<const Z*>(s.Bnext);
-    Z* q = reinterpret_cast<Z*>(s.out);
+    cpx<typename SeppHist<T>::S>* q = reinterpret_cast<cpx<typename SeppHist<T>::S>*>(s.out);
     const bool more = (Bn != nullptr);
     const bool same = (Bn == B);
 #pragma unroll
@@ -79,7 +109,7 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
       const int o = base + i * step;
       const Z b = B[o];
       v[i] = sepp_mul<KIND>(v[i], b);
-      if (valid) q[o] = v[i];
+      if (valid) q[o] = hist_out_c<T>(v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn[o]);
     }
     if (!more) return;
@@ -99,15 +129,22 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
 // PW 1: the first launch of a march (x B_1 on q_0 = st.in, then Kz); PW 2: Kz, x B_s,
 // store q_s, then (if st.Bnext) x B_{s+1}, Kz.
 template <typename T, int N> struct SeppZCfg {
-  static constexpr int THREADS = PencilsPerCta<T, N>::v * Plan<N>::TPC;
-  static constexpr int MINB = (512 / THREADS) > 0 ? 512 / THREADS : 1;
+  using PL = typename SeppPlan<T, N>::type;
+  // pencils per CTA as PencilsPerCta, for this plan's threads per pencil
+  static constexpr int unit = 32 / PL::TPC;
+  static constexpr int by_threads = 256 / PL::TPC;
+  static constexpr int by_smem = (48 * 1024) / (pencil_ld<T>(N) * (int)sizeof(cpx<T>));
+  static constexpr int raw = by_threads < by_smem ? by_threads : by_smem;
+  static constexpr int P = raw >= unit ? raw - raw % unit : unit;
+  static constexpr int THREADS = P * PL::TPC;
+  static constexpr int MINB = (sepp_occ<T>() / THREADS) > 0 ? sepp_occ<T>() / THREADS : 1;
 };
 template <typename T, int N, int KIND, int PW>
 __global__ void __launch_bounds__(SeppZCfg<T, N>::THREADS, SeppZCfg<T, N>::MINB)
 kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
   using Z = cpx<T>;
-  using PL = Plan<N>;
-  constexpr int E = PL::E, TPC = PL::TPC, P = PencilsPerCta<T, N>::v, LD = pencil_ld<T>(N);
+  using PL = typename SeppZCfg<T, N>::PL;
+  constexpr int E = PL::E, TPC = PL::TPC, P = SeppZCfg<T, N>::P, LD = pencil_ld<T>(N);
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];
   const int t = threadIdx.x % TPC;
@@ -137,10 +174,29 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
       f[rb + pos] = z.y;
     }
   };
+  // q_0 and q_s: the history's type
+  using HS = typename SeppHist<T>::S;
+  auto ldh = [&](const void* a, int pos) -> Z {
+    if constexpr (KIND == 1) {
+      return hist_in_c<T>(reinterpret_cast<const cpx<HS>*>(a)[lc * N + pos]);
+    } else {
+      const HS* f = reinterpret_cast<const HS*>(a);
+      return mk<T>(hist_in<T>(f[ra + pos]), hist_in<T>(f[rb + pos]));
+    }
+  };
+  auto sth = [&](void* a, int pos, Z z) {
+    if constexpr (KIND == 1) {
+      reinterpret_cast<cpx<HS>*>(a)[lc * N + pos] = hist_out_c<T>(z);
+    } else {
+      HS* f = reinterpret_cast<HS*>(a);
+      f[ra + pos] = hist_out<T>(z.x);
+      f[rb + pos] = hist_out<T>(z.y);
+    }
+  };
   Z v[E];
   if (PW == 1) {
 #pragma unroll
-    for (int i = 0; i < E; i++) v[i] = sepp_mul<KIND>(ld(s.in, t + TPC * i), ld(s.B, t + TPC * i));
+    for (int i = 0; i < E; i++) v[i] = sepp_mul<KIND>(ldh(s.in, t + TPC * i), ld(s.B, t + TPC * i));
   } else {
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = ld(s.spec, t + TPC * i);
@@ -154,7 +210,7 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
     for (int i = 0; i < E; i++) {
       const Z b = ld(s.B, t + TPC * i);
       v[i] = sepp_mul<KIND>(v[i], b);
-      if (valid) stz(s.out, t + TPC * i, v[i]);
+      if (valid) sth(s.out, t + TPC * i, v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : ld(s.Bnext, t + TPC * i));
     }
     if (!more) return;
@@ -180,16 +236,16 @@ cudaError_t sepp_line_n(const BatchStep* st, long long nlines, long long cin, lo
                         int members, cudaStream_t sm) {
   constexpr int C = Tile<T>::C;
   const dim3 grid((unsigned)((nlines + C - 1) / C), (unsigned)members);
-  kb_sepp_line<T, N, KIND, PW, AX><<<grid, C * Plan<N>::TPC, (size_t)N * C * sizeof(cpx<T>), sm>>>(
+  kb_sepp_line<T, N, KIND, PW, AX><<<grid, SeppLineCfg<T, N>::THREADS, (size_t)N * C * sizeof(cpx<T>), sm>>>(
       st, (int)nlines, (int)cin, (int)s_outer, (int)s_k);
   return cudaGetLastError();
 }
 
 template <typename T, int N, int KIND, int PW>
 cudaError_t sepp_z_n(const BatchStep* st, long long nlines, int members, cudaStream_t sm) {
-  constexpr int P = PencilsPerCta<T, N>::v;
+  constexpr int P = SeppZCfg<T, N>::P;
   const dim3 grid((unsigned)((nlines + P - 1) / P), (unsigned)members);
-  kb_sepp_z<T, N, KIND, PW><<<grid, P * Plan<N>::TPC, (size_t)P * pencil_ld<T>(N) * sizeof(cpx<T>), sm>>>(st, nlines);
+  kb_sepp_z<T, N, KIND, PW><<<grid, SeppZCfg<T, N>::THREADS, (size_t)P * pencil_ld<T>(N) * sizeof(cpx<T>), sm>>>(st, nlines);
   return cudaGetLastError();
 }
 

@@ -422,7 +422,9 @@ def pft_fma_throughput(precision=PFT_FP64, stream=None) -> float:
 
 
 def pft_set_plan(h, plane, streams=1):
-    """Fix the march plan: plane 0 pencils, 1 plane kernel + x pass, 2 separable march."""
+    """Fix the march plan: 0 pencil passes, 1 plane kernel + x pass, 2 separable march on the
+    plane kernel, 3 separable march on pencils, 4 the same in double-float arithmetic (FP64
+    contexts), 18 plan 2 with the alternative x kernel."""
     _check(_lib().pft_set_plan(h, int(plane), int(streams)), "pft_set_plan")
 
 

@@ -1,7 +1,7 @@
 """Complex Langevin over 1000 steps on the 64^3 diblock workload (Euler-Maruyama, Eq. 9,
 real Gaussian noise of Eq. 10 from the device Philox stream with the key and instance
-the oracle used): the FP64 and FP32-mixed GPU trajectories against the FP64 oracle
-trajectory stored by tests/golden/make_cl64_drift.py.
+the oracle used): the FP64 (IEEE and double-float march) and FP32-mixed GPU trajectories
+against the FP64 oracle trajectory stored by tests/golden/make_cl64_drift.py.
 
 Checked: the first steps follow the oracle step for step (identical noise; FP64 to
 1e-10 relative in H, FP32-mixed to 1e-5), and over steps 100..1000 the running means of
@@ -28,12 +28,14 @@ def _built():
     build.build()
 
 
-def _run(prec, ref, steps):
+def _run(prec, ref, steps, plan=None):
     w = wl.CL64
     wp, wm = wl.fields(w)
     rec = {"H": [], "m2A": [], "mAB": []}
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, pft.PFT_CL_COMPLEX, prec, seed=ref["noise_seed"],
                     instance=ref["noise_instance"]) as s:
+        if plan is not None:
+            pft.pft_set_plan(s.h, plan, 1)
         s.set_fields(wp, wm)
         for k in range(steps + 1):
             s.solve()
@@ -60,9 +62,11 @@ def test_cl64_1000_steps_against_the_oracle():
         ref = json.load(f)
     steps = ref["steps"]
     oref = {k: np.array([complex(a, b) for a, b in ref[k]]) for k in ("H", "m2A", "mAB")}
-    runs = {"FP64": _run(pft.PFT_FP64, ref, steps), "FP32-mixed": _run(pft.PFT_FP32_MIXED, ref, steps)}
+    runs = {"FP64": _run(pft.PFT_FP64, ref, steps),
+            "FP64 double-float march": _run(pft.PFT_FP64, ref, steps, plan=4),
+            "FP32-mixed": _run(pft.PFT_FP32_MIXED, ref, steps)}
     # step for step at the start
-    for name, tol in (("FP64", 1e-10), ("FP32-mixed", 1e-5)):
+    for name, tol in (("FP64", 1e-10), ("FP64 double-float march", 1e-10), ("FP32-mixed", 1e-5)):
         h = runs[name]["H"][:6]
         assert np.max(np.abs(h - oref["H"][:6]) / np.abs(oref["H"][:6])) <= tol, name
     # statistics over steps 100..steps

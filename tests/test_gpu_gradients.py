@@ -29,9 +29,10 @@ def fd5(f, h):
     return (8 * (f(h) - f(-h)) - (f(2 * h) - f(-2 * h))) / (12 * h)
 
 
-@pytest.mark.parametrize("prec,tol", [(FP64, 1e-9), (FP32, 2e-4)])
+# FP64 with its default plan and with the double-float march (plan 4) producing the histories
+@pytest.mark.parametrize("prec,tol,plan", [(FP64, 1e-9, None), (FP64, 1e-9, 4), (FP32, 2e-4, None)])
 @pytest.mark.parametrize("n,L,Ns,fA", [((16, 12, 8), (4.0, 3.0, 2.0), 20, 0.35), ((12, 24, 16), (3.0, 6.0, 4.0), 16, 0.5)])
-def test_gradients_match_oracle(n, L, Ns, fA, prec, tol):
+def test_gradients_match_oracle(n, L, Ns, fA, prec, tol, plan):
     chiN, C = 18.0, 2.0
     wp, wm = _fields(n, 31)
     ref = o.solve(wp, wm, n, L, Ns, fA, o.SCFT_REAL)
@@ -40,6 +41,8 @@ def test_gradients_match_oracle(n, L, Ns, fA, prec, tol):
     gH = o.dH_dL(H, ref, C, n, L)
     gp, gm = o.dH_dfields(wp, wm, ref, chiN, C, n, L, o.SCFT_REAL)
     with pft.System(n, L, Ns, fA, chiN, C, SCFT, prec) as s:
+        if plan is not None:
+            pft.pft_set_plan(s.h, plan, 1)
         s.set_fields(wp, wm)
         s.solve()
         a, b, dL, dq = s.gradients()

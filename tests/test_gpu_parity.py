@@ -285,11 +285,15 @@ def test_device_philox_normals_match_oracle():
 
 
 # ---------------------------------------------------- the paper's workloads
-def test_lamellar_scft_32cubed_50_steps():
-    """32^3, L=4, Ns=64, fA=0.5, chiN=15: one solve then 50 Euler steps (lambda=0.1)."""
+@pytest.mark.parametrize("plan", [None, 4])
+def test_lamellar_scft_32cubed_50_steps(plan):
+    """32^3, L=4, Ns=64, fA=0.5, chiN=15: one solve then 50 Euler steps (lambda=0.1); the
+    default FP64 plan and the double-float march (plan 4)."""
     w = wl.LAM32
     wp, wm = wl.fields(w)
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, SCFT, FP64) as s:
+        if plan is not None:
+            pft.pft_set_plan(s.h, plan, 1)
         s.set_fields(wp, wm)
         for it in range(w.steps):
             s.solve()

@@ -152,5 +152,8 @@ def test_default_plans():
     with pft.System((64, 64, 64), (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, SCFT, FP32) as s:
         assert pft.pft_get_plan(s.h) == (2, 1)
         with pytest.raises(pft.PftError) as e:
-            pft.pft_set_plan(s.h, 4, 1)
+            pft.pft_set_plan(s.h, 5, 1)
         assert e.value.status == pft.PFT_ERR_ARG
+        with pytest.raises(pft.PftError) as e:  # double-float arithmetic: FP64 contexts only
+            pft.pft_set_plan(s.h, 4, 1)
+        assert e.value.status == pft.PFT_ERR_UNSUPPORTED
