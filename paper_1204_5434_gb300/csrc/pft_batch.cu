@@ -36,7 +36,7 @@ struct BatchClass {
   int plan = 3;
   pft::BatchStep* d_conc = nullptr;  // [maxNs][2K]
   pft::BatchStep* d_sep = nullptr;   // the same entries with the per-axis factors of plans 2, 3
-  float tuned_ms[4] = {-1.f, -1.f, -1.f, -1.f};  // autotuner timings of the plans
+  float tuned_ms[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};  // autotuner timings of plans 0, 1, 2, 3, 19
   // the class's branch of the captured update: its marches, reductions and field steps
   // run on their own stream, forked from and joined back into the batch stream, so that
   // the classes overlap on the GPU
@@ -200,13 +200,13 @@ pft_status prepare_pairs(pft_batch* b, BatchClass& c) {
 pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches, cudaStream_t sm) {
   const int K = (int)c.members.size();
   pft::Engine* eng = b->inst[c.members[0]]->eng;
-  if (c.plan == 2 || c.plan == 3) {
+  if (c.plan == 2 || c.plan == 3 || c.plan == 19) {
     for (int j = 0; j <= c.maxNs; j++) {
       const pft::BatchStep* st = c.d_sep + (size_t)(j == 0 ? 0 : j - 1) * 2 * K;
       const int nact = 2 * c.active[j == 0 ? 0 : j - 1];
       cudaError_t e = eng->batch_sep_launch(c.g, st, j, nact, c.plan, b->d_err, sm);
       if (e != cudaSuccess) return bcuda(e, "batched separable step");
-      *launches += (c.plan == 3 && j > 0) ? 2 : 1;
+      *launches += (c.plan != 2 && j > 0) ? 2 : 1;
     }
     for (int i : c.members) {
       pft_ctx* x = b->inst[i];
@@ -510,7 +510,9 @@ pft_status pft_batch_autotune(pft_batch* b) {
     float best = -1.f;
     int bplan = c.plan;
     pft::Engine* eng = b->inst[c.members[0]]->eng;
-    for (int plan = 0; plan < 4 && st == PFT_OK; plan++) {
+    static const int kPlans[5] = {0, 1, 2, 3, 19};
+    for (int pi = 0; pi < 5 && st == PFT_OK; pi++) {
+      const int plan = kPlans[pi];
       if (!eng->batch_plan_ok(c.g, plan)) continue;
       c.plan = plan;
       if (plan >= 1 && (st = prepare_pairs(b, c)) != PFT_OK) break;
@@ -526,7 +528,7 @@ pft_status pft_batch_autotune(pft_batch* b) {
         st = bcuda(e, "autotune timing");
         break;
       }
-      c.tuned_ms[plan] = ms;
+      c.tuned_ms[pi] = ms;
       if (best < 0.f || ms < best) {
         best = ms;
         bplan = plan;
@@ -546,7 +548,7 @@ pft_status pft_batch_autotune(pft_batch* b) {
 
 pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
   if (!b || cls < -1 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
-  if (plan < 0 || plan > 3) return bfail(PFT_ERR_ARG, "plan must be 0, 1, 2 or 3");
+  if (plan < 0 || (plan > 3 && plan != 19)) return bfail(PFT_ERR_ARG, "plan must be 0, 1, 2, 3 or 19");
   if (cls >= 0 && !b->inst[b->classes[cls].members[0]]->eng->batch_plan_ok(b->classes[cls].g, plan))
     return bfail(PFT_ERR_UNSUPPORTED, "plan " + std::to_string(plan) + " does not apply to class " + std::to_string(cls));
   for (int k = 0; k < (int)b->classes.size(); k++) {
@@ -562,7 +564,7 @@ pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
 }
 
 pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind, int* members, int* plan,
-                                float tuned_ms[4]) {
+                                float tuned_ms[5]) {
   if (!b || cls < 0 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
   const BatchClass& c = b->classes[cls];
   if (n)
@@ -571,7 +573,7 @@ pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind
   if (members) *members = (int)c.members.size();
   if (plan) *plan = c.plan;
   if (tuned_ms)
-    for (int k = 0; k < 4; k++) tuned_ms[k] = c.tuned_ms[k];
+    for (int k = 0; k < 5; k++) tuned_ms[k] = c.tuned_ms[k];
   return PFT_OK;
 }
 

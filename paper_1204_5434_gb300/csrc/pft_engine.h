@@ -180,6 +180,7 @@ struct BatchGeom {
 struct SeppGeom {
   int n[3];
   int kind;
+  int lv = 0;  // line variant: 1 = register lines (FP32, x and y lengths with a register plan)
 };
 // Launch j (0..Ns) of a separable pencil march for `members` entries starting at ss (for
 // j >= 1 the entries of contour step j; j = 0 uses those of step 1).  Real fields need
@@ -196,7 +197,8 @@ class Engine {
   virtual bool plane_applies(const CtxData& c) const = 0;  // can the y/z plane kernel run this grid?
   virtual bool sep_applies(const CtxData& c) const = 0;    // can the separable march run it?
   virtual bool sepp_applies(const CtxData& c) const = 0;
-  virtual bool dd_applies(const CtxData& c) const = 0;     // the double-float separable march (plan 4)?   // can the separable pencil march run it?
+  virtual bool dd_applies(const CtxData& c) const = 0;     // the double-float separable march (plan 4)?
+  virtual bool sepp_reg_applies(const CtxData& c) const = 0;  // plan 3 with register lines (code 19)?   // can the separable pencil march run it?
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

@@ -88,6 +88,7 @@ class EngineT : public Engine {
   bool sep_applies(const CtxData& c) const override { return sep_supported(c); }
   bool sepp_applies(const CtxData& c) const override { return sepp_supported(c); }
   bool dd_applies(const CtxData& c) const override { return dd_supported(c); }
+  bool sepp_reg_applies(const CtxData& c) const override { return sepp_reg_supported(c); }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -582,10 +583,16 @@ class EngineT : public Engine {
   static bool sepp_supported(const CtxData& c) {
     return c.kind != PFT_SCFT_REAL || (c.n[1] % 2 == 0 && c.n[2] % 2 == 0);
   }
+  // Register lines (plan 3 with variant 1, code 19): FP32, and a register plan for the x
+  // and the y length.
+  static bool sepp_reg_supported(const CtxData& c) {
+    return std::is_same<T, float>::value && sepp_supported(c) && sepp_reg_ok(c.n[0]) && sepp_reg_ok(c.n[1]);
+  }
   cudaError_t sepp_march(CtxData& c, const BatchStep* st, int members, cudaStream_t sm) {
     SeppGeom g;
     for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
     g.kind = (c.kind == PFT_SCFT_REAL) ? 0 : 1;
+    g.lv = (c.plan_plane == 3 && c.plan_xv == 1) ? 1 : 0;
     for (int j = 0; j <= c.Ns; j++) {
       if (members == 2) mark(c, KK_PAIR_STEP);
       const BatchStep* ss = st + (size_t)2 * (j == 0 ? 0 : j - 1);
@@ -942,12 +949,13 @@ class EngineT : public Engine {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = -1.f;
     int bpl = c.plan_plane, bsm = c.plan_streams, bxv = c.plan_xv;
-    // candidates: separable pencil march, separable plane march (two x-kernel plans),
-    // plane kernel, pencil passes; two chains or two-member launches
-    for (int cand = 0; cand < 10 && e == cudaSuccess; cand++) {
-      static const int fam_of[5] = {3, 2, 2, 1, 0}, xv_of[5] = {0, 0, 1, 0, 0};
+    // candidates: separable pencil march (two line variants), separable plane march (two
+    // x-kernel plans), plane kernel, pencil passes; two chains or two-member launches
+    for (int cand = 0; cand < 12 && e == cudaSuccess; cand++) {
+      static const int fam_of[6] = {3, 3, 2, 2, 1, 0}, xv_of[6] = {0, 1, 0, 1, 0, 0};
       const int cpl = fam_of[cand / 2], cxv = xv_of[cand / 2], csm = (cand & 1) ? 0 : 1;
       if (cpl == 3 && !(sepp_supported(c) && c.stepsS)) continue;
+      if (cpl == 3 && cxv == 1 && !sepp_reg_supported(c)) continue;
       if (cpl == 2 && !(sep_supported(c) && c.stepsS)) continue;
       if (cpl == 1 && !plane_supported(c)) continue;
       c.plan_plane = cpl;
@@ -1004,6 +1012,7 @@ class EngineT : public Engine {
     cg.kind = g.kind;
     if (plan == 2) return sep_supported(cg);
     if (plan == 3) return sepp_supported(cg);
+    if (plan == 19) return sepp_reg_supported(cg);
     return false;
   }
 
@@ -1016,6 +1025,7 @@ class EngineT : public Engine {
     SeppGeom sg;
     for (int a = 0; a < 3; a++) sg.n[a] = g.n[a];
     sg.kind = (g.kind == PFT_SCFT_REAL) ? 0 : 1;
+    sg.lv = (plan == 19) ? 1 : 0;
     return std::is_same<T, float>::value ? sepp_launch_f32(sg, ss, j, nact, sm) : sepp_launch_f64(sg, ss, j, nact, sm);
   }
 

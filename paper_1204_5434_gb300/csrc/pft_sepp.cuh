@@ -66,22 +66,58 @@ template <typename T> constexpr int sepp_occ() { return std::is_same<T, dd>::val
 template <typename T, int N> struct SeppPlan { using type = Plan<N>; };
 template <> struct SeppPlan<dd, 128> { using type = PlanX<128, 8, 8, 4, 4>; };
 template <> struct SeppPlan<dd, 256> { using type = PlanX<256, 8, 8, 8, 4>; };
-template <typename T, int N> struct SeppLineCfg {
-  static constexpr int THREADS = Tile<T>::C * SeppPlan<T, N>::type::TPC;
+
+// Register lines (line variant 1, FP32 lines of at most 48 points): one thread holds a whole
+// line, so the exchanges between Stockham stages permute a thread's own elements through a
+// local array whose indices are compile-time constants once the stages are unrolled --
+// registers, no shared memory, no barriers.
+template <int N> struct RegPlan { static constexpr bool ok = false; };
+#define PFT_REGPLAN(N_, ...) \
+  template <> struct RegPlan<N_> : PlanX<N_, N_, __VA_ARGS__> { static constexpr bool ok = true; };
+PFT_REGPLAN(4, 4)
+PFT_REGPLAN(6, 3, 2)
+PFT_REGPLAN(8, 8)
+PFT_REGPLAN(12, 3, 4)
+PFT_REGPLAN(16, 16)
+PFT_REGPLAN(24, 3, 8)
+PFT_REGPLAN(32, 4, 8)
+PFT_REGPLAN(48, 3, 16)
+#undef PFT_REGPLAN
+inline bool sepp_reg_ok(int n) {
+  return n == 4 || n == 6 || n == 8 || n == 12 || n == 16 || n == 24 || n == 32 || n == 48;
+}
+template <typename T, int N> struct XchReg {
+  cpx<T> b[N];
+  __device__ __forceinline__ void put(int pos, cpx<T> z) { b[pos] = z; }
+  __device__ __forceinline__ cpx<T> get(int pos) const { return b[pos]; }
+  __device__ __forceinline__ void sync() const {}
+};
+
+// Line kernel configuration of variant V: plan, lines per CTA, threads.
+template <typename T, int N, int V> struct SeppLineCfg {
+  using PL = typename SeppPlan<T, N>::type;
+  static constexpr int C = Tile<T>::C;
+  static constexpr int THREADS = C * PL::TPC;
   static constexpr int MINB = (sepp_occ<T>() / THREADS) > 0 ? sepp_occ<T>() / THREADS : 1;
 };
+template <typename T, int N> struct SeppLineCfg<T, N, 1> {
+  using PL = RegPlan<N>;
+  static constexpr int C = 64;  // lines (threads) per CTA
+  static constexpr int THREADS = 64;
+  static constexpr int MINB = 4;  // up to 255 registers a thread (a 48-point complex line is 96)
+};
 // Offsets are 32-bit: a field holds fewer than 2^31 complex elements.
-template <typename T, int N, int KIND, int PW, int AX>
-__global__ void __launch_bounds__(SeppLineCfg<T, N>::THREADS, SeppLineCfg<T, N>::MINB)
+template <typename T, int N, int KIND, int PW, int AX, int V = 0>
+__global__ void __launch_bounds__(SeppLineCfg<T, N, V>::THREADS, SeppLineCfg<T, N, V>::MINB)
 kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer, int s_k) {
   using Z = cpx<T>;
-  using PL = typename SeppPlan<T, N>::type;
-  constexpr int E = PL::E, TPC = PL::TPC, C = Tile<T>::C;
+  using PL = typename SeppLineCfg<T, N, V>::PL;
+  constexpr int E = PL::E, TPC = PL::TPC, C = SeppLineCfg<T, N, V>::C;
   const BatchStep& s = st[blockIdx.y];
   extern __shared__ __align__(16) unsigned char smraw[];
   Z* sm = reinterpret_cast<Z*>(smraw);
   const int c = threadIdx.x % C;
-  const int t = threadIdx.x / C;
+  const int t = (V == 1) ? 0 : threadIdx.x / C;  // register lines: one thread a line
   const int col = blockIdx.x * C + c;
   const bool valid = col < nlines;
   const int colc = valid ? col : 0;
@@ -93,7 +129,14 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
   Z v[E];
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = F[base + i * step];
-  XchCols<T> x{sm, C, c};
+  auto make_x = [&]() {
+    if constexpr (V == 1) {
+      return XchReg<T, N>{};
+    } else {
+      return XchCols<T>{sm, C, c};
+    }
+  };
+  auto x = make_x();
   fft<T, false, N, PL>(v, t, tw, x);
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
@@ -231,14 +274,24 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
 namespace pft {
 
 // ------------------------------------------------------------------ launches
-template <typename T, int N, int KIND, int PW, int AX>
-cudaError_t sepp_line_n(const BatchStep* st, long long nlines, long long cin, long long s_outer, long long s_k,
+template <typename T, int N, int KIND, int PW, int AX, int V>
+cudaError_t sepp_line_v(const BatchStep* st, long long nlines, long long cin, long long s_outer, long long s_k,
                         int members, cudaStream_t sm) {
-  constexpr int C = Tile<T>::C;
+  using CF = SeppLineCfg<T, N, V>;
+  constexpr int C = CF::C;
   const dim3 grid((unsigned)((nlines + C - 1) / C), (unsigned)members);
-  kb_sepp_line<T, N, KIND, PW, AX><<<grid, SeppLineCfg<T, N>::THREADS, (size_t)N * C * sizeof(cpx<T>), sm>>>(
+  kb_sepp_line<T, N, KIND, PW, AX, V><<<grid, CF::THREADS, V == 1 ? 0 : (size_t)N * C * sizeof(cpx<T>), sm>>>(
       st, (int)nlines, (int)cin, (int)s_outer, (int)s_k);
   return cudaGetLastError();
+}
+// lv 1: register lines where the length has a register plan (FP32 only), else variant 0
+template <typename T, int N, int KIND, int PW, int AX>
+cudaError_t sepp_line_n(const BatchStep* st, long long nlines, long long cin, long long s_outer, long long s_k,
+                        int members, cudaStream_t sm, int lv) {
+  if constexpr (std::is_same<T, float>::value && RegPlan<N>::ok) {
+    if (lv == 1) return sepp_line_v<T, N, KIND, PW, AX, 1>(st, nlines, cin, s_outer, s_k, members, sm);
+  }
+  return sepp_line_v<T, N, KIND, PW, AX, 0>(st, nlines, cin, s_outer, s_k, members, sm);
 }
 
 template <typename T, int N, int KIND, int PW>
@@ -275,10 +328,10 @@ cudaError_t sepp_launch_k(const SeppGeom& g, const BatchStep* ss, int j, int mem
     return e;
   }
   // Ky on the lines (x, z element) along y
-  PFT_SEPP_AXIS(g.n[1], e = (sepp_line_n<T, N, KIND, 0, 1>(ss, nx * nzz, nzz, ny * nzz, nzz, members, sm)));
+  PFT_SEPP_AXIS(g.n[1], e = (sepp_line_n<T, N, KIND, 0, 1>(ss, nx * nzz, nzz, ny * nzz, nzz, members, sm, g.lv)));
   if (e != cudaSuccess) return e;
   if (j & 1) {  // Kx, x B_j, store q_j, x B_{j+1}, Kx
-    PFT_SEPP_AXIS(g.n[0], e = (sepp_line_n<T, N, KIND, 2, 0>(ss, ny * nzz, ny * nzz, 0, ny * nzz, members, sm)));
+    PFT_SEPP_AXIS(g.n[0], e = (sepp_line_n<T, N, KIND, 2, 0>(ss, ny * nzz, ny * nzz, 0, ny * nzz, members, sm, g.lv)));
   } else {      // Kz, x B_j, store q_j, x B_{j+1}, Kz
     const long long nl = KIND == 0 ? nx * ny / 2 : nx * ny;
     PFT_SEPP_AXIS(g.n[2], e = (sepp_z_n<T, N, KIND, 2>(ss, nl, members, sm)));

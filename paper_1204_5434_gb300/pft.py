@@ -359,11 +359,11 @@ def pft_batch_class_info(b, cls):
     kind = ct.c_int()
     members = ct.c_int()
     plan = ct.c_int()
-    ms = (ct.c_float * 4)()
+    ms = (ct.c_float * 5)()
     _check(_lib().pft_batch_class_info(b, int(cls), n, ct.byref(kind), ct.byref(members), ct.byref(plan), ms),
            "pft_batch_class_info")
     return {"n": tuple(n), "kind": kind.value, "members": members.value, "plan": plan.value,
-            "tuned_ms": tuple(ms[k] for k in range(4))}
+            "tuned_ms": tuple(ms[k] for k in range(5))}
 
 
 def pft_batch_synchronize(b):
@@ -424,7 +424,8 @@ def pft_fma_throughput(precision=PFT_FP64, stream=None) -> float:
 def pft_set_plan(h, plane, streams=1):
     """Fix the march plan: 0 pencil passes, 1 plane kernel + x pass, 2 separable march on the
     plane kernel, 3 separable march on pencils, 4 the same in double-float arithmetic (FP64
-    contexts), 18 plan 2 with the alternative x kernel."""
+    contexts), 18 plan 2 with the alternative x kernel, 19 plan 3 with register lines (FP32,
+    x and y lengths of at most 48 points)."""
     _check(_lib().pft_set_plan(h, int(plane), int(streams)), "pft_set_plan")
 
 

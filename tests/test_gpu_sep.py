@@ -143,6 +143,51 @@ def test_separable_pencil_march_matches_oracle(case):
     assert eQ <= t["Q"] and ephi <= t["phi"] and eq <= t["q"]
 
 
+# register lines (code 19): FP32 x and y lines of at most 48 points in one thread each
+RCASES = [
+    ((32, 32, 32), (4.0, 4.0, 4.0), 10, 0.3, SCFT, 1),
+    ((48, 48, 48), (6.0, 6.0, 6.0), 7, 0.45, SCFT, 0),
+    ((48, 32, 64), (6.0, 4.0, 8.0), 5, 0.5, SCFT, 1),
+    ((32, 32, 32), (4.0, 4.0, 4.0), 9, 0.5, CL, 1),
+    ((48, 48, 48), (6.0, 6.0, 6.0), 4, 0.38, CL, 0),
+    ((24, 12, 16), (3.0, 2.0, 4.0), 13, 0.4, CL, 1),
+]
+
+
+@pytest.mark.parametrize("case", range(len(RCASES)))
+def test_register_lines_match_oracle(case):
+    n, L, Ns, fA, kind, streams = RCASES[case]
+    wp, wm = _pfields(n, kind, 400 + case)
+    okind = o.SCFT_REAL if kind == SCFT else o.CL_COMPLEX
+    ref = o.solve(wp, wm, n, L, Ns, fA, okind)
+    with pft.System(n, L, Ns, fA, 17.0, 2.0, kind, FP32) as s:
+        pft.pft_set_plan(s.h, 19, streams)
+        s.set_fields(wp, wm)
+        s.solve()
+        s.solve()
+        assert pft.pft_get_plan(s.h) == (19, streams)
+        obs = s.observables()
+        phiA, phiB = s.densities()
+        eq = 0.0
+        for which, k in ((0, 1), (0, Ns), (2, 1), (2, Ns)):
+            g = s.propagator(which, k)
+            hist = ref.q if which == 0 else ref.qd
+            eq = max(eq, np.max(np.abs(g - hist[k])) / np.max(np.abs(hist[k])))
+    Q = obs["Q"] if kind == CL else obs["Q"].real
+    eQ = abs(Q - ref.Q) / abs(ref.Q)
+    ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+    print(f"\nregister lines {n} Ns={Ns} kind={kind}: Q rel {eQ:.2e} phi abs {ephi:.2e} slices {eq:.2e}")
+    assert eQ <= 2e-5 and ephi <= 2e-5 and eq <= 2e-5
+
+
+def test_register_lines_are_refused_where_they_do_not_apply():
+    for n, prec in (((64, 32, 32), FP32), ((32, 64, 32), FP32), ((32, 32, 32), FP64)):
+        with pft.System(n, (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, SCFT, prec) as s:
+            with pytest.raises(pft.PftError) as e:
+                pft.pft_set_plan(s.h, 19, 1)
+            assert e.value.status == pft.PFT_ERR_UNSUPPORTED
+
+
 def test_default_plans():
     for n, kind, prec, plan in (((64, 64, 64), CL, FP32, 2), ((32, 32, 32), SCFT, FP32, 0),
                                 ((64, 64, 64), SCFT, FP64, 3), ((256, 16, 256), CL, FP64, 3),
