@@ -53,12 +53,12 @@ FP64_NOMINAL_TFLOPS = 1.25
 # previous launches left them (so each launch is charged with the write-backs its stores
 # cause).  Reads are nearly nil (the field and both factors stay in L2); the writes are the
 # q slices.  Valid only for the kernel sources it was taken on: null once any changes.
-TRAFFIC_FP32 = {"bytes_per_contour_step": 8601062.4,
+TRAFFIC_FP32 = {"bytes_per_contour_step": 8598741.3,
                 "sources": ("paper_1204_5434_gb300/csrc/pft_sep.cuh", "paper_1204_5434_gb300/csrc/pft_sepp.cuh",
                             "paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_tma.cuh",
                             "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
-                            "paper_1204_5434_gb300/csrc/pft_fft.cuh"),
-                "sha256": "89a65bb531cc632d589d5df072455b9fe17cf834a483cfa331c55e64400bfc20"}
+                            "paper_1204_5434_gb300/csrc/pft_fft.cuh", "paper_1204_5434_gb300/csrc/pft_dd.cuh"),
+                "sha256": "160b855443531a37d00044c6d555d22245506fffc4f8731aa885e61090c16f2b"}
 
 
 def _traffic_fp32():

@@ -129,6 +129,16 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
   Z v[E];
 #pragma unroll
   for (int i = 0; i < E; i++) v[i] = F[base + i * step];
+  // double-float lines of 128 and 256 points (registers to spare under the 255 cap): B_s of
+  // the line first, so that its latency overlaps the transforms instead of stalling the
+  // multiply after them (at 64 points the extra registers cost more occupancy than it saves)
+  constexpr bool kPreB = std::is_same<T, dd>::value && PW == 2 && N >= 128;
+  Z bpre[kPreB ? E : 1];
+  if constexpr (kPreB) {
+    const Z* B = reinterpret_cast<const Z*>(s.B);
+#pragma unroll
+    for (int i = 0; i < E; i++) bpre[i] = B[base + i * step];
+  }
   auto make_x = [&]() {
     if constexpr (V == 1) {
       return XchReg<T, N>{};
@@ -150,7 +160,8 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
 #pragma unroll
     for (int i = 0; i < E; i++) {
       const int o = base + i * step;
-      const Z b = B[o];
+      Z b;
+      if constexpr (kPreB) b = bpre[i]; else b = B[o];
       v[i] = sepp_mul<KIND>(v[i], b);
       if (valid) q[o] = hist_out_c<T>(v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn[o]);
@@ -175,7 +186,9 @@ template <typename T, int N> struct SeppZCfg {
   using PL = typename SeppPlan<T, N>::type;
   // pencils per CTA as PencilsPerCta, for this plan's threads per pencil
   static constexpr int unit = 32 / PL::TPC;
-  static constexpr int by_threads = 256 / PL::TPC;
+  // double-float at 128 and 256 points: 128-thread CTAs (150 to 200 registers a thread: two
+  // or three CTAs an SM, not one)
+  static constexpr int by_threads = ((std::is_same<T, dd>::value && N >= 128) ? 128 : 256) / PL::TPC;
   static constexpr int by_smem = (48 * 1024) / (pencil_ld<T>(N) * (int)sizeof(cpx<T>));
   static constexpr int raw = by_threads < by_smem ? by_threads : by_smem;
   static constexpr int P = raw >= unit ? raw - raw % unit : unit;
@@ -243,6 +256,13 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
   } else {
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = ld(s.spec, t + TPC * i);
+    // double-float at 128 and 256 points: B_s first, as in the line kernel
+    constexpr bool kPreB = std::is_same<T, dd>::value && N >= 128;
+    Z bpre[kPreB ? E : 1];
+    if constexpr (kPreB) {
+#pragma unroll
+      for (int i = 0; i < E; i++) bpre[i] = ld(s.B, t + TPC * i);
+    }
     fft<T, false, N, PL>(v, t, tw, x);
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
@@ -251,7 +271,8 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
     const bool same = (s.Bnext == s.B);
 #pragma unroll
     for (int i = 0; i < E; i++) {
-      const Z b = ld(s.B, t + TPC * i);
+      Z b;
+      if constexpr (kPreB) b = bpre[i]; else b = ld(s.B, t + TPC * i);
       v[i] = sepp_mul<KIND>(v[i], b);
       if (valid) sth(s.out, t + TPC * i, v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : ld(s.Bnext, t + TPC * i));
