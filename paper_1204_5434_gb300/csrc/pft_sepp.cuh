@@ -64,6 +64,10 @@ template <typename T> constexpr int sepp_occ() { return std::is_same<T, dd>::val
 // elements a thread (radices 8, 4, 4 and 8, 8, 4): half the registers of Plan<N>'s 16, at
 // the cost of one more exchange.
 template <typename T, int N> struct SeppPlan { using type = Plan<N>; };
+// Fused kernels whose two convolutions run as two turns of a loop instead of two unrolled
+// copies: double-float (a dozen FP32 operations an FP64 one), and lines of 128 points and
+// more in any precision.
+template <typename T, int N> __host__ __device__ constexpr bool sepp_rolled() { return std::is_same<T, dd>::value || N >= 128; }
 template <> struct SeppPlan<dd, 128> { using type = PlanX<128, 8, 8, 4, 4>; };
 template <> struct SeppPlan<dd, 256> { using type = PlanX<256, 8, 8, 8, 4>; };
 
@@ -147,11 +151,13 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
     }
   };
   auto x = make_x();
-  fft<T, false, N, PL>(v, t, tw, x);
+  auto conv = [&]() {  // K_a: forward transform, x d_a, inverse transform
+    fft<T, false, N, PL>(v, t, tw, x);
 #pragma unroll
-  for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
-  fft<T, true, N, PL>(v, t, tw, x);
-  if (PW == 2) {
+    for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
+    fft<T, true, N, PL>(v, t, tw, x);
+  };
+  auto bsteps = [&]() -> bool {  // x B_s, store q_s, x B_{s+1}; false at the chain's end
     const Z* B = reinterpret_cast<const Z*>(s.B);
     const Z* Bn = reinterpret_cast<const Z*>(s.Bnext);
     cpx<typename SeppHist<T>::S>* q = reinterpret_cast<cpx<typename SeppHist<T>::S>*>(s.out);
@@ -166,11 +172,22 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
       if (valid) q[o] = hist_out_c<T>(v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn[o]);
     }
-    if (!more) return;
-    fft<T, false, N, PL>(v, t, tw, x);
-#pragma unroll
-    for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
-    fft<T, true, N, PL>(v, t, tw, x);
+    return more;
+  };
+  if constexpr (sepp_rolled<T, N>() && PW == 2) {
+    // the two convolutions as two turns of one loop: one copy of the unrolled transforms,
+    // which twice over overflow the instruction cache
+#pragma unroll 1
+    for (int r = 0; r < 2; r++) {
+      conv();
+      if (r == 0 && !bsteps()) return;
+    }
+  } else {
+    conv();
+    if (PW == 2) {
+      if (!bsteps()) return;
+      conv();
+    }
   }
   if (valid) {
 #pragma unroll
@@ -250,23 +267,16 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
     }
   };
   Z v[E];
-  if (PW == 1) {
-#pragma unroll
-    for (int i = 0; i < E; i++) v[i] = sepp_mul<KIND>(ldh(s.in, t + TPC * i), ld(s.B, t + TPC * i));
-  } else {
-#pragma unroll
-    for (int i = 0; i < E; i++) v[i] = ld(s.spec, t + TPC * i);
-    // double-float at 128 and 256 points: B_s first, as in the line kernel
-    constexpr bool kPreB = std::is_same<T, dd>::value && N >= 128;
-    Z bpre[kPreB ? E : 1];
-    if constexpr (kPreB) {
-#pragma unroll
-      for (int i = 0; i < E; i++) bpre[i] = ld(s.B, t + TPC * i);
-    }
+  // double-float at 128 and 256 points: B_s first, as in the line kernel
+  constexpr bool kPreB = std::is_same<T, dd>::value && N >= 128 && PW == 2;
+  Z bpre[kPreB ? E : 1];
+  auto conv = [&]() {  // Kz: forward transform, x d_z, inverse transform
     fft<T, false, N, PL>(v, t, tw, x);
 #pragma unroll
     for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
     fft<T, true, N, PL>(v, t, tw, x);
+  };
+  auto bsteps = [&]() -> bool {  // x B_s, store q_s, x B_{s+1}; false at the chain's end
     const bool more = (s.Bnext != nullptr);
     const bool same = (s.Bnext == s.B);
 #pragma unroll
@@ -277,13 +287,34 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
       if (valid) sth(s.out, t + TPC * i, v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : ld(s.Bnext, t + TPC * i));
     }
-    if (!more) return;
+    if (!more) return false;
     if (n_stages<PL>() > 1) __syncwarp();
-  }
-  fft<T, false, N, PL>(v, t, tw, x);
+    return true;
+  };
+  if (PW == 1) {
 #pragma unroll
-  for (int i = 0; i < E; i++) v[i] = cscale(v[i], d[t + TPC * i]);
-  fft<T, true, N, PL>(v, t, tw, x);
+    for (int i = 0; i < E; i++) v[i] = sepp_mul<KIND>(ldh(s.in, t + TPC * i), ld(s.B, t + TPC * i));
+    conv();
+  } else {
+#pragma unroll
+    for (int i = 0; i < E; i++) v[i] = ld(s.spec, t + TPC * i);
+    if constexpr (kPreB) {
+#pragma unroll
+      for (int i = 0; i < E; i++) bpre[i] = ld(s.B, t + TPC * i);
+    }
+    if constexpr (sepp_rolled<T, N>()) {
+      // the two convolutions as two turns of one loop (one copy of the code)
+#pragma unroll 1
+      for (int r = 0; r < 2; r++) {
+        conv();
+        if (r == 0 && !bsteps()) return;
+      }
+    } else {
+      conv();
+      if (!bsteps()) return;
+      conv();
+    }
+  }
   if (valid) {
 #pragma unroll
     for (int i = 0; i < E; i++) stz(s.spec, t + TPC * i, v[i]);
