@@ -315,23 +315,31 @@ pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_b
  * pft_get_plan's plan 2 (FP32 real classes with nx = ny = nz in {64, 128}); 3 -- the
  * separable march on pencils (plan 3 of pft_get_plan); 19 -- plan 3 with register lines
  * (FP32 classes whose x and y lengths are in {4, 6, 8, 12, 16, 24, 32, 48}: one thread
- * transforms a whole x or y line in registers, no shared-memory exchange).  Plans 2, 3 and 19
- * run both marches in the same launches and the quadrature after them, as plan 1.  The
- * default is plan 2 where it applies, else plan 3.
+ * transforms a whole x or y line in registers, no shared-memory exchange); 35 -- plan 3
+ * with the x and y lines in tiles of 32 lines a CTA instead of 16; 51 -- plan 3 with twice
+ * the elements a thread on the x and y lines, in another radix order (16 2 at 32 points,
+ * 3 8 2 at 48, 16 4 at 64), in tiles of 32 lines (35 and 51: FP32 classes whose x and y
+ * lengths are 32, 48 or 64).  Plans 2, 3, 19, 35 and 51 run both marches in the same
+ * launches and the quadrature after them, as plan 1.  The default is plan 2 where it
+ * applies, else plan 3.
  * Errors: PFT_ERR_STATE if an instance has no fields; PFT_ERR_OOM. */
 pft_status pft_batch_autotune(pft_batch* batch);
 
-/* Set the plan (0, 1, 2, 3 or 19, as for pft_batch_autotune) of class `cls`, or of every class it
+/* Set the plan (0, 1, 2, 3, 19, 35 or 51, as for pft_batch_autotune) of class `cls`, or of every class it
  * applies to for cls = -1.  Errors: PFT_ERR_ARG for a bad index or plan,
  * PFT_ERR_UNSUPPORTED for a plan that does not apply to class `cls`. */
 pft_status pft_batch_set_plan(pft_batch* batch, int cls, int plan);
 
+/* Number of batch plans the autotuner times, in the order of pft_batch_class_info's
+ * tuned_ms: 0, 1, 2, 3, 19, 35, 51. */
+#define PFT_BATCH_PLANS 7
+
 /* Class `cls` (0 .. classes-1 of pft_batch_info): grid n[3], field kind, member count, plan
- * in use and the autotuner's timings of plans 0, 1, 2, 3 and 19 in ms (tuned_ms[0..4]; -1
- * if not tuned or not applicable).  Any output pointer may be NULL.  Errors: PFT_ERR_ARG for
- * a bad index. */
+ * in use and the autotuner's timings of plans 0, 1, 2, 3, 19, 35 and 51 in ms
+ * (tuned_ms[0..PFT_BATCH_PLANS-1]; -1 if not tuned or not applicable).  Any output pointer
+ * may be NULL.  Errors: PFT_ERR_ARG for a bad index. */
 pft_status pft_batch_class_info(const pft_batch* batch, int cls, int n[3], int* kind, int* members, int* plan,
-                                float tuned_ms[5]);
+                                float tuned_ms[PFT_BATCH_PLANS]);
 
 /* Observables and densities of member i's last solve (synchronises). */
 pft_status pft_batch_get_observables(pft_batch* b, int i, pft_obs* obs);
@@ -421,7 +429,10 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
  * 48 significant bits, computed on the FP32 pipe; the history, the quadrature and
  * everything after the march stay FP64); 19 = plan 3 with register lines (FP32, x and y
  * lengths in {4, 6, 8, 12, 16, 24, 32, 48}: one thread transforms a whole x or y line in
- * registers, no shared-memory exchange); 18 = plan 2 with the x
+ * registers, no shared-memory exchange); 35 = plan 3 with the x and y lines in tiles of 32
+ * lines a CTA instead of 16; 51 = plan 3 with twice the elements a thread on the x and y
+ * lines, in another radix order, in tiles of 32 lines (35 and 51: FP32, x and y lengths of
+ * 32, 48 or 64); 18 = plan 2 with the x
  * kernel on half the elements a thread (twice the threads, one more exchange: at nx = 128
  * eight elements and radices 8, 4, 4 instead of 16 and 16, 8).  *streams = 1 if the
  * two propagators run as two chains on two streams.  Either pointer may be NULL.

@@ -871,16 +871,19 @@ pft_status pft_set_plan(pft_ctx* ctx, int code, int streams) {
   if (!ctx) return fail(PFT_ERR_ARG, "NULL ctx");
   CtxData& d = ctx->d;
   const int plane = code & 15, xv = code >> 4;
-  if (code < 0 || plane > 4 || xv > 1 || (xv && plane != 2 && plane != 3) || streams < 0 || streams > 1)
-    return fail(PFT_ERR_ARG, "plan code in {0, 1, 2, 3, 4, 18, 19}, streams in {0, 1}");
+  if (code < 0 || plane > 4 || xv > 3 || (xv && plane != 2 && plane != 3) || (xv > 1 && plane != 3) || streams < 0 ||
+      streams > 1)
+    return fail(PFT_ERR_ARG, "plan code in {0, 1, 2, 3, 4, 18, 19, 35, 51}, streams in {0, 1}");
   if (plane == 1 && !ctx->eng->plane_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the plane kernel needs FP32 with ny = nz = 64 or 128 (real) or 64 (complex)");
   if (plane == 2 && !ctx->eng->sep_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the separable march needs FP32 real fields, ny = nz and nx in {64, 128}");
   if (plane == 3 && !ctx->eng->sepp_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the separable pencil march needs ny and nz even for real fields");
-  if (plane == 3 && xv && !ctx->eng->sepp_reg_applies(d))
+  if (plane == 3 && xv == 1 && !ctx->eng->sepp_reg_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "register lines need FP32 and x, y lengths in {4, 6, 8, 12, 16, 24, 32, 48}");
+  if (plane == 3 && xv > 1 && !ctx->eng->sepp_lv_applies(d, xv))
+    return fail(PFT_ERR_UNSUPPORTED, "line variants 35 and 51 need FP32 and x, y lengths in {32, 48, 64}");
   if (plane == 4 && !ctx->eng->dd_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the double-float march needs an FP64 context and ny, nz even for real fields");
   d.plan_plane = plane;

@@ -19,6 +19,14 @@
 
 namespace {
 
+// The plans the batch autotuner times, in the order of BatchClass::tuned_ms.
+const int kBatchPlans[PFT_BATCH_PLANS] = {0, 1, 2, 3, 19, 35, 51};
+int batch_plan_index(int plan) {
+  for (int k = 0; k < PFT_BATCH_PLANS; k++)
+    if (kBatchPlans[k] == plan) return k;
+  return -1;
+}
+
 struct BatchClass {
   pft::BatchGeom g;
   pft_kind kind;
@@ -32,11 +40,12 @@ struct BatchClass {
   // of consecutive steps fused, the quadrature after the marches over both histories;
   // plan 2: the separable march on the plane and x kernels (FP32 real, ny = nz = nx in
   // {64, 128}); plan 3: the separable march on pencils -- both marches per launch, the
-  // quadrature after them, as plan 1
+  // quadrature after them, as plan 1; plans 19, 35, 51: plan 3 with line variant 1, 2, 3
+  // (register lines; 32-line tiles; twice the elements a thread in 32-line tiles)
   int plan = 3;
   pft::BatchStep* d_conc = nullptr;  // [maxNs][2K]
   pft::BatchStep* d_sep = nullptr;   // the same entries with the per-axis factors of plans 2, 3
-  float tuned_ms[5] = {-1.f, -1.f, -1.f, -1.f, -1.f};  // autotuner timings of plans 0, 1, 2, 3, 19
+  float tuned_ms[PFT_BATCH_PLANS] = {-1.f, -1.f, -1.f, -1.f, -1.f, -1.f, -1.f};  // autotuner timings of kBatchPlans
   // the class's branch of the captured update: its marches, reductions and field steps
   // run on their own stream, forked from and joined back into the batch stream, so that
   // the classes overlap on the GPU
@@ -200,7 +209,7 @@ pft_status prepare_pairs(pft_batch* b, BatchClass& c) {
 pft_status record_class_solve(pft_batch* b, BatchClass& c, long long* launches, cudaStream_t sm) {
   const int K = (int)c.members.size();
   pft::Engine* eng = b->inst[c.members[0]]->eng;
-  if (c.plan == 2 || c.plan == 3 || c.plan == 19) {
+  if (c.plan == 2 || (c.plan & 15) == 3) {
     for (int j = 0; j <= c.maxNs; j++) {
       const pft::BatchStep* st = c.d_sep + (size_t)(j == 0 ? 0 : j - 1) * 2 * K;
       const int nact = 2 * c.active[j == 0 ? 0 : j - 1];
@@ -510,9 +519,8 @@ pft_status pft_batch_autotune(pft_batch* b) {
     float best = -1.f;
     int bplan = c.plan;
     pft::Engine* eng = b->inst[c.members[0]]->eng;
-    static const int kPlans[5] = {0, 1, 2, 3, 19};
-    for (int pi = 0; pi < 5 && st == PFT_OK; pi++) {
-      const int plan = kPlans[pi];
+    for (int pi = 0; pi < PFT_BATCH_PLANS && st == PFT_OK; pi++) {
+      const int plan = kBatchPlans[pi];
       if (!eng->batch_plan_ok(c.g, plan)) continue;
       c.plan = plan;
       if (plan >= 1 && (st = prepare_pairs(b, c)) != PFT_OK) break;
@@ -548,7 +556,7 @@ pft_status pft_batch_autotune(pft_batch* b) {
 
 pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
   if (!b || cls < -1 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
-  if (plan < 0 || (plan > 3 && plan != 19)) return bfail(PFT_ERR_ARG, "plan must be 0, 1, 2, 3 or 19");
+  if (batch_plan_index(plan) < 0) return bfail(PFT_ERR_ARG, "plan must be 0, 1, 2, 3, 19, 35 or 51");
   if (cls >= 0 && !b->inst[b->classes[cls].members[0]]->eng->batch_plan_ok(b->classes[cls].g, plan))
     return bfail(PFT_ERR_UNSUPPORTED, "plan " + std::to_string(plan) + " does not apply to class " + std::to_string(cls));
   for (int k = 0; k < (int)b->classes.size(); k++) {
@@ -564,7 +572,7 @@ pft_status pft_batch_set_plan(pft_batch* b, int cls, int plan) {
 }
 
 pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind, int* members, int* plan,
-                                float tuned_ms[5]) {
+                                float tuned_ms[PFT_BATCH_PLANS]) {
   if (!b || cls < 0 || cls >= (int)b->classes.size()) return bfail(PFT_ERR_ARG, "bad batch or class index");
   const BatchClass& c = b->classes[cls];
   if (n)
@@ -573,7 +581,7 @@ pft_status pft_batch_class_info(const pft_batch* b, int cls, int n[3], int* kind
   if (members) *members = (int)c.members.size();
   if (plan) *plan = c.plan;
   if (tuned_ms)
-    for (int k = 0; k < 5; k++) tuned_ms[k] = c.tuned_ms[k];
+    for (int k = 0; k < PFT_BATCH_PLANS; k++) tuned_ms[k] = c.tuned_ms[k];
   return PFT_OK;
 }
 

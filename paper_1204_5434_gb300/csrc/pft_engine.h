@@ -112,7 +112,7 @@ struct CtxData {
   // on one stream (0); chosen by timing at the first solve when `autotune` is set
   int plan_plane = 1;
   int plan_streams = 1;
-  int plan_xv = 0;  // separable march: plan variant of the x kernel (0: Plan<nx>, 1: half the elements a thread)
+  int plan_xv = 0;  // plan variant: plan 2, the x kernel (0: Plan<nx>, 1: half the elements a thread); plan 3, the line variant (0-3)
   bool autotune = false;
   bool tuned = false;
   bool edw = false;   // Edwards homopolymer model: one field, q-dagger = q
@@ -198,7 +198,8 @@ class Engine {
   virtual bool sep_applies(const CtxData& c) const = 0;    // can the separable march run it?
   virtual bool sepp_applies(const CtxData& c) const = 0;
   virtual bool dd_applies(const CtxData& c) const = 0;     // the double-float separable march (plan 4)?
-  virtual bool sepp_reg_applies(const CtxData& c) const = 0;  // plan 3 with register lines (code 19)?   // can the separable pencil march run it?
+  virtual bool sepp_reg_applies(const CtxData& c) const = 0;  // plan 3 with register lines (code 19)?
+  virtual bool sepp_lv_applies(const CtxData& c, int lv) const = 0;  // plan 3 with line variant lv (code 3 + 16 lv)?
   virtual cudaError_t upload_tables(CtxData& c) = 0;
   virtual cudaError_t fill_ones(CtxData& c, void* dst) = 0;
   virtual cudaError_t prepare_fields(CtxData& c) = 0;   // Boltzmann factors + field term

@@ -89,6 +89,7 @@ class EngineT : public Engine {
   bool sepp_applies(const CtxData& c) const override { return sepp_supported(c); }
   bool dd_applies(const CtxData& c) const override { return dd_supported(c); }
   bool sepp_reg_applies(const CtxData& c) const override { return sepp_reg_supported(c); }
+  bool sepp_lv_applies(const CtxData& c, int lv) const override { return sepp_lv_supported(c, lv); }
 
   // ------------------------------------------------------------------ tables
   cudaError_t upload_tables(CtxData& c) override {
@@ -588,11 +589,21 @@ class EngineT : public Engine {
   static bool sepp_reg_supported(const CtxData& c) {
     return std::is_same<T, float>::value && sepp_supported(c) && sepp_reg_ok(c.n[0]) && sepp_reg_ok(c.n[1]);
   }
+  // Line variant lv of plan 3 (code 3 + 16 lv): 0 Plan<N> in 16-line tiles, 1 register lines,
+  // 2 Plan<N> in 32-line tiles, 3 twice the elements a thread in 32-line tiles (FP32, x and y
+  // lengths of 32, 48 or 64 for variants 2 and 3).
+  static bool sepp_lv_supported(const CtxData& c, int lv) {
+    if (lv == 0) return sepp_supported(c);
+    if (lv == 1) return sepp_reg_supported(c);
+    if (lv == 2 || lv == 3)
+      return std::is_same<T, float>::value && sepp_supported(c) && sepp_wide_ok(c.n[0]) && sepp_wide_ok(c.n[1]);
+    return false;
+  }
   cudaError_t sepp_march(CtxData& c, const BatchStep* st, int members, cudaStream_t sm) {
     SeppGeom g;
     for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
     g.kind = (c.kind == PFT_SCFT_REAL) ? 0 : 1;
-    g.lv = (c.plan_plane == 3 && c.plan_xv == 1) ? 1 : 0;
+    g.lv = (c.plan_plane == 3) ? c.plan_xv : 0;
     for (int j = 0; j <= c.Ns; j++) {
       if (members == 2) mark(c, KK_PAIR_STEP);
       const BatchStep* ss = st + (size_t)2 * (j == 0 ? 0 : j - 1);
@@ -938,7 +949,7 @@ class EngineT : public Engine {
     int pl = 0, sm = 0;
     if (plan_cache_lookup(key, &pl, &sm)) {
       const int fam = pl & 15;
-      c.plan_xv = (fam == 2) ? (pl >> 4) & 1 : 0;
+      c.plan_xv = (fam == 2) ? (pl >> 4) & 1 : (fam == 3 && sepp_lv_supported(c, pl >> 4)) ? (pl >> 4) : 0;
       if (fam == 3 && sepp_supported(c) && c.stepsS) c.plan_plane = 3;
       else c.plan_plane = (fam == 2 && sep_supported(c) && c.stepsS) ? 2 : ((fam == 1 && plane_supported(c)) ? 1 : 0);
       c.plan_streams = sm ? 1 : 0;
@@ -949,13 +960,13 @@ class EngineT : public Engine {
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     float best = -1.f;
     int bpl = c.plan_plane, bsm = c.plan_streams, bxv = c.plan_xv;
-    // candidates: separable pencil march (two line variants), separable plane march (two
+    // candidates: separable pencil march (four line variants), separable plane march (two
     // x-kernel plans), plane kernel, pencil passes; two chains or two-member launches
-    for (int cand = 0; cand < 12 && e == cudaSuccess; cand++) {
-      static const int fam_of[6] = {3, 3, 2, 2, 1, 0}, xv_of[6] = {0, 1, 0, 1, 0, 0};
+    for (int cand = 0; cand < 16 && e == cudaSuccess; cand++) {
+      static const int fam_of[8] = {3, 3, 3, 3, 2, 2, 1, 0}, xv_of[8] = {0, 1, 2, 3, 0, 1, 0, 0};
       const int cpl = fam_of[cand / 2], cxv = xv_of[cand / 2], csm = (cand & 1) ? 0 : 1;
       if (cpl == 3 && !(sepp_supported(c) && c.stepsS)) continue;
-      if (cpl == 3 && cxv == 1 && !sepp_reg_supported(c)) continue;
+      if (cpl == 3 && !sepp_lv_supported(c, cxv)) continue;
       if (cpl == 2 && !(sep_supported(c) && c.stepsS)) continue;
       if (cpl == 1 && !plane_supported(c)) continue;
       c.plan_plane = cpl;
@@ -1012,7 +1023,7 @@ class EngineT : public Engine {
     cg.kind = g.kind;
     if (plan == 2) return sep_supported(cg);
     if (plan == 3) return sepp_supported(cg);
-    if (plan == 19) return sepp_reg_supported(cg);
+    if ((plan & 15) == 3) return sepp_lv_supported(cg, plan >> 4);  // 19, 35, 51
     return false;
   }
 
@@ -1025,7 +1036,7 @@ class EngineT : public Engine {
     SeppGeom sg;
     for (int a = 0; a < 3; a++) sg.n[a] = g.n[a];
     sg.kind = (g.kind == PFT_SCFT_REAL) ? 0 : 1;
-    sg.lv = (plan == 19) ? 1 : 0;
+    sg.lv = ((plan & 15) == 3) ? plan >> 4 : 0;
     return std::is_same<T, float>::value ? sepp_launch_f32(sg, ss, j, nact, sm) : sepp_launch_f64(sg, ss, j, nact, sm);
   }
 

@@ -97,12 +97,39 @@ template <typename T, int N> struct XchReg {
   __device__ __forceinline__ void sync() const {}
 };
 
-// Line kernel configuration of variant V: plan, lines per CTA, threads.
+// Wide lines (line variant 3, FP32 lines of 32, 48 and 64 points): twice the elements a
+// thread of Plan<N>, in another radix order (16 2, 3 8 2, 16 4): fewer threads a line and
+// fewer exchanges at 32 and 64 points, more registers.
+template <int N> struct WidePlan { static constexpr bool ok = false; };
+#define PFT_WIDEPLAN(N_, E_, ...) \
+  template <> struct WidePlan<N_> : PlanX<N_, E_, __VA_ARGS__> { static constexpr bool ok = true; };
+PFT_WIDEPLAN(32, 16, 16, 2)
+PFT_WIDEPLAN(48, 24, 3, 8, 2)
+PFT_WIDEPLAN(64, 16, 16, 4)
+#undef PFT_WIDEPLAN
+// Lengths of line variants 2 and 3.
+inline bool sepp_wide_ok(int n) { return n == 32 || n == 48 || n == 64; }
+
+// Line kernel configuration of variant V: plan, lines per CTA, threads.  Variants 0 (Plan<N>,
+// 16 FP32 lines a CTA), 1 (register lines), 2 (Plan<N>, 32 lines a CTA: twice the CTA, a
+// warp's loads one 256-byte run), 3 (WidePlan<N>, 32 lines a CTA); the autotuners choose.
 template <typename T, int N, int V> struct SeppLineCfg {
   using PL = typename SeppPlan<T, N>::type;
   static constexpr int C = Tile<T>::C;
   static constexpr int THREADS = C * PL::TPC;
   static constexpr int MINB = (sepp_occ<T>() / THREADS) > 0 ? sepp_occ<T>() / THREADS : 1;
+};
+template <typename T, int N> struct SeppLineCfg<T, N, 2> {
+  using PL = typename SeppPlan<T, N>::type;
+  static constexpr int C = 32;
+  static constexpr int THREADS = C * PL::TPC;
+  static constexpr int MINB = (sepp_occ<T>() / THREADS) > 0 ? sepp_occ<T>() / THREADS : 1;
+};
+template <typename T, int N> struct SeppLineCfg<T, N, 3> {
+  using PL = WidePlan<N>;
+  static constexpr int C = 32;
+  static constexpr int THREADS = C * PL::TPC;
+  static constexpr int MINB = (384 / THREADS) > 0 ? 384 / THREADS : 1;  // up to 170 registers
 };
 template <typename T, int N> struct SeppLineCfg<T, N, 1> {
   using PL = RegPlan<N>;
@@ -336,12 +363,17 @@ cudaError_t sepp_line_v(const BatchStep* st, long long nlines, long long cin, lo
       st, (int)nlines, (int)cin, (int)s_outer, (int)s_k);
   return cudaGetLastError();
 }
-// lv 1: register lines where the length has a register plan (FP32 only), else variant 0
+// lv 1: register lines where the length has a register plan; lv 2 and 3: the 32-line tiles
+// (Plan<N> and WidePlan<N>) at 32, 48 and 64 points; FP32 only; variant 0 otherwise
 template <typename T, int N, int KIND, int PW, int AX>
 cudaError_t sepp_line_n(const BatchStep* st, long long nlines, long long cin, long long s_outer, long long s_k,
                         int members, cudaStream_t sm, int lv) {
   if constexpr (std::is_same<T, float>::value && RegPlan<N>::ok) {
     if (lv == 1) return sepp_line_v<T, N, KIND, PW, AX, 1>(st, nlines, cin, s_outer, s_k, members, sm);
+  }
+  if constexpr (std::is_same<T, float>::value && WidePlan<N>::ok) {
+    if (lv == 2) return sepp_line_v<T, N, KIND, PW, AX, 2>(st, nlines, cin, s_outer, s_k, members, sm);
+    if (lv == 3) return sepp_line_v<T, N, KIND, PW, AX, 3>(st, nlines, cin, s_outer, s_k, members, sm);
   }
   return sepp_line_v<T, N, KIND, PW, AX, 0>(st, nlines, cin, s_outer, s_k, members, sm);
 }

@@ -28,6 +28,7 @@ PFT_BATCH_GRAPHED, PFT_BATCH_PER_INSTANCE = 0, 1
 PFT_SCHEME_SPLIT2, PFT_SCHEME_RQM4 = 0, 1
 PFT_STEP_SCFT_SIS, PFT_STEP_CL_SIS = 2, 3
 PFT_ARCH_DIBLOCK, PFT_ARCH_EDWARDS = 0, 1
+PFT_BATCH_PLANS = 7  # batch plans 0, 1, 2, 3, 19, 35, 51 (the order of tuned_ms)
 
 
 class pft_grid(ct.Structure):
@@ -359,11 +360,11 @@ def pft_batch_class_info(b, cls):
     kind = ct.c_int()
     members = ct.c_int()
     plan = ct.c_int()
-    ms = (ct.c_float * 5)()
+    ms = (ct.c_float * PFT_BATCH_PLANS)()
     _check(_lib().pft_batch_class_info(b, int(cls), n, ct.byref(kind), ct.byref(members), ct.byref(plan), ms),
            "pft_batch_class_info")
     return {"n": tuple(n), "kind": kind.value, "members": members.value, "plan": plan.value,
-            "tuned_ms": tuple(ms[k] for k in range(5))}
+            "tuned_ms": tuple(ms[k] for k in range(PFT_BATCH_PLANS))}
 
 
 def pft_batch_synchronize(b):
@@ -425,7 +426,8 @@ def pft_set_plan(h, plane, streams=1):
     """Fix the march plan: 0 pencil passes, 1 plane kernel + x pass, 2 separable march on the
     plane kernel, 3 separable march on pencils, 4 the same in double-float arithmetic (FP64
     contexts), 18 plan 2 with the alternative x kernel, 19 plan 3 with register lines (FP32,
-    x and y lengths of at most 48 points)."""
+    x and y lengths of at most 48 points), 35 and 51 plan 3 with 32-line tiles and with twice
+    the elements a thread in 32-line tiles (FP32, x and y lengths of 32, 48 or 64)."""
     _check(_lib().pft_set_plan(h, int(plane), int(streams)), "pft_set_plan")
 
 

@@ -126,13 +126,14 @@ BENCH_CLASSES = [
 ]
 
 
-@pytest.mark.parametrize("plan", [1, 2, 3, 19])
+@pytest.mark.parametrize("plan", [1, 2, 3, 19, 35, 51])
 def test_batch_fp32_classes_of_the_timed_batch_match_oracle(plan):
     """FP32-mixed batch with one member per class of the timed batch, graph-captured, in
     plan 1 (both marches per launch; plane kernels for the 64^3 classes), plan 2 (the
     separable march on the plane and x kernels for the 64^3 classes, plan 1 elsewhere),
-    plan 3 (the separable march on pencils for every class) or plan 19 (plan 3 with
-    register lines for the 32^3 and 48^3 classes): each member's Q, phiA,
+    plan 3 (the separable march on pencils for every class), plan 19 (plan 3 with
+    register lines for the 32^3 and 48^3 classes), plan 35 (plan 3 with 32-line tiles) or
+    plan 51 (plan 3 with twice the elements a thread in 32-line tiles): each member's Q, phiA,
     phiB and fields after one update against the FP64 oracle.  FP32 tolerances of the
     single-context path (relative 2e-5 on Q, absolute 2e-5 on phi) scaled by the
     random-walk growth of the rounding error over 2 Ns <= 400 transform pairs (x sqrt 2)."""
@@ -204,8 +205,8 @@ def test_batch_plans_agree_and_autotune_picks_one(prec):
                 for k in range(info["classes"]):
                     ci = pft.pft_batch_class_info(b, k)
                     tuned = [v for v in ci["tuned_ms"] if v > 0]
-                    assert ci["plan"] in (0, 1, 2, 3, 19) and ci["tuned_ms"][0] > 0 and ci["tuned_ms"][1] > 0
-                    assert ci["tuned_ms"][{19: 4}.get(ci["plan"], ci["plan"])] == min(tuned)
+                    assert ci["plan"] in (0, 1, 2, 3, 19, 35, 51) and ci["tuned_ms"][0] > 0 and ci["tuned_ms"][1] > 0
+                    assert ci["tuned_ms"][{19: 4, 35: 5, 51: 6}.get(ci["plan"], ci["plan"])] == min(tuned)
                 pft.pft_batch_run(b, 1, LAM, DT, pft.PFT_BATCH_GRAPHED)
                 pft.pft_batch_synchronize(b)
         finally:

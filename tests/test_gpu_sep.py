@@ -188,6 +188,59 @@ def test_register_lines_are_refused_where_they_do_not_apply():
             assert e.value.status == pft.PFT_ERR_UNSUPPORTED
 
 
+# line variants 35 (32-line tiles) and 51 (twice the elements a thread, another radix order,
+# 32-line tiles): FP32 x and y lines of 32, 48 or 64 points; z any supported length
+WCASES = [
+    ((32, 32, 32), (4.0, 4.0, 4.0), 10, 0.3, SCFT, 1),
+    ((48, 48, 48), (6.0, 6.0, 6.0), 7, 0.45, SCFT, 0),
+    ((64, 48, 24), (8.0, 6.0, 3.0), 5, 0.5, SCFT, 1),
+    ((32, 64, 16), (4.0, 8.0, 2.0), 9, 0.5, CL, 1),
+    ((48, 32, 48), (6.0, 4.0, 6.0), 4, 0.38, CL, 0),
+    ((64, 64, 64), (8.0, 8.0, 8.0), 1, 0.4, CL, 1),
+]
+
+
+@pytest.mark.parametrize("code", [35, 51])
+@pytest.mark.parametrize("case", range(len(WCASES)))
+def test_line_variants_match_oracle(case, code):
+    n, L, Ns, fA, kind, streams = WCASES[case]
+    wp, wm = _pfields(n, kind, 500 + case)
+    okind = o.SCFT_REAL if kind == SCFT else o.CL_COMPLEX
+    ref = o.solve(wp, wm, n, L, Ns, fA, okind)
+    with pft.System(n, L, Ns, fA, 17.0, 2.0, kind, FP32) as s:
+        pft.pft_set_plan(s.h, code, streams)
+        s.set_fields(wp, wm)
+        s.solve()
+        s.solve()
+        assert pft.pft_get_plan(s.h) == (code, streams)
+        obs = s.observables()
+        phiA, phiB = s.densities()
+        eq = 0.0
+        for which, k in ((0, 1), (0, Ns), (2, 1), (2, Ns)):
+            g = s.propagator(which, k)
+            hist = ref.q if which == 0 else ref.qd
+            eq = max(eq, np.max(np.abs(g - hist[k])) / np.max(np.abs(hist[k])))
+    Q = obs["Q"] if kind == CL else obs["Q"].real
+    eQ = abs(Q - ref.Q) / abs(ref.Q)
+    ephi = max(np.max(np.abs(phiA - ref.phiA)), np.max(np.abs(phiB - ref.phiB)))
+    print(f"\nline variant {code} {n} Ns={Ns} kind={kind}: Q rel {eQ:.2e} phi abs {ephi:.2e} slices {eq:.2e}")
+    assert eQ <= 2e-5 and ephi <= 2e-5 and eq <= 2e-5
+
+
+def test_line_variants_are_refused_where_they_do_not_apply():
+    for n, prec in (((128, 32, 32), FP32), ((32, 96, 32), FP32), ((32, 32, 32), FP64)):
+        with pft.System(n, (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, SCFT, prec) as s:
+            for code in (35, 51):
+                with pytest.raises(pft.PftError) as e:
+                    pft.pft_set_plan(s.h, code, 1)
+                assert e.value.status == pft.PFT_ERR_UNSUPPORTED
+    with pft.System((32, 32, 32), (4.0, 4.0, 4.0), 4, 0.5, 15.0, 1.0, SCFT, FP32) as s:
+        for code in (67, 34, 50):
+            with pytest.raises(pft.PftError) as e:
+                pft.pft_set_plan(s.h, code, 1)
+            assert e.value.status == pft.PFT_ERR_ARG
+
+
 def test_default_plans():
     for n, kind, prec, plan in (((64, 64, 64), CL, FP32, 2), ((32, 32, 32), SCFT, FP32, 0),
                                 ((64, 64, 64), SCFT, FP64, 3), ((256, 16, 256), CL, FP64, 3),
