@@ -316,10 +316,10 @@ pft_status pft_batch_run(pft_batch* b, int updates, double lam, double dt, pft_b
  * separable march on pencils (plan 3 of pft_get_plan); 19 -- plan 3 with register lines
  * (FP32 classes whose x and y lengths are in {4, 6, 8, 12, 16, 24, 32, 48}: one thread
  * transforms a whole x or y line in registers, no shared-memory exchange); 35 -- plan 3
- * with the x and y lines in tiles of 32 lines a CTA instead of 16; 51 -- plan 3 with twice
- * the elements a thread on the x and y lines, in another radix order (16 2 at 32 points,
- * 3 8 2 at 48, 16 4 at 64), in tiles of 32 lines (35 and 51: FP32 classes whose x and y
- * lengths are 32, 48 or 64).  Plans 2, 3, 19, 35 and 51 run both marches in the same
+ * with the x and y lines in tiles of 32 lines a CTA instead of 16 (FP32 classes); 51 --
+ * plan 3 with twice the elements a thread on the x and y lines, in another radix order
+ * (16 2 at 32 points, 3 8 2 at 48, 16 4 at 64), in tiles of 32 lines (FP32 classes whose x
+ * and y lengths are 32, 48 or 64).  Plans 2, 3, 19, 35 and 51 run both marches in the same
  * launches and the quadrature after them, as plan 1.  The default is plan 2 where it
  * applies, else plan 3.
  * Errors: PFT_ERR_STATE if an instance has no fields; PFT_ERR_OOM. */
@@ -430,9 +430,9 @@ pft_status pft_debug_set_q0(pft_ctx* ctx, const void* q0, pft_mem where);
  * everything after the march stay FP64); 19 = plan 3 with register lines (FP32, x and y
  * lengths in {4, 6, 8, 12, 16, 24, 32, 48}: one thread transforms a whole x or y line in
  * registers, no shared-memory exchange); 35 = plan 3 with the x and y lines in tiles of 32
- * lines a CTA instead of 16; 51 = plan 3 with twice the elements a thread on the x and y
- * lines, in another radix order, in tiles of 32 lines (35 and 51: FP32, x and y lengths of
- * 32, 48 or 64); 18 = plan 2 with the x
+ * lines a CTA instead of 16 (FP32); 51 = plan 3 with twice the elements a thread on the x
+ * and y lines, in another radix order, in tiles of 32 lines (FP32, x and y lengths of 32,
+ * 48 or 64); 18 = plan 2 with the x
  * kernel on half the elements a thread (twice the threads, one more exchange: at nx = 128
  * eight elements and radices 8, 4, 4 instead of 16 and 16, 8).  *streams = 1 if the
  * two propagators run as two chains on two streams.  Either pointer may be NULL.

@@ -254,12 +254,13 @@ pft_status pft_create(pft_ctx** out, const pft_grid* grid, const pft_chain* chai
   c->eng = (d.prec == PFT_FP64) ? pft::make_engine_f64() : pft::make_engine_f32();
   d.scheme = (opts->scheme == PFT_SCHEME_RQM4) ? 1 : 0;
   d.autotune = opts->autotune != 0;
-  // the default plan (measured on GB300): FP32 -- the separable march on the plane kernel
-  // where it applies, else the plane kernel, else the pencil passes; FP64 -- the separable
-  // march on pencils (fewer passes of the FP64-pipe-bound transforms)
+  // the default plan (measured on GB300): the separable march on the plane kernel where it
+  // applies (FP32), else the plane kernel, else the separable march on pencils (FP64: fewer
+  // passes of the FP64-pipe-bound transforms; FP32: two field round trips a contour step
+  // against the pencil passes' four), else the pencil passes
   if (c->eng->sep_applies(d)) d.plan_plane = 2;
   else if (c->eng->plane_applies(d)) d.plan_plane = 1;
-  else if (d.prec == PFT_FP64 && c->eng->sepp_applies(d)) d.plan_plane = 3;
+  else if (c->eng->sepp_applies(d)) d.plan_plane = 3;
   else d.plan_plane = 0;
 
   const size_t M = (size_t)d.M;
@@ -883,7 +884,7 @@ pft_status pft_set_plan(pft_ctx* ctx, int code, int streams) {
   if (plane == 3 && xv == 1 && !ctx->eng->sepp_reg_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "register lines need FP32 and x, y lengths in {4, 6, 8, 12, 16, 24, 32, 48}");
   if (plane == 3 && xv > 1 && !ctx->eng->sepp_lv_applies(d, xv))
-    return fail(PFT_ERR_UNSUPPORTED, "line variants 35 and 51 need FP32 and x, y lengths in {32, 48, 64}");
+    return fail(PFT_ERR_UNSUPPORTED, "line variant 35 needs FP32, 51 FP32 and x, y lengths in {32, 48, 64}");
   if (plane == 4 && !ctx->eng->dd_applies(d))
     return fail(PFT_ERR_UNSUPPORTED, "the double-float march needs an FP64 context and ny, nz even for real fields");
   d.plan_plane = plane;

@@ -590,12 +590,13 @@ class EngineT : public Engine {
     return std::is_same<T, float>::value && sepp_supported(c) && sepp_reg_ok(c.n[0]) && sepp_reg_ok(c.n[1]);
   }
   // Line variant lv of plan 3 (code 3 + 16 lv): 0 Plan<N> in 16-line tiles, 1 register lines,
-  // 2 Plan<N> in 32-line tiles, 3 twice the elements a thread in 32-line tiles (FP32, x and y
-  // lengths of 32, 48 or 64 for variants 2 and 3).
+  // 2 Plan<N> in 32-line tiles (FP32), 3 twice the elements a thread in 32-line tiles (FP32, x
+  // and y lengths of 32, 48 or 64).
   static bool sepp_lv_supported(const CtxData& c, int lv) {
     if (lv == 0) return sepp_supported(c);
     if (lv == 1) return sepp_reg_supported(c);
-    if (lv == 2 || lv == 3)
+    if (lv == 2) return std::is_same<T, float>::value && sepp_supported(c);
+    if (lv == 3)
       return std::is_same<T, float>::value && sepp_supported(c) && sepp_wide_ok(c.n[0]) && sepp_wide_ok(c.n[1]);
     return false;
   }

@@ -110,9 +110,15 @@ PFT_WIDEPLAN(64, 16, 16, 4)
 // Lengths of line variants 2 and 3.
 inline bool sepp_wide_ok(int n) { return n == 32 || n == 48 || n == 64; }
 
+// FP32 kernels that carry B_s (x lines and z lines with PW 2, not register lines) stage it in
+// shared memory by cp.async at the start.
+template <typename T, int PW, int AX, int V> __host__ __device__ constexpr bool sepp_pre_smem() {
+  return std::is_same<T, float>::value && PW == 2 && AX != 1 && V != 1;
+}
+
 // Line kernel configuration of variant V: plan, lines per CTA, threads.  Variants 0 (Plan<N>,
-// 16 FP32 lines a CTA), 1 (register lines), 2 (Plan<N>, 32 lines a CTA: twice the CTA, a
-// warp's loads one 256-byte run), 3 (WidePlan<N>, 32 lines a CTA); the autotuners choose.
+// 16 FP32 lines a CTA), 1 (register lines), 2 (Plan<N>, 32 lines a CTA: twice the CTA, each
+// row of a tile one 256-byte run), 3 (WidePlan<N>, 32 lines a CTA); the autotuners choose.
 template <typename T, int N, int V> struct SeppLineCfg {
   using PL = typename SeppPlan<T, N>::type;
   static constexpr int C = Tile<T>::C;
@@ -170,6 +176,27 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
 #pragma unroll
     for (int i = 0; i < E; i++) bpre[i] = B[base + i * step];
   }
+  // FP32 x lines: B_s of the tile (N rows of C consecutive lines, after the exchange area)
+  // copied to shared memory by 16-byte cp.async now, so that its latency hides behind the
+  // first convolution (the lines sit at the 128-register cap: no room to hold it in
+  // registers); whole tiles with an even row pitch (16-byte chunks) only
+  constexpr bool kPreS = sepp_pre_smem<T, PW, AX, V>();
+  const bool pre = kPreS && (blockIdx.x + 1) * C <= nlines && (s_k % 2) == 0;
+  Z* Bt = sm + N * C;
+  if constexpr (kPreS) {
+    if (pre) {
+      constexpr int CH = C / 2;  // 16-byte chunks a tile row
+      const unsigned sb = (unsigned)__cvta_generic_to_shared(Bt);
+      const Z* Bg = reinterpret_cast<const Z*>(s.B) + blockIdx.x * C;
+      for (int k = threadIdx.x; k < N * CH; k += SeppLineCfg<T, N, V>::THREADS) {
+        const int xr = k / CH, ch = k % CH;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + (unsigned)((xr * C + 2 * ch) * 8)),
+                     "l"(Bg + (long long)xr * s_k + 2 * ch)
+                     : "memory");
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  }
   auto make_x = [&]() {
     if constexpr (V == 1) {
       return XchReg<T, N>{};
@@ -190,11 +217,19 @@ kb_sepp_line(const BatchStep* __restrict__ st, int nlines, int cin, int s_outer,
     cpx<typename SeppHist<T>::S>* q = reinterpret_cast<cpx<typename SeppHist<T>::S>*>(s.out);
     const bool more = (Bn != nullptr);
     const bool same = (Bn == B);
+    if constexpr (kPreS) {
+      if (pre) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();  // every thread's chunks of the tile have landed
+      }
+    }
 #pragma unroll
     for (int i = 0; i < E; i++) {
       const int o = base + i * step;
       Z b;
-      if constexpr (kPreB) b = bpre[i]; else b = B[o];
+      if constexpr (kPreB) b = bpre[i];
+      else if (kPreS && pre) b = Bt[(t + TPC * i) * C + c];
+      else b = B[o];
       v[i] = sepp_mul<KIND>(v[i], b);
       if (valid) q[o] = hist_out_c<T>(v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : Bn[o]);
@@ -297,6 +332,33 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
   // double-float at 128 and 256 points: B_s first, as in the line kernel
   constexpr bool kPreB = std::is_same<T, dd>::value && N >= 128 && PW == 2;
   Z bpre[kPreB ? E : 1];
+  // FP32: B_s of the CTA's P lines -- one contiguous run of P N 8-byte elements, complex
+  // (KIND 1) or the float row pairs (KIND 0) -- copied to shared memory after the exchange
+  // area by 16-byte cp.async at the start (whole tiles only)
+  constexpr bool kPreS = sepp_pre_smem<T, PW, 2, 0>();
+  const long long l0 = (long long)blockIdx.x * P;
+  const bool pre = kPreS && l0 + P <= nlines;
+  Z* Bt = reinterpret_cast<Z*>(smraw) + P * LD;
+  if constexpr (kPreS) {
+    if (pre) {
+      const unsigned sb = (unsigned)__cvta_generic_to_shared(Bt);
+      const char* Bg = reinterpret_cast<const char*>(s.B) + l0 * N * 8;
+      for (int k = threadIdx.x; k < P * N / 2; k += SeppZCfg<T, N>::THREADS)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sb + (unsigned)(k * 16)),
+                     "l"(Bg + (long long)k * 16)
+                     : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  }
+  // B_s at position pos of this thread's line from the staged tile
+  auto ldbt = [&](int pos) -> Z {
+    if constexpr (KIND == 1) {
+      return Bt[p * N + pos];
+    } else {
+      const T* f = reinterpret_cast<const T*>(Bt) + 2 * p * N;
+      return mk<T>(f[pos], f[N + pos]);
+    }
+  };
   auto conv = [&]() {  // Kz: forward transform, x d_z, inverse transform
     fft<T, false, N, PL>(v, t, tw, x);
 #pragma unroll
@@ -306,10 +368,18 @@ kb_sepp_z(const BatchStep* __restrict__ st, long long nlines) {
   auto bsteps = [&]() -> bool {  // x B_s, store q_s, x B_{s+1}; false at the chain's end
     const bool more = (s.Bnext != nullptr);
     const bool same = (s.Bnext == s.B);
+    if constexpr (kPreS) {
+      if (pre) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();  // every thread's chunks of the tile have landed
+      }
+    }
 #pragma unroll
     for (int i = 0; i < E; i++) {
       Z b;
-      if constexpr (kPreB) b = bpre[i]; else b = ld(s.B, t + TPC * i);
+      if constexpr (kPreB) b = bpre[i];
+      else if (kPreS && pre) b = ldbt(t + TPC * i);
+      else b = ld(s.B, t + TPC * i);
       v[i] = sepp_mul<KIND>(v[i], b);
       if (valid) sth(s.out, t + TPC * i, v[i]);
       if (more) v[i] = sepp_mul<KIND>(v[i], same ? b : ld(s.Bnext, t + TPC * i));
@@ -359,20 +429,28 @@ cudaError_t sepp_line_v(const BatchStep* st, long long nlines, long long cin, lo
   using CF = SeppLineCfg<T, N, V>;
   constexpr int C = CF::C;
   const dim3 grid((unsigned)((nlines + C - 1) / C), (unsigned)members);
-  kb_sepp_line<T, N, KIND, PW, AX, V><<<grid, CF::THREADS, V == 1 ? 0 : (size_t)N * C * sizeof(cpx<T>), sm>>>(
-      st, (int)nlines, (int)cin, (int)s_outer, (int)s_k);
+  // the exchange area, and the staged B_s tile after it
+  constexpr size_t smem = V == 1 ? 0 : (size_t)N * C * sizeof(cpx<T>) * (sepp_pre_smem<T, PW, AX, V>() ? 2 : 1);
+  auto kern = kb_sepp_line<T, N, KIND, PW, AX, V>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, CF::THREADS, smem, sm>>>(st, (int)nlines, (int)cin, (int)s_outer, (int)s_k);
   return cudaGetLastError();
 }
-// lv 1: register lines where the length has a register plan; lv 2 and 3: the 32-line tiles
-// (Plan<N> and WidePlan<N>) at 32, 48 and 64 points; FP32 only; variant 0 otherwise
+// lv 1: register lines where the length has a register plan; lv 2: 32-line tiles of Plan<N>;
+// lv 3: 32-line tiles of WidePlan<N> at 32, 48 and 64 points; FP32 only; variant 0 otherwise
 template <typename T, int N, int KIND, int PW, int AX>
 cudaError_t sepp_line_n(const BatchStep* st, long long nlines, long long cin, long long s_outer, long long s_k,
                         int members, cudaStream_t sm, int lv) {
   if constexpr (std::is_same<T, float>::value && RegPlan<N>::ok) {
     if (lv == 1) return sepp_line_v<T, N, KIND, PW, AX, 1>(st, nlines, cin, s_outer, s_k, members, sm);
   }
-  if constexpr (std::is_same<T, float>::value && WidePlan<N>::ok) {
+  if constexpr (std::is_same<T, float>::value) {
     if (lv == 2) return sepp_line_v<T, N, KIND, PW, AX, 2>(st, nlines, cin, s_outer, s_k, members, sm);
+  }
+  if constexpr (std::is_same<T, float>::value && WidePlan<N>::ok) {
     if (lv == 3) return sepp_line_v<T, N, KIND, PW, AX, 3>(st, nlines, cin, s_outer, s_k, members, sm);
   }
   return sepp_line_v<T, N, KIND, PW, AX, 0>(st, nlines, cin, s_outer, s_k, members, sm);
@@ -382,7 +460,15 @@ template <typename T, int N, int KIND, int PW>
 cudaError_t sepp_z_n(const BatchStep* st, long long nlines, int members, cudaStream_t sm) {
   constexpr int P = SeppZCfg<T, N>::P;
   const dim3 grid((unsigned)((nlines + P - 1) / P), (unsigned)members);
-  kb_sepp_z<T, N, KIND, PW><<<grid, SeppZCfg<T, N>::THREADS, (size_t)P * pencil_ld<T>(N) * sizeof(cpx<T>), sm>>>(st, nlines);
+  // the pencil exchange area, and the staged B_s tile after it
+  constexpr size_t smem = (size_t)P * pencil_ld<T>(N) * sizeof(cpx<T>) +
+                          (sepp_pre_smem<T, PW, 2, 0>() ? (size_t)P * N * sizeof(cpx<T>) : 0);
+  auto kern = kb_sepp_z<T, N, KIND, PW>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, SeppZCfg<T, N>::THREADS, smem, sm>>>(st, nlines);
   return cudaGetLastError();
 }
 

@@ -426,8 +426,8 @@ def pft_set_plan(h, plane, streams=1):
     """Fix the march plan: 0 pencil passes, 1 plane kernel + x pass, 2 separable march on the
     plane kernel, 3 separable march on pencils, 4 the same in double-float arithmetic (FP64
     contexts), 18 plan 2 with the alternative x kernel, 19 plan 3 with register lines (FP32,
-    x and y lengths of at most 48 points), 35 and 51 plan 3 with 32-line tiles and with twice
-    the elements a thread in 32-line tiles (FP32, x and y lengths of 32, 48 or 64)."""
+    x and y lengths of at most 48 points), 35 plan 3 with 32-line tiles (FP32), 51 plan 3 with
+    twice the elements a thread in 32-line tiles (FP32, x and y lengths of 32, 48 or 64)."""
     _check(_lib().pft_set_plan(h, int(plane), int(streams)), "pft_set_plan")
 
 

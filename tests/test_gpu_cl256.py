@@ -4,9 +4,9 @@ FP64 oracle.
 The complex Langevin 256^3 workload (L=16, fA=0.5, chiN=14, C=100; Eqs. 5, 8 and 13 with
 complex fields) runs no plane kernel: its complex z transforms of length 256 (the fused
 z-inverse / z-forward pencils), its x pass of length 256 and, at 256^3, its y passes all
-take the pencil kernels.  These tests drive exactly the plans the bench times -- FP32:
-the pencil passes of the 3D transform pair; FP64: the separable march on pencils (a y
-launch and an x or z launch per contour step) -- with two chains,
+take the pencil kernels.  These tests drive exactly the plan the bench times in both
+precisions -- the separable march on pencils (a y launch and an x or z launch per contour
+step; in FP32 the x and z kernels stage the Boltzmann factor's tile in shared memory) -- with two chains,
 full history (or every K-th slice) -- on seeded complex fields and compare Q, H, phiA,
 phiB and propagator slices element by element with the oracle.
 
@@ -54,9 +54,9 @@ def _check(w, prec, K, wp, wm):
     Href = o.hamiltonian(wp, wm, ref.lnQ, w.chiN, w.C, w.n, w.L, o.CL_COMPLEX)
     t = TOL[prec]
     with pft.System(w.n, w.L, w.Ns, w.fA, w.chiN, w.C, CL, prec, seed=w.seed, checkpoint=K) as s:
-        # the plan the bench's complex Langevin 256^3 line runs (pencil passes in FP32, the
-        # separable march on pencils in FP64), two chains on two streams
-        assert pft.pft_get_plan(s.h) == ((0, 1) if prec == FP32 else (3, 1))
+        # the plan the bench's complex Langevin 256^3 line runs (the separable march on
+        # pencils), two chains on two streams
+        assert pft.pft_get_plan(s.h) == (3, 1)
         assert pft.pft_get_checkpoint(s.h) == (1 if K in (0, 1) else K)
         s.set_fields(wp, wm)
         s.solve()
