@@ -202,19 +202,29 @@ WCASES = [
     ((32, 64, 16), (4.0, 8.0, 2.0), 9, 0.5, CL, 1),
     ((48, 32, 48), (6.0, 4.0, 6.0), 4, 0.38, CL, 0),
     ((64, 64, 64), (8.0, 8.0, 8.0), 1, 0.4, CL, 1),
-    # code 35 only: 256- and 128-point x lines, a 96-point y line, a ragged 12 x 6 tile grid
+    # 256-, 192- and 128-point x lines, a 96-point y line, ragged tile grids (12 x 6 and
+    # 128 x 6 x 12: 36 x lines, not whole 16-line tiles)
     ((256, 16, 128), (16.0, 1.0, 8.0), 3, 0.5, CL, 1),
     ((128, 96, 64), (8.0, 6.0, 4.0), 4, 0.35, SCFT, 0),
     ((12, 6, 12), (3.0, 1.5, 3.0), 5, 0.4, SCFT, 1),
+    ((192, 8, 16), (12.0, 1.0, 2.0), 6, 0.45, SCFT, 1),
+    ((128, 6, 12), (8.0, 1.5, 3.0), 2, 0.5, CL, 0),
+    ((256, 8, 32), (16.0, 1.0, 4.0), 1, 0.5, SCFT, 1),
 ]
+
+
+def _variant_applies(code, n):
+    if code == 51:
+        return all(a in (32, 48, 64) for a in n[:2])
+    return True
 
 
 @pytest.mark.parametrize("code", [35, 51])
 @pytest.mark.parametrize("case", range(len(WCASES)))
 def test_line_variants_match_oracle(case, code):
     n, L, Ns, fA, kind, streams = WCASES[case]
-    if code == 51 and case >= 6:
-        pytest.skip("line variant 51 needs x and y lengths of 32, 48 or 64")
+    if not _variant_applies(code, n):
+        pytest.skip(f"line variant {code} does not apply to {n}")
     wp, wm = _pfields(n, kind, 500 + case)
     okind = o.SCFT_REAL if kind == SCFT else o.CL_COMPLEX
     ref = o.solve(wp, wm, n, L, Ns, fA, okind)
