@@ -123,7 +123,8 @@ void free_all(pft_ctx* c) {
   for (cudaEvent_t ev : d.ev) cudaEventDestroy(ev);
   void* bufs[] = {d.wp, d.wm, d.BA, d.BB, d.hist, d.qd[0], d.qd[1], d.qd0, d.spec, d.spec2,
                   d.accA, d.accB, d.partials, d.scal, d.tables, c->io, d.kerr, d.qdh, d.steps2, d.stepsS, d.stepsg,
-                  d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa, d.stepsap, d.adjS, d.stepsAS, d.ddbuf, d.stepsD};
+                  d.BAh, d.BBh, d.rq, d.qw, d.sis, d.adj, d.stepsa, d.stepsap, d.adjS, d.stepsAS, d.ddbuf, d.stepsD,
+                  d.stepsCK, d.pairsCK, d.qdk};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (d.scal_host) cudaFreeHost(d.scal_host);

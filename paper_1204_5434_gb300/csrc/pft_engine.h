@@ -105,6 +105,13 @@ struct CtxData {
   size_t ddB_off[2] = {0, 0};
   void* stepsD = nullptr;   // [2 * Ns]
   void* stepsg = nullptr;   // [2 * Ns] BatchStep: the two spectra of the box derivative
+  // checkpointed history (ckK >= 2) on the separable pencil march: the step entries of the
+  // forward march [Ns], of every segment recompute [<= Ns] and of the conjugate march [Ns];
+  // the quadrature pairs (q_{Ns-m}, qd_m) [Ns]; K conjugate slices of the current chunk
+  void* stepsCK = nullptr;
+  void* pairsCK = nullptr;
+  void* qdk = nullptr;
+  std::vector<int> ckRoff;  // first recompute entry of segment g
   // RQM4 (scheme 1): quarter-step Boltzmann factors, half-step diffusion tables, three
   // scratch slices for the full and the two half steps, quadrature weight tables
   // plan of the concurrent pass march: plane kernel (1) or pencil passes (0) where the

@@ -517,6 +517,73 @@ __global__ void __launch_bounds__(PW_THREADS) k_quadrature_cplx(const cpx<T>* __
   }
 }
 
+// One chunk of the contour quadrature of Eq. 8 on the checkpointed separable march: for
+// the np pairs (q_{Ns-m}, qd_m) of the chunk, accA += sum cA q qd and accB += sum cB q qd
+// (trapezoid weights of the pair's forward slice; 0, 1/2 or 1).  FP32 propagators: the
+// products and the weighted sum in compensated FP32 (TwoSum), flushed into the FP64
+// accumulators once per chunk; FP64: one FMA per term.
+struct QuadPair {
+  const void* q;
+  const void* qd;
+  double cA, cB;
+};
+template <typename T, int KIND>
+__global__ void __launch_bounds__(PW_THREADS) k_quad_pairs(const QuadPair* __restrict__ pr, int np, long long M,
+                                                           double* __restrict__ accA, double* __restrict__ accB) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < M; i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (KIND == 0) {
+      double a = accA[i], b = accB[i];
+      if constexpr (sizeof(T) == 4) {
+        F2Sum fa, fb;
+        for (int p = 0; p < np; p++) {
+          const float v = __fmul_rn(reinterpret_cast<const float*>(pr[p].q)[i], reinterpret_cast<const float*>(pr[p].qd)[i]);
+          fa.add(__fmul_rn(v, (float)pr[p].cA));
+          fb.add(__fmul_rn(v, (float)pr[p].cB));
+        }
+        fa.flush(&a);
+        fb.flush(&b);
+      } else {
+        for (int p = 0; p < np; p++) {
+          const double v = reinterpret_cast<const double*>(pr[p].q)[i] * reinterpret_cast<const double*>(pr[p].qd)[i];
+          a = fma(pr[p].cA, v, a);
+          b = fma(pr[p].cB, v, b);
+        }
+      }
+      accA[i] = a;
+      accB[i] = b;
+    } else {
+      double2* A2 = reinterpret_cast<double2*>(accA);
+      double2* B2 = reinterpret_cast<double2*>(accB);
+      double2 a = A2[i], b = B2[i];
+      if constexpr (sizeof(T) == 4) {
+        F2Sum far, fai, fbr, fbi;
+        for (int p = 0; p < np; p++) {
+          const float2 v = cmul(reinterpret_cast<const float2*>(pr[p].q)[i], reinterpret_cast<const float2*>(pr[p].qd)[i]);
+          const float wa = (float)pr[p].cA, wb = (float)pr[p].cB;
+          far.add(__fmul_rn(v.x, wa));
+          fai.add(__fmul_rn(v.y, wa));
+          fbr.add(__fmul_rn(v.x, wb));
+          fbi.add(__fmul_rn(v.y, wb));
+        }
+        far.flush(&a.x);
+        fai.flush(&a.y);
+        fbr.flush(&b.x);
+        fbi.flush(&b.y);
+      } else {
+        for (int p = 0; p < np; p++) {
+          const double2 v = cmul(reinterpret_cast<const double2*>(pr[p].q)[i], reinterpret_cast<const double2*>(pr[p].qd)[i]);
+          a.x = fma(pr[p].cA, v.x, a.x);
+          a.y = fma(pr[p].cA, v.y, a.y);
+          b.x = fma(pr[p].cB, v.x, b.x);
+          b.y = fma(pr[p].cB, v.y, b.y);
+        }
+      }
+      A2[i] = a;
+      B2[i] = b;
+    }
+  }
+}
+
 // Contour quadrature of Eq. 8 with a weight table: accA = sum_n w[n] q_n qd_{Ns-n},
 // accB = sum_n w[Ns+1+n] q_n qd_{Ns-n} (composite Simpson weights of the 4th-order
 // scheme).  Integrand in the propagators' precision, FP64 sums; two grid points per

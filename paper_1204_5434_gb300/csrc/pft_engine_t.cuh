@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include <type_traits>
@@ -299,10 +300,121 @@ class EngineT : public Engine {
     return cudaSuccess;
   }
 
+  // ------------------------------------------- checkpointed history, separable march
+  // With every K-th slice kept (ckK >= 2) on a context whose plan is a separable march
+  // (2 or 3; the pencil kernels serve both): the forward march stores the checkpoints (the
+  // other slices go to the segment slots, overwritten later); then, from the top segment
+  // down, each segment q_{gK+1} .. q_{gK+K-1} is recomputed from its checkpoint by a short
+  // separable march, the conjugate march advances by the segment's chunk of steps (one
+  // chain across the chunks, its field in spec2, the chunk's qd slices in K slots), and one
+  // kernel adds the chunk's pairs to the accumulators of Eq. 8.
+  static bool ck_sepp_applies(const CtxData& c) {
+    return c.concurrent && c.ckK >= 2 && c.scheme == 0 && !c.edw && (c.plan_plane == 2 || c.plan_plane == 3) &&
+           sepp_supported(c);
+  }
+  int ck_top(const CtxData& c) const { return (c.Ns - 1) / c.ckK; }
+  cudaError_t prepare_ck_sepp(CtxData& c) {
+    if (c.stepsCK) return cudaSuccess;
+    const int K = c.ckK, Ns = c.Ns;
+    const size_t slice = slice_bytes(c, sizeof(T));
+    cudaError_t e = cudaMalloc(&c.qdk, (size_t)K * slice);
+    if (e != cudaSuccess) return e;
+    c.bytes += (size_t)K * slice;
+    const char* t = (const char*)c.tables;
+    auto blk = [&](int s) -> const void* { return (s <= c.NsA) ? c.BA : c.BB; };
+    auto entry = [&](const void* in, const void* B, void* out, void* spec, const void* Bn) {
+      BatchStep x;
+      memset(&x, 0, sizeof(x));
+      x.in = in;
+      x.B = B;
+      x.out = out;
+      x.spec = spec;
+      x.Bnext = Bn;
+      for (int a = 0; a < 4; a++) x.tw[a] = t + c.tw_off[a];
+      for (int a = 0; a < 3; a++) x.d[a] = t + c.sd_off[a];
+      return x;
+    };
+    std::vector<BatchStep> h;
+    for (int s = 1; s <= Ns; s++)  // forward march: entry s-1 stores q_s
+      h.push_back(entry(q_at(c, s - 1), blk(s), q_at(c, s), c.spec, s < Ns ? blk(s + 1) : nullptr));
+    c.ckRoff.assign((size_t)ck_top(c) + 1, 0);
+    for (int g = ck_top(c); g >= 0; g--) {  // segment recomputes (field in spec, free after the forward march)
+      const int n0 = g * K, n1 = std::min(n0 + K - 1, Ns - 1);
+      c.ckRoff[g] = (int)h.size();
+      for (int s = n0 + 1; s <= n1; s++)
+        h.push_back(entry(q_at(c, n0), blk(s), q_at(c, s), c.spec, s < n1 ? blk(s + 1) : nullptr));
+    }
+    const size_t coff = h.size();
+    std::vector<QuadPair> pr((size_t)Ns);
+    for (int g = ck_top(c); g >= 0; g--) {  // conjugate march in chunks: qd_m pairs with q_{Ns-m}
+      const int n0 = g * K, n1 = std::min(n0 + K - 1, Ns - 1);
+      const int m0 = Ns - n1, m1 = Ns - n0;
+      for (int m = m0; m <= m1; m++) {
+        const int nb = Ns + 1 - m;  // split step index of this conjugate step
+        void* out = (m == Ns) ? c.qd[Ns & 1] : (void*)((char*)c.qdk + (size_t)(m - m0) * slice);
+        h.push_back(entry(m == 1 ? c.qd0 : nullptr, blk(nb), out, c.spec2, m < Ns ? blk(nb - 1) : nullptr));
+        QuadPair& p = pr[(size_t)m - 1];
+        p.q = q_at(c, Ns - m);
+        p.qd = out;
+        trapezoid_weight(Ns - m, Ns, c.NsA, &p.cA, &p.cB);
+      }
+    }
+    if (h.size() != coff + (size_t)Ns) return cudaErrorInvalidValue;
+    c.ckRoff.push_back((int)coff);  // the conjugate entries start here
+    e = cudaMalloc(&c.stepsCK, h.size() * sizeof(BatchStep));
+    if (e == cudaSuccess) e = cudaMemcpy(c.stepsCK, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return e;
+    c.bytes += h.size() * sizeof(BatchStep);
+    e = cudaMalloc(&c.pairsCK, pr.size() * sizeof(QuadPair));
+    if (e == cudaSuccess) e = cudaMemcpy(c.pairsCK, pr.data(), pr.size() * sizeof(QuadPair), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) c.bytes += pr.size() * sizeof(QuadPair);
+    return e;
+  }
+  // Launches j0 .. j1 of a separable pencil march whose entries (one member) start at st.
+  cudaError_t ck_run(CtxData& c, const SeppGeom& g, const BatchStep* st, int j0, int j1, cudaStream_t sm) {
+    for (int j = j0; j <= j1; j++) {
+      mark(c, KK_PAIR_STEP);
+      cudaError_t e = std::is_same<T, float>::value ? sepp_launch_f32(g, st + (j == 0 ? 0 : j - 1), j, 1, sm)
+                                                    : sepp_launch_f64(g, st + (j == 0 ? 0 : j - 1), j, 1, sm);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t record_solve_ck_sepp(CtxData& c) {
+    const int K = c.ckK, Ns = c.Ns;
+    SeppGeom g;
+    for (int a = 0; a < 3; a++) g.n[a] = c.n[a];
+    g.kind = (c.kind == PFT_SCFT_REAL) ? 0 : 1;
+    g.lv = (c.plan_plane == 3) ? c.plan_xv : 0;
+    const BatchStep* st = (const BatchStep*)c.stepsCK;
+    const BatchStep* cst = st + c.ckRoff.back();
+    const QuadPair* pr = (const QuadPair*)c.pairsCK;
+    cudaError_t e = ck_run(c, g, st, 0, Ns, c.stream);  // forward march, checkpoints kept
+    if (e != cudaSuccess) return e;
+    if ((e = solve_mid(c)) != cudaSuccess) return e;  // Q and the (q_Ns, qd_0) term
+    cudaStream_t rs = c.stream;
+    for (int s = ck_top(c); s >= 0; s--) {
+      const int n0 = s * K, n1 = std::min(n0 + K - 1, Ns - 1);
+      if (n1 > n0 && (e = ck_run(c, g, st + c.ckRoff[s], 0, n1 - n0, rs)) != cudaSuccess) return e;
+      const int m0 = Ns - n1, m1 = Ns - n0;
+      if ((e = ck_run(c, g, cst, m0 == 1 ? 0 : m0, m1, c.stream)) != cudaSuccess) return e;
+      mark(c, KK_QUADRATURE);
+      if (c.kind == PFT_SCFT_REAL)
+        k_quad_pairs<T, 0><<<c.npart, PW_THREADS, 0, c.stream>>>(pr + (m0 - 1), m1 - m0 + 1, c.M, (double*)c.accA,
+                                                                  (double*)c.accB);
+      else
+        k_quad_pairs<T, 1><<<c.npart, PW_THREADS, 0, c.stream>>>(pr + (m0 - 1), m1 - m0 + 1, c.M, (double*)c.accA,
+                                                                  (double*)c.accB);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return solve_tail(c);  // densities and force norms
+  }
+
   cudaError_t record_solve(CtxData& c) {
     cudaError_t e;
     if (c.scheme == 1) return record_solve_rqm4(c);
     if (c.concurrent && c.ckK == 1) return record_solve_concurrent(c);
+    if (ck_sepp_applies(c) && c.stepsCK) return record_solve_ck_sepp(c);
     // forward march (Eqs. 5, 13); a checkpointed history keeps every K-th slice and q_Ns
     for (int n = 1; n <= c.Ns; n++) {
       const void* B = (n <= c.NsA) ? c.BA : c.BB;
@@ -1481,6 +1593,9 @@ class EngineT : public Engine {
       if (c.autotune && !c.tuned && !c.edw && !c.profiling) {
         if ((e = tune_plan(c)) != cudaSuccess) return e;
       }
+    } else if (ck_sepp_applies(c)) {
+      cudaError_t e = prepare_ck_sepp(c);
+      if (e != cudaSuccess) return e;
     }
     if (!c.use_graph || c.profiling) return record_solve(c);
     if (!c.graph_valid) {
