@@ -373,7 +373,7 @@ class EngineT : public Engine {
   // Launches j0 .. j1 of a separable pencil march whose entries (one member) start at st.
   cudaError_t ck_run(CtxData& c, const SeppGeom& g, const BatchStep* st, int j0, int j1, cudaStream_t sm) {
     for (int j = j0; j <= j1; j++) {
-      mark(c, KK_PAIR_STEP);
+      if (sm == c.stream) mark(c, KK_PAIR_STEP);
       cudaError_t e = std::is_same<T, float>::value ? sepp_launch_f32(g, st + (j == 0 ? 0 : j - 1), j, 1, sm)
                                                     : sepp_launch_f64(g, st + (j == 0 ? 0 : j - 1), j, 1, sm);
       if (e != cudaSuccess) return e;
@@ -392,12 +392,22 @@ class EngineT : public Engine {
     cudaError_t e = ck_run(c, g, st, 0, Ns, c.stream);  // forward march, checkpoints kept
     if (e != cudaSuccess) return e;
     if ((e = solve_mid(c)) != cudaSuccess) return e;  // Q and the (q_Ns, qd_0) term
-    cudaStream_t rs = c.stream;
+    // the segment recomputes on the second stream (field in spec, free once the forward
+    // march is done), each after the quadrature of the chunk before it has read the segment
+    // slots, so that recompute g runs beside conjugate chunk g
+    const bool two = !c.profiling && c.plan_streams;
+    cudaStream_t rs = two ? c.stream2 : c.stream;
+    if (two) {
+      if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(rs, c.fork_ev, 0)) != cudaSuccess) return e;
+    }
     for (int s = ck_top(c); s >= 0; s--) {
       const int n0 = s * K, n1 = std::min(n0 + K - 1, Ns - 1);
       if (n1 > n0 && (e = ck_run(c, g, st + c.ckRoff[s], 0, n1 - n0, rs)) != cudaSuccess) return e;
+      if (two && (e = cudaEventRecord(c.join_ev, rs)) != cudaSuccess) return e;
       const int m0 = Ns - n1, m1 = Ns - n0;
       if ((e = ck_run(c, g, cst, m0 == 1 ? 0 : m0, m1, c.stream)) != cudaSuccess) return e;
+      if (two && (e = cudaStreamWaitEvent(c.stream, c.join_ev, 0)) != cudaSuccess) return e;
       mark(c, KK_QUADRATURE);
       if (c.kind == PFT_SCFT_REAL)
         k_quad_pairs<T, 0><<<c.npart, PW_THREADS, 0, c.stream>>>(pr + (m0 - 1), m1 - m0 + 1, c.M, (double*)c.accA,
@@ -406,7 +416,13 @@ class EngineT : public Engine {
         k_quad_pairs<T, 1><<<c.npart, PW_THREADS, 0, c.stream>>>(pr + (m0 - 1), m1 - m0 + 1, c.M, (double*)c.accA,
                                                                   (double*)c.accB);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if (two && s > 0) {  // the next recompute overwrites the slots this quadrature read
+        if ((e = cudaEventRecord(c.fork_ev, c.stream)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(rs, c.fork_ev, 0)) != cudaSuccess) return e;
+      }
     }
+    // the second stream's last work (the bottom segment's recompute) precedes the last
+    // quadrature, which the context stream already waited for
     return solve_tail(c);  // densities and force norms
   }
 
