@@ -37,7 +37,10 @@ def test_autotuned_plan_computes_the_same_solve():
     o0, p0, plan0 = _solve(0)
     o1, p1, plan1 = _solve(1)
     assert plan0 == (2, 1)
-    assert plan1[0] in (0, 1, 2) and plan1[1] in (0, 1)
+    # any plan the autotuner may pick at 64^3 FP32 real: pencil passes, plane kernel, the
+    # separable march on the plane kernel (x-kernel variants 2, 18) or on pencils (line
+    # variants 3, 19, 35, 51)
+    assert plan1[0] in (0, 1, 2, 18, 3, 19, 35, 51) and plan1[1] in (0, 1)
     assert abs(o1["Q"].real - o0["Q"].real) <= 2e-5 * o0["Q"].real
     assert np.max(np.abs(p1 - p0)) <= 2e-5
 
