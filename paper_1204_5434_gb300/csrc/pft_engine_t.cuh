@@ -317,9 +317,11 @@ class EngineT : public Engine {
     if (c.stepsCK) return cudaSuccess;
     const int K = c.ckK, Ns = c.Ns;
     const size_t slice = slice_bytes(c, sizeof(T));
-    cudaError_t e = cudaMalloc(&c.qdk, (size_t)K * slice);
-    if (e != cudaSuccess) return e;
-    c.bytes += (size_t)K * slice;
+    cudaError_t e = cudaSuccess;
+    if (!c.qdk) {  // kept if a later allocation below fails, and reused by the next attempt
+      if ((e = cudaMalloc(&c.qdk, (size_t)K * slice)) != cudaSuccess) return e;
+      c.bytes += (size_t)K * slice;
+    }
     const char* t = (const char*)c.tables;
     auto blk = [&](int s) -> const void* { return (s <= c.NsA) ? c.BA : c.BB; };
     auto entry = [&](const void* in, const void* B, void* out, void* spec, const void* Bn) {
@@ -361,14 +363,22 @@ class EngineT : public Engine {
     }
     if (h.size() != coff + (size_t)Ns) return cudaErrorInvalidValue;
     c.ckRoff.push_back((int)coff);  // the conjugate entries start here
-    e = cudaMalloc(&c.stepsCK, h.size() * sizeof(BatchStep));
-    if (e == cudaSuccess) e = cudaMemcpy(c.stepsCK, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return e;
-    c.bytes += h.size() * sizeof(BatchStep);
-    e = cudaMalloc(&c.pairsCK, pr.size() * sizeof(QuadPair));
-    if (e == cudaSuccess) e = cudaMemcpy(c.pairsCK, pr.data(), pr.size() * sizeof(QuadPair), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) c.bytes += pr.size() * sizeof(QuadPair);
-    return e;
+    // the pair table first: stepsCK marks the path as prepared, so it is set last
+    void* dpr = nullptr;
+    void* dst = nullptr;
+    e = cudaMalloc(&dpr, pr.size() * sizeof(QuadPair));
+    if (e == cudaSuccess) e = cudaMemcpy(dpr, pr.data(), pr.size() * sizeof(QuadPair), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&dst, h.size() * sizeof(BatchStep));
+    if (e == cudaSuccess) e = cudaMemcpy(dst, h.data(), h.size() * sizeof(BatchStep), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      if (dpr) cudaFree(dpr);
+      if (dst) cudaFree(dst);
+      return e;
+    }
+    c.pairsCK = dpr;
+    c.stepsCK = dst;
+    c.bytes += pr.size() * sizeof(QuadPair) + h.size() * sizeof(BatchStep);
+    return cudaSuccess;
   }
   // Launches j0 .. j1 of a separable pencil march whose entries (one member) start at st.
   cudaError_t ck_run(CtxData& c, const SeppGeom& g, const BatchStep* st, int j0, int j1, cudaStream_t sm) {
