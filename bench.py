@@ -53,12 +53,12 @@ FP64_NOMINAL_TFLOPS = 1.25
 # previous launches left them (so each launch is charged with the write-backs its stores
 # cause).  Reads are nearly nil (the field and both factors stay in L2); the writes are the
 # q slices.  Valid only for the kernel sources it was taken on: null once any changes.
-TRAFFIC_FP32 = {"bytes_per_contour_step": 8598741.3,
+TRAFFIC_FP32 = {"bytes_per_contour_step": 8607257.6,
                 "sources": ("paper_1204_5434_gb300/csrc/pft_sep.cuh", "paper_1204_5434_gb300/csrc/pft_sepp.cuh",
                             "paper_1204_5434_gb300/csrc/pft_plane.cuh", "paper_1204_5434_gb300/csrc/pft_tma.cuh",
                             "paper_1204_5434_gb300/csrc/pft_batch.cuh", "paper_1204_5434_gb300/csrc/pft_passes.cuh",
                             "paper_1204_5434_gb300/csrc/pft_fft.cuh", "paper_1204_5434_gb300/csrc/pft_dd.cuh"),
-                "sha256": "160b855443531a37d00044c6d555d22245506fffc4f8731aa885e61090c16f2b"}
+                "sha256": "a5c42a028a5e668d181a9e1d713064fe9e968e698dac53e4ef9fae5b65572f79"}
 
 
 def _traffic_fp32():
