@@ -111,10 +111,15 @@ typedef struct {
                                60% of the free device memory, else every ceil(sqrt(Ns))-th),
                                1 = every slice, K >= 2 = every K-th slice (clamped to Ns): the
                                conjugate march recomputes each segment of K-1 slices from its
-                               checkpoint (one extra forward march).  K >= 2 needs the SPLIT2
-                               scheme (else PFT_ERR_UNSUPPORTED). */
-  int autotune;             /* 1: at the first solve, time the plans of the pass march (plane
-                               kernel or pencil passes; two propagator chains on two streams or
+                               checkpoint (one extra forward march).  Under a separable plan (2
+                               or 3) the marches run on the separable pencil kernels and the
+                               conjugate march's slices of a segment's chunk occupy K extra
+                               slots; otherwise the pencil passes march one propagator after the
+                               other.  K >= 2 needs the SPLIT2 scheme (else PFT_ERR_UNSUPPORTED). */
+  int autotune;             /* 1: at the first solve, time the plans of the march that apply
+                               (separable march on pencils with its line variants, separable
+                               march on the plane kernel with its x variants, plane kernel,
+                               pencil passes; two propagator chains on two streams or
                                two-member launches) on the context's own data and keep the
                                fastest; cached per (grid, field kind, precision, Ns) in memory and,
                                if the environment variable PFT_AUTOTUNE_CACHE names a file, in
